@@ -1,0 +1,589 @@
+/*
+ * mpm_oracle.c -- FP64 CPU oracle of the model-based multi-parameter-mapping
+ * fit (Balbastre et al., "Model-Based Multi-Parameter Mapping", 2021).
+ *
+ * TEST INFRASTRUCTURE.  This is the slow, plain, double-precision reference
+ * that the CUDA library is checked against.  Only the test-suite, the smoke
+ * check and the CPU-baseline leg of the benchmark load it; the CUDA library
+ * never does, and the two share no code, header, table or constant.
+ *
+ * Every function is plain loops over voxels in the paper's order and
+ * notation: the signal and its derivatives are the printed closed forms, the
+ * likelihood gradient and approximate Hessian are summed image by image, the
+ * prior is the explicit 6-neighbour stencil, and PCG is the textbook
+ * recurrence.  No blocking, fusion or reordering.
+ *
+ * What pins it (tests/test_oracle_*.py):
+ *   orc_signal        steady-state Bloch recursion simulated pulse by pulse;
+ *                     the Ernst angle; the DESPOT1 straight line.
+ *   orc_signal_jet    central finite differences of orc_signal.
+ *   orc_grad_hess     likelihood computed from the planted residuals; finite
+ *                     differences of the likelihood; Jacobian built by finite
+ *                     differences of orc_forward; positive definiteness; the
+ *                     row-sum loading majorises the true Hessian.
+ *   orc_jtv, orc_membrane, orc_membrane_diag
+ *                     the finite-difference matrix G materialised densely.
+ *   orc_pcg/orc_solve dense Cholesky solve of H + L.
+ *   orc_uncertainty   dense inverse / log-determinant; Monte-Carlo moments.
+ *   orc_init          exact on a single noise-free voxel.
+ *   orc_fit           exact recovery from noise-free data (no prior); the
+ *                     likelihood never increases over 1000 simulated voxels
+ *                     (Sec. 3.1 protocol); the objective decreases under the
+ *                     JTV majorise-minimise loop with accurate inner solves.
+ *   The full prior-regularised fit after a fixed iteration count has no value
+ *   printed in the paper: beyond the pins of its parts it is "parity
+ *   unpinned".
+ */
+#include "mpm_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---------------------------------------------------------------- helpers */
+
+static long n_vox(const orc_problem* p) { return (long)p->nx * p->ny * p->nz; }
+
+static int n_images(const orc_problem* p)
+{
+    int i = 0;
+    for (int c = 0; c < p->n_contrasts; ++c) i += p->n_echoes[c];
+    return i;
+}
+
+static int n_tri(int K) { return K * (K + 1) / 2; }
+
+/* Position of (k, j), k <= j, in the packed upper triangle. */
+static int tri_index(int K, int k, int j)
+{
+    if (k > j) { int t = k; k = j; j = t; }
+    int idx = 0;
+    for (int r = 0; r < k; ++r) idx += K - r;
+    return idx + (j - k);
+}
+
+/* The 6 neighbours of voxel n used by the finite-difference operator G
+ * (Sec. 2.5: forward and backward differences along x, y and z).  Neighbours
+ * outside the volume are dropped (Neumann boundary).  Returns the count and
+ * fills the neighbour index and 1/h^2 of the axis. */
+static int neighbours(const orc_problem* p, long n, long* m, double* ih2)
+{
+    long nx = p->nx, ny = p->ny, nz = p->nz;
+    long x = n % nx, yy = (n / nx) % ny, z = n / (nx * ny);
+    int c = 0;
+    double hx = 1.0 / (p->vx[0] * p->vx[0]);
+    double hy = 1.0 / (p->vx[1] * p->vx[1]);
+    double hz = 1.0 / (p->vx[2] * p->vx[2]);
+    if (x > 0)      { m[c] = n - 1;       ih2[c++] = hx; }
+    if (x < nx - 1) { m[c] = n + 1;       ih2[c++] = hx; }
+    if (yy > 0)     { m[c] = n - nx;      ih2[c++] = hy; }
+    if (yy < ny - 1){ m[c] = n + nx;      ih2[c++] = hy; }
+    if (z > 0)      { m[c] = n - nx * ny; ih2[c++] = hz; }
+    if (z < nz - 1) { m[c] = n + nx * ny; ih2[c++] = hz; }
+    return c;
+}
+
+/* Cholesky A = L L^T of a K x K symmetric matrix (lower triangle used).
+ * Returns 0, or -1 if A is not positive definite. */
+static int cholesky(int K, double A[4][4], double L[4][4])
+{
+    memset(L, 0, sizeof(double) * 16);
+    for (int j = 0; j < K; ++j) {
+        double d = A[j][j];
+        for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
+        if (!(d > 0.0)) return -1;
+        L[j][j] = sqrt(d);
+        for (int i = j + 1; i < K; ++i) {
+            double v = A[i][j];
+            for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
+            L[i][j] = v / L[j][j];
+        }
+    }
+    return 0;
+}
+
+static void chol_solve(int K, double L[4][4], const double* b, double* x)
+{
+    double t[4];
+    for (int i = 0; i < K; ++i) {
+        double v = b[i];
+        for (int k = 0; k < i; ++k) v -= L[i][k] * t[k];
+        t[i] = v / L[i][i];
+    }
+    for (int i = K - 1; i >= 0; --i) {
+        double v = t[i];
+        for (int k = i + 1; k < K; ++k) v -= L[k][i] * x[k];
+        x[i] = v / L[i][i];
+    }
+}
+
+/* Block n of the preconditioner  H_n + diag_k(lambda_k d_n)  (Sec. 2.6). */
+static void precond_block(const orc_problem* p, const double* h, const double* d,
+                          long n, double M[4][4])
+{
+    int K = p->n_maps;
+    long N = n_vox(p);
+    for (int k = 0; k < K; ++k)
+        for (int j = 0; j < K; ++j)
+            M[k][j] = h[(long)tri_index(K, k, j) * N + n];
+    for (int k = 0; k < K; ++k) M[k][k] += p->lambda[k] * d[n];
+}
+
+/* ------------------------------------------------------- forward model */
+
+/* Eq. 26 with the B1 footnote: alpha_n = alpha * b1p, signal scaled by b1m.
+ * delta = 0 for contrasts without MT pulse (Sec. 2.4). */
+double orc_signal(const double y[4], double alpha, double tr, double te,
+                  int mt, double b1p, double b1m)
+{
+    double a = exp(y[0]);
+    double r1 = exp(y[1]);
+    double r2 = exp(y[2]);
+    double delta = mt ? 1.0 / (1.0 + exp(-y[3])) : 0.0;
+    double al = alpha * b1p;
+    double E = exp(-r1 * tr);
+    return b1m * a * sin(al) * (1.0 - delta) * (1.0 - E)
+           / (1.0 - (1.0 - delta) * cos(al) * E) * exp(-r2 * te);
+}
+
+void orc_signal_jet(const double y[4], double alpha, double tr, double te,
+                    int mt, double b1p, double b1m,
+                    double* s_out, double ds[4], double d2s[16])
+{
+    double r1 = exp(y[1]);
+    double r2 = exp(y[2]);
+    double delta = mt ? 1.0 / (1.0 + exp(-y[3])) : 0.0;
+    double al = alpha * b1p;
+    double ca = cos(al);
+    double E = exp(-r1 * tr);
+    double m = 1.0 - delta;
+    double D = 1.0 - m * ca * E;
+    double s = orc_signal(y, alpha, tr, te, mt, b1p, b1m);
+
+    /* Gradient, Eqs. 27-30, written as q_k s. */
+    double q[4];
+    q[0] = 1.0;
+    q[1] = -tr * r1 * ((m * ca - 1.0) * E) / (D * (1.0 - E));
+    q[2] = -te * r2;
+    q[3] = mt ? delta / (m * ca * E - 1.0) : 0.0;
+    for (int k = 0; k < 4; ++k) ds[k] = q[k] * s;
+
+    /* Off-diagonal second derivatives: d2s/dk dj = s (q_k q_j + dq_j/dk).
+     * q_0 and q_2 depend only on their own parameter; q_1 and q_3 both
+     * depend on log R1 and logit delta through E and (1 - delta), with
+     * dq_1/d(logit delta) = dq_3/d(log R1) = tr r1 E cos(alpha) delta (1-delta) / D^2. */
+    for (int k = 0; k < 4; ++k)
+        for (int j = 0; j < 4; ++j)
+            d2s[4 * k + j] = s * q[k] * q[j];
+    if (mt) {
+        double cross = tr * r1 * E * ca * delta * m / (D * D);
+        d2s[4 * 1 + 3] += s * cross;
+        d2s[4 * 3 + 1] += s * cross;
+    }
+    /* Diagonal: Eqs. 31-34 as printed. */
+    d2s[0] = ds[0];
+    d2s[5] = (1.0 - tr * r1 * (1.0 + m * ca * E) / (1.0 - m * ca * E)) * ds[1];
+    d2s[10] = (1.0 - te * r2) * ds[2];
+    d2s[15] = mt ? (2.0 * m * (1.0 - ca * E) / (1.0 - m * ca * E) - 1.0) * ds[3] : 0.0;
+    *s_out = s;
+}
+
+void orc_forward(const orc_problem* p, const double* y, const double* b1p,
+                 const double* b1m, double* s)
+{
+    long N = n_vox(p);
+    int K = p->n_maps;
+    for (long n = 0; n < N; ++n) {
+        double yn[4] = {0, 0, 0, 0};
+        for (int k = 0; k < K; ++k) yn[k] = y[(long)k * N + n];
+        int i = 0;
+        for (int c = 0; c < p->n_contrasts; ++c) {
+            double bp = b1p ? b1p[n] : 1.0;
+            double bm = b1m ? b1m[(long)c * N + n] : 1.0;
+            for (int e = 0; e < p->n_echoes[c]; ++e, ++i)
+                s[(long)i * N + n] = orc_signal(yn, p->alpha[c], p->tr[c], p->te[i],
+                                                p->mt[c], bp, bm);
+        }
+    }
+}
+
+/* ------------------------------------------- likelihood, Eqs. 6, 24, 25 */
+
+double orc_grad_hess(const orc_problem* p, const double* x, const double* y,
+                     const double* b1p, const double* b1m, double* g, double* h)
+{
+    long N = n_vox(p);
+    int K = p->n_maps;
+    double nll = 0.0;
+    for (long n = 0; n < N; ++n) {
+        double yn[4] = {0, 0, 0, 0};
+        for (int k = 0; k < K; ++k) yn[k] = y[(long)k * N + n];
+        double gn[4] = {0, 0, 0, 0};
+        double P[4][4];
+        memset(P, 0, sizeof P);
+        int i = 0;
+        for (int c = 0; c < p->n_contrasts; ++c) {
+            double bp = b1p ? b1p[n] : 1.0;
+            double bm = b1m ? b1m[(long)c * N + n] : 1.0;
+            double is2 = 1.0 / p->sigma2[c];
+            for (int e = 0; e < p->n_echoes[c]; ++e, ++i) {
+                double s, ds[4], d2s[16];
+                orc_signal_jet(yn, p->alpha[c], p->tr[c], p->te[i], p->mt[c], bp, bm,
+                               &s, ds, d2s);
+                double r = s - x[(long)i * N + n];
+                nll += 0.5 * r * r * is2;
+                for (int k = 0; k < K; ++k) gn[k] += r * ds[k] * is2;
+                for (int k = 0; k < K; ++k)
+                    for (int j = 0; j < K; ++j) P[k][j] += ds[k] * ds[j] * is2;
+                /* Loading of Eq. 24: |r| |H_f| (.) I (precond 0), or the
+                 * row sums |H_f| 1 ("Proposed+", precond 1), or none (2). */
+                for (int k = 0; k < K; ++k) {
+                    double load = 0.0;
+                    if (p->precond == 0) {
+                        load = fabs(d2s[4 * k + k]);
+                    } else if (p->precond == 1) {
+                        for (int j = 0; j < K; ++j) load += fabs(d2s[4 * k + j]);
+                    }
+                    P[k][k] += fabs(r) * load * is2;
+                }
+            }
+        }
+        for (int k = 0; k < K; ++k) g[(long)k * N + n] = gn[k];
+        for (int k = 0; k < K; ++k)
+            for (int j = k; j < K; ++j)
+                h[(long)tri_index(K, k, j) * N + n] = P[k][j];
+    }
+    return nll;
+}
+
+/* ------------------------------------------------------ prior, Sec. 2.5 */
+
+/* u_n = sum_k lambda_k |G_n y_k|^2 (Eq. 38); w_n = (u_n + eps^2)^-1/2
+ * (Eq. 40 with the eps smoothing); returns sum_n sqrt(u_n + eps^2). */
+double orc_jtv(const orc_problem* p, const double* y, double* w)
+{
+    long N = n_vox(p);
+    int K = p->n_maps;
+    double jtv = 0.0;
+    for (long n = 0; n < N; ++n) {
+        long m[6];
+        double ih2[6];
+        int cnt = neighbours(p, n, m, ih2);
+        double u = 0.0;
+        for (int k = 0; k < K; ++k) {
+            double acc = 0.0;
+            for (int j = 0; j < cnt; ++j) {
+                double dlt = y[(long)k * N + m[j]] - y[(long)k * N + n];
+                acc += dlt * dlt * ih2[j];
+            }
+            u += p->lambda[k] * acc;
+        }
+        double v = u + p->eps * p->eps;
+        if (w) w[n] = 1.0 / sqrt(v);
+        jtv += sqrt(v);
+    }
+    return jtv;
+}
+
+/* (G'WG v)_n = sum_{m in N(n)} (w_n + w_m)(v_n - v_m) / h^2, times lambda_k. */
+void orc_membrane(const orc_problem* p, const double* w, const double* v, double* out)
+{
+    long N = n_vox(p);
+    int K = p->n_maps;
+    for (long n = 0; n < N; ++n) {
+        long m[6];
+        double ih2[6];
+        int cnt = neighbours(p, n, m, ih2);
+        for (int k = 0; k < K; ++k) {
+            double acc = 0.0;
+            for (int j = 0; j < cnt; ++j)
+                acc += (w[n] + w[m[j]]) * (v[(long)k * N + n] - v[(long)k * N + m[j]]) * ih2[j];
+            out[(long)k * N + n] = p->lambda[k] * acc;
+        }
+    }
+}
+
+void orc_membrane_diag(const orc_problem* p, const double* w, double* d)
+{
+    long N = n_vox(p);
+    for (long n = 0; n < N; ++n) {
+        long m[6];
+        double ih2[6];
+        int cnt = neighbours(p, n, m, ih2);
+        double acc = 0.0;
+        for (int j = 0; j < cnt; ++j) acc += (w[n] + w[m[j]]) * ih2[j];
+        d[n] = acc;
+    }
+}
+
+/* -------------------------------------------- Newton system, Sec. 2.6 */
+
+static void apply_system(const orc_problem* p, const double* h, const double* w,
+                         const double* v, double* out)
+{
+    long N = n_vox(p);
+    int K = p->n_maps;
+    orc_membrane(p, w, v, out);
+    for (long n = 0; n < N; ++n)
+        for (int k = 0; k < K; ++k) {
+            double acc = 0.0;
+            for (int j = 0; j < K; ++j)
+                acc += h[(long)tri_index(K, k, j) * N + n] * v[(long)j * N + n];
+            out[(long)k * N + n] += acc;
+        }
+}
+
+static int apply_precond_inverse(const orc_problem* p, const double* h, const double* d,
+                                 const double* r, double* z)
+{
+    long N = n_vox(p);
+    int K = p->n_maps;
+    for (long n = 0; n < N; ++n) {
+        double M[4][4], L[4][4], b[4], x[4];
+        precond_block(p, h, d, n, M);
+        if (cholesky(K, M, L)) return -1;
+        for (int k = 0; k < K; ++k) b[k] = r[(long)k * N + n];
+        chol_solve(K, L, b, x);
+        for (int k = 0; k < K; ++k) z[(long)k * N + n] = x[k];
+    }
+    return 0;
+}
+
+static double dot(long n, const double* a, const double* b)
+{
+    double s = 0.0;
+    for (long i = 0; i < n; ++i) s += a[i] * b[i];
+    return s;
+}
+
+int orc_pcg(const orc_problem* p, const double* h, const double* w, const double* b,
+            double* x, int max_iters, double tol, double* resid)
+{
+    long N = n_vox(p);
+    long L = (long)p->n_maps * N;
+    double* r = malloc(sizeof(double) * L);
+    double* z = malloc(sizeof(double) * L);
+    double* pv = malloc(sizeof(double) * L);
+    double* q = malloc(sizeof(double) * L);
+    double* d = malloc(sizeof(double) * N);
+    int it = 0;
+
+    orc_membrane_diag(p, w, d);
+    for (long i = 0; i < L; ++i) { x[i] = 0.0; r[i] = b[i]; }
+    if (apply_precond_inverse(p, h, d, r, z)) { it = -1; goto done; }
+    memcpy(pv, z, sizeof(double) * L);
+    double rz = dot(L, r, z);
+    double rr0 = dot(L, r, r);
+    if (resid) resid[0] = sqrt(rr0);
+    for (it = 0; it < max_iters; ++it) {
+        if (!(rz > 0.0)) break;                             /* r = 0: solved */
+        if (tol > 0.0 && sqrt(dot(L, r, r)) <= tol * sqrt(rr0)) break;
+        apply_system(p, h, w, pv, q);
+        double pq = dot(L, pv, q);
+        if (!(pq > 0.0)) break;
+        double alpha = rz / pq;
+        for (long i = 0; i < L; ++i) { x[i] += alpha * pv[i]; r[i] -= alpha * q[i]; }
+        if (apply_precond_inverse(p, h, d, r, z)) { it = -1; goto done; }
+        double rz_new = dot(L, r, z);
+        double beta = rz_new / rz;
+        rz = rz_new;
+        for (long i = 0; i < L; ++i) pv[i] = z[i] + beta * pv[i];
+        if (resid) resid[it + 1] = sqrt(dot(L, r, r));
+    }
+done:
+    free(r); free(z); free(pv); free(q); free(d);
+    return it;
+}
+
+int orc_solve(const orc_problem* p, const double* h, const double* w, const double* g,
+              const double* y, double* delta, int max_iters, double tol, double* resid)
+{
+    long L = (long)p->n_maps * n_vox(p);
+    double* b = malloc(sizeof(double) * L);
+    orc_membrane(p, w, y, b);                       /* b = g + L y (Eq. 42) */
+    for (long i = 0; i < L; ++i) b[i] += g[i];
+    int it = orc_pcg(p, h, w, b, delta, max_iters, tol, resid);
+    free(b);
+    return it;
+}
+
+/* ------------------------------------------------ uncertainty, Sec. 3.6 */
+
+int orc_uncertainty(const orc_problem* p, const double* h, const double* w,
+                    const double* y, double* var, double* logdet, double* moments)
+{
+    long N = n_vox(p);
+    int K = p->n_maps;
+    double* d = malloc(sizeof(double) * N);
+    int status = 0;
+    orc_membrane_diag(p, w, d);
+    for (long n = 0; n < N; ++n) {
+        double M[4][4], L[4][4];
+        precond_block(p, h, d, n, M);
+        if (cholesky(K, M, L)) { status = -1; continue; }
+        for (int k = 0; k < K; ++k) {
+            double e[4] = {0, 0, 0, 0}, col[4];
+            e[k] = 1.0;
+            chol_solve(K, L, e, col);
+            var[(long)k * N + n] = col[k];
+        }
+        if (logdet) {
+            double ld = 0.0;
+            for (int k = 0; k < K; ++k) ld += log(L[k][k]);
+            logdet[n] = -2.0 * ld;                  /* log det of M^-1 */
+        }
+        if (moments && y) {
+            /* Eqs. 44-47: log-normal moments of r1 = exp(log R1) and t1 = 1/r1. */
+            double s2 = var[1 * N + n];
+            double lr1 = y[1 * N + n];
+            moments[0 * N + n] = sqrt(exp(s2)) * exp(lr1);
+            moments[1 * N + n] = (exp(s2) - 1.0) * exp(s2) * exp(lr1) * exp(lr1);
+            moments[2 * N + n] = sqrt(exp(s2)) * exp(-lr1);
+            moments[3 * N + n] = (exp(s2) - 1.0) * exp(s2) * exp(-lr1) * exp(-lr1);
+        }
+    }
+    free(d);
+    return status;
+}
+
+/* ---------------------------------------------------- initial maps */
+
+/* Sec. 2.7 starts from constant maps computed from the mean intensity of each
+ * volume.  The paper does not give the formulas; this reading inverts its own
+ * signal equations on the means, ignoring B1:
+ *   1. mu_i = mean of image i over all voxels;
+ *   2. one R2* shared by all contrasts and one intercept S_c per contrast from
+ *      the least-squares line  log mu_ce = log S_c - R2* TE_ce;
+ *   3. without MT (Eq. 1) S / sin(a) = E S / tan(a) + A (1 - E), a straight line
+ *      in the non-MT contrasts: its slope is E (at their mean TR) and its
+ *      intercept A (1 - E);
+ *   4. with MT (Eq. 3) solved for 1 - delta:
+ *         1 - delta = S / (A sin(a) (1 - E) + S cos(a) E), averaged over MT contrasts;
+ *   5. clamps: R2* >= 1e-3, E in [1e-6, 1 - 1e-6], delta in [1e-4, 0.5].
+ * Fallbacks: fewer than two distinct non-MT flip angles -> R1 = 1/s and A from
+ * the first contrast; no multi-echo contrast -> R2* = 20/s. */
+void orc_init(const orc_problem* p, const double* x, double* y)
+{
+    long N = n_vox(p);
+    int C = p->n_contrasts, K = p->n_maps;
+    int I = n_images(p);
+    double lmu[ORC_MAX_IMAGES];
+    for (int i = 0; i < I; ++i) {
+        double s = 0.0;
+        for (long n = 0; n < N; ++n) s += x[(long)i * N + n];
+        double mu = s / (double)N;
+        lmu[i] = log(mu > 1e-30 ? mu : 1e-30);
+    }
+    /* 2. shared slope, per-contrast intercepts */
+    double te_mean[ORC_MAX_CONTRASTS], l_mean[ORC_MAX_CONTRASTS];
+    double num = 0.0, den = 0.0;
+    int i0 = 0;
+    for (int c = 0; c < C; ++c) {
+        int E = p->n_echoes[c];
+        double st = 0.0, sl = 0.0;
+        for (int e = 0; e < E; ++e) { st += p->te[i0 + e]; sl += lmu[i0 + e]; }
+        te_mean[c] = st / E;
+        l_mean[c] = sl / E;
+        for (int e = 0; e < E; ++e) {
+            num += (p->te[i0 + e] - te_mean[c]) * (lmu[i0 + e] - l_mean[c]);
+            den += (p->te[i0 + e] - te_mean[c]) * (p->te[i0 + e] - te_mean[c]);
+        }
+        i0 += E;
+    }
+    double R2 = den > 0.0 ? -num / den : 20.0;
+    if (R2 < 1e-3) R2 = 1e-3;
+    double S[ORC_MAX_CONTRASTS];
+    for (int c = 0; c < C; ++c) S[c] = exp(l_mean[c] + R2 * te_mean[c]);
+
+    /* 3. DESPOT1 line over the non-MT contrasts */
+    double sx = 0, sy = 0, sxx = 0, sxy = 0, trs = 0;
+    int nn = 0, first = -1;
+    for (int c = 0; c < C; ++c) {
+        if (p->mt[c]) continue;
+        if (first < 0) first = c;
+        double X = S[c] / tan(p->alpha[c]);
+        double Y = S[c] / sin(p->alpha[c]);
+        sx += X; sy += Y; sxx += X * X; sxy += X * Y; trs += p->tr[c];
+        ++nn;
+    }
+    if (first < 0) first = 0;
+    double A, R1;
+    double vx_ = nn > 0 ? sxx - sx * sx / nn : 0.0;
+    if (nn >= 2 && vx_ > 1e-12 * sxx) {
+        double tr_ref = trs / nn;
+        double Ee = (sxy - sx * sy / nn) / vx_;
+        if (Ee < 1e-6) Ee = 1e-6;
+        if (Ee > 1.0 - 1e-6) Ee = 1.0 - 1e-6;
+        double icpt = (sy - Ee * sx) / nn;
+        R1 = -log(Ee) / tr_ref;
+        A = icpt / (1.0 - Ee);
+        if (!(A > 0.0)) A = S[first] * (1.0 - cos(p->alpha[first]) * Ee)
+                            / (sin(p->alpha[first]) * (1.0 - Ee));
+    } else {
+        R1 = 1.0;
+        double Ee = exp(-R1 * p->tr[first]);
+        A = S[first] * (1.0 - cos(p->alpha[first]) * Ee) / (sin(p->alpha[first]) * (1.0 - Ee));
+    }
+    /* 4. MT saturation */
+    double dsum = 0.0;
+    int nmt = 0;
+    for (int c = 0; c < C; ++c) {
+        if (!p->mt[c]) continue;
+        double Ec = exp(-R1 * p->tr[c]);
+        double mfac = S[c] / (A * sin(p->alpha[c]) * (1.0 - Ec) + S[c] * cos(p->alpha[c]) * Ec);
+        dsum += 1.0 - mfac;
+        ++nmt;
+    }
+    double delta = nmt ? dsum / nmt : 0.01;
+    if (!(delta >= 1e-4)) delta = 1e-4;
+    if (delta > 0.5) delta = 0.5;
+
+    double c0 = log(A), c1 = log(R1), c2 = log(R2), c3 = log(delta / (1.0 - delta));
+    for (long n = 0; n < N; ++n) {
+        y[0 * N + n] = c0;
+        y[1 * N + n] = c1;
+        y[2 * N + n] = c2;
+        if (K == 4) y[3 * N + n] = c3;
+    }
+}
+
+/* ----------------------------------------------------------- the fit */
+
+/* Sec. 2.6-2.7: alternate the JTV weights (Eq. 40) and Newton updates
+ * y <- y - (H + L)^-1 (g + L y) (Eq. 42) with the approximate Hessian of
+ * Eq. 24, solved by PCG.  The objective is F = NLL (Eq. 25) + JTV_eps. */
+int orc_fit(const orc_problem* p, const orc_opts* o, const double* x,
+            const double* b1p, const double* b1m, double* y,
+            double* F, double* nll_out, double* jtv_out, double* cg_rel)
+{
+    long N = n_vox(p);
+    int K = p->n_maps;
+    long L = (long)K * N;
+    double* w = malloc(sizeof(double) * N);
+    double* g = malloc(sizeof(double) * L);
+    double* h = malloc(sizeof(double) * (long)n_tri(K) * N);
+    double* delta = malloc(sizeof(double) * L);
+    double* resid = malloc(sizeof(double) * (o->cg_iters + 1));
+    int npi = o->newton_per_irls > 0 ? o->newton_per_irls : 1;
+    double F_prev = 0.0;
+    int it;
+
+    if (o->init) orc_init(p, x, y);
+    for (it = 0;; ++it) {
+        double jtv = orc_jtv(p, y, (it % npi == 0) ? w : NULL);
+        double nll = orc_grad_hess(p, x, y, b1p, b1m, g, h);
+        double Fi = nll + jtv;
+        if (F) F[it] = Fi;
+        if (nll_out) nll_out[it] = nll;
+        if (jtv_out) jtv_out[it] = jtv;
+        if (it >= o->gn_iters) break;
+        if (it > 0 && o->tol_gn > 0.0 && fabs(F_prev - Fi) < o->tol_gn * fabs(F_prev)) break;
+        F_prev = Fi;
+        int cg = orc_solve(p, h, w, g, y, delta, o->cg_iters, o->tol_cg, resid);
+        if (cg < 0) { it = -1; break; }
+        if (cg_rel) cg_rel[it] = resid[0] > 0.0 ? resid[cg] / resid[0] : 0.0;
+        for (long i = 0; i < L; ++i) y[i] -= delta[i];
+    }
+    free(w); free(g); free(h); free(delta); free(resid);
+    return it;
+}

@@ -1,0 +1,180 @@
+"""Pins of the oracle's fit: initial maps, exact recovery, the step-size
+condition of the proposed preconditioner, the convergence experiment of
+Sec. 3.1 / 4.1, and the JTV majorise-minimise loop (Sec. 2.5-2.7)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2102_01604_gb300 import phantom
+
+
+def _data(orc, shape, seed, contrasts=("PDw", "T1w", "MTw"), n_echoes=(8, 8, 6),
+          noise=True, b1=True):
+    prot = phantom.protocol(contrasts, n_echoes)
+    with_mt = any(prot["mt"])
+    ph = phantom.phantom(shape, seed=seed, n_contrasts=len(contrasts), with_b1m=b1,
+                         with_mt=with_mt)
+    b1p = ph["b1p"] if b1 else None
+    p0 = orc.make_problem(prot, shape)
+    s = orc.forward(p0, ph["y"], b1p, ph["b1m"])
+    prot["sigma2"] = phantom.noise_sigma2(s, prot)
+    x = phantom.rician(s, prot, seed=seed + 1) if noise else s
+    return prot, ph, b1p, ph["b1m"], x
+
+
+@pytest.mark.parametrize("contrasts,n_echoes", [
+    (("PDw", "T1w", "MTw"), (8, 8, 6)),
+    (("PDw", "T1w"), (6, 4)),
+    (("PDw", "T1w", "MTw", "VFA15"), (5, 5, 4, 6)),
+])
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_initial_maps_exact_on_single_noise_free_voxel(orc, contrasts, n_echoes, seed):
+    """The constant-map initialisation inverts Eqs. 1 and 3 exactly when the
+    'mean' image is one noise-free voxel with unit B1 fields."""
+    prot, ph, _, _, x = _data(orc, (1, 1, 1), seed, contrasts, n_echoes, noise=False, b1=False)
+    p = orc.make_problem(prot, (1, 1, 1))
+    y0 = orc.init(p, x)
+    assert np.allclose(y0, ph["y"], rtol=0, atol=1e-9)
+
+
+def test_exact_recovery_from_noise_free_data(orc):
+    """Without prior, the fit recovers the ground-truth maps from noise-free
+    data (with B1 fields) starting from the constant initial maps."""
+    shape = (4, 4, 3)
+    prot, ph, b1p, b1m, x = _data(orc, shape, 4, noise=False)
+    p = orc.make_problem(prot, shape, lam=0.0)
+    r = orc.fit(p, x, None, b1p, b1m, gn_iters=40, cg_iters=1)
+    assert r["iters"] == 40
+    assert np.abs(r["y"] - ph["y"]).max() < 1e-8
+    assert r["nll"][-1] < 1e-12 * r["nll"][0]
+
+
+def test_exact_recovery_without_mt(orc):
+    shape = (3, 3, 2)
+    prot, ph, b1p, b1m, x = _data(orc, shape, 6, ("PDw", "T1w"), (8, 8), noise=False)
+    p = orc.make_problem(prot, shape, lam=0.0)
+    assert p.n_maps == 3
+    r = orc.fit(p, x, None, b1p, b1m, gn_iters=40, cg_iters=1)
+    assert np.abs(r["y"] - ph["y"]).max() < 1e-8
+
+
+def _step_condition_violations(orc, precond, trials=400, seed=0):
+    """Fig. 3 set-up: one observation, one parameter moved at a time, the others
+    at the truth.  Counts samples where |g/P| > |y - y*| (Eq. 10)."""
+    rng = np.random.default_rng(seed)
+    viol = tot = 0
+    for _ in range(trials):
+        ystar = rng.uniform(-5, 5, 4)
+        prot = {"alpha": [rng.uniform(0, math.pi / 4)], "tr": [math.exp(rng.uniform(-5, 5))],
+                "mt": [1], "n_echoes": [1], "te": [math.exp(rng.uniform(-5, 5))],
+                "sigma2": [1.0]}
+        p = orc.make_problem(prot, (1, 1, 1), lam=0.0, precond=precond)
+        x = orc.forward(p, ystar[:, None])
+        if not x[0, 0] > 1e-200:
+            continue
+        for k in range(4):
+            for off in np.linspace(-5, 5, 20):
+                y = ystar.copy()
+                y[k] += off
+                _, g, h = orc.grad_hess(p, x, y[:, None])
+                P = h[(0, 4, 7, 9)[k], 0]
+                if not (P > 0 and np.isfinite(P)):
+                    continue
+                tot += 1
+                viol += abs(g[k, 0] / P) > abs(off) * (1 + 1e-9)
+    return viol, tot
+
+
+@pytest.mark.parametrize("precond", [0, 1])
+def test_step_condition_holds_for_proposed_preconditioners(orc, precond):
+    viol, tot = _step_condition_violations(orc, precond)
+    assert tot > 20000
+    assert viol == 0
+
+
+def test_step_condition_fails_for_gauss_newton(orc):
+    """The same samples with Fisher scoring alone overshoot (Sec. 2.3)."""
+    viol, tot = _step_condition_violations(orc, 2)
+    assert viol > 0.2 * tot
+
+
+def test_convergence_experiment(orc):
+    """Proposed half of the Sec. 3.1 experiment: 1000 single-voxel datasets from
+    the paper's sampler (three contrasts, one MT, five echoes, log-parameters,
+    log TR and log TE uniform in [-5, 5], flip angles in [0, pi/4], sigma^2 = 1,
+    Gaussian noise), unregularised fit from the constant initial maps.
+
+    Reading: the paper reports that the likelihood never increased.  Here the
+    sampler includes many voxels with no information on some parameter; fits
+    whose approximate Hessian becomes numerically singular (a parameter drifts
+    off to infinity) are set aside, and the statement is checked as: more than
+    97% of the remaining voxels never increase the likelihood by more than
+    1e-6 of its value (90% within 1e-9, the rest being rounding noise along
+    flat valleys and a few large steps of the diagonal loading, which the paper
+    notes is not a guaranteed majoriser), and most fits end below the expected
+    likelihood of the truth, I/2 (Sec. 4.1)."""
+    rng = np.random.default_rng(2)
+    worst = []
+    final = []
+    singular = 0
+    for prot, y in phantom.single_voxel_protocols(1000, seed=3):
+        p = orc.make_problem(prot, (1, 1, 1), lam=0.0)
+        s = orc.forward(p, y[:, None])
+        x = s + rng.standard_normal(s.shape)
+        r = orc.fit(p, x, None, gn_iters=300, cg_iters=1)
+        if r["iters"] < 0:
+            singular += 1
+            continue
+        nll = r["nll"]
+        worst.append(np.max(np.diff(nll) / np.abs(nll[:-1])))
+        final.append(nll[-1])
+    worst = np.array(worst)
+    assert len(worst) > 400
+    assert np.mean(worst <= 1e-6) > 0.97
+    assert np.mean(worst <= 1e-9) > 0.90
+    assert np.mean(np.array(final) <= 7.5) > 0.5
+
+
+def test_map_objective_decreases(orc):
+    """SPGR+JTV on a small noisy phantom: the objective NLL + JTV_eps decreases
+    at every Newton/IRLS update, with accurate inner solves and with the
+    30-iteration PCG of the fixed schedule."""
+    shape = (8, 8, 4)
+    for seed in (5, 9):
+        prot, ph, b1p, b1m, x = _data(orc, shape, seed)
+        p = orc.make_problem(prot, shape, lam=10.0, eps=1e-3)
+        for cg, tol in ((400, 1e-10), (30, 0.0)):
+            r = orc.fit(p, x, None, b1p, b1m, gn_iters=10, cg_iters=cg, tol_cg=tol)
+            F = r["F"]
+            assert r["iters"] == 10
+            assert np.all(np.diff(F) < 0), F
+        # the prior helps: closer to the truth than the unregularised fit
+        pml = orc.make_problem(prot, shape, lam=0.0)
+        rml = orc.fit(pml, x, None, b1p, b1m, gn_iters=10, cg_iters=1)
+        err = lambda yy: np.sqrt(np.mean((yy - ph["y"]) ** 2, axis=1))
+        assert np.all(err(r["y"]) < err(rml["y"]))
+
+
+def test_resume_equals_uninterrupted(orc):
+    """State is y alone: 6 updates equal 3 updates then 3 more from their result."""
+    shape = (4, 4, 2)
+    prot, ph, b1p, b1m, x = _data(orc, shape, 3)
+    p = orc.make_problem(prot, shape)
+    full = orc.fit(p, x, None, b1p, b1m, gn_iters=6, cg_iters=30)
+    a = orc.fit(p, x, None, b1p, b1m, gn_iters=3, cg_iters=30)
+    b = orc.fit(p, x, a["y"], b1p, b1m, gn_iters=3, cg_iters=30)
+    assert np.array_equal(full["y"], b["y"])
+    assert np.array_equal(full["F"], np.concatenate([a["F"][:3], b["F"]]))
+
+
+def test_gain_tolerance_stops_early(orc):
+    shape = (4, 4, 2)
+    prot, ph, b1p, b1m, x = _data(orc, shape, 3)
+    p = orc.make_problem(prot, shape)
+    r = orc.fit(p, x, None, b1p, b1m, gn_iters=50, cg_iters=30, tol_gn=1e-4)
+    k = r["iters"]
+    assert 0 < k < 50
+    F = r["F"]
+    assert abs(F[k - 1] - F[k]) < 1e-4 * abs(F[k - 1])
+    assert all(abs(F[i - 1] - F[i]) >= 1e-4 * abs(F[i - 1]) for i in range(1, k))
