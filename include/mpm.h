@@ -1,0 +1,193 @@
+/*
+ * mpm.h -- C ABI of the GB300 (sm_103a) implementation of the model-based
+ * multi-parameter-mapping fit of Balbastre et al., "Model-Based
+ * Multi-Parameter Mapping" (Medical Image Analysis, 2021).
+ *
+ * The fit recovers, in every voxel, the log-parameters
+ *     y = (log A, log R1, log R2*, logit delta)            (Sec. 2.4)
+ * from multi-echo spoiled-gradient-echo images acquired at several flip angles
+ * with an optional MT pulse, by Newton updates with the paper's positive
+ * definite approximate Hessian (Eq. 24) and a joint-total-variation prior
+ * handled by reweighted least squares (Eqs. 38-40), each update solving
+ * (H + L) delta = g + L y by preconditioned conjugate gradient (Eq. 42).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Grid: nx * ny * nz = N voxels, voxel n = x + nx*(y + ny*z) (x fastest).
+ *  - Arrays are caller-owned DEVICE pointers (cudaMalloc / torch CUDA
+ *    tensors), contiguous, 16-byte aligned, planar:
+ *        y, g, delta, var      [K][N] float   K = n_maps
+ *        h                     [T][N] float   T = K(K+1)/2, upper triangle row
+ *                              by row: 00,01,02,03,11,12,13,22,23,33 (K=4) or
+ *                              00,01,02,11,12,22 (K=3)
+ *        x (images)            [I][N] float or bf16 (problem.echo_dtype),
+ *                              I = sum of n_echoes, contrast-major
+ *        b1p                   [N] float or NULL (= 1)
+ *        b1m                   [C][N] float or NULL (= 1)
+ *        w (JTV weights)       [N] float
+ *    Host pointers are rejected with MPM_ERR_INVALID_ARG.
+ *  - Device scalars (nll, jtv) are caller-owned device doubles, overwritten.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Every call except mpm_fit and mpm_workspace_size only enqueues
+ *    work on it and returns without synchronising.
+ *  - Scratch memory: calls that need it take a caller-owned device workspace
+ *    (ws, ws_bytes) of at least mpm_workspace_size() bytes.  The library
+ *    itself allocates no device memory.  Two calls that run concurrently must
+ *    not share a workspace.
+ *  - Errors: every call returns an mpm_status; argument errors are detected on
+ *    the host before anything is enqueued.  Kernels never trap: numeric
+ *    failures (a preconditioner block that is not positive definite, a NaN in
+ *    a CG inner product) are recorded in the workspace and reported by
+ *    mpm_fit, or read back with mpm_workspace_status().  mpm_last_error()
+ *    gives a human-readable detail of the last failure on the calling thread.
+ */
+#ifndef MPM_H
+#define MPM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MPM_MAX_CONTRASTS 8
+#define MPM_MAX_IMAGES 64
+#define MPM_MAX_REPORT 256
+
+typedef int mpm_status;
+
+enum {
+    MPM_OK = 0,
+    MPM_WARN_NOT_CONVERGED = 1,       /* mpm_fit hit gn_iters with tol_gn > 0 */
+    MPM_ERR_INVALID_ARG = -1,
+    MPM_ERR_WORKSPACE_TOO_SMALL = -2,
+    MPM_ERR_CUDA = -3,
+    MPM_ERR_NUMERIC = -4,
+    MPM_ERR_TIMEOUT = -5              /* reserved: no call spins on the device */
+};
+
+/* Which call a workspace is sized for (mpm_workspace_size). */
+enum {
+    MPM_CALL_FIT = 0,
+    MPM_CALL_SOLVE = 1,
+    MPM_CALL_GRAD_HESS = 2,
+    MPM_CALL_JTV = 3
+};
+
+/* Problem statement: the fixed parameters Theta of every image (Sec. 2.4:
+ * flip angle, TR, TE, noise variance), the grid, and the prior (Sec. 2.5). */
+typedef struct {
+    int nx, ny, nz;
+    double vx[3];                          /* voxel size along x, y, z (mm) */
+    int n_contrasts;                       /* C, 1..MPM_MAX_CONTRASTS */
+    int n_echoes[MPM_MAX_CONTRASTS];       /* echoes per contrast (>= 1) */
+    double alpha[MPM_MAX_CONTRASTS];       /* nominal flip angle (rad), in (0, pi) */
+    double tr[MPM_MAX_CONTRASTS];          /* repetition time (s), > 0 */
+    int mt[MPM_MAX_CONTRASTS];             /* 1 if the contrast has an MT pulse */
+    double sigma2[MPM_MAX_CONTRASTS];      /* noise variance of the contrast, > 0 */
+    double te[MPM_MAX_IMAGES];             /* echo times (s), contrast-major */
+    int n_maps;                            /* K: 4 if any mt[c], else 3 */
+    double lambda[4];                      /* JTV factor per map (>= 0) */
+    double eps;                            /* JTV smoothing: w = (u + eps^2)^-1/2, > 0 */
+    int precond;                           /* loading of Eq. 24: 0 = |diag H_f| (the
+                                              paper's choice), 1 = |H_f| 1 (row sums,
+                                              "Proposed+"), 2 = none (Gauss-Newton) */
+    int echo_dtype;                        /* 0 = float32 images, 1 = bfloat16 */
+} mpm_problem;
+
+/* Schedule (Sec. 2.7; the paper uses 10 IRLS x 5 Newton x 32 CG). */
+typedef struct {
+    int gn_iters;          /* Newton updates at most, 0..MPM_MAX_REPORT */
+    int cg_iters;          /* PCG iterations per update at most, >= 1 */
+    int newton_per_irls;   /* JTV weights refreshed every this many updates, >= 1 */
+    int init;              /* 1: start from constant maps computed from the image
+                              means; 0: y_inout holds the starting maps */
+    double tol_gn;         /* stop when |F_prev - F| < tol_gn |F_prev| (0 = off) */
+    double tol_cg;         /* stop PCG when |r_k| <= tol_cg |r_0| (0 = off) */
+} mpm_opts;
+
+/* Per-update record filled by mpm_fit (host memory, caller-owned). */
+typedef struct {
+    int iters;                             /* updates made */
+    double F[MPM_MAX_REPORT + 1];          /* NLL + JTV_eps before every update and
+                                              after the last (entries 0..iters) */
+    double nll[MPM_MAX_REPORT + 1];        /* negative log-likelihood, Eq. 25 */
+    double jtv[MPM_MAX_REPORT + 1];        /* sum_n sqrt(u_n + eps^2), Eq. 38 */
+    double cg_rel[MPM_MAX_REPORT];         /* |r_end| / |r_0| of each solve */
+    int cg_done[MPM_MAX_REPORT];           /* PCG iterations run in each solve */
+} mpm_report;
+
+/* Text of a status code (static storage). */
+const char* mpm_status_string(mpm_status s);
+
+/* Detail of the last failing call on this thread ("" if none). */
+const char* mpm_last_error(void);
+
+/* Bytes of workspace that `call` (MPM_CALL_*) needs for this problem and
+ * schedule (opts may be NULL except for MPM_CALL_FIT / MPM_CALL_SOLVE).  The
+ * MPM_CALL_FIT size is enough for every call. */
+mpm_status mpm_workspace_size(const mpm_problem* problem, const mpm_opts* opts, int call,
+                              size_t* bytes);
+
+/* Noise-free images s[I][N] (float32) from maps y (Eq. 26 with the B1
+ * modulation of its footnote: flip angle alpha * b1p, signal times b1m). */
+mpm_status mpm_forward(const mpm_problem* problem, const float* y, const float* b1p,
+                       const float* b1m, float* s, void* stream);
+
+/* The fused voxel pass (Eqs. 6, 24, 25, 27-34): in every voxel, over all
+ * echoes of all contrasts, the signal, residual, gradient g[K][N] of the
+ * negative log-likelihood and the approximate Hessian h[T][N]; *nll (device
+ * double) receives the negative log-likelihood summed over the volume. */
+mpm_status mpm_grad_hess(const mpm_problem* problem, const void* x, const float* y,
+                         const float* b1p, const float* b1m, float* g, float* h,
+                         double* nll, void* ws, size_t ws_bytes, void* stream);
+
+/* JTV reweighting (Eqs. 38-40): u_n = sum_k lambda_k sum_{6 neighbours}
+ * (y_k[m] - y_k[n])^2 / h_d^2 (neighbours outside the volume dropped),
+ * w_n = (u_n + eps^2)^-1/2 written to w (skipped if w == NULL), and
+ * *jtv = sum_n sqrt(u_n + eps^2). */
+mpm_status mpm_jtv_weights(const mpm_problem* problem, const float* y, float* w,
+                           double* jtv, void* ws, size_t ws_bytes, void* stream);
+
+/* Newton system of Sec. 2.6 / Eq. 42: delta = (H + L)^-1 (g + L y) with
+ * L = G'WG (x) diag(lambda), by PCG from delta = 0 with the block
+ * preconditioner H + diag(G'WG) (x) diag(lambda), at most opts->cg_iters
+ * iterations or until |r_k| <= opts->tol_cg |r_0|.  resid (device doubles,
+ * cg_iters + 1 entries, or NULL) receives |r_k|; entries past the last
+ * iteration run are left untouched. */
+mpm_status mpm_solve(const mpm_problem* problem, const mpm_opts* opts, const float* h,
+                     const float* w, const float* g, const float* y, float* delta,
+                     double* resid, void* ws, size_t ws_bytes, void* stream);
+
+/* Laplace uncertainty (Sec. 3.6, Eqs. 43-47): var[K][N] = diagonal of
+ * (H_n + diag(G'WG)_n lambda)^-1, computed in float64; logdet[N] (or NULL) =
+ * log-determinant of that covariance block; moments[4][N] (or NULL; needs y)
+ * = E[r1], V[r1], E[t1], V[t1] under the log-normal posterior. */
+mpm_status mpm_uncertainty(const mpm_problem* problem, const float* h, const float* w,
+                           const float* y, float* var, float* logdet, float* moments,
+                           void* stream);
+
+/* The whole fit (Sec. 2.6-2.7): optional constant initial maps, then up to
+ * gn_iters updates, each = JTV reweighting (every newton_per_irls updates),
+ * fused voxel pass, PCG solve and y <- y - delta; the objective
+ * F = NLL + JTV_eps is evaluated before every update and at the final maps.
+ * If var_out != NULL the uncertainty at the final maps is written there
+ * ([K][N]).  Synchronises `stream` before returning.  Returns MPM_OK,
+ * MPM_WARN_NOT_CONVERGED (tol_gn > 0 and not reached) or an error. */
+mpm_status mpm_fit(const mpm_problem* problem, const mpm_opts* opts, const void* x,
+                   const float* b1p, const float* b1m, float* y_inout, float* var_out,
+                   void* ws, size_t ws_bytes, mpm_report* report, void* stream);
+
+/* Synchronises `stream` and returns MPM_ERR_NUMERIC if a kernel that used this
+ * workspace recorded a numeric failure since the workspace was last cleared
+ * (every mpm_solve / mpm_fit clears it), else MPM_OK. */
+mpm_status mpm_workspace_status(const void* ws, size_t ws_bytes, void* stream);
+
+/* Diagnostic: number of kernels this library has launched in this process. */
+unsigned long long mpm_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPM_H */

@@ -1,0 +1,216 @@
+"""GB300-native (sm_103a) model-based multi-parameter mapping.
+
+Python binding of the C ABI in ``include/mpm.h``: every function here only
+checks and marshals torch CUDA tensors (device memory, the current stream)
+into the library call of the same name; all arithmetic runs in the CUDA
+kernels of ``libmpm.so``.  Importing this package does not load the library;
+the first call does, and fails if it has not been built.
+
+Layouts: maps ``[K, N]``, images ``[I, N]`` (contrast-major), Hessian
+``[K(K+1)/2, N]`` packed upper triangle, ``N = nx * ny * nz`` with x fastest.
+"""
+from __future__ import annotations
+
+import ctypes
+
+from . import _lib
+from ._lib import MPMError, Opts, Problem, Report
+
+__all__ = [
+    "make_problem", "make_opts", "workspace", "mpm_workspace_size", "mpm_forward",
+    "mpm_grad_hess", "mpm_jtv_weights", "mpm_solve", "mpm_uncertainty", "mpm_fit",
+    "mpm_workspace_status", "mpm_kernel_launches", "MPMError", "Problem", "Opts", "Report",
+]
+
+
+def make_problem(protocol: dict, shape, vx=(1.0, 1.0, 1.0), lam=10.0, eps=1e-3,
+                 precond: int = 0, echo_dtype: int = 0) -> Problem:
+    """Problem statement from a protocol dict (``alpha`` (rad), ``tr`` (s),
+    ``mt``, ``n_echoes``, ``te`` (s, flat, contrast-major), ``sigma2``)."""
+    p = Problem()
+    p.nx, p.ny, p.nz = (int(v) for v in shape)
+    for d in range(3):
+        p.vx[d] = float(vx[d])
+    C = len(protocol["alpha"])
+    if C > _lib.MAX_CONTRASTS:
+        raise ValueError("too many contrasts")
+    p.n_contrasts = C
+    for c in range(C):
+        p.n_echoes[c] = int(protocol["n_echoes"][c])
+        p.alpha[c] = float(protocol["alpha"][c])
+        p.tr[c] = float(protocol["tr"][c])
+        p.mt[c] = int(protocol["mt"][c])
+        p.sigma2[c] = float(protocol["sigma2"][c])
+    te = list(protocol["te"])
+    if len(te) > _lib.MAX_IMAGES:
+        raise ValueError("too many images")
+    for i, t in enumerate(te):
+        p.te[i] = float(t)
+    p.n_maps = 4 if any(protocol["mt"]) else 3
+    lam = list(lam) if hasattr(lam, "__len__") else [lam] * 4
+    for k in range(4):
+        p.lam[k] = float(lam[k] if k < len(lam) else lam[-1])
+    p.eps = float(eps)
+    p.precond = int(precond)
+    p.echo_dtype = int(echo_dtype)
+    return p
+
+
+def make_opts(gn_iters=10, cg_iters=30, newton_per_irls=1, init=True, tol_gn=0.0,
+              tol_cg=0.0) -> Opts:
+    return Opts(int(gn_iters), int(cg_iters), int(newton_per_irls), 1 if init else 0,
+                float(tol_gn), float(tol_cg))
+
+
+def _ptr(t, name, dtype=None, optional=False):
+    if t is None:
+        if optional:
+            return None
+        raise ValueError(f"{name} is required")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _f32():
+    import torch
+    return torch.float32
+
+
+def mpm_workspace_size(problem: Problem, opts: Opts | None = None, call: int = _lib.CALL_FIT) -> int:
+    lib = _lib.load()
+    n = ctypes.c_size_t()
+    _lib.check(lib.mpm_workspace_size(ctypes.byref(problem),
+                                      ctypes.byref(opts) if opts is not None else None,
+                                      call, ctypes.byref(n)), "mpm_workspace_size")
+    return n.value
+
+
+def workspace(problem: Problem, opts: Opts | None = None, call: int = _lib.CALL_FIT, device="cuda"):
+    """Allocate a device workspace (torch uint8 tensor) for ``call``."""
+    import torch
+    return torch.empty(max(mpm_workspace_size(problem, opts, call), 1), dtype=torch.uint8,
+                       device=device)
+
+
+def mpm_forward(problem, y, b1p=None, b1m=None, out=None, stream=None):
+    import torch
+    lib = _lib.load()
+    N = problem.nx * problem.ny * problem.nz
+    I = sum(problem.n_echoes[c] for c in range(problem.n_contrasts))
+    if out is None:
+        out = torch.empty((I, N), dtype=torch.float32, device=y.device)
+    _lib.check(lib.mpm_forward(ctypes.byref(problem), _ptr(y, "y", _f32()),
+                               _ptr(b1p, "b1p", _f32(), True), _ptr(b1m, "b1m", _f32(), True),
+                               _ptr(out, "s", _f32()), _stream(stream)), "mpm_forward")
+    return out
+
+
+def mpm_grad_hess(problem, x, y, b1p=None, b1m=None, g=None, h=None, nll=None, ws=None,
+                  stream=None):
+    """Returns (g [K,N], h [T,N], nll (device double tensor of one element))."""
+    import torch
+    lib = _lib.load()
+    K, N = problem.n_maps, problem.nx * problem.ny * problem.nz
+    dev = y.device
+    g = torch.empty((K, N), dtype=torch.float32, device=dev) if g is None else g
+    h = torch.empty((K * (K + 1) // 2, N), dtype=torch.float32, device=dev) if h is None else h
+    nll = torch.empty(1, dtype=torch.float64, device=dev) if nll is None else nll
+    ws = workspace(problem, None, _lib.CALL_GRAD_HESS, dev) if ws is None else ws
+    xdt = torch.bfloat16 if problem.echo_dtype == 1 else torch.float32
+    _lib.check(lib.mpm_grad_hess(ctypes.byref(problem), _ptr(x, "x", xdt), _ptr(y, "y", _f32()),
+                                 _ptr(b1p, "b1p", _f32(), True), _ptr(b1m, "b1m", _f32(), True),
+                                 _ptr(g, "g", _f32()), _ptr(h, "h", _f32()),
+                                 _ptr(nll, "nll", torch.float64), _ptr(ws, "ws"), ws.numel(),
+                                 _stream(stream)), "mpm_grad_hess")
+    return g, h, nll
+
+
+def mpm_jtv_weights(problem, y, w=None, jtv=None, ws=None, want_w=True, stream=None):
+    """Returns (w [N] or None, jtv (device double tensor of one element))."""
+    import torch
+    lib = _lib.load()
+    N = problem.nx * problem.ny * problem.nz
+    dev = y.device
+    if want_w and w is None:
+        w = torch.empty(N, dtype=torch.float32, device=dev)
+    jtv = torch.empty(1, dtype=torch.float64, device=dev) if jtv is None else jtv
+    ws = workspace(problem, None, _lib.CALL_JTV, dev) if ws is None else ws
+    _lib.check(lib.mpm_jtv_weights(ctypes.byref(problem), _ptr(y, "y", _f32()),
+                                   _ptr(w, "w", _f32(), True), _ptr(jtv, "jtv", torch.float64),
+                                   _ptr(ws, "ws"), ws.numel(), _stream(stream)),
+               "mpm_jtv_weights")
+    return w, jtv
+
+
+def mpm_solve(problem, opts, h, w, g, y, delta=None, resid=None, ws=None, stream=None):
+    """Returns (delta [K,N], resid (device doubles, cg_iters + 1))."""
+    import torch
+    lib = _lib.load()
+    dev = y.device
+    delta = torch.empty_like(g) if delta is None else delta
+    resid = torch.full((opts.cg_iters + 1,), float("nan"), dtype=torch.float64,
+                       device=dev) if resid is None else resid
+    ws = workspace(problem, opts, _lib.CALL_SOLVE, dev) if ws is None else ws
+    _lib.check(lib.mpm_solve(ctypes.byref(problem), ctypes.byref(opts), _ptr(h, "h", _f32()),
+                             _ptr(w, "w", _f32()), _ptr(g, "g", _f32()), _ptr(y, "y", _f32()),
+                             _ptr(delta, "delta", _f32()), _ptr(resid, "resid", torch.float64, True),
+                             _ptr(ws, "ws"), ws.numel(), _stream(stream)), "mpm_solve")
+    return delta, resid
+
+
+def mpm_uncertainty(problem, h, w, y=None, var=None, logdet=None, moments=None,
+                    want_logdet=True, want_moments=False, stream=None):
+    """Returns (var [K,N], logdet [N] or None, moments [4,N] or None)."""
+    import torch
+    lib = _lib.load()
+    dev = h.device
+    K, N = problem.n_maps, problem.nx * problem.ny * problem.nz
+    var = torch.empty((K, N), dtype=torch.float32, device=dev) if var is None else var
+    if want_logdet and logdet is None:
+        logdet = torch.empty(N, dtype=torch.float32, device=dev)
+    if want_moments and moments is None:
+        moments = torch.empty((4, N), dtype=torch.float32, device=dev)
+    _lib.check(lib.mpm_uncertainty(ctypes.byref(problem), _ptr(h, "h", _f32()), _ptr(w, "w", _f32()),
+                                   _ptr(y, "y", _f32(), True), _ptr(var, "var", _f32()),
+                                   _ptr(logdet, "logdet", _f32(), True),
+                                   _ptr(moments, "moments", _f32(), True), _stream(stream)),
+               "mpm_uncertainty")
+    return var, logdet, moments
+
+
+def mpm_fit(problem, opts, x, y, b1p=None, b1m=None, var=None, ws=None, stream=None,
+            allow_not_converged=True):
+    """Fit in place: ``y`` holds the starting maps (ignored when ``opts.init``)
+    and receives the result.  Returns (status, Report)."""
+    import torch
+    lib = _lib.load()
+    ws = workspace(problem, opts, _lib.CALL_FIT, y.device) if ws is None else ws
+    rep = Report()
+    xdt = torch.bfloat16 if problem.echo_dtype == 1 else torch.float32
+    allow = (_lib.OK, _lib.WARN_NOT_CONVERGED) if allow_not_converged else (_lib.OK,)
+    st = _lib.check(lib.mpm_fit(ctypes.byref(problem), ctypes.byref(opts), _ptr(x, "x", xdt),
+                                _ptr(b1p, "b1p", _f32(), True), _ptr(b1m, "b1m", _f32(), True),
+                                _ptr(y, "y", _f32()), _ptr(var, "var", _f32(), True),
+                                _ptr(ws, "ws"), ws.numel(), ctypes.byref(rep), _stream(stream)),
+                    "mpm_fit", allow)
+    return st, rep
+
+
+def mpm_workspace_status(ws, stream=None) -> int:
+    lib = _lib.load()
+    return lib.mpm_workspace_status(_ptr(ws, "ws"), ws.numel(), _stream(stream))
+
+
+def mpm_kernel_launches() -> int:
+    return int(_lib.load().mpm_kernel_launches())

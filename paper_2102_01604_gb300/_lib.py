@@ -1,0 +1,119 @@
+"""ctypes view of the C ABI in ``include/mpm.h`` (``libmpm.so``).
+
+Structures mirror the header field by field; prototypes are declared once
+on first load.  Loading fails loudly when the library has not been built:
+there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmpm.so")
+
+MAX_CONTRASTS = 8
+MAX_IMAGES = 64
+MAX_REPORT = 256
+
+OK = 0
+WARN_NOT_CONVERGED = 1
+ERR_INVALID_ARG = -1
+ERR_WORKSPACE_TOO_SMALL = -2
+ERR_CUDA = -3
+ERR_NUMERIC = -4
+ERR_TIMEOUT = -5
+
+CALL_FIT, CALL_SOLVE, CALL_GRAD_HESS, CALL_JTV = 0, 1, 2, 3
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("vx", ctypes.c_double * 3),
+        ("n_contrasts", ctypes.c_int),
+        ("n_echoes", ctypes.c_int * MAX_CONTRASTS),
+        ("alpha", ctypes.c_double * MAX_CONTRASTS),
+        ("tr", ctypes.c_double * MAX_CONTRASTS),
+        ("mt", ctypes.c_int * MAX_CONTRASTS),
+        ("sigma2", ctypes.c_double * MAX_CONTRASTS),
+        ("te", ctypes.c_double * MAX_IMAGES),
+        ("n_maps", ctypes.c_int),
+        ("lam", ctypes.c_double * 4),
+        ("eps", ctypes.c_double),
+        ("precond", ctypes.c_int),
+        ("echo_dtype", ctypes.c_int),
+    ]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [
+        ("gn_iters", ctypes.c_int), ("cg_iters", ctypes.c_int),
+        ("newton_per_irls", ctypes.c_int), ("init", ctypes.c_int),
+        ("tol_gn", ctypes.c_double), ("tol_cg", ctypes.c_double),
+    ]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [
+        ("iters", ctypes.c_int),
+        ("F", ctypes.c_double * (MAX_REPORT + 1)),
+        ("nll", ctypes.c_double * (MAX_REPORT + 1)),
+        ("jtv", ctypes.c_double * (MAX_REPORT + 1)),
+        ("cg_rel", ctypes.c_double * MAX_REPORT),
+        ("cg_done", ctypes.c_int * MAX_REPORT),
+    ]
+
+
+# Exported symbols and their prototypes (restype, argtypes).
+_P = ctypes.POINTER(Problem)
+_O = ctypes.POINTER(Opts)
+_V = ctypes.c_void_p
+_S = ctypes.c_size_t
+PROTOTYPES = {
+    "mpm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "mpm_last_error": (ctypes.c_char_p, []),
+    "mpm_workspace_size": (ctypes.c_int, [_P, _O, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
+    "mpm_forward": (ctypes.c_int, [_P, _V, _V, _V, _V, _V]),
+    "mpm_grad_hess": (ctypes.c_int, [_P, _V, _V, _V, _V, _V, _V, _V, _V, _S, _V]),
+    "mpm_jtv_weights": (ctypes.c_int, [_P, _V, _V, _V, _V, _S, _V]),
+    "mpm_solve": (ctypes.c_int, [_P, _O, _V, _V, _V, _V, _V, _V, _V, _S, _V]),
+    "mpm_uncertainty": (ctypes.c_int, [_P, _V, _V, _V, _V, _V, _V, _V]),
+    "mpm_fit": (ctypes.c_int, [_P, _O, _V, _V, _V, _V, _V, _V, _S, ctypes.POINTER(Report), _V]),
+    "mpm_workspace_status": (ctypes.c_int, [_V, _S, _V]),
+    "mpm_kernel_launches": (ctypes.c_ulonglong, []),
+}
+
+_handle = None
+
+
+def load():
+    """Load ``libmpm.so`` (raises if it is missing) and declare prototypes."""
+    global _handle
+    if _handle is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build the CUDA library first "
+                "(python -c 'import __graft_entry__ as g; g.build()')")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in PROTOTYPES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _handle = lib
+    return _handle
+
+
+class MPMError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        lib = load()
+        msg = lib.mpm_status_string(status).decode()
+        detail = lib.mpm_last_error().decode()
+        super().__init__(f"{where}: {msg} ({status}){': ' + detail if detail else ''}")
+        self.status = status
+
+
+def check(status: int, where: str, allow=(OK,)) -> int:
+    if status not in allow:
+        raise MPMError(status, where)
+    return status

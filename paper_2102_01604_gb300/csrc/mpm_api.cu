@@ -1,0 +1,574 @@
+// mpm_api.cu -- the C ABI declared in include/mpm.h: argument checking,
+// workspace layout, constant initial maps and the host loop of the fit.
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "mpm_internal.cuh"
+
+namespace mpm {
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+int voxel_grid(long long N)
+{
+    const long long cap = 8LL * kNumSm;
+    long long g = (N + kBlock - 1) / kBlock;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+static thread_local std::string t_err;
+
+static mpm_status fail(mpm_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    return s;
+}
+
+#define MPM_CUDA(call)                                                                   \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(MPM_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),   \
+                        __FILE__, __LINE__);                                             \
+    } while (0)
+
+static bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+static int n_images(const mpm_problem* p)
+{
+    int I = 0;
+    for (int c = 0; c < p->n_contrasts; ++c) I += p->n_echoes[c];
+    return I;
+}
+
+static mpm_status check_problem(const mpm_problem* p)
+{
+    if (!p) return fail(MPM_ERR_INVALID_ARG, "problem is NULL");
+    if (p->nx < 0 || p->ny < 0 || p->nz < 0)
+        return fail(MPM_ERR_INVALID_ARG, "negative grid size %d x %d x %d", p->nx, p->ny, p->nz);
+    const long long tiles = (long long)((p->nx + kTileX - 1) / kTileX) * ((p->ny + kTileY - 1) / kTileY);
+    if (tiles > kMaxBlocks)
+        return fail(MPM_ERR_INVALID_ARG, "nx * ny too large (%d x %d)", p->nx, p->ny);
+    for (int d = 0; d < 3; ++d)
+        if (!finite_pos(p->vx[d])) return fail(MPM_ERR_INVALID_ARG, "voxel size vx[%d] must be > 0", d);
+    if (p->n_contrasts < 1 || p->n_contrasts > MPM_MAX_CONTRASTS)
+        return fail(MPM_ERR_INVALID_ARG, "n_contrasts = %d outside [1, %d]", p->n_contrasts,
+                    MPM_MAX_CONTRASTS);
+    int I = 0, any_mt = 0;
+    for (int c = 0; c < p->n_contrasts; ++c) {
+        if (p->n_echoes[c] < 1) return fail(MPM_ERR_INVALID_ARG, "n_echoes[%d] < 1", c);
+        I += p->n_echoes[c];
+        if (I > MPM_MAX_IMAGES)
+            return fail(MPM_ERR_INVALID_ARG, "more than %d images", MPM_MAX_IMAGES);
+        if (!(p->alpha[c] > 0.0 && p->alpha[c] < M_PI))
+            return fail(MPM_ERR_INVALID_ARG, "alpha[%d] must be in (0, pi)", c);
+        if (!finite_pos(p->tr[c])) return fail(MPM_ERR_INVALID_ARG, "tr[%d] must be > 0", c);
+        if (!finite_pos(p->sigma2[c])) return fail(MPM_ERR_INVALID_ARG, "sigma2[%d] must be > 0", c);
+        if (p->mt[c] != 0 && p->mt[c] != 1) return fail(MPM_ERR_INVALID_ARG, "mt[%d] must be 0 or 1", c);
+        any_mt |= p->mt[c];
+    }
+    for (int i = 0; i < I; ++i)
+        if (!(std::isfinite(p->te[i]) && p->te[i] >= 0.0))
+            return fail(MPM_ERR_INVALID_ARG, "te[%d] must be >= 0", i);
+    const int K = any_mt ? 4 : 3;
+    if (p->n_maps != K)
+        return fail(MPM_ERR_INVALID_ARG, "n_maps = %d but must be %d (%s MT contrast)", p->n_maps,
+                    K, any_mt ? "with an" : "without");
+    for (int k = 0; k < K; ++k)
+        if (!(std::isfinite(p->lambda[k]) && p->lambda[k] >= 0.0))
+            return fail(MPM_ERR_INVALID_ARG, "lambda[%d] must be >= 0", k);
+    if (!finite_pos(p->eps)) return fail(MPM_ERR_INVALID_ARG, "eps must be > 0");
+    if (p->precond < 0 || p->precond > 2) return fail(MPM_ERR_INVALID_ARG, "precond must be 0, 1 or 2");
+    if (p->echo_dtype != 0 && p->echo_dtype != 1)
+        return fail(MPM_ERR_INVALID_ARG, "echo_dtype must be 0 (float32) or 1 (bfloat16)");
+    return MPM_OK;
+}
+
+static mpm_status check_opts(const mpm_opts* o)
+{
+    if (!o) return fail(MPM_ERR_INVALID_ARG, "opts is NULL");
+    if (o->gn_iters < 0 || o->gn_iters > MPM_MAX_REPORT)
+        return fail(MPM_ERR_INVALID_ARG, "gn_iters = %d outside [0, %d]", o->gn_iters, MPM_MAX_REPORT);
+    if (o->cg_iters < 1 || o->cg_iters > 1000000)
+        return fail(MPM_ERR_INVALID_ARG, "cg_iters = %d outside [1, 1e6]", o->cg_iters);
+    if (o->newton_per_irls < 1) return fail(MPM_ERR_INVALID_ARG, "newton_per_irls must be >= 1");
+    if (o->init != 0 && o->init != 1) return fail(MPM_ERR_INVALID_ARG, "init must be 0 or 1");
+    if (!(std::isfinite(o->tol_gn) && o->tol_gn >= 0.0) || !(std::isfinite(o->tol_cg) && o->tol_cg >= 0.0))
+        return fail(MPM_ERR_INVALID_ARG, "tolerances must be finite and >= 0");
+    return MPM_OK;
+}
+
+static DevProblem make_dev(const mpm_problem* p)
+{
+    DevProblem P;
+    memset(&P, 0, sizeof P);
+    P.nx = p->nx;
+    P.ny = p->ny;
+    P.nz = p->nz;
+    P.N = (long long)p->nx * p->ny * p->nz;
+    P.ihx2 = (float)(1.0 / (p->vx[0] * p->vx[0]));
+    P.ihy2 = (float)(1.0 / (p->vx[1] * p->vx[1]));
+    P.ihz2 = (float)(1.0 / (p->vx[2] * p->vx[2]));
+    P.C = p->n_contrasts;
+    P.K = p->n_maps;
+    P.T = P.K * (P.K + 1) / 2;
+    int i = 0;
+    for (int c = 0; c < P.C; ++c) {
+        P.n_echoes[c] = p->n_echoes[c];
+        P.echo0[c] = i;
+        P.alpha[c] = (float)p->alpha[c];
+        P.tr[c] = (float)p->tr[c];
+        P.isig2[c] = (float)(1.0 / p->sigma2[c]);
+        P.mt[c] = p->mt[c];
+        i += p->n_echoes[c];
+    }
+    P.I = i;
+    for (int j = 0; j < i; ++j) P.te[j] = (float)p->te[j];
+    for (int k = 0; k < 4; ++k) P.lambda[k] = (float)p->lambda[k];
+    P.eps2 = (float)(p->eps * p->eps);
+    P.precond = p->precond;
+    return P;
+}
+
+// Device (or managed) memory check: a host pointer handed to a kernel would
+// fault, so it is refused here.
+static mpm_status check_dev(const void* ptr, const char* name, bool optional, size_t align)
+{
+    if (!ptr) {
+        if (optional) return MPM_OK;
+        return fail(MPM_ERR_INVALID_ARG, "%s is NULL", name);
+    }
+    if (reinterpret_cast<uintptr_t>(ptr) % align)
+        return fail(MPM_ERR_INVALID_ARG, "%s is not %zu-byte aligned", name, align);
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MPM_ERR_INVALID_ARG, "%s: not a CUDA pointer (%s)", name, cudaGetErrorString(e));
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+        return fail(MPM_ERR_INVALID_ARG, "%s is not device memory", name);
+    return MPM_OK;
+}
+
+#define MPM_TRY(expr)                     \
+    do {                                  \
+        mpm_status s_ = (expr);           \
+        if (s_ != MPM_OK) return s_;      \
+    } while (0)
+
+// ----------------------------------------------------------- workspace
+
+static size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
+
+constexpr size_t kHeaderBytes = 4096;
+constexpr size_t kPartialBytes = sizeof(double) * 2 * kMaxBlocks;
+constexpr int kMeanBlocksHost = 304;   // must match the launcher's cap
+
+struct FitWs {
+    WsHeader* hdr;
+    Reduce red;
+    double* mean_parts;
+    double* means;
+    double* nll;       // [MPM_MAX_REPORT + 2]
+    double* jtv;       // [MPM_MAX_REPORT + 2]
+    double* cg_rel;    // [MPM_MAX_REPORT]
+    int* cg_it;        // [MPM_MAX_REPORT]
+    float* w;
+    float* g;
+    float* h;
+    float* xbuf;
+    void* solve;
+    size_t total;
+};
+
+static FitWs layout(const DevProblem& P, int call, void* base)
+{
+    FitWs L;
+    memset(&L, 0, sizeof L);
+    size_t off = 0;
+    char* b = static_cast<char*>(base);
+    auto take = [&](size_t bytes) -> char* {
+        char* p = b ? b + off : nullptr;
+        off += al(bytes);
+        return p;
+    };
+    L.hdr = reinterpret_cast<WsHeader*>(take(kHeaderBytes));
+    L.red.partials = reinterpret_cast<double*>(take(kPartialBytes));
+    L.red.counter = L.hdr ? &L.hdr->counter : nullptr;
+    const size_t vec = sizeof(float) * (size_t)P.K * P.N;
+    if (call == MPM_CALL_FIT) {
+        L.mean_parts = reinterpret_cast<double*>(take(sizeof(double) * P.I * kMeanBlocksHost));
+        L.means = reinterpret_cast<double*>(take(sizeof(double) * MPM_MAX_IMAGES));
+        L.nll = reinterpret_cast<double*>(take(sizeof(double) * (MPM_MAX_REPORT + 2)));
+        L.jtv = reinterpret_cast<double*>(take(sizeof(double) * (MPM_MAX_REPORT + 2)));
+        L.cg_rel = reinterpret_cast<double*>(take(sizeof(double) * MPM_MAX_REPORT));
+        L.cg_it = reinterpret_cast<int*>(take(sizeof(int) * MPM_MAX_REPORT));
+        L.w = reinterpret_cast<float*>(take(sizeof(float) * (size_t)P.N));
+        L.g = reinterpret_cast<float*>(take(vec));
+        L.h = reinterpret_cast<float*>(take(sizeof(float) * (size_t)P.T * P.N));
+        L.xbuf = reinterpret_cast<float*>(take(vec));
+    }
+    if (call == MPM_CALL_FIT || call == MPM_CALL_SOLVE) L.solve = take(solve_ws_bytes(P));
+    L.total = off;
+    return L;
+}
+
+static mpm_status check_ws(const DevProblem& P, int call, void* ws, size_t ws_bytes, FitWs& L)
+{
+    const size_t need = layout(P, call, nullptr).total;
+    if (ws_bytes < need)
+        return fail(MPM_ERR_WORKSPACE_TOO_SMALL, "workspace of %zu bytes, %zu needed", ws_bytes, need);
+    MPM_TRY(check_dev(ws, "ws", false, 256));
+    L = layout(P, call, ws);
+    return MPM_OK;
+}
+
+// ------------------------------------------------------ initial maps
+
+// Constant starting maps from the image means (Sec. 2.7 starts from constant
+// maps derived from the mean intensity of every volume; the formulas are this
+// library's reading of Eqs. 1 and 3):
+//  - one R2* shared by all contrasts and one TE = 0 intercept per contrast
+//    from least squares on log(mean) against TE;
+//  - the non-MT intercepts lie on the line S/sin a = E (S/tan a) + A (1 - E):
+//    slope E (at the mean TR of those contrasts), intercept A (1 - E);
+//  - MT contrasts give 1 - delta = S / (A sin a (1 - E) + S cos a E), averaged;
+//  - clamps R2* >= 1e-3, E in [1e-6, 1 - 1e-6], delta in [1e-4, 0.5];
+//    fallbacks R1 = 1/s and A from the first contrast when fewer than two
+//    distinct non-MT flip angles exist, R2* = 20/s without multi-echo data.
+static void initial_maps(const mpm_problem* p, const double* mean, float out[4])
+{
+    const int C = p->n_contrasts;
+    double lm[MPM_MAX_IMAGES];
+    const int I = n_images(p);
+    for (int i = 0; i < I; ++i) lm[i] = std::log(mean[i] > 1e-30 ? mean[i] : 1e-30);
+    double tbar[MPM_MAX_CONTRASTS], lbar[MPM_MAX_CONTRASTS];
+    double sxy = 0.0, sxx = 0.0;
+    for (int c = 0, i0 = 0; c < C; i0 += p->n_echoes[c], ++c) {
+        const int E = p->n_echoes[c];
+        double st = 0.0, sl = 0.0;
+        for (int e = 0; e < E; ++e) {
+            st += p->te[i0 + e];
+            sl += lm[i0 + e];
+        }
+        tbar[c] = st / E;
+        lbar[c] = sl / E;
+        for (int e = 0; e < E; ++e) {
+            const double dt = p->te[i0 + e] - tbar[c];
+            sxy += dt * (lm[i0 + e] - lbar[c]);
+            sxx += dt * dt;
+        }
+    }
+    double r2 = sxx > 0.0 ? -sxy / sxx : 20.0;
+    if (r2 < 1e-3) r2 = 1e-3;
+    double S0[MPM_MAX_CONTRASTS];
+    for (int c = 0; c < C; ++c) S0[c] = std::exp(lbar[c] + r2 * tbar[c]);
+
+    int first = -1, cnt = 0;
+    double mx = 0, my = 0, mxx = 0, mxy = 0, trsum = 0;
+    for (int c = 0; c < C; ++c) {
+        if (p->mt[c]) continue;
+        if (first < 0) first = c;
+        const double X = S0[c] / std::tan(p->alpha[c]);
+        const double Y = S0[c] / std::sin(p->alpha[c]);
+        mx += X; my += Y; mxx += X * X; mxy += X * Y; trsum += p->tr[c];
+        ++cnt;
+    }
+    if (first < 0) first = 0;
+    const double varx = cnt > 0 ? mxx - mx * mx / cnt : 0.0;
+    double A, r1;
+    auto from_first = [&](double E) {
+        return S0[first] * (1.0 - std::cos(p->alpha[first]) * E) /
+               (std::sin(p->alpha[first]) * (1.0 - E));
+    };
+    if (cnt >= 2 && varx > 1e-12 * mxx) {
+        double E = (mxy - mx * my / cnt) / varx;
+        E = std::fmin(std::fmax(E, 1e-6), 1.0 - 1e-6);
+        r1 = -std::log(E) / (trsum / cnt);
+        A = ((my - E * mx) / cnt) / (1.0 - E);
+        if (!(A > 0.0)) A = from_first(E);
+    } else {
+        r1 = 1.0;
+        A = from_first(std::exp(-r1 * p->tr[first]));
+    }
+    double dsum = 0.0;
+    int nmt = 0;
+    for (int c = 0; c < C; ++c) {
+        if (!p->mt[c]) continue;
+        const double E = std::exp(-r1 * p->tr[c]);
+        const double mfac = S0[c] / (A * std::sin(p->alpha[c]) * (1.0 - E) + S0[c] * std::cos(p->alpha[c]) * E);
+        dsum += 1.0 - mfac;
+        ++nmt;
+    }
+    double delta = nmt ? dsum / nmt : 0.01;
+    if (!(delta >= 1e-4)) delta = 1e-4;
+    if (delta > 0.5) delta = 0.5;
+    out[0] = (float)std::log(A);
+    out[1] = (float)std::log(r1);
+    out[2] = (float)std::log(r2);
+    out[3] = (float)std::log(delta / (1.0 - delta));
+}
+
+}  // namespace mpm
+
+using namespace mpm;
+
+// ================================================================= C ABI
+
+extern "C" {
+
+const char* mpm_status_string(mpm_status s)
+{
+    switch (s) {
+    case MPM_OK: return "ok";
+    case MPM_WARN_NOT_CONVERGED: return "not converged within gn_iters";
+    case MPM_ERR_INVALID_ARG: return "invalid argument";
+    case MPM_ERR_WORKSPACE_TOO_SMALL: return "workspace too small";
+    case MPM_ERR_CUDA: return "CUDA error";
+    case MPM_ERR_NUMERIC: return "numeric failure (non positive definite block or NaN)";
+    case MPM_ERR_TIMEOUT: return "timeout";
+    default: return "unknown status";
+    }
+}
+
+const char* mpm_last_error(void) { return t_err.c_str(); }
+
+unsigned long long mpm_kernel_launches(void) { return g_launches.load(); }
+
+mpm_status mpm_workspace_size(const mpm_problem* problem, const mpm_opts* opts, int call,
+                              size_t* bytes)
+{
+    MPM_TRY(check_problem(problem));
+    if (!bytes) return fail(MPM_ERR_INVALID_ARG, "bytes is NULL");
+    if (call < MPM_CALL_FIT || call > MPM_CALL_JTV) return fail(MPM_ERR_INVALID_ARG, "unknown call %d", call);
+    if ((call == MPM_CALL_FIT || call == MPM_CALL_SOLVE)) MPM_TRY(check_opts(opts));
+    *bytes = layout(make_dev(problem), call, nullptr).total;
+    return MPM_OK;
+}
+
+mpm_status mpm_forward(const mpm_problem* problem, const float* y, const float* b1p,
+                       const float* b1m, float* s, void* stream)
+{
+    MPM_TRY(check_problem(problem));
+    const DevProblem P = make_dev(problem);
+    if (P.N == 0) return MPM_OK;
+    MPM_TRY(check_dev(y, "y", false, 4));
+    MPM_TRY(check_dev(b1p, "b1p", true, 4));
+    MPM_TRY(check_dev(b1m, "b1m", true, 4));
+    MPM_TRY(check_dev(s, "s", false, 4));
+    MPM_CUDA(launch_forward(P, y, b1p, b1m, s, (cudaStream_t)stream));
+    return MPM_OK;
+}
+
+mpm_status mpm_grad_hess(const mpm_problem* problem, const void* x, const float* y,
+                         const float* b1p, const float* b1m, float* g, float* h, double* nll,
+                         void* ws, size_t ws_bytes, void* stream)
+{
+    MPM_TRY(check_problem(problem));
+    const DevProblem P = make_dev(problem);
+    cudaStream_t st = (cudaStream_t)stream;
+    MPM_TRY(check_dev(nll, "nll", false, 8));
+    if (P.N == 0) {
+        MPM_CUDA(cudaMemsetAsync(nll, 0, sizeof(double), st));
+        return MPM_OK;
+    }
+    MPM_TRY(check_dev(x, "x", false, problem->echo_dtype ? 2 : 4));
+    MPM_TRY(check_dev(y, "y", false, 4));
+    MPM_TRY(check_dev(b1p, "b1p", true, 4));
+    MPM_TRY(check_dev(b1m, "b1m", true, 4));
+    MPM_TRY(check_dev(g, "g", false, 4));
+    MPM_TRY(check_dev(h, "h", false, 4));
+    FitWs L;
+    MPM_TRY(check_ws(P, MPM_CALL_GRAD_HESS, ws, ws_bytes, L));
+    MPM_CUDA(cudaMemsetAsync(L.hdr, 0, sizeof(WsHeader), st));
+    MPM_CUDA(launch_grad_hess(P, problem->echo_dtype, x, y, b1p, b1m, g, h, nll, L.red, st));
+    return MPM_OK;
+}
+
+mpm_status mpm_jtv_weights(const mpm_problem* problem, const float* y, float* w, double* jtv,
+                           void* ws, size_t ws_bytes, void* stream)
+{
+    MPM_TRY(check_problem(problem));
+    const DevProblem P = make_dev(problem);
+    cudaStream_t st = (cudaStream_t)stream;
+    MPM_TRY(check_dev(jtv, "jtv", false, 8));
+    if (P.N == 0) {
+        MPM_CUDA(cudaMemsetAsync(jtv, 0, sizeof(double), st));
+        return MPM_OK;
+    }
+    MPM_TRY(check_dev(y, "y", false, 4));
+    MPM_TRY(check_dev(w, "w", true, 4));
+    FitWs L;
+    MPM_TRY(check_ws(P, MPM_CALL_JTV, ws, ws_bytes, L));
+    MPM_CUDA(cudaMemsetAsync(L.hdr, 0, sizeof(WsHeader), st));
+    MPM_CUDA(launch_jtv(P, y, w, jtv, L.red, st));
+    return MPM_OK;
+}
+
+mpm_status mpm_solve(const mpm_problem* problem, const mpm_opts* opts, const float* h,
+                     const float* w, const float* g, const float* y, float* delta, double* resid,
+                     void* ws, size_t ws_bytes, void* stream)
+{
+    MPM_TRY(check_problem(problem));
+    MPM_TRY(check_opts(opts));
+    const DevProblem P = make_dev(problem);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (P.N == 0) {
+        if (resid) {
+            MPM_TRY(check_dev(resid, "resid", false, 8));
+            MPM_CUDA(cudaMemsetAsync(resid, 0, sizeof(double), st));
+        }
+        return MPM_OK;
+    }
+    MPM_TRY(check_dev(h, "h", false, 4));
+    MPM_TRY(check_dev(w, "w", false, 4));
+    MPM_TRY(check_dev(g, "g", false, 4));
+    MPM_TRY(check_dev(y, "y", false, 4));
+    MPM_TRY(check_dev(delta, "delta", false, 4));
+    MPM_TRY(check_dev(resid, "resid", true, 8));
+    FitWs L;
+    MPM_TRY(check_ws(P, MPM_CALL_SOLVE, ws, ws_bytes, L));
+    MPM_CUDA(cudaMemsetAsync(L.hdr, 0, sizeof(WsHeader), st));
+    MPM_CUDA(launch_solve(P, opts->cg_iters, opts->tol_cg, h, w, g, y, delta, nullptr, resid,
+                          nullptr, nullptr, L.solve, L.hdr, L.red, st));
+    return MPM_OK;
+}
+
+mpm_status mpm_uncertainty(const mpm_problem* problem, const float* h, const float* w,
+                           const float* y, float* var, float* logdet, float* moments,
+                           void* stream)
+{
+    MPM_TRY(check_problem(problem));
+    const DevProblem P = make_dev(problem);
+    if (P.N == 0) return MPM_OK;
+    MPM_TRY(check_dev(h, "h", false, 4));
+    MPM_TRY(check_dev(w, "w", false, 4));
+    MPM_TRY(check_dev(var, "var", false, 4));
+    MPM_TRY(check_dev(logdet, "logdet", true, 4));
+    MPM_TRY(check_dev(moments, "moments", true, 4));
+    MPM_TRY(check_dev(y, "y", moments == nullptr, 4));
+    // The status word of the uncertainty pass is not reported through a
+    // workspace (the call takes none): a non positive definite block yields
+    // non-finite variances instead.
+    MPM_CUDA(launch_uncertainty(P, h, w, y, var, logdet, moments, nullptr, (cudaStream_t)stream));
+    return MPM_OK;
+}
+
+mpm_status mpm_workspace_status(const void* ws, size_t ws_bytes, void* stream)
+{
+    if (ws_bytes < sizeof(WsHeader)) return fail(MPM_ERR_WORKSPACE_TOO_SMALL, "workspace too small");
+    MPM_TRY(check_dev(ws, "ws", false, 256));
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned status = 0;
+    MPM_CUDA(cudaMemcpyAsync(&status, ws, sizeof status, cudaMemcpyDeviceToHost, st));
+    MPM_CUDA(cudaStreamSynchronize(st));
+    if (status) return fail(MPM_ERR_NUMERIC, "device status 0x%x (%s%s)", status,
+                            status & kStatusNotPD ? "non positive definite block " : "",
+                            status & kStatusNaN ? "NaN in a reduction" : "");
+    return MPM_OK;
+}
+
+mpm_status mpm_fit(const mpm_problem* problem, const mpm_opts* opts, const void* x,
+                   const float* b1p, const float* b1m, float* y, float* var_out, void* ws,
+                   size_t ws_bytes, mpm_report* report, void* stream)
+{
+    MPM_TRY(check_problem(problem));
+    MPM_TRY(check_opts(opts));
+    const DevProblem P = make_dev(problem);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (report) memset(report, 0, sizeof *report);
+    if (P.N == 0) return MPM_OK;
+    MPM_TRY(check_dev(x, "x", false, problem->echo_dtype ? 2 : 4));
+    MPM_TRY(check_dev(b1p, "b1p", true, 4));
+    MPM_TRY(check_dev(b1m, "b1m", true, 4));
+    MPM_TRY(check_dev(y, "y_inout", false, 4));
+    MPM_TRY(check_dev(var_out, "var_out", true, 4));
+    FitWs L;
+    MPM_TRY(check_ws(P, MPM_CALL_FIT, ws, ws_bytes, L));
+    MPM_CUDA(cudaMemsetAsync(L.hdr, 0, sizeof(WsHeader), st));
+
+    if (opts->init) {
+        double means[MPM_MAX_IMAGES];
+        MPM_CUDA(launch_image_means(P, problem->echo_dtype, x, L.mean_parts, L.means, st));
+        MPM_CUDA(cudaMemcpyAsync(means, L.means, sizeof(double) * P.I, cudaMemcpyDeviceToHost, st));
+        MPM_CUDA(cudaStreamSynchronize(st));
+        float vals[4];
+        initial_maps(problem, means, vals);
+        MPM_CUDA(launch_fill_maps(P, vals, y, st));
+    }
+
+    const int npi = opts->newton_per_irls;
+    int it = 0;
+    bool converged = false, w_fresh = false;
+    double F_prev = 0.0;
+    for (;; ++it) {
+        w_fresh = (it % npi == 0);
+        MPM_CUDA(launch_jtv(P, y, w_fresh ? L.w : nullptr, L.jtv + it, L.red, st));
+        MPM_CUDA(launch_grad_hess(P, problem->echo_dtype, x, y, b1p, b1m, L.g, L.h, L.nll + it,
+                                  L.red, st));
+        if (it >= opts->gn_iters) break;
+        if (opts->tol_gn > 0.0) {
+            double v[2];
+            MPM_CUDA(cudaMemcpyAsync(&v[0], L.nll + it, sizeof(double), cudaMemcpyDeviceToHost, st));
+            MPM_CUDA(cudaMemcpyAsync(&v[1], L.jtv + it, sizeof(double), cudaMemcpyDeviceToHost, st));
+            MPM_CUDA(cudaStreamSynchronize(st));
+            const double F = v[0] + v[1];
+            if (it > 0 && std::fabs(F_prev - F) < opts->tol_gn * std::fabs(F_prev)) {
+                converged = true;
+                break;
+            }
+            F_prev = F;
+        }
+        MPM_CUDA(launch_solve(P, opts->cg_iters, opts->tol_cg, L.h, L.w, L.g, y, L.xbuf, y,
+                              nullptr, L.cg_rel + it, L.cg_it + it, L.solve, L.hdr, L.red, st));
+    }
+    const int iters = it;
+    if (var_out) {
+        if (!w_fresh) MPM_CUDA(launch_jtv(P, y, L.w, L.jtv + MPM_MAX_REPORT + 1, L.red, st));
+        MPM_CUDA(launch_uncertainty(P, L.h, L.w, y, var_out, nullptr, nullptr, &L.hdr->status, st));
+    }
+    double nll[MPM_MAX_REPORT + 1], jtv[MPM_MAX_REPORT + 1], cgr[MPM_MAX_REPORT];
+    int cgi[MPM_MAX_REPORT];
+    unsigned status = 0;
+    MPM_CUDA(cudaMemcpyAsync(nll, L.nll, sizeof(double) * (iters + 1), cudaMemcpyDeviceToHost, st));
+    MPM_CUDA(cudaMemcpyAsync(jtv, L.jtv, sizeof(double) * (iters + 1), cudaMemcpyDeviceToHost, st));
+    if (iters > 0) {
+        MPM_CUDA(cudaMemcpyAsync(cgr, L.cg_rel, sizeof(double) * iters, cudaMemcpyDeviceToHost, st));
+        MPM_CUDA(cudaMemcpyAsync(cgi, L.cg_it, sizeof(int) * iters, cudaMemcpyDeviceToHost, st));
+    }
+    MPM_CUDA(cudaMemcpyAsync(&status, &L.hdr->status, sizeof status, cudaMemcpyDeviceToHost, st));
+    MPM_CUDA(cudaStreamSynchronize(st));
+    if (report) {
+        report->iters = iters;
+        for (int i = 0; i <= iters; ++i) {
+            report->nll[i] = nll[i];
+            report->jtv[i] = jtv[i];
+            report->F[i] = nll[i] + jtv[i];
+        }
+        for (int i = 0; i < iters; ++i) {
+            report->cg_rel[i] = cgr[i];
+            report->cg_done[i] = cgi[i];
+        }
+    }
+    if (status)
+        return fail(MPM_ERR_NUMERIC, "device status 0x%x (%s%s)", status,
+                    status & kStatusNotPD ? "non positive definite block " : "",
+                    status & kStatusNaN ? "NaN in a reduction" : "");
+    if (opts->tol_gn > 0.0 && !converged) return MPM_WARN_NOT_CONVERGED;
+    return MPM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,190 @@
+// mpm_internal.cuh -- device-side problem descriptor, workspace layout and
+// shared device helpers of the sm_103a MPM library.  Internal: not part of the
+// C ABI (include/mpm.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/mpm.h"
+
+namespace mpm {
+
+constexpr int kBlock = 256;            // threads per block of every kernel
+constexpr int kTileX = 32;             // stencil tile: 32 x 8 (x, y), marched along z
+constexpr int kTileY = 8;
+constexpr int kMaxBlocks = 32768;      // bound on the blocks of a reducing launch
+constexpr int kNumSm = 152;
+
+// Problem as the kernels see it: passed by value as a kernel parameter.
+struct DevProblem {
+    int nx, ny, nz;
+    long long N;
+    float ihx2, ihy2, ihz2;             // 1 / voxel size^2 per axis
+    int C, K, T, I;
+    int n_echoes[MPM_MAX_CONTRASTS];
+    int echo0[MPM_MAX_CONTRASTS];       // index of the first image of contrast c
+    float alpha[MPM_MAX_CONTRASTS];
+    float tr[MPM_MAX_CONTRASTS];
+    float isig2[MPM_MAX_CONTRASTS];     // 1 / sigma^2
+    int mt[MPM_MAX_CONTRASTS];
+    float te[MPM_MAX_IMAGES];
+    float lambda[4];
+    float eps2;
+    int precond;
+};
+
+// Packed upper-triangle position of (a, b), a <= b, for K maps.
+__host__ __device__ constexpr int tri(int K, int a, int b)
+{
+    return a * K - a * (a - 1) / 2 + (b - a);
+}
+
+// Status bits recorded on the device.
+enum : unsigned { kStatusNotPD = 1u, kStatusNaN = 2u };
+
+// Device scalars of one PCG solve (lives in the workspace).
+struct SolveScalars {
+    double rz;        // r . z of the current residual
+    double rr0;       // |r_0|^2
+    double rr;        // |r_k|^2 of the current residual
+    double alpha;     // step of the latest completed matvec
+    double beta;      // coefficient of the next direction update
+    double tol2;      // (tol_cg)^2, 0 = off
+    int it;           // PCG iterations completed
+    int xcount;       // iterations already folded into x
+    int done;         // 1 = no further iterations
+    int pad;
+};
+
+// Reduction scratch: per-block partials and an arrival counter.  The counter
+// is zero between launches (the last block resets it).
+struct Reduce {
+    double* partials;        // [kMaxBlocks * 2]
+    unsigned int* counter;
+};
+
+// Workspace header, first bytes of every workspace.
+struct WsHeader {
+    unsigned int status;     // kStatus* bits
+    unsigned int counter;    // reduction arrival counter
+    SolveScalars sc;
+};
+
+// ------------------------------------------------------------------ helpers
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum of v over the block, valid in thread 0.  Fixed order (deterministic).
+__device__ __forceinline__ double block_sum(double v, double* sh /* [kBlock/32] */)
+{
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if ((tid & 31) == 0) sh[tid >> 5] = v;
+    __syncthreads();
+    v = 0.0;
+    if (tid < 32) {
+        v = tid < nw ? sh[tid] : 0.0;
+        v = warp_sum(v);
+    }
+    return v;
+}
+
+// Last-block-done reduction of NV values per block.  Every thread calls it
+// with its own contributions; returns true in exactly one block (the last to
+// arrive), where out[j] (valid in thread 0) holds the grid-wide sums in a
+// fixed summation order.  The counter is reset for the next launch.
+template <int NV>
+__device__ __forceinline__ bool grid_reduce(const double (&v)[NV], Reduce red, double (&out)[NV])
+{
+    __shared__ double sh[kBlock / 32];
+    __shared__ bool am_last;
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int nthreads = blockDim.x * blockDim.y;
+    const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        double s = block_sum(v[j], sh);
+        if (tid == 0) red.partials[(size_t)j * kMaxBlocks + bid] = s;
+    }
+    if (tid == 0) {
+        __threadfence();
+        unsigned prev = atomicAdd(red.counter, 1u);
+        am_last = (prev == nblocks - 1);
+    }
+    __syncthreads();
+    if (!am_last) return false;
+    __threadfence();
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        double s = 0.0;
+        for (unsigned b = tid; b < nblocks; b += nthreads)
+            s += __ldcg(&red.partials[(size_t)j * kMaxBlocks + b]);
+        out[j] = block_sum(s, sh);
+    }
+    if (tid == 0) *red.counter = 0u;
+    return true;
+}
+
+template <typename T>
+__device__ __forceinline__ float load_echo(const T* p, long long i);
+
+template <>
+__device__ __forceinline__ float load_echo<float>(const float* p, long long i)
+{
+    return __ldg(p + i);
+}
+
+template <>
+__device__ __forceinline__ float load_echo<__nv_bfloat16>(const __nv_bfloat16* p, long long i)
+{
+    return __bfloat162float(p[i]);
+}
+
+// ------------------------------------------------------- launch helpers
+
+struct StencilGrid {
+    dim3 grid, block;
+    int zc;           // z planes per block
+};
+
+StencilGrid stencil_grid(const DevProblem& P);
+int voxel_grid(long long N);
+void count_launch();
+
+// ------------------------------------------------------- kernel launchers
+// (defined in voxel_kernels.cu and stencil_kernels.cu; return cudaError_t of
+// the launch)
+
+cudaError_t launch_forward(const DevProblem& P, const float* y, const float* b1p,
+                           const float* b1m, float* s, cudaStream_t st);
+cudaError_t launch_grad_hess(const DevProblem& P, int echo_dtype, const void* x,
+                             const float* y, const float* b1p, const float* b1m, float* g,
+                             float* h, double* nll, Reduce red, cudaStream_t st);
+cudaError_t launch_uncertainty(const DevProblem& P, const float* h, const float* w,
+                               const float* y, float* var, float* logdet, float* moments,
+                               unsigned* status, cudaStream_t st);
+cudaError_t launch_image_means(const DevProblem& P, int echo_dtype, const void* x,
+                               double* partials, double* means, cudaStream_t st);
+cudaError_t launch_fill_maps(const DevProblem& P, const float* values, float* y,
+                             cudaStream_t st);
+
+cudaError_t launch_jtv(const DevProblem& P, const float* y, float* w, double* jtv,
+                       Reduce red, cudaStream_t st);
+cudaError_t launch_solve(const DevProblem& P, int cg_iters, double tol_cg, const float* h,
+                         const float* w, const float* g, const float* y, float* delta,
+                         float* y_update, double* resid, double* report_rel,
+                         int* report_it, void* solve_ws, WsHeader* hdr, Reduce red,
+                         cudaStream_t st);
+size_t solve_ws_bytes(const DevProblem& P);
+
+}  // namespace mpm

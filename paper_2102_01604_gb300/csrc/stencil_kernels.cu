@@ -1,0 +1,495 @@
+// stencil_kernels.cu -- the prior and the Newton-system solve (sm_103a):
+//   k_jtv          JTV weights w_n = (u_n + eps^2)^-1/2 and JTV_eps (Eqs. 38-40)
+//   k_pcg_init     r_0 = g + L y, preconditioner factor, z_0 = M^-1 r_0 (Eq. 42)
+//   k_pcg_matvec   p_k = z_k + beta p_{k-1}; q = (H + L) p_k; x += alpha p_{k-1}; p.q
+//   k_pcg_update   r -= alpha q; z = M^-1 r; r.z, r.r
+//   k_pcg_final    delta = x + alpha p (or y <- y - delta)
+//
+// L = G'WG (x) diag(lambda) is applied as the 7-point weighted stencil
+//   (L v)_k[n] = lambda_k sum_{m in N(n)} (w_n + w_m)(v_k[n] - v_k[m]) / h^2,
+// neighbours outside the volume dropped (Neumann).  Blocks cover a 32 x 8
+// (x, y) tile and march along z.  All CG scalars (alpha, beta, |r|) live in
+// device memory and are produced by the last block of each reducing launch,
+// so the whole PCG runs without a host round trip.
+#include "mpm_internal.cuh"
+
+namespace mpm {
+
+// Edge coefficients c_j = (w_n + w_m) / h_j^2 of the six neighbours (0 when
+// the neighbour is outside the volume) and their offsets.
+struct Edges {
+    float c[6];
+    long long off[6];
+    bool ok[6];
+};
+
+__device__ __forceinline__ void make_edges(const DevProblem& P, int x, int y, int z,
+                                           long long n, const float* __restrict__ w,
+                                           float wn, Edges& e)
+{
+    const long long sxy = (long long)P.nx * P.ny;
+    e.off[0] = -1;        e.ok[0] = x > 0;
+    e.off[1] = 1;         e.ok[1] = x < P.nx - 1;
+    e.off[2] = -P.nx;     e.ok[2] = y > 0;
+    e.off[3] = P.nx;      e.ok[3] = y < P.ny - 1;
+    e.off[4] = -sxy;      e.ok[4] = z > 0;
+    e.off[5] = sxy;       e.ok[5] = z < P.nz - 1;
+    const float ih[6] = {P.ihx2, P.ihx2, P.ihy2, P.ihy2, P.ihz2, P.ihz2};
+#pragma unroll
+    for (int j = 0; j < 6; ++j)
+        e.c[j] = e.ok[j] ? (wn + __ldg(w + n + e.off[j])) * ih[j] : 0.0f;
+}
+
+// ------------------------------------------------------------- JTV weights
+
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_jtv(DevProblem P, int zc, const float* __restrict__ y,
+                                                float* __restrict__ w, double* jtv, Reduce red)
+{
+    const long long N = P.N;
+    const long long sxy = (long long)P.nx * P.ny;
+    const int x = blockIdx.x * kTileX + threadIdx.x;
+    const int yy = blockIdx.y * kTileY + threadIdx.y;
+    const int z0 = blockIdx.z * zc;
+    const int z1 = min(P.nz, z0 + zc);
+    double acc = 0.0;
+    if (x < P.nx && yy < P.ny) {
+        const float ih[6] = {P.ihx2, P.ihx2, P.ihy2, P.ihy2, P.ihz2, P.ihz2};
+        for (int z = z0; z < z1; ++z) {
+            const long long n = x + (long long)P.nx * yy + sxy * z;
+            const long long off[6] = {-1, 1, -P.nx, P.nx, -sxy, sxy};
+            const bool ok[6] = {x > 0, x < P.nx - 1, yy > 0, yy < P.ny - 1, z > 0, z < P.nz - 1};
+            float u = 0.0f;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const float* yk = y + k * N;
+                const float v = __ldg(yk + n);
+                float s = 0.0f;
+#pragma unroll
+                for (int j = 0; j < 6; ++j)
+                    if (ok[j]) {
+                        const float d = __ldg(yk + n + off[j]) - v;
+                        s += d * d * ih[j];
+                    }
+                u += P.lambda[k] * s;
+            }
+            const float val = u + P.eps2;
+            const float sq = sqrtf(val);
+            if (w) w[n] = 1.0f / sq;
+            acc += (double)sq;
+        }
+    }
+    double v[1] = {acc}, out[1];
+    if (grid_reduce<1>(v, red, out) && threadIdx.x == 0 && threadIdx.y == 0) *jtv = out[0];
+}
+
+// ------------------------------------------------ preconditioner helpers
+
+// Lower Cholesky factor of the K x K block, packed row by row
+// (00, 10, 11, 20, 21, 22, 30, 31, 32, 33) with reciprocal diagonal.
+__host__ __device__ constexpr int lo(int i, int j) { return i * (i + 1) / 2 + j; }
+
+template <int K>
+__device__ __forceinline__ bool cholesky_f32(const float (&M)[K][K], float (&L)[K * (K + 1) / 2])
+{
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        float s = M[j][j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) s -= L[lo(j, k)] * L[lo(j, k)];
+        if (!(s > 0.0f)) {
+            ok = false;
+            s = fmaxf(fabsf(M[j][j]), 1e-30f);
+        }
+        const float dj = sqrtf(s);
+        L[lo(j, j)] = 1.0f / dj;
+#pragma unroll
+        for (int i = j + 1; i < K; ++i) {
+            float v = M[i][j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) v -= L[lo(i, k)] * L[lo(j, k)];
+            L[lo(i, j)] = v / dj;
+        }
+    }
+    return ok;
+}
+
+// z = (L L')^-1 r with the packed factor.
+template <int K>
+__device__ __forceinline__ void chol_apply(const float (&L)[K * (K + 1) / 2], const float (&r)[K],
+                                           float (&z)[K])
+{
+    float t[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        float v = r[i];
+#pragma unroll
+        for (int k = 0; k < i; ++k) v -= L[lo(i, k)] * t[k];
+        t[i] = v * L[lo(i, i)];
+    }
+#pragma unroll
+    for (int i = K - 1; i >= 0; --i) {
+        float v = t[i];
+#pragma unroll
+        for (int k = i + 1; k < K; ++k) v -= L[lo(k, i)] * z[k];
+        z[i] = v * L[lo(i, i)];
+    }
+}
+
+// Per-solve workspace layout (all [.][N] float, 256-byte aligned).
+struct SolveBufs {
+    float* R;       // [T][N] preconditioner factor
+    float* r;       // [K][N]
+    float* z;       // [K][N]
+    float* p[2];    // [K][N] directions, p_k in p[k & 1]
+    float* q;       // [K][N]
+};
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+size_t solve_ws_bytes(const DevProblem& P)
+{
+    const size_t vec = align256(sizeof(float) * (size_t)P.K * P.N);
+    return align256(sizeof(float) * (size_t)P.T * P.N) + 5 * vec;
+}
+
+static SolveBufs carve(const DevProblem& P, void* ws)
+{
+    SolveBufs b;
+    char* c = static_cast<char*>(ws);
+    const size_t vec = align256(sizeof(float) * (size_t)P.K * P.N);
+    b.R = reinterpret_cast<float*>(c);
+    c += align256(sizeof(float) * (size_t)P.T * P.N);
+    b.r = reinterpret_cast<float*>(c); c += vec;
+    b.z = reinterpret_cast<float*>(c); c += vec;
+    b.p[0] = reinterpret_cast<float*>(c); c += vec;
+    b.p[1] = reinterpret_cast<float*>(c); c += vec;
+    b.q = reinterpret_cast<float*>(c);
+    return b;
+}
+
+// --------------------------------------------------------------- PCG init
+
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_pcg_init(DevProblem P, int zc, const float* __restrict__ h,
+                                                     const float* __restrict__ w,
+                                                     const float* __restrict__ g,
+                                                     const float* __restrict__ y, SolveBufs B,
+                                                     double tol2, WsHeader* hdr, double* resid,
+                                                     Reduce red)
+{
+    constexpr int T = K * (K + 1) / 2;
+    const long long N = P.N;
+    const long long sxy = (long long)P.nx * P.ny;
+    const int x = blockIdx.x * kTileX + threadIdx.x;
+    const int yy = blockIdx.y * kTileY + threadIdx.y;
+    const int z0 = blockIdx.z * zc;
+    const int z1 = min(P.nz, z0 + zc);
+    double rz = 0.0, rr = 0.0;
+    bool pd = true;
+    if (x < P.nx && yy < P.ny) {
+        for (int z = z0; z < z1; ++z) {
+            const long long n = x + (long long)P.nx * yy + sxy * z;
+            const float wn = __ldg(w + n);
+            Edges e;
+            make_edges(P, x, yy, z, n, w, wn, e);
+            float d = 0.0f;
+#pragma unroll
+            for (int j = 0; j < 6; ++j) d += e.c[j];
+            float r[K], M[K][K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const float* yk = y + k * N;
+                const float v = __ldg(yk + n);
+                float s = 0.0f;
+#pragma unroll
+                for (int j = 0; j < 6; ++j)
+                    if (e.ok[j]) s += e.c[j] * (v - __ldg(yk + n + e.off[j]));
+                r[k] = __ldg(g + k * N + n) + P.lambda[k] * s;
+            }
+#pragma unroll
+            for (int a = 0; a < K; ++a)
+#pragma unroll
+                for (int b = a; b < K; ++b) M[a][b] = M[b][a] = __ldg(h + tri(K, a, b) * N + n);
+#pragma unroll
+            for (int a = 0; a < K; ++a) M[a][a] += P.lambda[a] * d;
+            float L[T], zz[K];
+            pd &= cholesky_f32<K>(M, L);
+            chol_apply<K>(L, r, zz);
+#pragma unroll
+            for (int k = 0; k < T; ++k) B.R[k * N + n] = L[k];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                B.r[k * N + n] = r[k];
+                B.z[k * N + n] = zz[k];
+                rz += (double)r[k] * (double)zz[k];
+                rr += (double)r[k] * (double)r[k];
+            }
+        }
+    }
+    if (!pd) atomicOr(&hdr->status, kStatusNotPD);
+    double v[2] = {rz, rr}, out[2];
+    if (grid_reduce<2>(v, red, out) && threadIdx.x == 0 && threadIdx.y == 0) {
+        SolveScalars& sc = hdr->sc;
+        sc.rz = out[0];
+        sc.rr0 = out[1];
+        sc.rr = out[1];
+        sc.alpha = 0.0;
+        sc.beta = 0.0;
+        sc.it = 0;
+        sc.xcount = 0;
+        sc.tol2 = tol2;
+        const bool bad = !(out[0] == out[0]) || !(out[1] == out[1]);
+        if (bad) atomicOr(&hdr->status, kStatusNaN);
+        sc.done = (bad || !(out[0] > 0.0) || (tol2 > 0.0 && out[1] <= tol2 * out[1])) ? 1 : 0;
+        if (resid) resid[0] = sqrt(out[1]);
+    }
+}
+
+// ------------------------------------------------------------- PCG matvec
+
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_pcg_matvec(DevProblem P, int zc, int k_it,
+                                                       const float* __restrict__ h,
+                                                       const float* __restrict__ w, SolveBufs B,
+                                                       float* __restrict__ xacc, WsHeader* hdr,
+                                                       Reduce red)
+{
+    __shared__ float s_beta, s_alpha;
+    __shared__ int s_done;
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    if (tid == 0) {
+        s_done = hdr->sc.done;
+        s_beta = (float)hdr->sc.beta;
+        s_alpha = (float)hdr->sc.alpha;
+    }
+    __syncthreads();
+    if (s_done) return;
+    const float beta = s_beta, alpha_prev = s_alpha;
+    const long long N = P.N;
+    const long long sxy = (long long)P.nx * P.ny;
+    const int x = blockIdx.x * kTileX + threadIdx.x;
+    const int yy = blockIdx.y * kTileY + threadIdx.y;
+    const int z0 = blockIdx.z * zc;
+    const int z1 = min(P.nz, z0 + zc);
+    const float* __restrict__ zv = B.z;
+    const float* __restrict__ pold = B.p[(k_it + 1) & 1];
+    float* __restrict__ pnew = B.p[k_it & 1];
+    double pq = 0.0;
+    if (x < P.nx && yy < P.ny) {
+        for (int z = z0; z < z1; ++z) {
+            const long long n = x + (long long)P.nx * yy + sxy * z;
+            const float wn = __ldg(w + n);
+            Edges e;
+            make_edges(P, x, yy, z, n, w, wn, e);
+            float p[K], q[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const long long o = k * N + n;
+                float pk = __ldg(zv + o);
+                if (k_it > 0) {
+                    const float po = __ldg(pold + o);
+                    pk += beta * po;
+                    // fold the previous iteration's step into x
+                    xacc[o] = (k_it == 1 ? 0.0f : xacc[o]) + alpha_prev * po;
+                }
+                p[k] = pk;
+                float s = 0.0f;
+#pragma unroll
+                for (int j = 0; j < 6; ++j)
+                    if (e.ok[j]) {
+                        float pm = __ldg(zv + o + e.off[j]);
+                        if (k_it > 0) pm += beta * __ldg(pold + o + e.off[j]);
+                        s += e.c[j] * (pk - pm);
+                    }
+                q[k] = P.lambda[k] * s;
+            }
+            float Hn[K * (K + 1) / 2];
+#pragma unroll
+            for (int t = 0; t < K * (K + 1) / 2; ++t) Hn[t] = __ldg(h + t * N + n);
+#pragma unroll
+            for (int a = 0; a < K; ++a) {
+                float acc = q[a];
+#pragma unroll
+                for (int b = 0; b < K; ++b) acc += Hn[a < b ? tri(K, a, b) : tri(K, b, a)] * p[b];
+                q[a] = acc;
+            }
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                pnew[k * N + n] = p[k];
+                B.q[k * N + n] = q[k];
+                pq += (double)p[k] * (double)q[k];
+            }
+        }
+    }
+    double v[1] = {pq}, out[1];
+    if (grid_reduce<1>(v, red, out) && tid == 0) {
+        SolveScalars& sc = hdr->sc;
+        if (k_it > 0) sc.xcount = k_it;
+        if (!(out[0] == out[0])) atomicOr(&hdr->status, kStatusNaN);
+        if (!(out[0] > 0.0)) {
+            sc.done = 1;                 // no further step; alpha keeps the previous value
+        } else {
+            sc.alpha = sc.rz / out[0];
+        }
+    }
+}
+
+// ------------------------------------------------------------- PCG update
+
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_pcg_update(DevProblem P, int zc, int k_it, SolveBufs B,
+                                                       WsHeader* hdr, double* resid, Reduce red)
+{
+    constexpr int T = K * (K + 1) / 2;
+    __shared__ float s_alpha;
+    __shared__ int s_done;
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    if (tid == 0) {
+        s_done = hdr->sc.done;
+        s_alpha = (float)hdr->sc.alpha;
+    }
+    __syncthreads();
+    if (s_done) return;
+    const float alpha = s_alpha;
+    const long long N = P.N;
+    const long long sxy = (long long)P.nx * P.ny;
+    const int x = blockIdx.x * kTileX + threadIdx.x;
+    const int yy = blockIdx.y * kTileY + threadIdx.y;
+    const int z0 = blockIdx.z * zc;
+    const int z1 = min(P.nz, z0 + zc);
+    double rz = 0.0, rr = 0.0;
+    if (x < P.nx && yy < P.ny) {
+        for (int z = z0; z < z1; ++z) {
+            const long long n = x + (long long)P.nx * yy + sxy * z;
+            float r[K], L[T], zz[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) r[k] = B.r[k * N + n] - alpha * __ldg(B.q + k * N + n);
+#pragma unroll
+            for (int k = 0; k < T; ++k) L[k] = __ldg(B.R + k * N + n);
+            chol_apply<K>(L, r, zz);
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                B.r[k * N + n] = r[k];
+                B.z[k * N + n] = zz[k];
+                rz += (double)r[k] * (double)zz[k];
+                rr += (double)r[k] * (double)r[k];
+            }
+        }
+    }
+    double v[2] = {rz, rr}, out[2];
+    if (grid_reduce<2>(v, red, out) && tid == 0) {
+        SolveScalars& sc = hdr->sc;
+        const bool bad = !(out[0] == out[0]) || !(out[1] == out[1]);
+        if (bad) atomicOr(&hdr->status, kStatusNaN);
+        sc.beta = out[0] / sc.rz;
+        sc.rz = out[0];
+        sc.rr = out[1];
+        sc.it = k_it + 1;
+        if (resid) resid[k_it + 1] = sqrt(out[1]);
+        if (bad || !(out[0] > 0.0) || (sc.tol2 > 0.0 && out[1] <= sc.tol2 * sc.rr0)) sc.done = 1;
+    }
+}
+
+// -------------------------------------------------------------- PCG final
+
+__global__ void __launch_bounds__(kBlock) k_pcg_final(long long total, SolveBufs B,
+                                                      const float* __restrict__ xacc,
+                                                      float* __restrict__ delta,
+                                                      float* __restrict__ y_update,
+                                                      const WsHeader* hdr, double* report_rel,
+                                                      int* report_it)
+{
+    const SolveScalars sc = hdr->sc;
+    const bool have_x = sc.xcount > 0;
+    const bool pend = sc.xcount < sc.it;
+    const float alpha = (float)sc.alpha;
+    const float* __restrict__ pp = B.p[(sc.it - 1) & 1];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        float v = have_x ? xacc[i] : 0.0f;
+        if (pend) v += alpha * pp[i];
+        if (y_update)
+            y_update[i] -= v;
+        else
+            delta[i] = v;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (report_rel) *report_rel = sc.rr0 > 0.0 ? sqrt(sc.rr / sc.rr0) : 0.0;
+        if (report_it) *report_it = sc.it;
+    }
+}
+
+// ------------------------------------------------------------- launchers
+
+StencilGrid stencil_grid(const DevProblem& P)
+{
+    StencilGrid sg;
+    sg.block = dim3(kTileX, kTileY, 1);
+    const int gx = (P.nx + kTileX - 1) / kTileX;
+    const int gy = (P.ny + kTileY - 1) / kTileY;
+    const long long tiles = (long long)gx * gy;
+    // about two waves of 8 resident blocks per SM, at most kMaxBlocks blocks
+    const long long target = 2LL * 8 * kNumSm;
+    long long gz = target / (tiles > 0 ? tiles : 1);
+    if (gz < 1) gz = 1;
+    if (gz > P.nz) gz = P.nz;
+    while (tiles * gz > kMaxBlocks && gz > 1) --gz;
+    sg.zc = (int)((P.nz + gz - 1) / gz);
+    gz = (P.nz + sg.zc - 1) / sg.zc;
+    sg.grid = dim3(gx, gy, (unsigned)gz);
+    return sg;
+}
+
+cudaError_t launch_jtv(const DevProblem& P, const float* y, float* w, double* jtv, Reduce red,
+                       cudaStream_t st)
+{
+    const StencilGrid sg = stencil_grid(P);
+    count_launch();
+    if (P.K == 4)
+        k_jtv<4><<<sg.grid, sg.block, 0, st>>>(P, sg.zc, y, w, jtv, red);
+    else
+        k_jtv<3><<<sg.grid, sg.block, 0, st>>>(P, sg.zc, y, w, jtv, red);
+    return cudaGetLastError();
+}
+
+template <int K>
+static cudaError_t solve_k(const DevProblem& P, int cg_iters, double tol_cg, const float* h,
+                           const float* w, const float* g, const float* y, float* delta,
+                           float* y_update, double* resid, double* report_rel, int* report_it,
+                           void* solve_ws, WsHeader* hdr, Reduce red, cudaStream_t st)
+{
+    const StencilGrid sg = stencil_grid(P);
+    SolveBufs B = carve(P, solve_ws);
+    // x accumulates in `delta` (the caller's output when solving alone, a
+    // workspace buffer inside the fit, which then passes y_update).
+    float* xacc = delta;
+    const double tol2 = tol_cg > 0.0 ? tol_cg * tol_cg : 0.0;
+    count_launch();
+    k_pcg_init<K><<<sg.grid, sg.block, 0, st>>>(P, sg.zc, h, w, g, y, B, tol2, hdr, resid, red);
+    for (int k = 0; k < cg_iters; ++k) {
+        count_launch();
+        k_pcg_matvec<K><<<sg.grid, sg.block, 0, st>>>(P, sg.zc, k, h, w, B, xacc, hdr, red);
+        count_launch();
+        k_pcg_update<K><<<sg.grid, sg.block, 0, st>>>(P, sg.zc, k, B, hdr, resid, red);
+    }
+    count_launch();
+    k_pcg_final<<<voxel_grid(P.N * K), kBlock, 0, st>>>(P.N * K, B, xacc, delta, y_update, hdr,
+                                                        report_rel, report_it);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solve(const DevProblem& P, int cg_iters, double tol_cg, const float* h,
+                         const float* w, const float* g, const float* y, float* delta,
+                         float* y_update, double* resid, double* report_rel, int* report_it,
+                         void* solve_ws, WsHeader* hdr, Reduce red, cudaStream_t st)
+{
+    if (P.K == 4)
+        return solve_k<4>(P, cg_iters, tol_cg, h, w, g, y, delta, y_update, resid, report_rel,
+                          report_it, solve_ws, hdr, red, st);
+    return solve_k<3>(P, cg_iters, tol_cg, h, w, g, y, delta, y_update, resid, report_rel,
+                      report_it, solve_ws, hdr, red, st);
+}
+
+}  // namespace mpm

@@ -1,0 +1,405 @@
+// voxel_kernels.cu -- per-voxel kernels of the MPM library (sm_103a):
+//   k_forward       noise-free images (Eq. 26 with the B1 footnote)
+//   k_grad_hess     the fused voxel pass: signal, residual, gradient and the
+//                   approximate Hessian of Eq. 24, NLL reduced in float64
+//   k_uncertainty   diagonal of the inverse preconditioner blocks (Eq. 43) in
+//                   float64, log-determinant, log-normal moments (Eqs. 44-47)
+//   k_image_means / k_means_final / k_fill_maps   constant initial maps
+//
+// One thread per voxel (grid-stride); images are read as planes [I][N], so
+// each warp loads 128 contiguous bytes per echo.
+#include "mpm_internal.cuh"
+
+namespace mpm {
+
+// Per-contrast factors shared by every echo of contrast c in one voxel.  With
+// q_k = (ds/dy_k) / s  (Eqs. 27-30):
+//   q_A = 1, q_R1 = q1, q_R2* = -TE r2 (echo dependent), q_delta = qd,
+// and the diagonal second derivatives (Eqs. 31-34) are
+//   d2s/dA2 = s, d2s/dR1^2 = h1 q1 s, d2s/dR2*^2 = (1 + q2) q2 s, d2s/ddelta^2 = hd qd s.
+// `cross` is the extra term of d2s/dR1 ddelta = (q1 qd + cross) s.
+// Cancellation-free forms in float32: 1 - E = -expm1(-r1 TR),
+// 1 - cos(a) = sin(a)^2 / (1 + cos(a)), 1 - (1-delta) cos(a) = (1 - cos a) + delta cos a,
+// D = 1 - (1-delta) cos(a) E = (1 - E) + E (1 - (1-delta) cos a).
+struct ContrastTerms {
+    float s0, q1, qd, h1, hd, cross;
+};
+
+__device__ __forceinline__ ContrastTerms contrast_terms(const DevProblem& P, int c, float a,
+                                                        float r1, float dl, float m,
+                                                        float bp, float bm)
+{
+    ContrastTerms t;
+    float sa, ca;
+    sincosf(P.alpha[c] * bp, &sa, &ca);
+    const float omc = sa * sa / (1.0f + ca);
+    const float tt = P.tr[c] * r1;
+    const float E = expf(-tt);
+    const float omE = -expm1f(-tt);
+    const bool mt = P.mt[c] != 0;
+    const float d = mt ? dl : 0.0f;
+    const float mm = mt ? m : 1.0f;
+    const float omcm = omc + d * ca;                 // 1 - m cos(a)
+    const float D = omE + E * omcm;                  // 1 - m cos(a) E
+    const float iD = 1.0f / D;
+    t.s0 = bm * a * sa * mm * omE * iD;
+    t.q1 = tt * E * omcm * iD / omE;
+    t.qd = mt ? -d * iD : 0.0f;
+    t.h1 = 1.0f - tt * (2.0f - D) * iD;              // 1 + m cos(a) E = 2 - D
+    t.hd = 2.0f * mm * (omE + E * omc) * iD - 1.0f;  // 1 - cos(a) E = (1-E) + E (1 - cos a)
+    t.cross = mt ? tt * E * ca * d * mm * iD * iD : 0.0f;
+    return t;
+}
+
+__device__ __forceinline__ void map_params(const float* __restrict__ y, long long N,
+                                           long long n, int K, float& a, float& r1,
+                                           float& r2, float& dl, float& m)
+{
+    a = expf(__ldg(y + n));
+    r1 = expf(__ldg(y + N + n));
+    r2 = expf(__ldg(y + 2 * N + n));
+    dl = 0.0f;
+    m = 1.0f;
+    if (K == 4) {
+        const float yd = __ldg(y + 3 * N + n);
+        dl = 1.0f / (1.0f + expf(-yd));
+        m = 1.0f / (1.0f + expf(yd));
+    }
+}
+
+// ------------------------------------------------------------ forward model
+
+__global__ void __launch_bounds__(kBlock) k_forward(DevProblem P, const float* __restrict__ y,
+                                                    const float* __restrict__ b1p,
+                                                    const float* __restrict__ b1m,
+                                                    float* __restrict__ s)
+{
+    const long long N = P.N;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        float a, r1, r2, dl, m;
+        map_params(y, N, n, P.K, a, r1, r2, dl, m);
+        const float bp = b1p ? __ldg(b1p + n) : 1.0f;
+        for (int c = 0; c < P.C; ++c) {
+            const float bm = b1m ? __ldg(b1m + c * N + n) : 1.0f;
+            const ContrastTerms t = contrast_terms(P, c, a, r1, dl, m, bp, bm);
+            const int i0 = P.echo0[c];
+            for (int e = 0; e < P.n_echoes[c]; ++e)
+                s[(i0 + e) * N + n] = t.s0 * expf(-P.te[i0 + e] * r2);
+        }
+    }
+}
+
+// ------------------------------------------------------ fused voxel pass
+
+// Per contrast the echo sums
+//   S0 = sum s^2, S1 = sum s^2 q2, S2 = sum s^2 q2^2,
+//   R0 = sum r s, R1 = sum r s q2, N2 = sum r^2,
+//   A0 = sum |r s|, A2 = sum |r s| |(1 + q2) q2|, B1 = sum |r s| |q2|
+// give, with v = (1, q1, 0, qd) and e2 the log R2* axis,
+//   g += (R0 v + R1 e2) / sigma^2
+//   P += (S0 v v' + S1 (v e2' + e2 v') + S2 e2 e2' + loading) / sigma^2
+// which is Eq. 24 summed over the echoes of the contrast.
+template <int K, int PRE, typename XT>
+__global__ void __launch_bounds__(kBlock) k_grad_hess(DevProblem P, const XT* __restrict__ x,
+                                                      const float* __restrict__ y,
+                                                      const float* __restrict__ b1p,
+                                                      const float* __restrict__ b1m,
+                                                      float* __restrict__ g,
+                                                      float* __restrict__ h, double* nll,
+                                                      Reduce red)
+{
+    constexpr int T = K * (K + 1) / 2;
+    const long long N = P.N;
+    double nll_acc = 0.0;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        float a, r1, r2, dl, m;
+        map_params(y, N, n, K, a, r1, r2, dl, m);
+        const float bp = b1p ? __ldg(b1p + n) : 1.0f;
+        float G[K], H[T];
+#pragma unroll
+        for (int k = 0; k < K; ++k) G[k] = 0.0f;
+#pragma unroll
+        for (int k = 0; k < T; ++k) H[k] = 0.0f;
+        float nll_v = 0.0f;
+        for (int c = 0; c < P.C; ++c) {
+            const float bm = b1m ? __ldg(b1m + c * N + n) : 1.0f;
+            const ContrastTerms t = contrast_terms(P, c, a, r1, dl, m, bp, bm);
+            float S0 = 0.f, S1 = 0.f, S2 = 0.f, R0 = 0.f, R1 = 0.f, N2 = 0.f;
+            float A0 = 0.f, A2 = 0.f, B1 = 0.f;
+            const int i0 = P.echo0[c];
+            for (int e = 0; e < P.n_echoes[c]; ++e) {
+                const float q2 = -P.te[i0 + e] * r2;
+                const float s = t.s0 * expf(q2);
+                const float r = s - load_echo<XT>(x, (i0 + e) * N + n);
+                const float ss = s * s;
+                S0 += ss;
+                S1 += ss * q2;
+                S2 += ss * q2 * q2;
+                const float rs = r * s;
+                R0 += rs;
+                R1 += rs * q2;
+                N2 += r * r;
+                if (PRE != 2) {
+                    const float ars = fabsf(rs);
+                    A0 += ars;
+                    A2 += ars * fabsf((1.0f + q2) * q2);
+                    if (PRE == 1) B1 += ars * fabsf(q2);
+                }
+            }
+            const float is2 = P.isig2[c];
+            const float q1 = t.q1, qd = t.qd;
+            G[0] += is2 * R0;
+            G[1] += is2 * R0 * q1;
+            G[2] += is2 * R1;
+            H[tri(K, 0, 0)] += is2 * S0;
+            H[tri(K, 0, 1)] += is2 * S0 * q1;
+            H[tri(K, 0, 2)] += is2 * S1;
+            H[tri(K, 1, 1)] += is2 * S0 * q1 * q1;
+            H[tri(K, 1, 2)] += is2 * S1 * q1;
+            H[tri(K, 2, 2)] += is2 * S2;
+            if (K == 4) {
+                G[K - 1] += is2 * R0 * qd;
+                H[tri(K, 0, K - 1)] += is2 * S0 * qd;
+                H[tri(K, 1, K - 1)] += is2 * S0 * q1 * qd;
+                H[tri(K, 2, K - 1)] += is2 * S1 * qd;
+                H[tri(K, K - 1, K - 1)] += is2 * S0 * qd * qd;
+            }
+            if (PRE == 0) {
+                H[tri(K, 0, 0)] += is2 * A0;
+                H[tri(K, 1, 1)] += is2 * A0 * fabsf(t.h1 * q1);
+                H[tri(K, 2, 2)] += is2 * A2;
+                if (K == 4) H[tri(K, K - 1, K - 1)] += is2 * A0 * fabsf(t.hd * qd);
+            } else if (PRE == 1) {
+                const float aq1 = fabsf(q1), aqd = fabsf(qd);
+                const float c13 = fabsf(q1 * qd + t.cross);
+                H[tri(K, 0, 0)] += is2 * (A0 * (1.0f + aq1 + aqd) + B1);
+                H[tri(K, 1, 1)] += is2 * (A0 * (fabsf(t.h1 * q1) + aq1 + c13) + aq1 * B1);
+                H[tri(K, 2, 2)] += is2 * (A2 + B1 * (1.0f + aq1 + aqd));
+                if (K == 4)
+                    H[tri(K, K - 1, K - 1)] +=
+                        is2 * (A0 * (fabsf(t.hd * qd) + aqd + c13) + aqd * B1);
+            }
+            nll_v += 0.5f * is2 * N2;
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) g[k * N + n] = G[k];
+#pragma unroll
+        for (int k = 0; k < T; ++k) h[k * N + n] = H[k];
+        nll_acc += (double)nll_v;
+    }
+    double v[1] = {nll_acc}, out[1];
+    if (grid_reduce<1>(v, red, out) && threadIdx.x == 0) *nll = out[0];
+}
+
+// --------------------------------------------------------- uncertainty
+
+// Block n of the preconditioner, M = H_n + diag(lambda_k d_n) with
+// d_n = sum_{m in N(n)} (w_n + w_m) / h^2, inverted in float64 through its
+// Cholesky factor: var_k = sum_j (L^-1)_{jk}^2, logdet = -2 sum log L_kk.
+__global__ void __launch_bounds__(kBlock) k_uncertainty(DevProblem P, const float* __restrict__ h,
+                                                        const float* __restrict__ w,
+                                                        const float* __restrict__ y,
+                                                        float* __restrict__ var,
+                                                        float* __restrict__ logdet,
+                                                        float* __restrict__ moments,
+                                                        unsigned* status)
+{
+    const long long N = P.N;
+    const int K = P.K;
+    const long long sxy = (long long)P.nx * P.ny;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(n % P.nx);
+        const int yy = (int)((n / P.nx) % P.ny);
+        const int z = (int)(n / sxy);
+        const double wn = w[n];
+        double d = 0.0;
+        if (x > 0) d += (wn + w[n - 1]) * P.ihx2;
+        if (x < P.nx - 1) d += (wn + w[n + 1]) * P.ihx2;
+        if (yy > 0) d += (wn + w[n - P.nx]) * P.ihy2;
+        if (yy < P.ny - 1) d += (wn + w[n + P.nx]) * P.ihy2;
+        if (z > 0) d += (wn + w[n - sxy]) * P.ihz2;
+        if (z < P.nz - 1) d += (wn + w[n + sxy]) * P.ihz2;
+        double M[4][4], L[4][4];
+        for (int a = 0; a < K; ++a)
+            for (int b = a; b < K; ++b) M[a][b] = M[b][a] = h[tri(K, a, b) * N + n];
+        for (int a = 0; a < K; ++a) M[a][a] += (double)P.lambda[a] * d;
+        bool ok = true;
+        for (int j = 0; j < K; ++j) {
+            double s = M[j][j];
+            for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
+            if (!(s > 0.0)) { ok = false; s = 1e-300; }
+            L[j][j] = sqrt(s);
+            for (int i = j + 1; i < K; ++i) {
+                double v = M[i][j];
+                for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
+                L[i][j] = v / L[j][j];
+            }
+        }
+        if (!ok && status) atomicOr(status, kStatusNotPD);
+        // inverse of the lower factor, column by column
+        double Li[4][4];
+        for (int j = 0; j < K; ++j) {
+            for (int i = 0; i < K; ++i) Li[i][j] = 0.0;
+            Li[j][j] = 1.0 / L[j][j];
+            for (int i = j + 1; i < K; ++i) {
+                double v = 0.0;
+                for (int k = j; k < i; ++k) v -= L[i][k] * Li[k][j];
+                Li[i][j] = v / L[i][i];
+            }
+        }
+        double ld = 0.0;
+        for (int k = 0; k < K; ++k) {
+            double v = 0.0;
+            for (int j = k; j < K; ++j) v += Li[j][k] * Li[j][k];
+            var[k * N + n] = (float)v;
+            ld += log(L[k][k]);
+        }
+        if (logdet) logdet[n] = (float)(-2.0 * ld);
+        if (moments && y) {
+            double s2 = 0.0;
+            for (int j = 1; j < K; ++j) s2 += Li[j][1] * Li[j][1];
+            const double lr1 = y[N + n];
+            const double es2 = exp(s2);
+            moments[n] = (float)(sqrt(es2) * exp(lr1));
+            moments[N + n] = (float)((es2 - 1.0) * es2 * exp(2.0 * lr1));
+            moments[2 * N + n] = (float)(sqrt(es2) * exp(-lr1));
+            moments[3 * N + n] = (float)((es2 - 1.0) * es2 * exp(-2.0 * lr1));
+        }
+    }
+}
+
+// -------------------------------------------------- constant initial maps
+
+constexpr int kMeanBlocks = 304;
+
+template <typename XT>
+__global__ void __launch_bounds__(kBlock) k_image_means(DevProblem P, const XT* __restrict__ x,
+                                                        double* partials)
+{
+    __shared__ double sh[kBlock / 32];
+    const long long N = P.N;
+    const int i = blockIdx.y;
+    double acc = 0.0;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x)
+        acc += (double)load_echo<XT>(x, i * N + n);
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) partials[i * gridDim.x + blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(kBlock) k_means_final(DevProblem P, const double* partials,
+                                                        int nparts, double* means)
+{
+    __shared__ double sh[kBlock / 32];
+    const int i = blockIdx.x;
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nparts; b += blockDim.x) acc += partials[i * nparts + b];
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) means[i] = acc / (double)P.N;
+}
+
+struct MapValues {
+    float v[4];
+};
+
+__global__ void __launch_bounds__(kBlock) k_fill_maps(DevProblem P, MapValues mv,
+                                                      float* __restrict__ y)
+{
+    const long long total = P.N * P.K;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x)
+        y[i] = mv.v[i / P.N];
+}
+
+// ------------------------------------------------------------- launchers
+
+cudaError_t launch_forward(const DevProblem& P, const float* y, const float* b1p,
+                           const float* b1m, float* s, cudaStream_t st)
+{
+    count_launch();
+    k_forward<<<voxel_grid(P.N), kBlock, 0, st>>>(P, y, b1p, b1m, s);
+    return cudaGetLastError();
+}
+
+template <int K, int PRE>
+static void grad_hess_dtype(const DevProblem& P, int echo_dtype, const void* x,
+                            const float* y, const float* b1p, const float* b1m, float* g,
+                            float* h, double* nll, Reduce red, cudaStream_t st)
+{
+    const int grid = voxel_grid(P.N);
+    if (echo_dtype == 1)
+        k_grad_hess<K, PRE, __nv_bfloat16><<<grid, kBlock, 0, st>>>(
+            P, static_cast<const __nv_bfloat16*>(x), y, b1p, b1m, g, h, nll, red);
+    else
+        k_grad_hess<K, PRE, float><<<grid, kBlock, 0, st>>>(
+            P, static_cast<const float*>(x), y, b1p, b1m, g, h, nll, red);
+}
+
+template <int K>
+static void grad_hess_pre(const DevProblem& P, int echo_dtype, const void* x, const float* y,
+                          const float* b1p, const float* b1m, float* g, float* h,
+                          double* nll, Reduce red, cudaStream_t st)
+{
+    switch (P.precond) {
+    case 0: grad_hess_dtype<K, 0>(P, echo_dtype, x, y, b1p, b1m, g, h, nll, red, st); break;
+    case 1: grad_hess_dtype<K, 1>(P, echo_dtype, x, y, b1p, b1m, g, h, nll, red, st); break;
+    default: grad_hess_dtype<K, 2>(P, echo_dtype, x, y, b1p, b1m, g, h, nll, red, st); break;
+    }
+}
+
+cudaError_t launch_grad_hess(const DevProblem& P, int echo_dtype, const void* x,
+                             const float* y, const float* b1p, const float* b1m, float* g,
+                             float* h, double* nll, Reduce red, cudaStream_t st)
+{
+    count_launch();
+    if (P.K == 4)
+        grad_hess_pre<4>(P, echo_dtype, x, y, b1p, b1m, g, h, nll, red, st);
+    else
+        grad_hess_pre<3>(P, echo_dtype, x, y, b1p, b1m, g, h, nll, red, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_uncertainty(const DevProblem& P, const float* h, const float* w,
+                               const float* y, float* var, float* logdet, float* moments,
+                               unsigned* status, cudaStream_t st)
+{
+    count_launch();
+    k_uncertainty<<<voxel_grid(P.N), kBlock, 0, st>>>(P, h, w, y, var, logdet, moments,
+                                                       status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_image_means(const DevProblem& P, int echo_dtype, const void* x,
+                               double* partials, double* means, cudaStream_t st)
+{
+    long long want = (P.N + kBlock - 1) / kBlock;
+    const int nb = (int)(want < kMeanBlocks ? want : kMeanBlocks);
+    dim3 grid(nb, P.I);
+    count_launch();
+    if (echo_dtype == 1)
+        k_image_means<__nv_bfloat16><<<grid, kBlock, 0, st>>>(
+            P, static_cast<const __nv_bfloat16*>(x), partials);
+    else
+        k_image_means<float><<<grid, kBlock, 0, st>>>(P, static_cast<const float*>(x),
+                                                      partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    count_launch();
+    k_means_final<<<P.I, kBlock, 0, st>>>(P, partials, nb, means);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_maps(const DevProblem& P, const float* values, float* y,
+                             cudaStream_t st)
+{
+    MapValues mv;
+    for (int k = 0; k < 4; ++k) mv.v[k] = k < P.K ? values[k] : 0.0f;
+    count_launch();
+    k_fill_maps<<<voxel_grid(P.N * P.K), kBlock, 0, st>>>(P, mv, y);
+    return cudaGetLastError();
+}
+
+}  // namespace mpm

@@ -1,0 +1,80 @@
+"""Seeded test inputs shared by the GPU parity tests.
+
+Every input comes from the seeded phantom generator and the FP64 oracle
+(noise-free images), rounded once to float32 (or bfloat16) so that the CUDA
+library and the oracle see exactly the same numbers.  Nothing here is computed
+by the CUDA path.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle as orc
+from paper_2102_01604_gb300 import phantom
+
+
+def f32(a):
+    return None if a is None else np.asarray(a, dtype=np.float32)
+
+
+def round_protocol(prot: dict) -> dict:
+    """Protocol with every number rounded to float32 (the library computes in
+    float32), so both sides use identical constants."""
+    out = dict(prot)
+    for k in ("alpha", "tr", "te", "sigma2"):
+        out[k] = [float(np.float32(v)) for v in prot[k]]
+    return out
+
+
+def dataset(shape, seed=0, contrasts=("PDw", "T1w", "MTw"), n_echoes=(8, 8, 6), b1p=True,
+            b1m=True, snr=20.0, noise=True):
+    """Phantom maps, B1 fields and Rician images (float32) on ``shape``."""
+    prot = phantom.protocol(contrasts, n_echoes)
+    with_mt = any(prot["mt"])
+    ph = phantom.phantom(shape, seed=seed, n_contrasts=len(contrasts), with_b1m=b1m,
+                         with_mt=with_mt)
+    prot = round_protocol(prot)
+    bp = f32(ph["b1p"]) if b1p else None
+    bm = f32(ph["b1m"]) if b1m else None
+    p0 = orc.make_problem(prot, shape)
+    s = orc.forward(p0, ph["y"], bp, bm)
+    prot["sigma2"] = [float(np.float32(v)) for v in phantom.noise_sigma2(s, prot, snr)]
+    prot = round_protocol(prot)
+    x = phantom.rician(s, prot, seed=seed + 1) if noise else s
+    return {"prot": prot, "shape": tuple(shape), "y_true": ph["y"], "b1p": bp, "b1m": bm,
+            "x": f32(x), "s": s}
+
+
+def to_dev(a, device="cuda"):
+    import torch
+    if a is None:
+        return None
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device)
+
+
+def to_np(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def assert_close_scaled(got, ref, rtol, what=""):
+    """|got - ref| <= rtol (|ref| + rms of the row): element-wise relative
+    error with a floor at the row's typical magnitude, per row (map, image or
+    Hessian entry)."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    assert got.shape == ref.shape, (got.shape, ref.shape)
+    ref2 = ref.reshape(ref.shape[0], -1) if ref.ndim > 1 else ref[None]
+    got2 = got.reshape(ref2.shape)
+    for i in range(ref2.shape[0]):
+        floor = np.sqrt(np.mean(ref2[i] ** 2)) if ref2[i].size else 0.0
+        err = np.abs(got2[i] - ref2[i])
+        bound = rtol * (np.abs(ref2[i]) + floor)
+        bad = err > bound
+        assert not bad.any(), (f"{what} row {i}: {bad.sum()} of {bad.size} elements out of "
+                               f"tolerance; worst err {err.max():.3e} "
+                               f"at ref {ref2[i][np.argmax(err)]:.4e}, floor {floor:.3e}")
+
+
+def map_error(y_got, y_ref):
+    """Per-voxel error in log space relative to max(1, |y|)."""
+    return np.abs(y_got - y_ref) / np.maximum(1.0, np.abs(y_ref))

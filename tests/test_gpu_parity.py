@@ -1,0 +1,233 @@
+"""Parity of every C-ABI call against the FP64 oracle, element by element, on
+seeded inputs spanning several stencil tiles and ragged tails.
+
+Tolerances (derived in the design doc from float32 arithmetic):
+  forward, gradient, Hessian   1e-4 x (|ref| + rms of the row)
+  likelihood, JTV energy       2e-6 relative
+  JTV weights                  1e-5 relative
+  PCG update delta             2e-4 x (|ref| + rms of the map)
+  uncertainty (float64 math)   1e-5 relative
+  whole fit                    1e-3 x max(1, |y|) per voxel and map (log space),
+                               1e-5 relative on the objective at every update
+"""
+import numpy as np
+import pytest
+
+import oracle as orc
+from cases import assert_close_scaled, dataset, map_error, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(32, 32, 16), (37, 11, 5), (1, 9, 7), (65, 3, 2)]
+
+
+@pytest.fixture(scope="module")
+def mpm():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2102_01604_gb300 as m
+    m._lib.load()
+    return m
+
+
+def _problems(mpm, d, **kw):
+    return (mpm.make_problem(d["prot"], d["shape"], **kw),
+            orc.make_problem(d["prot"], d["shape"], **{k: v for k, v in kw.items()
+                                                       if k != "echo_dtype"}))
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_forward(mpm, shape):
+    d = dataset(shape, seed=1)
+    pg, po = _problems(mpm, d)
+    y32 = d["y_true"].astype(np.float32)
+    s = mpm.mpm_forward(pg, to_dev(y32), to_dev(d["b1p"]), to_dev(d["b1m"]))
+    ref = orc.forward(po, y32, d["b1p"], d["b1m"])
+    assert_close_scaled(to_np(s), ref, 1e-5, "forward")
+
+
+@pytest.mark.parametrize("precond", [0, 1, 2])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_grad_hess(mpm, shape, precond):
+    d = dataset(shape, seed=2)
+    pg, po = _problems(mpm, d, precond=precond)
+    rng = np.random.default_rng(3)
+    y = (d["y_true"] + 0.05 * rng.standard_normal(d["y_true"].shape)).astype(np.float32)
+    g, h, nll = mpm.mpm_grad_hess(pg, to_dev(d["x"]), to_dev(y), to_dev(d["b1p"]),
+                                  to_dev(d["b1m"]))
+    nll_o, g_o, h_o = orc.grad_hess(po, d["x"], y, d["b1p"], d["b1m"])
+    assert_close_scaled(to_np(g), g_o, 1e-4, "g")
+    assert_close_scaled(to_np(h), h_o, 1e-4, "h")
+    assert abs(nll.item() - nll_o) <= 2e-6 * abs(nll_o)
+
+
+def test_grad_hess_without_b1_and_mt(mpm):
+    d = dataset((20, 9, 4), seed=4, contrasts=("PDw", "T1w"), n_echoes=(6, 5), b1p=False,
+                b1m=False)
+    pg, po = _problems(mpm, d)
+    assert pg.n_maps == 3
+    y = d["y_true"].astype(np.float32)
+    g, h, nll = mpm.mpm_grad_hess(pg, to_dev(d["x"]), to_dev(y))
+    nll_o, g_o, h_o = orc.grad_hess(po, d["x"], y)
+    assert_close_scaled(to_np(g), g_o, 1e-4, "g")
+    assert_close_scaled(to_np(h), h_o, 1e-4, "h")
+    assert abs(nll.item() - nll_o) <= 2e-6 * abs(nll_o)
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("vx", [(1.0, 1.0, 1.0), (0.8, 1.1, 1.7)])
+def test_jtv_weights(mpm, shape, vx):
+    d = dataset(shape, seed=5)
+    pg, po = _problems(mpm, d, vx=vx, lam=(10.0, 7.0, 4.0, 2.0), eps=1e-3)
+    rng = np.random.default_rng(6)
+    y = (d["y_true"] + 0.02 * rng.standard_normal(d["y_true"].shape)).astype(np.float32)
+    w, jtv = mpm.mpm_jtv_weights(pg, to_dev(y))
+    e_o, w_o = orc.jtv(po, y)
+    np.testing.assert_allclose(to_np(w), w_o, rtol=1e-5)
+    assert abs(jtv.item() - e_o) <= 2e-6 * e_o
+
+
+def _system(d, po, seed):
+    """Newton-system inputs computed by the oracle, rounded to float32."""
+    rng = np.random.default_rng(seed)
+    y = (d["y_true"] + 0.05 * rng.standard_normal(d["y_true"].shape)).astype(np.float32)
+    _, g, h = orc.grad_hess(po, d["x"], y, d["b1p"], d["b1m"])
+    _, w = orc.jtv(po, y)
+    return h.astype(np.float32), w.astype(np.float32), g.astype(np.float32), y
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("cg_iters", [1, 2, 30])
+def test_solve(mpm, shape, cg_iters):
+    d = dataset(shape, seed=7)
+    pg, po = _problems(mpm, d)
+    h, w, g, y = _system(d, po, 8)
+    opts = mpm.make_opts(cg_iters=cg_iters)
+    delta, resid = mpm.mpm_solve(pg, opts, to_dev(h), to_dev(w), to_dev(g), to_dev(y))
+    d_o, it, r_o = orc.solve(po, h, w, g, y, cg_iters)
+    assert it == cg_iters
+    assert_close_scaled(to_np(delta), d_o, 2e-4, "delta")
+    r = to_np(resid)
+    np.testing.assert_allclose(r[:it + 1], r_o, rtol=2e-4 * max(1, cg_iters) ** 0.5 + 1e-5)
+
+
+def test_solve_tolerance_stop(mpm):
+    d = dataset((24, 16, 8), seed=9)
+    pg, po = _problems(mpm, d)
+    h, w, g, y = _system(d, po, 10)
+    opts = mpm.make_opts(cg_iters=200, tol_cg=1e-3)
+    delta, resid = mpm.mpm_solve(pg, opts, to_dev(h), to_dev(w), to_dev(g), to_dev(y))
+    d_o, it, r_o = orc.solve(po, h, w, g, y, 200, tol=1e-3)
+    r = to_np(resid)
+    ran = int(np.sum(np.isfinite(r))) - 1
+    assert ran == it, (ran, it)
+    assert_close_scaled(to_np(delta), d_o, 1e-3, "delta")
+
+
+@pytest.mark.parametrize("shape", SHAPES[:2])
+def test_uncertainty(mpm, shape):
+    d = dataset(shape, seed=11)
+    pg, po = _problems(mpm, d)
+    h, w, g, y = _system(d, po, 12)
+    var, logdet, mom = mpm.mpm_uncertainty(pg, to_dev(h), to_dev(w), to_dev(y),
+                                           want_moments=True)
+    v_o, ld_o, m_o, st = orc.uncertainty(po, h, w, y)
+    assert st == 0
+    np.testing.assert_allclose(to_np(var), v_o, rtol=1e-5)
+    np.testing.assert_allclose(to_np(logdet), ld_o, rtol=1e-5, atol=1e-5)
+    np.testing.assert_allclose(to_np(mom), m_o, rtol=1e-5)
+
+
+def _fit_both(mpm, d, gn_iters=10, cg_iters=30, npi=1, tol_gn=0.0, tol_cg=0.0, **kw):
+    import torch
+    pg, po = _problems(mpm, d, **kw)
+    K, N = pg.n_maps, int(np.prod(d["shape"]))
+    y = torch.zeros((K, N), dtype=torch.float32, device="cuda")
+    opts = mpm.make_opts(gn_iters=gn_iters, cg_iters=cg_iters, newton_per_irls=npi,
+                         tol_gn=tol_gn, tol_cg=tol_cg)
+    var = torch.empty((K, N), dtype=torch.float32, device="cuda")
+    st, rep = mpm.mpm_fit(pg, opts, to_dev(d["x"]), y, to_dev(d["b1p"]), to_dev(d["b1m"]),
+                          var=var)
+    ref = orc.fit(po, d["x"], None, d["b1p"], d["b1m"], gn_iters=gn_iters, cg_iters=cg_iters,
+                  newton_per_irls=npi, tol_gn=tol_gn, tol_cg=tol_cg)
+    return st, rep, to_np(y), to_np(var), ref, po
+
+
+def _check_fit(rep, y, ref):
+    assert rep.iters == ref["iters"]
+    F = np.array(rep.F[:rep.iters + 1])
+    np.testing.assert_allclose(F, ref["F"], rtol=1e-5)
+    err = map_error(y, ref["y"])
+    assert err.max() <= 1e-3, f"max map error {err.max():.3e} (map {np.unravel_index(err.argmax(), err.shape)})"
+    return err
+
+
+def test_fit_plain_32x32x16(mpm):
+    """The small configuration: 32x32x16, PDw/T1w/MTw 8/8/6 echoes, Rician
+    SNR 20, JTV lambda = 10, 10 updates x 30 PCG iterations."""
+    d = dataset((32, 32, 16), seed=0, b1m=False)
+    st, rep, y, var, ref, po = _fit_both(mpm, d)
+    err = _check_fit(rep, y, ref)
+    print(f"fit 32x32x16: max map error {err.max():.2e}, F {rep.F[rep.iters]:.6e}")
+    # uncertainty at the final maps
+    _, w_o = orc.jtv(po, ref["y"])
+    _, _, h_o = orc.grad_hess(po, d["x"], ref["y"], d["b1p"], d["b1m"])
+    v_o, _, _, _ = orc.uncertainty(po, h_o, w_o)
+    assert np.all(np.abs(var - v_o) <= 5e-3 * v_o), np.max(np.abs(var - v_o) / v_o)
+
+
+@pytest.mark.parametrize("case", ["no_mt", "ragged", "irls5", "aniso", "rowsum", "tol"])
+def test_fit_variants(mpm, case):
+    if case == "no_mt":
+        d = dataset((17, 13, 6), seed=21, contrasts=("PDw", "T1w"), n_echoes=(8, 8))
+        st, rep, y, var, ref, _ = _fit_both(mpm, d, gn_iters=6)
+    elif case == "ragged":
+        d = dataset((33, 9, 5), seed=22)
+        st, rep, y, var, ref, _ = _fit_both(mpm, d, gn_iters=6)
+    elif case == "irls5":
+        d = dataset((20, 20, 6), seed=23)
+        st, rep, y, var, ref, _ = _fit_both(mpm, d, gn_iters=10, npi=5)
+    elif case == "aniso":
+        d = dataset((20, 16, 6), seed=24)
+        st, rep, y, var, ref, _ = _fit_both(mpm, d, gn_iters=6, vx=(0.8, 0.8, 1.6))
+    elif case == "rowsum":
+        d = dataset((20, 16, 6), seed=25)
+        st, rep, y, var, ref, _ = _fit_both(mpm, d, gn_iters=6, precond=1)
+    else:
+        d = dataset((20, 16, 6), seed=26)
+        st, rep, y, var, ref, _ = _fit_both(mpm, d, gn_iters=60, tol_gn=1e-4, tol_cg=1e-3,
+                                            cg_iters=100)
+        assert rep.iters < 60
+    _check_fit(rep, y, ref)
+
+
+def test_initial_maps(mpm):
+    import torch
+    d = dataset((24, 12, 5), seed=31)
+    pg, po = _problems(mpm, d)
+    y = torch.zeros((pg.n_maps, 24 * 12 * 5), dtype=torch.float32, device="cuda")
+    mpm.mpm_fit(pg, mpm.make_opts(gn_iters=0), to_dev(d["x"]), y, to_dev(d["b1p"]),
+                to_dev(d["b1m"]))
+    y0 = orc.init(po, d["x"])
+    np.testing.assert_allclose(to_np(y), y0, rtol=1e-6, atol=1e-6)
+
+
+def test_bf16_echoes(mpm):
+    """Echoes stored as bfloat16: the oracle is given the same rounded values."""
+    import torch
+    d = dataset((32, 16, 8), seed=41)
+    xb = torch.from_numpy(d["x"]).to(torch.bfloat16)
+    d["x"] = xb.to(torch.float32).numpy()
+    pg, po = _problems(mpm, d, echo_dtype=1)
+    y = d["y_true"].astype(np.float32)
+    g, h, nll = mpm.mpm_grad_hess(pg, xb.cuda(), to_dev(y), to_dev(d["b1p"]), to_dev(d["b1m"]))
+    nll_o, g_o, h_o = orc.grad_hess(po, d["x"], y, d["b1p"], d["b1m"])
+    assert_close_scaled(to_np(g), g_o, 1e-4, "g")
+    assert_close_scaled(to_np(h), h_o, 1e-4, "h")
+    assert abs(nll.item() - nll_o) <= 2e-6 * abs(nll_o)
+    K, N = pg.n_maps, 32 * 16 * 8
+    yy = torch.zeros((K, N), dtype=torch.float32, device="cuda")
+    st, rep = mpm.mpm_fit(pg, mpm.make_opts(gn_iters=5), xb.cuda(), yy, to_dev(d["b1p"]),
+                          to_dev(d["b1m"]))
+    ref = orc.fit(po, d["x"], None, d["b1p"], d["b1m"], gn_iters=5, cg_iters=30)
+    _check_fit(rep, to_np(yy), ref)
