@@ -1,0 +1,467 @@
+#!/usr/bin/env python
+"""Throughput of the 1 mm MPM JTV-MAP fit on GB300, in Mvoxel.GN-iter/s.
+
+Workload: a 176 x 240 x 256 volume at 1 mm, PDw / T1w / MTw SPGR contrasts
+(6 / 21 / 6 degrees, TR 25 ms, 8 / 8 / 6 echoes 2.3 ms apart) of a seeded
+piecewise-smooth phantom with smooth B1+ / B1- fields and Rician noise at
+first-echo SNR 20, float32 throughout, JTV lambda = 10; one step is one whole
+mpm_fit call: constant initial maps, 20 Newton updates with 30 PCG iterations
+each, and the posterior variance at the final maps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank fits its own subject
+(independent replicas, weak scaling); the step time is the maximum over ranks.
+``--impl reference`` times the FP64 CPU oracle on the host cores on a bounded
+slab of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Mvoxel·GN-iter/s, 1mm MPM JTV fit"
+UNIT = "Mvoxel·GN-iter/s"
+SHAPE = (176, 240, 256)
+GN_ITERS = 20
+CG_ITERS = 30
+LAMBDA = 10.0
+EPS = 1e-3
+SNR = 20.0
+L2_BYTES = 129 * 2 ** 20
+CPU_SAMPLE_Z = 32        # cpu_baseline: a 176 x 240 x 32 slab, one update
+REF_SAMPLE_Z = 8         # reference arm: a 176 x 240 x 8 slab per step, one update
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args(argv)
+
+
+# ------------------------------------------------------------ distributed
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def aggregate(seconds: float, units: float, world: int, backend_device=None):
+    """Whole-job value over replicas: total units / max seconds over ranks."""
+    if world <= 1:
+        return units / seconds, seconds
+    import torch
+    import torch.distributed as dist
+    dev = backend_device if backend_device is not None else torch.device("cpu")
+    t = torch.tensor([seconds], dtype=torch.float64, device=dev)
+    u = torch.tensor([units], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return u.item() / t.item(), t.item()
+
+
+# --------------------------------------------------------------- inputs
+
+def workload_inputs(seed: int, device):
+    """Phantom maps and B1 fields on the host, noise-free images from the
+    library's own forward model on the GPU, Rician noise drawn on the GPU."""
+    import torch
+
+    import paper_2102_01604_gb300 as mpm
+    from paper_2102_01604_gb300 import phantom
+
+    prot = phantom.protocol()
+    ph = phantom.phantom(SHAPE, seed=seed)
+    y_true = torch.from_numpy(ph["y"].astype(np.float32)).to(device)
+    b1p = torch.from_numpy(ph["b1p"].astype(np.float32)).to(device)
+    b1m = torch.from_numpy(ph["b1m"].astype(np.float32)).to(device)
+    p0 = mpm.make_problem(prot, SHAPE)
+    s = mpm.mpm_forward(p0, y_true, b1p, b1m)
+    sig2, i = [], 0
+    for ne in prot["n_echoes"]:
+        m = s[i].double().mean().item() / SNR
+        sig2.append(m * m)
+        i += ne
+    prot["sigma2"] = sig2
+    x = phantom.rician_torch(s, prot, seed + 1)
+    del s
+    torch.cuda.synchronize()
+    return prot, ph, x, b1p, b1m
+
+
+# ------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [v.strip() for v in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ roofline
+
+def algorithmic_bytes(K: int, C: int, I: int, echo_bytes: int = 4):
+    """Bytes each kernel must move per voxel (reads + writes of its operands,
+    float32, every array touched once); PCG matvec bytes are per solve."""
+    T = K * (K + 1) // 2
+    f = 4
+    mv0 = K * f + T * f + f + 2 * K * f                 # k = 0: read z, H, w; write p, q
+    mv1 = mv0 + K * f + K * f                           # k = 1: + read p_old, write x
+    mvk = mv1 + K * f                                   # k >= 2: + read x
+    return {
+        "grad_hess": I * echo_bytes + K * f + f + C * f + K * f + T * f,
+        "jtv": K * f + f,
+        "pcg_init": f + 2 * K * f + T * f + T * f + 2 * K * f,
+        "pcg_matvec_per_solve": mv0 + (mv1 if CG_ITERS > 1 else 0) + mvk * max(CG_ITERS - 2, 0),
+        "pcg_update": 2 * K * f + T * f + 2 * K * f,
+        "pcg_final": 4 * K * f,
+        "uncertainty": T * f + f + K * f,
+    }
+
+
+def kernel_roofline(prof: dict, n_vox: int, steps: int, K: int, C: int, I: int, peak_gbs: float):
+    ab = algorithmic_bytes(K, C, I)
+    solves = steps * GN_ITERS
+    per_kernel = {}
+    for kind, v in prof.items():
+        if not v["launches"]:
+            continue
+        if kind == "pcg_matvec":
+            total_bytes = ab["pcg_matvec_per_solve"] * n_vox * solves
+        elif kind in ab:
+            total_bytes = ab[kind] * n_vox * v["launches"]
+        else:
+            total_bytes = None
+        entry = {"ms_total": round(v["ms"], 3), "launches": v["launches"],
+                 "us_per_launch": round(1000.0 * v["ms"] / v["launches"], 2)}
+        if total_bytes is not None and v["ms"] > 0:
+            gbs = total_bytes / (v["ms"] * 1e-3) / 1e9
+            entry["bytes_per_launch"] = int(total_bytes / v["launches"])
+            entry["achieved_gbs"] = round(gbs, 1)
+            entry["frac_of_measured_hbm"] = round(gbs / peak_gbs, 4)
+        per_kernel[kind] = entry
+    return per_kernel
+
+
+def measured_peak():
+    try:
+        with open(PEAKS_FILE) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("stencil_kernels.cu", "voxel_kernels.cu", "mpm_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2102_01604_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kind: str, n_vox: int):
+    """DRAM bytes per launch from the committed ncu capture, scaled to this
+    volume; None when the kernels changed since the capture."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            tr = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if tr.get("source_hash") != kernel_source_hash():
+        return None
+    k = tr.get("kernels", {}).get(kind)
+    if not k:
+        return None
+    return int(k["dram_bytes_per_voxel"] * n_vox)
+
+
+# ---------------------------------------------------------- CPU oracle
+
+def oracle_sample(z_planes: int, seed: int):
+    """The oracle's inputs for a 176 x 240 x z slab of the bench phantom."""
+    import oracle as orc
+    from paper_2102_01604_gb300 import phantom
+
+    shape = (SHAPE[0], SHAPE[1], z_planes)
+    ph = phantom.phantom(SHAPE, seed=seed)
+    n = shape[0] * shape[1] * shape[2]
+    y, b1p, b1m = ph["y"][:, :n], ph["b1p"][:n], ph["b1m"][:, :n]
+    prot = phantom.protocol()
+    s = orc.forward(orc.make_problem(prot, shape), y, b1p, b1m)
+    prot["sigma2"] = phantom.noise_sigma2(s, prot, SNR)
+    x = phantom.rician(s, prot, seed + 1).astype(np.float32)
+    return orc.make_problem(prot, shape, lam=LAMBDA, eps=EPS), shape, x, b1p, b1m
+
+
+def time_oracle(z_planes: int, seed: int, reps: int = 1):
+    import oracle as orc
+    p, shape, x, b1p, b1m = oracle_sample(z_planes, seed)
+    n = shape[0] * shape[1] * shape[2]
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        r = orc.fit(p, x, None, b1p, b1m, gn_iters=1, cg_iters=CG_ITERS)
+        times.append(time.perf_counter() - t0)
+        assert r["iters"] == 1
+    return n, times
+
+
+def cpu_baseline(seed: int):
+    n, times = time_oracle(CPU_SAMPLE_Z, seed)
+    t = times[0]
+    return {"value": round(n / t / 1e6, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"176x240x{CPU_SAMPLE_Z} slab of the same phantom, 1 update (30 PCG) "
+                      f"with objective at both ends, FP64 single-threaded C; {t:.2f} s; "
+                      f"host has {os.cpu_count()} cores"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        time_oracle(REF_SAMPLE_Z, args.seed)
+    total_t, total_units = 0.0, 0
+    for _ in range(args.steps):
+        n, times = time_oracle(REF_SAMPLE_Z, args.seed)
+        total_t += times[0]
+        total_units += n * 1
+    value = total_units / total_t / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1000 * total_t / args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"176x240x{REF_SAMPLE_Z} slab of the 1 mm MPM JTV-MAP "
+                               f"workload, 1 update x {CG_ITERS} PCG per step",
+                   "runs_on": "host CPU (FP64 oracle)"},
+        "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"176x240x{REF_SAMPLE_Z} slab, 1 update per step"},
+        "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+
+    import paper_2102_01604_gb300 as mpm
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    seed = args.seed + 1000 * rank
+
+    prot, ph, x, b1p, b1m = workload_inputs(seed, dev)
+    problem = mpm.make_problem(prot, SHAPE, lam=LAMBDA, eps=EPS)
+    opts = mpm.make_opts(gn_iters=GN_ITERS, cg_iters=CG_ITERS, newton_per_irls=1, init=True)
+    K, C = problem.n_maps, problem.n_contrasts
+    I = sum(prot["n_echoes"])
+    N = int(np.prod(SHAPE))
+    y = torch.empty((K, N), dtype=torch.float32, device=dev)
+    var = torch.empty((K, N), dtype=torch.float32, device=dev)
+    ws = mpm.workspace(problem, opts, device=dev)
+
+    def step():
+        st, rep = mpm.mpm_fit(problem, opts, x, y, b1p, b1m, var=var, ws=ws)
+        return rep
+
+    for _ in range(args.warmup):
+        rep = step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: device time of K whole fits
+    mpm.mpm_profile_enable(True)
+    mpm.mpm_profile_read()
+    launches0 = mpm.mpm_kernel_launches()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        rep = step()
+    e1.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    launches = mpm.mpm_kernel_launches() - launches0
+    prof = mpm.mpm_profile_read()
+    mpm.mpm_profile_enable(False)
+    seconds = e0.elapsed_time(e1) / 1000.0
+    units = float(N) * GN_ITERS * args.steps
+    value, t_max = aggregate(seconds, units, world, dev)
+    final_F = rep.F[rep.iters]
+
+    # ---- end to end: pinned host inputs in, maps and variances out
+    e2e = None
+    if not args.no_e2e:
+        xh = x.cpu().pin_memory()
+        bph = b1p.cpu().pin_memory()
+        bmh = b1m.cpu().pin_memory()
+        yh = torch.empty((K, N), dtype=torch.float32).pin_memory()
+        vh = torch.empty((K, N), dtype=torch.float32).pin_memory()
+        xd, bpd, bmd = torch.empty_like(x), torch.empty_like(b1p), torch.empty_like(b1m)
+
+        def e2e_step():
+            xd.copy_(xh, non_blocking=True)
+            bpd.copy_(bph, non_blocking=True)
+            bmd.copy_(bmh, non_blocking=True)
+            mpm.mpm_fit(problem, opts, xd, y, bpd, bmd, var=var, ws=ws)
+            yh.copy_(y, non_blocking=True)
+            vh.copy_(var, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record()
+        for _ in range(args.steps):
+            e2e_step()
+        f1.record()
+        torch.cuda.synchronize()
+        e2e_val, _ = aggregate(f0.elapsed_time(f1) / 1000.0, units, world, dev)
+        h2d = xh.numel() * xh.element_size() + bph.numel() * 4 + bmh.numel() * 4
+        d2h = 2 * K * N * 4
+        e2e = {"value": round(e2e_val / 1e6, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    peak, peak_src = measured_peak()
+    kern = kernel_roofline(prof, N, args.steps, K, C, I, peak)
+    dominant = max(kern, key=lambda k: kern[k]["ms_total"])
+    dk = kern[dominant]
+    traffic = measured_traffic(dominant, N)
+    roofline = {"bound": "hbm", "kernel": dominant, "achieved": dk.get("achieved_gbs"),
+                "peak": peak, "unit": "GB/s",
+                "frac": dk.get("frac_of_measured_hbm"), "traffic": traffic,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
+                else "fallback 6.8 TB/s",
+                "share_of_step": round(dk["ms_total"] / (1000 * seconds), 3)}
+    cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline(args.seed)
+    line = {
+        "metric": METRIC, "value": round(value / 1e6, 3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1000 * t_max / args.steps, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "1 mm MPM JTV-MAP fit, 176x240x256 voxels, PDw/T1w/MTw 8/8/6 "
+                               "echoes, Rician SNR 20, 20 updates x 30 PCG + posterior variance",
+                   "voxels": N, "gn_iters": GN_ITERS, "cg_iters": CG_ITERS, "lambda": LAMBDA,
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (images 951 MB, L2 129 MB); no flush",
+                   "final_objective": final_F},
+        "roofline": roofline,
+        "kernels": kern,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -186,6 +186,28 @@ mpm_status mpm_workspace_status(const void* ws, size_t ws_bytes, void* stream);
 /* Diagnostic: number of kernels this library has launched in this process. */
 unsigned long long mpm_kernel_launches(void);
 
+/* Kernel kinds reported by mpm_profile_read. */
+enum {
+    MPM_KERNEL_GRAD_HESS = 0,    /* fused voxel pass */
+    MPM_KERNEL_JTV = 1,          /* JTV weights */
+    MPM_KERNEL_PCG_INIT = 2,     /* r0 = g + L y, preconditioner factor, z0 */
+    MPM_KERNEL_PCG_MATVEC = 3,   /* p update, q = (H + L) p */
+    MPM_KERNEL_PCG_UPDATE = 4,   /* r update, z = M^-1 r */
+    MPM_KERNEL_PCG_FINAL = 5,    /* delta or y update */
+    MPM_KERNEL_UNCERTAINTY = 6,
+    MPM_KERNEL_FORWARD = 7,
+    MPM_KERNEL_INIT = 8,         /* image means and constant maps */
+    MPM_KERNEL_KINDS = 9
+};
+
+/* Diagnostic timing.  While enabled (on != 0, process-wide), every kernel
+ * launch is bracketed by two CUDA events recorded on its stream.
+ * mpm_profile_read waits for those events, writes per kind the summed
+ * milliseconds (ms[k]) and launch counts (launches[k]) for k < n, and clears
+ * the records.  Either output may be NULL. */
+mpm_status mpm_profile_enable(int on);
+mpm_status mpm_profile_read(double* ms, unsigned long long* launches, int n);
+
 #ifdef __cplusplus
 }
 #endif

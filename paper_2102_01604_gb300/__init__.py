@@ -19,7 +19,8 @@ from ._lib import MPMError, Opts, Problem, Report
 __all__ = [
     "make_problem", "make_opts", "workspace", "mpm_workspace_size", "mpm_forward",
     "mpm_grad_hess", "mpm_jtv_weights", "mpm_solve", "mpm_uncertainty", "mpm_fit",
-    "mpm_workspace_status", "mpm_kernel_launches", "MPMError", "Problem", "Opts", "Report",
+    "mpm_workspace_status", "mpm_kernel_launches", "mpm_profile_enable", "mpm_profile_read",
+    "MPMError", "Problem", "Opts", "Report",
 ]
 
 
@@ -214,3 +215,17 @@ def mpm_workspace_status(ws, stream=None) -> int:
 
 def mpm_kernel_launches() -> int:
     return int(_lib.load().mpm_kernel_launches())
+
+
+def mpm_profile_enable(on: bool = True) -> None:
+    _lib.check(_lib.load().mpm_profile_enable(1 if on else 0), "mpm_profile_enable")
+
+
+def mpm_profile_read() -> dict:
+    """Per kernel kind: {"ms": summed milliseconds, "launches": count}; clears
+    the records."""
+    n = len(_lib.KERNEL_KINDS)
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_ulonglong * n)()
+    _lib.check(_lib.load().mpm_profile_read(ms, cnt, n), "mpm_profile_read")
+    return {k: {"ms": ms[i], "launches": int(cnt[i])} for i, k in enumerate(_lib.KERNEL_KINDS)}

@@ -82,7 +82,13 @@ PROTOTYPES = {
     "mpm_fit": (ctypes.c_int, [_P, _O, _V, _V, _V, _V, _V, _V, _S, ctypes.POINTER(Report), _V]),
     "mpm_workspace_status": (ctypes.c_int, [_V, _S, _V]),
     "mpm_kernel_launches": (ctypes.c_ulonglong, []),
+    "mpm_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+    "mpm_profile_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int]),
 }
+
+KERNEL_KINDS = ["grad_hess", "jtv", "pcg_init", "pcg_matvec", "pcg_update", "pcg_final",
+                "uncertainty", "forward", "init"]
 
 _handle = None
 

@@ -5,14 +5,59 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
+#include <vector>
 
 #include "mpm_internal.cuh"
 
 namespace mpm {
 
 static std::atomic<unsigned long long> g_launches{0};
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// ------------------------------------------------- diagnostic kernel timing
+
+struct ProfRecord {
+    int kind;
+    cudaEvent_t a, b;
+};
+
+static std::atomic<bool> g_prof_on{false};
+static std::mutex g_prof_mu;
+static std::vector<ProfRecord> g_prof;
+static std::vector<cudaEvent_t> g_pool;
+
+static cudaEvent_t pool_get()
+{
+    if (!g_pool.empty()) {
+        cudaEvent_t e = g_pool.back();
+        g_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+LaunchScope::LaunchScope(int k, cudaStream_t s) : kind(k), st(s), rec(nullptr)
+{
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (!g_prof_on.load(std::memory_order_relaxed)) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    ProfRecord r{kind, pool_get(), pool_get()};
+    if (!r.a || !r.b) return;
+    cudaEventRecord(r.a, st);
+    g_prof.push_back(r);
+    rec = reinterpret_cast<void*>(g_prof.size());      // 1-based index of the record
+}
+
+LaunchScope::~LaunchScope()
+{
+    if (!rec) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    const size_t i = reinterpret_cast<size_t>(rec) - 1;
+    if (i < g_prof.size()) cudaEventRecord(g_prof[i].b, st);
+}
 
 int voxel_grid(long long N)
 {
@@ -347,6 +392,37 @@ const char* mpm_status_string(mpm_status s)
 const char* mpm_last_error(void) { return t_err.c_str(); }
 
 unsigned long long mpm_kernel_launches(void) { return g_launches.load(); }
+
+mpm_status mpm_profile_enable(int on)
+{
+    g_prof_on.store(on != 0);
+    return MPM_OK;
+}
+
+mpm_status mpm_profile_read(double* ms, unsigned long long* launches, int n)
+{
+    if (n < 0) return fail(MPM_ERR_INVALID_ARG, "n < 0");
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (int k = 0; k < n; ++k) {
+        if (ms) ms[k] = 0.0;
+        if (launches) launches[k] = 0;
+    }
+    mpm_status st = MPM_OK;
+    for (const ProfRecord& r : g_prof) {
+        float t = 0.0f;
+        if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) {
+            cudaGetLastError();
+            st = fail(MPM_ERR_CUDA, "event timing failed");
+        } else if (r.kind < n) {
+            if (ms) ms[r.kind] += t;
+            if (launches) launches[r.kind] += 1;
+        }
+        g_pool.push_back(r.a);
+        g_pool.push_back(r.b);
+    }
+    g_prof.clear();
+    return st;
+}
 
 mpm_status mpm_workspace_size(const mpm_problem* problem, const mpm_opts* opts, int call,
                               size_t* bytes)

@@ -159,7 +159,17 @@ struct StencilGrid {
 
 StencilGrid stencil_grid(const DevProblem& P);
 int voxel_grid(long long N);
-void count_launch();
+
+// Every kernel launch goes through a LaunchScope: it counts the launch and,
+// when diagnostic timing is on (mpm_profile_enable), brackets it with CUDA
+// events on its stream, accumulated per kernel kind (MPM_KERNEL_*).
+struct LaunchScope {
+    LaunchScope(int kind, cudaStream_t st);
+    ~LaunchScope();
+    int kind;
+    cudaStream_t st;
+    void* rec;
+};
 
 // ------------------------------------------------------- kernel launchers
 // (defined in voxel_kernels.cu and stencil_kernels.cu; return cudaError_t of

@@ -446,7 +446,7 @@ cudaError_t launch_jtv(const DevProblem& P, const float* y, float* w, double* jt
                        cudaStream_t st)
 {
     const StencilGrid sg = stencil_grid(P);
-    count_launch();
+    LaunchScope ls(MPM_KERNEL_JTV, st);
     if (P.K == 4)
         k_jtv<4><<<sg.grid, sg.block, 0, st>>>(P, sg.zc, y, w, jtv, red);
     else
@@ -466,15 +466,19 @@ static cudaError_t solve_k(const DevProblem& P, int cg_iters, double tol_cg, con
     // workspace buffer inside the fit, which then passes y_update).
     float* xacc = delta;
     const double tol2 = tol_cg > 0.0 ? tol_cg * tol_cg : 0.0;
-    count_launch();
-    k_pcg_init<K><<<sg.grid, sg.block, 0, st>>>(P, sg.zc, h, w, g, y, B, tol2, hdr, resid, red);
+    {
+        LaunchScope ls(MPM_KERNEL_PCG_INIT, st);
+        k_pcg_init<K><<<sg.grid, sg.block, 0, st>>>(P, sg.zc, h, w, g, y, B, tol2, hdr, resid, red);
+    }
     for (int k = 0; k < cg_iters; ++k) {
-        count_launch();
-        k_pcg_matvec<K><<<sg.grid, sg.block, 0, st>>>(P, sg.zc, k, h, w, B, xacc, hdr, red);
-        count_launch();
+        {
+            LaunchScope ls(MPM_KERNEL_PCG_MATVEC, st);
+            k_pcg_matvec<K><<<sg.grid, sg.block, 0, st>>>(P, sg.zc, k, h, w, B, xacc, hdr, red);
+        }
+        LaunchScope ls(MPM_KERNEL_PCG_UPDATE, st);
         k_pcg_update<K><<<sg.grid, sg.block, 0, st>>>(P, sg.zc, k, B, hdr, resid, red);
     }
-    count_launch();
+    LaunchScope ls(MPM_KERNEL_PCG_FINAL, st);
     k_pcg_final<<<voxel_grid(P.N * K), kBlock, 0, st>>>(P.N * K, B, xacc, delta, y_update, hdr,
                                                         report_rel, report_it);
     return cudaGetLastError();

@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(kBlock) k_fill_maps(DevProblem P, MapValues mv
 cudaError_t launch_forward(const DevProblem& P, const float* y, const float* b1p,
                            const float* b1m, float* s, cudaStream_t st)
 {
-    count_launch();
+    LaunchScope ls(MPM_KERNEL_FORWARD, st);
     k_forward<<<voxel_grid(P.N), kBlock, 0, st>>>(P, y, b1p, b1m, s);
     return cudaGetLastError();
 }
@@ -354,7 +354,7 @@ cudaError_t launch_grad_hess(const DevProblem& P, int echo_dtype, const void* x,
                              const float* y, const float* b1p, const float* b1m, float* g,
                              float* h, double* nll, Reduce red, cudaStream_t st)
 {
-    count_launch();
+    LaunchScope ls(MPM_KERNEL_GRAD_HESS, st);
     if (P.K == 4)
         grad_hess_pre<4>(P, echo_dtype, x, y, b1p, b1m, g, h, nll, red, st);
     else
@@ -366,7 +366,7 @@ cudaError_t launch_uncertainty(const DevProblem& P, const float* h, const float*
                                const float* y, float* var, float* logdet, float* moments,
                                unsigned* status, cudaStream_t st)
 {
-    count_launch();
+    LaunchScope ls(MPM_KERNEL_UNCERTAINTY, st);
     k_uncertainty<<<voxel_grid(P.N), kBlock, 0, st>>>(P, h, w, y, var, logdet, moments,
                                                        status);
     return cudaGetLastError();
@@ -378,16 +378,18 @@ cudaError_t launch_image_means(const DevProblem& P, int echo_dtype, const void* 
     long long want = (P.N + kBlock - 1) / kBlock;
     const int nb = (int)(want < kMeanBlocks ? want : kMeanBlocks);
     dim3 grid(nb, P.I);
-    count_launch();
-    if (echo_dtype == 1)
-        k_image_means<__nv_bfloat16><<<grid, kBlock, 0, st>>>(
-            P, static_cast<const __nv_bfloat16*>(x), partials);
-    else
-        k_image_means<float><<<grid, kBlock, 0, st>>>(P, static_cast<const float*>(x),
-                                                      partials);
+    {
+        LaunchScope ls(MPM_KERNEL_INIT, st);
+        if (echo_dtype == 1)
+            k_image_means<__nv_bfloat16><<<grid, kBlock, 0, st>>>(
+                P, static_cast<const __nv_bfloat16*>(x), partials);
+        else
+            k_image_means<float><<<grid, kBlock, 0, st>>>(P, static_cast<const float*>(x),
+                                                          partials);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    count_launch();
+    LaunchScope ls(MPM_KERNEL_INIT, st);
     k_means_final<<<P.I, kBlock, 0, st>>>(P, partials, nb, means);
     return cudaGetLastError();
 }
@@ -397,7 +399,7 @@ cudaError_t launch_fill_maps(const DevProblem& P, const float* values, float* y,
 {
     MapValues mv;
     for (int k = 0; k < 4; ++k) mv.v[k] = k < P.K ? values[k] : 0.0f;
-    count_launch();
+    LaunchScope ls(MPM_KERNEL_INIT, st);
     k_fill_maps<<<voxel_grid(P.N * P.K), kBlock, 0, st>>>(P, mv, y);
     return cudaGetLastError();
 }

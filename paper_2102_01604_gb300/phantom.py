@@ -45,23 +45,27 @@ def protocol(contrasts=("PDw", "T1w", "MTw"), n_echoes=(8, 8, 6), sigma2=None) -
             "n_echoes": list(n_echoes), "te": te, "sigma2": list(sigma2)}
 
 
-def _grid(shape):
+def _axes(shape):
+    """Normalised coordinates along x, y, z (each in [0, 1))."""
+    return [np.arange(n, dtype=np.float64) / n for n in shape]
+
+
+def _separable(shape, fx, fy, fz):
+    """Volume f(x) g(y) h(z) flattened with x fastest."""
     nx, ny, nz = shape
-    z, y, x = np.meshgrid(np.arange(nz, dtype=np.float64) / nz,
-                          np.arange(ny, dtype=np.float64) / ny,
-                          np.arange(nx, dtype=np.float64) / nx, indexing="ij")
-    return x.ravel(), y.ravel(), z.ravel()
+    return (fz[:, None, None] * fy[None, :, None] * fx[None, None, :]).reshape(-1)
 
 
-def _smooth_field(rng, coords):
-    """Product of one low-frequency cosine per axis, in [-1, 1]."""
-    f = np.ones_like(coords[0])
-    for c in coords:
+def _smooth_field(rng, axes, shape):
+    """Product of one low-frequency cosine per axis, scaled to [-1, 1]."""
+    f = []
+    for a in axes:
         freq = rng.integers(1, 3)
         phase = rng.uniform(0.0, 2.0 * math.pi)
-        f = f * np.cos(math.pi * freq * c + phase)
-    m = np.max(np.abs(f))
-    return f / m if m > 0 else f
+        f.append(np.cos(math.pi * freq * a + phase))
+    m = np.max(np.abs(f[0])) * np.max(np.abs(f[1])) * np.max(np.abs(f[2]))
+    out = _separable(shape, *f)
+    return out / m if m > 0 else out
 
 
 def phantom(shape, seed: int = 0, n_regions: int = 12, n_contrasts: int = 3,
@@ -76,29 +80,31 @@ def phantom(shape, seed: int = 0, n_regions: int = 12, n_contrasts: int = 3,
     factor ``1 + 0.05 prod_d cos(pi f_d x_d + phi_d)``.  The phantom fills the
     whole volume (no air background)."""
     rng = np.random.default_rng(seed)
-    coords = _grid(shape)
-    N = coords[0].size
+    shape = tuple(int(v) for v in shape)
+    axes = _axes(shape)
+    N = int(np.prod(shape))
     centres = rng.uniform(0.0, 1.0, size=(n_regions, 3))
     best = np.full(N, np.inf)
     label = np.zeros(N, dtype=np.int64)
     for r in range(n_regions):
-        d = ((coords[0] - centres[r, 0]) ** 2 + (coords[1] - centres[r, 1]) ** 2
-             + (coords[2] - centres[r, 2]) ** 2)
+        d = (((axes[2] - centres[r, 2]) ** 2)[:, None, None]
+             + ((axes[1] - centres[r, 1]) ** 2)[None, :, None]
+             + ((axes[0] - centres[r, 0]) ** 2)[None, None, :]).reshape(-1)
         closer = d < best
-        best = np.where(closer, d, best)
-        label = np.where(closer, r, label)
+        best[closer] = d[closer]
+        label[closer] = r
     ranges = [(2000.0, 4000.0), (0.5, 1.5), (10.0, 40.0), (0.002, 0.02)]
     K = 4 if with_mt else 3
     y = np.empty((K, N))
     for k in range(K):
         lo, hi = ranges[k]
         vals = rng.uniform(lo, hi, size=n_regions)[label]
-        vals = vals * (1.0 + 0.05 * _smooth_field(rng, coords))
+        vals *= 1.0 + 0.05 * _smooth_field(rng, axes, shape)
         y[k] = np.log(vals / (1.0 - vals)) if k == 3 else np.log(vals)
-    b1p = 1.0 + 0.2 * _smooth_field(rng, coords)
+    b1p = 1.0 + 0.2 * _smooth_field(rng, axes, shape)
     b1m = None
     if with_b1m:
-        b1m = np.stack([1.0 + 0.1 * _smooth_field(rng, coords) for _ in range(n_contrasts)])
+        b1m = np.stack([1.0 + 0.1 * _smooth_field(rng, axes, shape) for _ in range(n_contrasts)])
     return {"y": y, "b1p": b1p, "b1m": b1m, "label": label}
 
 

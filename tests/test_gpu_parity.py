@@ -108,7 +108,9 @@ def test_solve(mpm, shape, cg_iters):
     assert it == cg_iters
     assert_close_scaled(to_np(delta), d_o, 2e-4, "delta")
     r = to_np(resid)
-    np.testing.assert_allclose(r[:it + 1], r_o, rtol=2e-4 * max(1, cg_iters) ** 0.5 + 1e-5)
+    # float32 residuals bottom out near 1e-7 of |r_0|: compare above that floor
+    np.testing.assert_allclose(r[:it + 1], r_o, rtol=2e-4 * max(1, cg_iters) ** 0.5 + 1e-5,
+                               atol=1e-6 * r_o[0])
 
 
 def test_solve_tolerance_stop(mpm):
