@@ -58,7 +58,14 @@ def parse_args(argv=None):
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    return ap.parse_args(argv)
+    ap.add_argument("--shape", default=None,
+                    help="override the volume (nx,ny,nz) for profiling runs on a smaller case")
+    args = ap.parse_args(argv)
+    if args.shape:
+        global SHAPE
+        SHAPE = tuple(int(v) for v in args.shape.split(","))
+        assert len(SHAPE) == 3
+    return args
 
 
 # ------------------------------------------------------------ distributed
@@ -437,11 +444,13 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(1000 * t_max / args.steps, 2), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "1 mm MPM JTV-MAP fit, 176x240x256 voxels, PDw/T1w/MTw 8/8/6 "
-                               "echoes, Rician SNR 20, 20 updates x 30 PCG + posterior variance",
+        "config": {"workload": f"1 mm MPM JTV-MAP fit, {SHAPE[0]}x{SHAPE[1]}x{SHAPE[2]} voxels, "
+                               "PDw/T1w/MTw 8/8/6 echoes, Rician SNR 20, 20 updates x 30 PCG "
+                               "+ posterior variance",
                    "voxels": N, "gn_iters": GN_ITERS, "cg_iters": CG_ITERS, "lambda": LAMBDA,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "l2": "inputs larger than L2 (images 951 MB, L2 129 MB); no flush",
+                   "l2": f"inputs larger than L2 (images {x.numel() * 4 / 1e6:.0f} MB, L2 129 MB); "
+                         "no flush",
                    "final_objective": final_F},
         "roofline": roofline,
         "kernels": kern,
