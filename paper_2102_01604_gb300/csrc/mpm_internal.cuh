@@ -74,6 +74,31 @@ struct WsHeader {
 
 // ------------------------------------------------------------------ helpers
 
+// Compensated float32 accumulator for the float64-class sums (CG inner
+// products, residual norms, likelihood and JTV energy).  GB300 issues float64
+// arithmetic at a small fraction of its float32 rate, so each thread keeps its
+// running sum as an unevaluated pair hi + lo updated by Knuth's two-sum (an
+// error-free transformation: hi + lo is the exact sum of the added float32
+// values up to the rounding of lo); warps combine pairs the same way, and only
+// per-warp and per-block partials are converted to float64 and reduced in a
+// fixed order.
+struct Acc {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float s = __fadd_rn(hi, x);
+        const float bp = __fsub_rn(s, hi);
+        const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+        hi = s;
+        lo = __fadd_rn(lo, e);
+    }
+    __device__ __forceinline__ void add(const Acc& o)
+    {
+        add(o.hi);
+        lo = __fadd_rn(lo, o.lo);
+    }
+};
+
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll
@@ -98,12 +123,42 @@ __device__ __forceinline__ double block_sum(double v, double* sh /* [kBlock/32] 
     return v;
 }
 
+// Warp-level combination of compensated pairs (lane 0 holds the result),
+// then float64 for the few per-warp values.
+__device__ __forceinline__ double warp_acc(Acc a)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        Acc b;
+        b.hi = __shfl_down_sync(0xffffffffu, a.hi, o);
+        b.lo = __shfl_down_sync(0xffffffffu, a.lo, o);
+        a.add(b);
+    }
+    return (double)a.hi + (double)a.lo;
+}
+
+__device__ __forceinline__ double block_acc(Acc a, double* sh /* [kBlock/32] */)
+{
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+    const double w = warp_acc(a);
+    __syncthreads();
+    if ((tid & 31) == 0) sh[tid >> 5] = w;
+    __syncthreads();
+    double v = 0.0;
+    if (tid < 32) {
+        v = tid < nw ? sh[tid] : 0.0;
+        v = warp_sum(v);
+    }
+    return v;
+}
+
 // Last-block-done reduction of NV values per block.  Every thread calls it
-// with its own contributions; returns true in exactly one block (the last to
-// arrive), where out[j] (valid in thread 0) holds the grid-wide sums in a
-// fixed summation order.  The counter is reset for the next launch.
+// with its own compensated partials; returns true in exactly one block (the
+// last to arrive), where out[j] (valid in thread 0) holds the grid-wide sums
+// in a fixed summation order.  The counter is reset for the next launch.
 template <int NV>
-__device__ __forceinline__ bool grid_reduce(const double (&v)[NV], Reduce red, double (&out)[NV])
+__device__ __forceinline__ bool grid_reduce(const Acc (&v)[NV], Reduce red, double (&out)[NV])
 {
     __shared__ double sh[kBlock / 32];
     __shared__ bool am_last;
@@ -113,7 +168,7 @@ __device__ __forceinline__ bool grid_reduce(const double (&v)[NV], Reduce red, d
     const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
-        double s = block_sum(v[j], sh);
+        double s = block_acc(v[j], sh);
         if (tid == 0) red.partials[(size_t)j * kMaxBlocks + bid] = s;
     }
     if (tid == 0) {
@@ -157,7 +212,7 @@ struct StencilGrid {
     int zc;           // z planes per block
 };
 
-StencilGrid stencil_grid(const DevProblem& P);
+StencilGrid stencil_grid(const DevProblem& P, int tile_x, int tile_y);
 int voxel_grid(long long N);
 
 // Every kernel launch goes through a LaunchScope: it counts the launch and,

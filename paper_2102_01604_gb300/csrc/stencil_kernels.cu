@@ -11,6 +11,8 @@
 // (x, y) tile and march along z.  All CG scalars (alpha, beta, |r|) live in
 // device memory and are produced by the last block of each reducing launch,
 // so the whole PCG runs without a host round trip.
+#include <type_traits>
+
 #include "mpm_internal.cuh"
 
 namespace mpm {
@@ -52,7 +54,7 @@ __global__ void __launch_bounds__(kBlock) k_jtv(DevProblem P, int zc, const floa
     const int yy = blockIdx.y * kTileY + threadIdx.y;
     const int z0 = blockIdx.z * zc;
     const int z1 = min(P.nz, z0 + zc);
-    double acc = 0.0;
+    Acc acc;
     if (x < P.nx && yy < P.ny) {
         const float ih[6] = {P.ihx2, P.ihx2, P.ihy2, P.ihy2, P.ihz2, P.ihz2};
         for (int z = z0; z < z1; ++z) {
@@ -76,10 +78,11 @@ __global__ void __launch_bounds__(kBlock) k_jtv(DevProblem P, int zc, const floa
             const float val = u + P.eps2;
             const float sq = sqrtf(val);
             if (w) w[n] = 1.0f / sq;
-            acc += (double)sq;
+            acc.add(sq);
         }
     }
-    double v[1] = {acc}, out[1];
+    Acc v[1] = {acc};
+    double out[1];
     if (grid_reduce<1>(v, red, out) && threadIdx.x == 0 && threadIdx.y == 0) *jtv = out[0];
 }
 
@@ -186,7 +189,7 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(DevProblem P, int zc, const
     const int yy = blockIdx.y * kTileY + threadIdx.y;
     const int z0 = blockIdx.z * zc;
     const int z1 = min(P.nz, z0 + zc);
-    double rz = 0.0, rr = 0.0;
+    Acc rz, rr;
     bool pd = true;
     if (x < P.nx && yy < P.ny) {
         for (int z = z0; z < z1; ++z) {
@@ -219,17 +222,21 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(DevProblem P, int zc, const
             chol_apply<K>(L, r, zz);
 #pragma unroll
             for (int k = 0; k < T; ++k) B.R[k * N + n] = L[k];
+            float vrz = 0.0f, vrr = 0.0f;
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 B.r[k * N + n] = r[k];
                 B.z[k * N + n] = zz[k];
-                rz += (double)r[k] * (double)zz[k];
-                rr += (double)r[k] * (double)r[k];
+                vrz += r[k] * zz[k];
+                vrr += r[k] * r[k];
             }
+            rz.add(vrz);
+            rr.add(vrr);
         }
     }
     if (!pd) atomicOr(&hdr->status, kStatusNotPD);
-    double v[2] = {rz, rr}, out[2];
+    Acc v[2] = {rz, rr};
+    double out[2];
     if (grid_reduce<2>(v, red, out) && threadIdx.x == 0 && threadIdx.y == 0) {
         SolveScalars& sc = hdr->sc;
         sc.rz = out[0];
@@ -249,16 +256,31 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(DevProblem P, int zc, const
 
 // ------------------------------------------------------------- PCG matvec
 
+// Tiled 2.5-D stencil: a block owns a kMvX x kMvY (x, y) tile and marches up a
+// run of z planes.  The direction p_k = z_k + beta p_{k-1} of the current plane
+// (with a one-voxel x/y halo) and the JTV weights are staged in shared memory;
+// the planes below and above live in registers, so every operand is loaded
+// from memory about once per voxel.
+constexpr int kMvX = 16, kMvY = 16;
+
 template <int K>
-__global__ void __launch_bounds__(kBlock) k_pcg_matvec(DevProblem P, int zc, int k_it,
-                                                       const float* __restrict__ h,
-                                                       const float* __restrict__ w, SolveBufs B,
-                                                       float* __restrict__ xacc, WsHeader* hdr,
-                                                       Reduce red)
+__global__ void __launch_bounds__(kMvX * kMvY) k_pcg_matvec(DevProblem P, int zc, int k_it,
+                                                           const float* __restrict__ h,
+                                                           const float* __restrict__ w,
+                                                           const float* __restrict__ zv,
+                                                           const float* __restrict__ pold,
+                                                           float* __restrict__ pnew,
+                                                           float* __restrict__ qout,
+                                                           float* __restrict__ xacc,
+                                                           WsHeader* hdr, Reduce red)
 {
+    constexpr int T = K * (K + 1) / 2;
+    __shared__ float sp[K][kMvY + 2][kMvX + 2];
+    __shared__ float sw[kMvY + 2][kMvX + 2];
     __shared__ float s_beta, s_alpha;
     __shared__ int s_done;
-    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = tx + ty * kMvX;
     if (tid == 0) {
         s_done = hdr->sc.done;
         s_beta = (float)hdr->sc.beta;
@@ -267,63 +289,158 @@ __global__ void __launch_bounds__(kBlock) k_pcg_matvec(DevProblem P, int zc, int
     __syncthreads();
     if (s_done) return;
     const float beta = s_beta, alpha_prev = s_alpha;
+    const bool has_old = k_it > 0;
     const long long N = P.N;
-    const long long sxy = (long long)P.nx * P.ny;
-    const int x = blockIdx.x * kTileX + threadIdx.x;
-    const int yy = blockIdx.y * kTileY + threadIdx.y;
+    const int nx = P.nx, ny = P.ny, nz = P.nz;
+    const long long sxy = (long long)nx * ny;
+    const int x = blockIdx.x * kMvX + tx;
+    const int y = blockIdx.y * kMvY + ty;
     const int z0 = blockIdx.z * zc;
-    const int z1 = min(P.nz, z0 + zc);
-    const float* __restrict__ zv = B.z;
-    const float* __restrict__ pold = B.p[(k_it + 1) & 1];
-    float* __restrict__ pnew = B.p[k_it & 1];
-    double pq = 0.0;
-    if (x < P.nx && yy < P.ny) {
-        for (int z = z0; z < z1; ++z) {
-            const long long n = x + (long long)P.nx * yy + sxy * z;
-            const float wn = __ldg(w + n);
-            Edges e;
-            make_edges(P, x, yy, z, n, w, wn, e);
-            float p[K], q[K];
+    const int z1 = min(nz, z0 + zc);
+    const bool inside = x < nx && y < ny;
+    const float ihx = P.ihx2, ihy = P.ihy2, ihz = P.ihz2;
+
+    // p_k at voxel n for every map; po receives p_{k-1}
+    auto load_p = [&](long long n, float (&pv)[K], float (&po)[K]) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const float zz = __ldg(zv + k * N + n);
+            const float o = has_old ? __ldg(pold + k * N + n) : 0.0f;
+            po[k] = o;
+            pv[k] = has_old ? zz + beta * o : zz;
+        }
+    };
+    auto load_p_only = [&](long long n, float (&pv)[K]) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const float zz = __ldg(zv + k * N + n);
+            pv[k] = has_old ? zz + beta * __ldg(pold + k * N + n) : zz;
+        }
+    };
+
+    const long long col = (long long)x + (long long)nx * y;   // (x, y) column offset
+    float pc[K], pp[K], pn[K], oc[K], on[K], dummy[K];
+    float wc = 0.f, wp = 0.f, wn = 0.f;
+    if (inside) {
+        const long long n0 = col + sxy * z0;
+        load_p(n0, pc, oc);
+        wc = __ldg(w + n0);
+        if (z0 > 0) {
+            load_p_only(n0 - sxy, pp);
+            wp = __ldg(w + n0 - sxy);
+        }
+        if (z0 + 1 < nz) {
+            load_p(n0 + sxy, pn, on);
+            wn = __ldg(w + n0 + sxy);
+        }
+    }
+    (void)dummy;
+    Acc pq;
+    for (int z = z0; z < z1; ++z) {
+        const long long n = col + sxy * z;
+        float Hn[T], xo[K];
+        if (inside) {
+#pragma unroll
+            for (int t = 0; t < T; ++t) Hn[t] = __ldg(h + t * N + n);
+            if (k_it > 1) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) xo[k] = xacc[k * N + n];
+            }
+        }
+        // stage the current plane (own value and x / y halo) in shared memory
+        __syncthreads();
+        if (inside) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) sp[k][ty + 1][tx + 1] = pc[k];
+            sw[ty + 1][tx + 1] = wc;
+            if (tx == 0 && x > 0) {
+                float hv[K];
+                load_p_only(n - 1, hv);
+#pragma unroll
+                for (int k = 0; k < K; ++k) sp[k][ty + 1][0] = hv[k];
+                sw[ty + 1][0] = __ldg(w + n - 1);
+            }
+            if (tx == kMvX - 1 && x + 1 < nx) {
+                float hv[K];
+                load_p_only(n + 1, hv);
+#pragma unroll
+                for (int k = 0; k < K; ++k) sp[k][ty + 1][kMvX + 1] = hv[k];
+                sw[ty + 1][kMvX + 1] = __ldg(w + n + 1);
+            }
+            if (ty == 0 && y > 0) {
+                float hv[K];
+                load_p_only(n - nx, hv);
+#pragma unroll
+                for (int k = 0; k < K; ++k) sp[k][0][tx + 1] = hv[k];
+                sw[0][tx + 1] = __ldg(w + n - nx);
+            }
+            if (ty == kMvY - 1 && y + 1 < ny) {
+                float hv[K];
+                load_p_only(n + nx, hv);
+#pragma unroll
+                for (int k = 0; k < K; ++k) sp[k][kMvY + 1][tx + 1] = hv[k];
+                sw[kMvY + 1][tx + 1] = __ldg(w + n + nx);
+            }
+        }
+        __syncthreads();
+        if (inside) {
+            // edge coefficients (w_n + w_m) / h^2 of the six neighbours
+            const bool okxm = x > 0, okxp = x + 1 < nx, okym = y > 0, okyp = y + 1 < ny;
+            const bool okzm = z > 0, okzp = z + 1 < nz;
+            const float cxm = okxm ? (wc + sw[ty + 1][tx]) * ihx : 0.f;
+            const float cxp = okxp ? (wc + sw[ty + 1][tx + 2]) * ihx : 0.f;
+            const float cym = okym ? (wc + sw[ty][tx + 1]) * ihy : 0.f;
+            const float cyp = okyp ? (wc + sw[ty + 2][tx + 1]) * ihy : 0.f;
+            const float czm = okzm ? (wc + wp) * ihz : 0.f;
+            const float czp = okzp ? (wc + wn) * ihz : 0.f;
+            float q[K];
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                const long long o = k * N + n;
-                float pk = __ldg(zv + o);
-                if (k_it > 0) {
-                    const float po = __ldg(pold + o);
-                    pk += beta * po;
-                    // fold the previous iteration's step into x
-                    xacc[o] = (k_it == 1 ? 0.0f : xacc[o]) + alpha_prev * po;
-                }
-                p[k] = pk;
-                float s = 0.0f;
-#pragma unroll
-                for (int j = 0; j < 6; ++j)
-                    if (e.ok[j]) {
-                        float pm = __ldg(zv + o + e.off[j]);
-                        if (k_it > 0) pm += beta * __ldg(pold + o + e.off[j]);
-                        s += e.c[j] * (pk - pm);
-                    }
+                const float v = pc[k];
+                float s = 0.f;
+                if (okxm) s += cxm * (v - sp[k][ty + 1][tx]);
+                if (okxp) s += cxp * (v - sp[k][ty + 1][tx + 2]);
+                if (okym) s += cym * (v - sp[k][ty][tx + 1]);
+                if (okyp) s += cyp * (v - sp[k][ty + 2][tx + 1]);
+                if (okzm) s += czm * (v - pp[k]);
+                if (okzp) s += czp * (v - pn[k]);
                 q[k] = P.lambda[k] * s;
             }
-            float Hn[K * (K + 1) / 2];
-#pragma unroll
-            for (int t = 0; t < K * (K + 1) / 2; ++t) Hn[t] = __ldg(h + t * N + n);
 #pragma unroll
             for (int a = 0; a < K; ++a) {
                 float acc = q[a];
 #pragma unroll
-                for (int b = 0; b < K; ++b) acc += Hn[a < b ? tri(K, a, b) : tri(K, b, a)] * p[b];
+                for (int b = 0; b < K; ++b) acc += Hn[a < b ? tri(K, a, b) : tri(K, b, a)] * pc[b];
                 q[a] = acc;
             }
+            float vpq = 0.0f;
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                pnew[k * N + n] = p[k];
-                B.q[k * N + n] = q[k];
-                pq += (double)p[k] * (double)q[k];
+                pnew[k * N + n] = pc[k];
+                qout[k * N + n] = q[k];
+                vpq += pc[k] * q[k];
+                // fold the previous iteration's step into x
+                if (k_it == 1) xacc[k * N + n] = alpha_prev * oc[k];
+                else if (k_it > 1) xacc[k * N + n] = xo[k] + alpha_prev * oc[k];
+            }
+            pq.add(vpq);
+            // march: the plane above becomes current
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                pp[k] = pc[k];
+                pc[k] = pn[k];
+                oc[k] = on[k];
+            }
+            wp = wc;
+            wc = wn;
+            if (z + 2 < nz && z + 1 < z1) {
+                load_p(n + 2 * sxy, pn, on);
+                wn = __ldg(w + n + 2 * sxy);
             }
         }
     }
-    double v[1] = {pq}, out[1];
+    Acc v[1] = {pq};
+    double out[1];
     if (grid_reduce<1>(v, red, out) && tid == 0) {
         SolveScalars& sc = hdr->sc;
         if (k_it > 0) sc.xcount = k_it;
@@ -338,15 +455,17 @@ __global__ void __launch_bounds__(kBlock) k_pcg_matvec(DevProblem P, int zc, int
 
 // ------------------------------------------------------------- PCG update
 
-template <int K>
-__global__ void __launch_bounds__(kBlock) k_pcg_update(DevProblem P, int zc, int k_it, SolveBufs B,
+// Streaming kernel: VPT consecutive voxels per thread (float4 loads when
+// VPT = 4), grid-stride over the volume.
+template <int K, int VPT>
+__global__ void __launch_bounds__(kBlock) k_pcg_update(DevProblem P, int k_it, SolveBufs B,
                                                        WsHeader* hdr, double* resid, Reduce red)
 {
     constexpr int T = K * (K + 1) / 2;
+    using V = typename std::conditional<VPT == 4, float4, float>::type;
     __shared__ float s_alpha;
     __shared__ int s_done;
-    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    if (tid == 0) {
+    if (threadIdx.x == 0) {
         s_done = hdr->sc.done;
         s_alpha = (float)hdr->sc.alpha;
     }
@@ -354,32 +473,54 @@ __global__ void __launch_bounds__(kBlock) k_pcg_update(DevProblem P, int zc, int
     if (s_done) return;
     const float alpha = s_alpha;
     const long long N = P.N;
-    const long long sxy = (long long)P.nx * P.ny;
-    const int x = blockIdx.x * kTileX + threadIdx.x;
-    const int yy = blockIdx.y * kTileY + threadIdx.y;
-    const int z0 = blockIdx.z * zc;
-    const int z1 = min(P.nz, z0 + zc);
-    double rz = 0.0, rr = 0.0;
-    if (x < P.nx && yy < P.ny) {
-        for (int z = z0; z < z1; ++z) {
-            const long long n = x + (long long)P.nx * yy + sxy * z;
+    const long long NV = N / VPT;           // vectors per map (N % VPT == 0)
+    const V* __restrict__ r4 = reinterpret_cast<const V*>(B.r);
+    const V* __restrict__ q4 = reinterpret_cast<const V*>(B.q);
+    const V* __restrict__ R4 = reinterpret_cast<const V*>(B.R);
+    V* __restrict__ rw = reinterpret_cast<V*>(B.r);
+    V* __restrict__ zw = reinterpret_cast<V*>(B.z);
+    Acc rz, rr;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < NV;
+         i += (long long)gridDim.x * blockDim.x) {
+        V rv[K], qv[K], Lv[T];
+#pragma unroll
+        for (int k = 0; k < K; ++k) rv[k] = r4[k * NV + i];
+#pragma unroll
+        for (int k = 0; k < K; ++k) qv[k] = __ldg(q4 + k * NV + i);
+#pragma unroll
+        for (int t = 0; t < T; ++t) Lv[t] = __ldg(R4 + t * NV + i);
+        V zo[K];
+#pragma unroll
+        for (int j = 0; j < VPT; ++j) {
             float r[K], L[T], zz[K];
 #pragma unroll
-            for (int k = 0; k < K; ++k) r[k] = B.r[k * N + n] - alpha * __ldg(B.q + k * N + n);
+            for (int k = 0; k < K; ++k) {
+                r[k] = reinterpret_cast<const float*>(&rv[k])[j] -
+                       alpha * reinterpret_cast<const float*>(&qv[k])[j];
+                reinterpret_cast<float*>(&rv[k])[j] = r[k];
+            }
 #pragma unroll
-            for (int k = 0; k < T; ++k) L[k] = __ldg(B.R + k * N + n);
+            for (int t = 0; t < T; ++t) L[t] = reinterpret_cast<const float*>(&Lv[t])[j];
             chol_apply<K>(L, r, zz);
+            float vrz = 0.0f, vrr = 0.0f;
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                B.r[k * N + n] = r[k];
-                B.z[k * N + n] = zz[k];
-                rz += (double)r[k] * (double)zz[k];
-                rr += (double)r[k] * (double)r[k];
+                reinterpret_cast<float*>(&zo[k])[j] = zz[k];
+                vrz += r[k] * zz[k];
+                vrr += r[k] * r[k];
             }
+            rz.add(vrz);
+            rr.add(vrr);
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            rw[k * NV + i] = rv[k];
+            zw[k * NV + i] = zo[k];
         }
     }
-    double v[2] = {rz, rr}, out[2];
-    if (grid_reduce<2>(v, red, out) && tid == 0) {
+    Acc v[2] = {rz, rr};
+    double out[2];
+    if (grid_reduce<2>(v, red, out) && threadIdx.x == 0) {
         SolveScalars& sc = hdr->sc;
         const bool bad = !(out[0] == out[0]) || !(out[1] == out[1]);
         if (bad) atomicOr(&hdr->status, kStatusNaN);
@@ -423,12 +564,31 @@ __global__ void __launch_bounds__(kBlock) k_pcg_final(long long total, SolveBufs
 
 // ------------------------------------------------------------- launchers
 
-StencilGrid stencil_grid(const DevProblem& P)
+// One wave of resident blocks for a grid-stride streaming kernel.
+template <int K, int VPT>
+static int update_grid(long long units)
+{
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pcg_update<K, VPT>, kBlock, 0) !=
+                cudaSuccess || b < 1)
+            b = 1;
+        per_sm = b;
+    }
+    long long g = (units + kBlock - 1) / kBlock;
+    const long long cap = (long long)per_sm * kNumSm;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+StencilGrid stencil_grid(const DevProblem& P, int tx, int ty)
 {
     StencilGrid sg;
-    sg.block = dim3(kTileX, kTileY, 1);
-    const int gx = (P.nx + kTileX - 1) / kTileX;
-    const int gy = (P.ny + kTileY - 1) / kTileY;
+    sg.block = dim3(tx, ty, 1);
+    const int gx = (P.nx + tx - 1) / tx;
+    const int gy = (P.ny + ty - 1) / ty;
     const long long tiles = (long long)gx * gy;
     // about two waves of 8 resident blocks per SM, at most kMaxBlocks blocks
     const long long target = 2LL * 8 * kNumSm;
@@ -445,7 +605,7 @@ StencilGrid stencil_grid(const DevProblem& P)
 cudaError_t launch_jtv(const DevProblem& P, const float* y, float* w, double* jtv, Reduce red,
                        cudaStream_t st)
 {
-    const StencilGrid sg = stencil_grid(P);
+    const StencilGrid sg = stencil_grid(P, kTileX, kTileY);
     LaunchScope ls(MPM_KERNEL_JTV, st);
     if (P.K == 4)
         k_jtv<4><<<sg.grid, sg.block, 0, st>>>(P, sg.zc, y, w, jtv, red);
@@ -460,7 +620,7 @@ static cudaError_t solve_k(const DevProblem& P, int cg_iters, double tol_cg, con
                            float* y_update, double* resid, double* report_rel, int* report_it,
                            void* solve_ws, WsHeader* hdr, Reduce red, cudaStream_t st)
 {
-    const StencilGrid sg = stencil_grid(P);
+    const StencilGrid sg = stencil_grid(P, kTileX, kTileY);
     SolveBufs B = carve(P, solve_ws);
     // x accumulates in `delta` (the caller's output when solving alone, a
     // workspace buffer inside the fit, which then passes y_update).
@@ -470,13 +630,23 @@ static cudaError_t solve_k(const DevProblem& P, int cg_iters, double tol_cg, con
         LaunchScope ls(MPM_KERNEL_PCG_INIT, st);
         k_pcg_init<K><<<sg.grid, sg.block, 0, st>>>(P, sg.zc, h, w, g, y, B, tol2, hdr, resid, red);
     }
+    const StencilGrid mg = stencil_grid(P, kMvX, kMvY);
+    // float4 streaming needs whole vectors per map and 16-byte aligned rows
+    const bool vec4 = (P.N % 4 == 0) &&
+                      ((reinterpret_cast<uintptr_t>(B.r) | reinterpret_cast<uintptr_t>(B.q) |
+                        reinterpret_cast<uintptr_t>(B.z) | reinterpret_cast<uintptr_t>(B.R)) % 16 == 0);
+    const int ugrid = vec4 ? update_grid<K, 4>(P.N / 4) : update_grid<K, 1>(P.N);
     for (int k = 0; k < cg_iters; ++k) {
         {
             LaunchScope ls(MPM_KERNEL_PCG_MATVEC, st);
-            k_pcg_matvec<K><<<sg.grid, sg.block, 0, st>>>(P, sg.zc, k, h, w, B, xacc, hdr, red);
+            k_pcg_matvec<K><<<mg.grid, mg.block, 0, st>>>(P, mg.zc, k, h, w, B.z, B.p[(k + 1) & 1],
+                                                           B.p[k & 1], B.q, xacc, hdr, red);
         }
         LaunchScope ls(MPM_KERNEL_PCG_UPDATE, st);
-        k_pcg_update<K><<<sg.grid, sg.block, 0, st>>>(P, sg.zc, k, B, hdr, resid, red);
+        if (vec4)
+            k_pcg_update<K, 4><<<ugrid, kBlock, 0, st>>>(P, k, B, hdr, resid, red);
+        else
+            k_pcg_update<K, 1><<<ugrid, kBlock, 0, st>>>(P, k, B, hdr, resid, red);
     }
     LaunchScope ls(MPM_KERNEL_PCG_FINAL, st);
     k_pcg_final<<<voxel_grid(P.N * K), kBlock, 0, st>>>(P.N * K, B, xacc, delta, y_update, hdr,

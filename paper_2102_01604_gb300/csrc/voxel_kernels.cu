@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kBlock) k_grad_hess(DevProblem P, const XT* __
 {
     constexpr int T = K * (K + 1) / 2;
     const long long N = P.N;
-    double nll_acc = 0.0;
+    Acc nll_acc;
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
          n += (long long)gridDim.x * blockDim.x) {
         float a, r1, r2, dl, m;
@@ -187,9 +187,10 @@ __global__ void __launch_bounds__(kBlock) k_grad_hess(DevProblem P, const XT* __
         for (int k = 0; k < K; ++k) g[k * N + n] = G[k];
 #pragma unroll
         for (int k = 0; k < T; ++k) h[k * N + n] = H[k];
-        nll_acc += (double)nll_v;
+        nll_acc.add(nll_v);
     }
-    double v[1] = {nll_acc}, out[1];
+    Acc v[1] = {nll_acc};
+    double out[1];
     if (grid_reduce<1>(v, red, out) && threadIdx.x == 0) *nll = out[0];
 }
 
@@ -282,12 +283,12 @@ __global__ void __launch_bounds__(kBlock) k_image_means(DevProblem P, const XT* 
     __shared__ double sh[kBlock / 32];
     const long long N = P.N;
     const int i = blockIdx.y;
-    double acc = 0.0;
+    Acc acc;
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
          n += (long long)gridDim.x * blockDim.x)
-        acc += (double)load_echo<XT>(x, i * N + n);
-    acc = block_sum(acc, sh);
-    if (threadIdx.x == 0) partials[i * gridDim.x + blockIdx.x] = acc;
+        acc.add(load_echo<XT>(x, i * N + n));
+    const double tot = block_acc(acc, sh);
+    if (threadIdx.x == 0) partials[i * gridDim.x + blockIdx.x] = tot;
 }
 
 __global__ void __launch_bounds__(kBlock) k_means_final(DevProblem P, const double* partials,
