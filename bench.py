@@ -184,17 +184,18 @@ class ClockSampler:
 
 def algorithmic_bytes(K: int, C: int, I: int, echo_bytes: int = 4):
     """Bytes each kernel must move per voxel (reads + writes of its operands,
-    float32, every array touched once); PCG matvec bytes are per solve."""
+    float32, every array touched once); the PCG direction bytes are per solve
+    (its first launch reads no x)."""
     T = K * (K + 1) // 2
     f = 4
-    mv0 = K * f + T * f + f + 2 * K * f                 # k = 0: read z, H, w; write p, q
-    mv1 = mv0 + K * f + K * f                           # k = 1: + read p_old, write x
-    mvk = mv1 + K * f                                   # k >= 2: + read x
+    dir1 = 2 * K * f + 2 * K * f                        # k = 1: read z, p_old; write p, x
+    dirk = dir1 + K * f                                 # k >= 2: + read x
     return {
         "grad_hess": I * echo_bytes + K * f + f + C * f + K * f + T * f,
         "jtv": K * f + f,
-        "pcg_init": f + 2 * K * f + T * f + T * f + 2 * K * f,
-        "pcg_matvec_per_solve": mv0 + (mv1 if CG_ITERS > 1 else 0) + mvk * max(CG_ITERS - 2, 0),
+        "pcg_init": f + 2 * K * f + T * f + T * f + 3 * K * f,
+        "pcg_direction_per_solve": (dir1 + dirk * max(CG_ITERS - 2, 0)) if CG_ITERS > 1 else 0,
+        "pcg_matvec": K * f + T * f + f + K * f,
         "pcg_update": 2 * K * f + T * f + 2 * K * f,
         "pcg_final": 4 * K * f,
         "uncertainty": T * f + f + K * f,
@@ -208,8 +209,8 @@ def kernel_roofline(prof: dict, n_vox: int, steps: int, K: int, C: int, I: int, 
     for kind, v in prof.items():
         if not v["launches"]:
             continue
-        if kind == "pcg_matvec":
-            total_bytes = ab["pcg_matvec_per_solve"] * n_vox * solves
+        if kind == "pcg_direction":
+            total_bytes = ab["pcg_direction_per_solve"] * n_vox * solves
         elif kind in ab:
             total_bytes = ab[kind] * n_vox * v["launches"]
         else:

@@ -191,13 +191,14 @@ enum {
     MPM_KERNEL_GRAD_HESS = 0,    /* fused voxel pass */
     MPM_KERNEL_JTV = 1,          /* JTV weights */
     MPM_KERNEL_PCG_INIT = 2,     /* r0 = g + L y, preconditioner factor, z0 */
-    MPM_KERNEL_PCG_MATVEC = 3,   /* p update, q = (H + L) p */
+    MPM_KERNEL_PCG_MATVEC = 3,   /* q = (H + L) p */
     MPM_KERNEL_PCG_UPDATE = 4,   /* r update, z = M^-1 r */
     MPM_KERNEL_PCG_FINAL = 5,    /* delta or y update */
     MPM_KERNEL_UNCERTAINTY = 6,
     MPM_KERNEL_FORWARD = 7,
     MPM_KERNEL_INIT = 8,         /* image means and constant maps */
-    MPM_KERNEL_KINDS = 9
+    MPM_KERNEL_PCG_DIRECTION = 9, /* p = z + beta p, x += alpha p */
+    MPM_KERNEL_KINDS = 10
 };
 
 /* Diagnostic timing.  While enabled (on != 0, process-wide), every kernel

@@ -88,7 +88,7 @@ PROTOTYPES = {
 }
 
 KERNEL_KINDS = ["grad_hess", "jtv", "pcg_init", "pcg_matvec", "pcg_update", "pcg_final",
-                "uncertainty", "forward", "init"]
+                "uncertainty", "forward", "init", "pcg_direction"]
 
 _handle = None
 

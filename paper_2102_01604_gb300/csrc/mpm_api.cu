@@ -181,6 +181,18 @@ static DevProblem make_dev(const mpm_problem* p)
     }
     P.I = i;
     for (int j = 0; j < i; ++j) P.te[j] = (float)p->te[j];
+    for (int c = 0; c < P.C; ++c) {
+        const int E = P.n_echoes[c], i0 = P.echo0[c];
+        const double t0 = p->te[i0];
+        const double dt = E > 1 ? (p->te[i0 + E - 1] - t0) / (E - 1) : 0.0;
+        bool uni = true;
+        for (int e = 0; e < E; ++e)
+            if (std::fabs(p->te[i0 + e] - (t0 + e * dt)) > 1e-7 * std::fabs(p->te[i0 + E - 1]) + 1e-12)
+                uni = false;
+        P.te_uniform[c] = uni ? 1 : 0;
+        P.dte[c] = (float)dt;
+        P.same_tr[c] = (c > 0 && p->tr[c] == p->tr[c - 1]) ? 1 : 0;
+    }
     for (int k = 0; k < 4; ++k) P.lambda[k] = (float)p->lambda[k];
     P.eps2 = (float)(p->eps * p->eps);
     P.precond = p->precond;

@@ -30,6 +30,9 @@ struct DevProblem {
     float isig2[MPM_MAX_CONTRASTS];     // 1 / sigma^2
     int mt[MPM_MAX_CONTRASTS];
     float te[MPM_MAX_IMAGES];
+    float dte[MPM_MAX_CONTRASTS];       // echo spacing when the echoes are equally spaced
+    int te_uniform[MPM_MAX_CONTRASTS];  // 1: te = te0 + e * dte for every echo of c
+    int same_tr[MPM_MAX_CONTRASTS];     // 1: tr[c] == tr[c - 1]
     float lambda[4];
     float eps2;
     int precond;

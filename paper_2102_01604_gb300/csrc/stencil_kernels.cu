@@ -1,7 +1,8 @@
 // stencil_kernels.cu -- the prior and the Newton-system solve (sm_103a):
 //   k_jtv          JTV weights w_n = (u_n + eps^2)^-1/2 and JTV_eps (Eqs. 38-40)
 //   k_pcg_init     r_0 = g + L y, preconditioner factor, z_0 = M^-1 r_0 (Eq. 42)
-//   k_pcg_matvec   p_k = z_k + beta p_{k-1}; q = (H + L) p_k; x += alpha p_{k-1}; p.q
+//   k_pcg_direction p_k = z_k + beta p_{k-1}; x += alpha p_{k-1}
+//   k_pcg_matvec   q = (H + L) p_k; p.q
 //   k_pcg_update   r -= alpha q; z = M^-1 r; r.z, r.r
 //   k_pcg_final    delta = x + alpha p (or y <- y - delta)
 //
@@ -227,6 +228,7 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(DevProblem P, int zc, const
             for (int k = 0; k < K; ++k) {
                 B.r[k * N + n] = r[k];
                 B.z[k * N + n] = zz[k];
+                B.p[0][k * N + n] = zz[k];                // p_0 = z_0
                 vrz += r[k] * zz[k];
                 vrr += r[k] * r[k];
             }
@@ -254,42 +256,79 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(DevProblem P, int zc, const
     }
 }
 
-// ------------------------------------------------------------- PCG matvec
+// ---------------------------------------------------------- PCG direction
 
-// Tiled 2.5-D stencil: a block owns a kMvX x kMvY (x, y) tile and marches up a
-// run of z planes.  The direction p_k = z_k + beta p_{k-1} of the current plane
-// (with a one-voxel x/y halo) and the JTV weights are staged in shared memory;
-// the planes below and above live in registers, so every operand is loaded
-// from memory about once per voxel.
-constexpr int kMvX = 16, kMvY = 16;
-
-template <int K>
-__global__ void __launch_bounds__(kMvX * kMvY) k_pcg_matvec(DevProblem P, int zc, int k_it,
-                                                           const float* __restrict__ h,
-                                                           const float* __restrict__ w,
-                                                           const float* __restrict__ zv,
-                                                           const float* __restrict__ pold,
-                                                           float* __restrict__ pnew,
-                                                           float* __restrict__ qout,
-                                                           float* __restrict__ xacc,
-                                                           WsHeader* hdr, Reduce red)
+// p_k = z_k + beta_{k-1} p_{k-1} and x += alpha_{k-1} p_{k-1} (k >= 1), a
+// streaming pass over the K*N entries (float4 when VPT = 4).
+template <int VPT>
+__global__ void __launch_bounds__(kBlock) k_pcg_direction(long long total, int k_it,
+                                                          const float* __restrict__ zv,
+                                                          const float* __restrict__ pold,
+                                                          float* __restrict__ pnew,
+                                                          float* __restrict__ xacc,
+                                                          const WsHeader* hdr)
 {
-    constexpr int T = K * (K + 1) / 2;
-    __shared__ float sp[K][kMvY + 2][kMvX + 2];
-    __shared__ float sw[kMvY + 2][kMvX + 2];
+    using V = typename std::conditional<VPT == 4, float4, float>::type;
     __shared__ float s_beta, s_alpha;
     __shared__ int s_done;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int tid = tx + ty * kMvX;
-    if (tid == 0) {
+    if (threadIdx.x == 0) {
         s_done = hdr->sc.done;
         s_beta = (float)hdr->sc.beta;
         s_alpha = (float)hdr->sc.alpha;
     }
     __syncthreads();
     if (s_done) return;
-    const float beta = s_beta, alpha_prev = s_alpha;
-    const bool has_old = k_it > 0;
+    const float beta = s_beta, alpha = s_alpha;
+    const long long nv = total / VPT;
+    const V* __restrict__ z4 = reinterpret_cast<const V*>(zv);
+    const V* __restrict__ o4 = reinterpret_cast<const V*>(pold);
+    V* __restrict__ p4 = reinterpret_cast<V*>(pnew);
+    V* __restrict__ x4 = reinterpret_cast<V*>(xacc);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nv;
+         i += (long long)gridDim.x * blockDim.x) {
+        const V zz = __ldg(z4 + i);
+        const V o = __ldg(o4 + i);
+        V xo;
+        if (k_it > 1) xo = x4[i];
+        V pv, xv;
+#pragma unroll
+        for (int j = 0; j < VPT; ++j) {
+            const float oj = reinterpret_cast<const float*>(&o)[j];
+            reinterpret_cast<float*>(&pv)[j] = reinterpret_cast<const float*>(&zz)[j] + beta * oj;
+            const float xj = k_it > 1 ? reinterpret_cast<const float*>(&xo)[j] : 0.0f;
+            reinterpret_cast<float*>(&xv)[j] = xj + alpha * oj;
+        }
+        p4[i] = pv;
+        x4[i] = xv;
+    }
+}
+
+// ------------------------------------------------------------- PCG matvec
+
+// q = (H + L) p with p already formed.  Tiled 2.5-D stencil: a block owns a
+// kMvX x kMvY (x, y) tile and marches up a run of z planes; the current plane
+// of p (with a one-voxel x / y halo) and of the JTV weights is staged in
+// shared memory, the planes below and above live in registers, so each
+// operand is read from memory about once per voxel.
+constexpr int kMvX = 16, kMvY = 16;
+
+template <int K>
+__global__ void __launch_bounds__(kMvX * kMvY, 4) k_pcg_matvec(DevProblem P, int zc, int k_it,
+                                                              const float* __restrict__ h,
+                                                              const float* __restrict__ w,
+                                                              const float* __restrict__ pin,
+                                                              float* __restrict__ qout,
+                                                              WsHeader* hdr, Reduce red)
+{
+    constexpr int T = K * (K + 1) / 2;
+    __shared__ float sp[K][kMvY + 2][kMvX + 2];
+    __shared__ float sw[kMvY + 2][kMvX + 2];
+    __shared__ int s_done;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = tx + ty * kMvX;
+    if (tid == 0) s_done = hdr->sc.done;
+    __syncthreads();
+    if (s_done) return;
     const long long N = P.N;
     const int nx = P.nx, ny = P.ny, nz = P.nz;
     const long long sxy = (long long)nx * ny;
@@ -298,54 +337,54 @@ __global__ void __launch_bounds__(kMvX * kMvY) k_pcg_matvec(DevProblem P, int zc
     const int z0 = blockIdx.z * zc;
     const int z1 = min(nz, z0 + zc);
     const bool inside = x < nx && y < ny;
-    const float ihx = P.ihx2, ihy = P.ihy2, ihz = P.ihz2;
-
-    // p_k at voxel n for every map; po receives p_{k-1}
-    auto load_p = [&](long long n, float (&pv)[K], float (&po)[K]) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            const float zz = __ldg(zv + k * N + n);
-            const float o = has_old ? __ldg(pold + k * N + n) : 0.0f;
-            po[k] = o;
-            pv[k] = has_old ? zz + beta * o : zz;
-        }
-    };
-    auto load_p_only = [&](long long n, float (&pv)[K]) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            const float zz = __ldg(zv + k * N + n);
-            pv[k] = has_old ? zz + beta * __ldg(pold + k * N + n) : zz;
-        }
-    };
+    // Halo roles: border threads of the tile also load the neighbour just
+    // outside it (one plane ahead, so the loads overlap the compute).
+    const bool hx = inside && ((tx == 0 && x > 0) || (tx == kMvX - 1 && x + 1 < nx));
+    const bool hy = inside && ((ty == 0 && y > 0) || (ty == kMvY - 1 && y + 1 < ny));
+    const long long ox = tx == 0 ? -1 : 1;
+    const long long oy = ty == 0 ? -(long long)nx : (long long)nx;
+    const int sx = tx == 0 ? 0 : kMvX + 1;
+    const int sy = ty == 0 ? 0 : kMvY + 1;
 
     const long long col = (long long)x + (long long)nx * y;   // (x, y) column offset
-    float pc[K], pp[K], pn[K], oc[K], on[K], dummy[K];
+    float pc[K], pp[K], pn[K], hxv[K + 1], hyv[K + 1];
     float wc = 0.f, wp = 0.f, wn = 0.f;
+    auto load_halo = [&](long long n) {
+        if (hx) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) hxv[k] = __ldg(pin + k * N + n + ox);
+            hxv[K] = __ldg(w + n + ox);
+        }
+        if (hy) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) hyv[k] = __ldg(pin + k * N + n + oy);
+            hyv[K] = __ldg(w + n + oy);
+        }
+    };
     if (inside) {
         const long long n0 = col + sxy * z0;
-        load_p(n0, pc, oc);
+#pragma unroll
+        for (int k = 0; k < K; ++k) pc[k] = __ldg(pin + k * N + n0);
         wc = __ldg(w + n0);
+        load_halo(n0);
         if (z0 > 0) {
-            load_p_only(n0 - sxy, pp);
+#pragma unroll
+            for (int k = 0; k < K; ++k) pp[k] = __ldg(pin + k * N + n0 - sxy);
             wp = __ldg(w + n0 - sxy);
         }
         if (z0 + 1 < nz) {
-            load_p(n0 + sxy, pn, on);
+#pragma unroll
+            for (int k = 0; k < K; ++k) pn[k] = __ldg(pin + k * N + n0 + sxy);
             wn = __ldg(w + n0 + sxy);
         }
     }
-    (void)dummy;
     Acc pq;
     for (int z = z0; z < z1; ++z) {
         const long long n = col + sxy * z;
-        float Hn[T], xo[K];
+        float Hn[T];
         if (inside) {
 #pragma unroll
             for (int t = 0; t < T; ++t) Hn[t] = __ldg(h + t * N + n);
-            if (k_it > 1) {
-#pragma unroll
-                for (int k = 0; k < K; ++k) xo[k] = xacc[k * N + n];
-            }
         }
         // stage the current plane (own value and x / y halo) in shared memory
         __syncthreads();
@@ -353,90 +392,67 @@ __global__ void __launch_bounds__(kMvX * kMvY) k_pcg_matvec(DevProblem P, int zc
 #pragma unroll
             for (int k = 0; k < K; ++k) sp[k][ty + 1][tx + 1] = pc[k];
             sw[ty + 1][tx + 1] = wc;
-            if (tx == 0 && x > 0) {
-                float hv[K];
-                load_p_only(n - 1, hv);
+            if (hx) {
 #pragma unroll
-                for (int k = 0; k < K; ++k) sp[k][ty + 1][0] = hv[k];
-                sw[ty + 1][0] = __ldg(w + n - 1);
+                for (int k = 0; k < K; ++k) sp[k][ty + 1][sx] = hxv[k];
+                sw[ty + 1][sx] = hxv[K];
             }
-            if (tx == kMvX - 1 && x + 1 < nx) {
-                float hv[K];
-                load_p_only(n + 1, hv);
+            if (hy) {
 #pragma unroll
-                for (int k = 0; k < K; ++k) sp[k][ty + 1][kMvX + 1] = hv[k];
-                sw[ty + 1][kMvX + 1] = __ldg(w + n + 1);
-            }
-            if (ty == 0 && y > 0) {
-                float hv[K];
-                load_p_only(n - nx, hv);
-#pragma unroll
-                for (int k = 0; k < K; ++k) sp[k][0][tx + 1] = hv[k];
-                sw[0][tx + 1] = __ldg(w + n - nx);
-            }
-            if (ty == kMvY - 1 && y + 1 < ny) {
-                float hv[K];
-                load_p_only(n + nx, hv);
-#pragma unroll
-                for (int k = 0; k < K; ++k) sp[k][kMvY + 1][tx + 1] = hv[k];
-                sw[kMvY + 1][tx + 1] = __ldg(w + n + nx);
+                for (int k = 0; k < K; ++k) sp[k][sy][tx + 1] = hyv[k];
+                sw[sy][tx + 1] = hyv[K];
             }
         }
         __syncthreads();
         if (inside) {
+            // prefetch the next plane's halo and the plane after it
+            const bool more = z + 1 < z1;
+            if (more) load_halo(n + sxy);
+            float pn_keep[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) pn_keep[k] = pn[k];
+            const float wn_keep = wn;
+            if (more && z + 2 < nz) {
+                const long long n2 = n + 2 * sxy;
+#pragma unroll
+                for (int k = 0; k < K; ++k) pn[k] = __ldg(pin + k * N + n2);
+                wn = __ldg(w + n2);
+            }
             // edge coefficients (w_n + w_m) / h^2 of the six neighbours
             const bool okxm = x > 0, okxp = x + 1 < nx, okym = y > 0, okyp = y + 1 < ny;
             const bool okzm = z > 0, okzp = z + 1 < nz;
-            const float cxm = okxm ? (wc + sw[ty + 1][tx]) * ihx : 0.f;
-            const float cxp = okxp ? (wc + sw[ty + 1][tx + 2]) * ihx : 0.f;
-            const float cym = okym ? (wc + sw[ty][tx + 1]) * ihy : 0.f;
-            const float cyp = okyp ? (wc + sw[ty + 2][tx + 1]) * ihy : 0.f;
-            const float czm = okzm ? (wc + wp) * ihz : 0.f;
-            const float czp = okzp ? (wc + wn) * ihz : 0.f;
-            float q[K];
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                const float v = pc[k];
-                float s = 0.f;
-                if (okxm) s += cxm * (v - sp[k][ty + 1][tx]);
-                if (okxp) s += cxp * (v - sp[k][ty + 1][tx + 2]);
-                if (okym) s += cym * (v - sp[k][ty][tx + 1]);
-                if (okyp) s += cyp * (v - sp[k][ty + 2][tx + 1]);
-                if (okzm) s += czm * (v - pp[k]);
-                if (okzp) s += czp * (v - pn[k]);
-                q[k] = P.lambda[k] * s;
-            }
-#pragma unroll
-            for (int a = 0; a < K; ++a) {
-                float acc = q[a];
-#pragma unroll
-                for (int b = 0; b < K; ++b) acc += Hn[a < b ? tri(K, a, b) : tri(K, b, a)] * pc[b];
-                q[a] = acc;
-            }
+            const float cxm = okxm ? (wc + sw[ty + 1][tx]) * P.ihx2 : 0.f;
+            const float cxp = okxp ? (wc + sw[ty + 1][tx + 2]) * P.ihx2 : 0.f;
+            const float cym = okym ? (wc + sw[ty][tx + 1]) * P.ihy2 : 0.f;
+            const float cyp = okyp ? (wc + sw[ty + 2][tx + 1]) * P.ihy2 : 0.f;
+            const float czm = okzm ? (wc + wp) * P.ihz2 : 0.f;
+            const float czp = okzp ? (wc + wn_keep) * P.ihz2 : 0.f;
             float vpq = 0.0f;
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                pnew[k * N + n] = pc[k];
-                qout[k * N + n] = q[k];
-                vpq += pc[k] * q[k];
-                // fold the previous iteration's step into x
-                if (k_it == 1) xacc[k * N + n] = alpha_prev * oc[k];
-                else if (k_it > 1) xacc[k * N + n] = xo[k] + alpha_prev * oc[k];
+            for (int a = 0; a < K; ++a) {
+                const float v = pc[a];
+                float s = 0.f;
+                if (okxm) s += cxm * (v - sp[a][ty + 1][tx]);
+                if (okxp) s += cxp * (v - sp[a][ty + 1][tx + 2]);
+                if (okym) s += cym * (v - sp[a][ty][tx + 1]);
+                if (okyp) s += cyp * (v - sp[a][ty + 2][tx + 1]);
+                if (okzm) s += czm * (v - pp[a]);
+                if (okzp) s += czp * (v - pn_keep[a]);
+                float acc = P.lambda[a] * s;
+#pragma unroll
+                for (int b = 0; b < K; ++b) acc += Hn[a < b ? tri(K, a, b) : tri(K, b, a)] * pc[b];
+                qout[a * N + n] = acc;
+                vpq += v * acc;
             }
             pq.add(vpq);
             // march: the plane above becomes current
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 pp[k] = pc[k];
-                pc[k] = pn[k];
-                oc[k] = on[k];
+                pc[k] = pn_keep[k];
             }
             wp = wc;
-            wc = wn;
-            if (z + 2 < nz && z + 1 < z1) {
-                load_p(n + 2 * sxy, pn, on);
-                wn = __ldg(w + n + 2 * sxy);
-            }
+            wc = wn_keep;
         }
     }
     Acc v[1] = {pq};
@@ -634,13 +650,24 @@ static cudaError_t solve_k(const DevProblem& P, int cg_iters, double tol_cg, con
     // float4 streaming needs whole vectors per map and 16-byte aligned rows
     const bool vec4 = (P.N % 4 == 0) &&
                       ((reinterpret_cast<uintptr_t>(B.r) | reinterpret_cast<uintptr_t>(B.q) |
-                        reinterpret_cast<uintptr_t>(B.z) | reinterpret_cast<uintptr_t>(B.R)) % 16 == 0);
+                        reinterpret_cast<uintptr_t>(B.z) | reinterpret_cast<uintptr_t>(B.R) |
+                        reinterpret_cast<uintptr_t>(B.p[0]) | reinterpret_cast<uintptr_t>(B.p[1]) |
+                        reinterpret_cast<uintptr_t>(xacc)) % 16 == 0);
     const int ugrid = vec4 ? update_grid<K, 4>(P.N / 4) : update_grid<K, 1>(P.N);
+    const long long KN = (long long)K * P.N;
+    const int dgrid = voxel_grid(vec4 ? KN / 4 : KN);
     for (int k = 0; k < cg_iters; ++k) {
+        float* pk = B.p[k & 1];
+        if (k > 0) {
+            LaunchScope ls(MPM_KERNEL_PCG_DIRECTION, st);
+            if (vec4)
+                k_pcg_direction<4><<<dgrid, kBlock, 0, st>>>(KN, k, B.z, B.p[(k + 1) & 1], pk, xacc, hdr);
+            else
+                k_pcg_direction<1><<<dgrid, kBlock, 0, st>>>(KN, k, B.z, B.p[(k + 1) & 1], pk, xacc, hdr);
+        }
         {
             LaunchScope ls(MPM_KERNEL_PCG_MATVEC, st);
-            k_pcg_matvec<K><<<mg.grid, mg.block, 0, st>>>(P, mg.zc, k, h, w, B.z, B.p[(k + 1) & 1],
-                                                           B.p[k & 1], B.q, xacc, hdr, red);
+            k_pcg_matvec<K><<<mg.grid, mg.block, 0, st>>>(P, mg.zc, k, h, w, pk, B.q, hdr, red);
         }
         LaunchScope ls(MPM_KERNEL_PCG_UPDATE, st);
         if (vec4)

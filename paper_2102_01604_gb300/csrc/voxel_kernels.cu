@@ -25,17 +25,29 @@ struct ContrastTerms {
     float s0, q1, qd, h1, hd, cross;
 };
 
+// Longitudinal relaxation over one TR: tt = r1 TR, E = exp(-tt), omE = 1 - E.
+struct Relax {
+    float tt, E, omE;
+};
+
+__device__ __forceinline__ Relax relax(float tr, float r1)
+{
+    Relax R;
+    R.tt = tr * r1;
+    R.E = expf(-R.tt);
+    R.omE = -expm1f(-R.tt);
+    return R;
+}
+
 __device__ __forceinline__ ContrastTerms contrast_terms(const DevProblem& P, int c, float a,
-                                                        float r1, float dl, float m,
+                                                        const Relax& R, float dl, float m,
                                                         float bp, float bm)
 {
     ContrastTerms t;
     float sa, ca;
     sincosf(P.alpha[c] * bp, &sa, &ca);
-    const float omc = sa * sa / (1.0f + ca);
-    const float tt = P.tr[c] * r1;
-    const float E = expf(-tt);
-    const float omE = -expm1f(-tt);
+    const float omc = __fdividef(sa * sa, 1.0f + ca);
+    const float tt = R.tt, E = R.E, omE = R.omE;
     const bool mt = P.mt[c] != 0;
     const float d = mt ? dl : 0.0f;
     const float mm = mt ? m : 1.0f;
@@ -43,7 +55,7 @@ __device__ __forceinline__ ContrastTerms contrast_terms(const DevProblem& P, int
     const float D = omE + E * omcm;                  // 1 - m cos(a) E
     const float iD = 1.0f / D;
     t.s0 = bm * a * sa * mm * omE * iD;
-    t.q1 = tt * E * omcm * iD / omE;
+    t.q1 = __fdividef(tt * E * omcm * iD, omE);
     t.qd = mt ? -d * iD : 0.0f;
     t.h1 = 1.0f - tt * (2.0f - D) * iD;              // 1 + m cos(a) E = 2 - D
     t.hd = 2.0f * mm * (omE + E * omc) * iD - 1.0f;  // 1 - cos(a) E = (1-E) + E (1 - cos a)
@@ -51,6 +63,8 @@ __device__ __forceinline__ ContrastTerms contrast_terms(const DevProblem& P, int
     return t;
 }
 
+// exp of the log-parameters; delta = logistic(y_delta) and m = 1 - delta from
+// one exponential of -|y_delta| (no overflow, no cancellation).
 __device__ __forceinline__ void map_params(const float* __restrict__ y, long long N,
                                            long long n, int K, float& a, float& r1,
                                            float& r2, float& dl, float& m)
@@ -62,8 +76,11 @@ __device__ __forceinline__ void map_params(const float* __restrict__ y, long lon
     m = 1.0f;
     if (K == 4) {
         const float yd = __ldg(y + 3 * N + n);
-        dl = 1.0f / (1.0f + expf(-yd));
-        m = 1.0f / (1.0f + expf(yd));
+        const float e = expf(-fabsf(yd));
+        const float i1 = 1.0f / (1.0f + e);
+        const float big = i1, small = e * i1;
+        dl = yd >= 0.0f ? big : small;
+        m = yd >= 0.0f ? small : big;
     }
 }
 
@@ -82,7 +99,7 @@ __global__ void __launch_bounds__(kBlock) k_forward(DevProblem P, const float* _
         const float bp = b1p ? __ldg(b1p + n) : 1.0f;
         for (int c = 0; c < P.C; ++c) {
             const float bm = b1m ? __ldg(b1m + c * N + n) : 1.0f;
-            const ContrastTerms t = contrast_terms(P, c, a, r1, dl, m, bp, bm);
+            const ContrastTerms t = contrast_terms(P, c, a, relax(P.tr[c], r1), dl, m, bp, bm);
             const int i0 = P.echo0[c];
             for (int e = 0; e < P.n_echoes[c]; ++e)
                 s[(i0 + e) * N + n] = t.s0 * expf(-P.te[i0 + e] * r2);
@@ -123,16 +140,34 @@ __global__ void __launch_bounds__(kBlock) k_grad_hess(DevProblem P, const XT* __
 #pragma unroll
         for (int k = 0; k < T; ++k) H[k] = 0.0f;
         float nll_v = 0.0f;
+        Relax R{0.f, 0.f, 0.f};
         for (int c = 0; c < P.C; ++c) {
             const float bm = b1m ? __ldg(b1m + c * N + n) : 1.0f;
-            const ContrastTerms t = contrast_terms(P, c, a, r1, dl, m, bp, bm);
+            if (!P.same_tr[c]) R = relax(P.tr[c], r1);
+            const ContrastTerms t = contrast_terms(P, c, a, R, dl, m, bp, bm);
             float S0 = 0.f, S1 = 0.f, S2 = 0.f, R0 = 0.f, R1 = 0.f, N2 = 0.f;
             float A0 = 0.f, A2 = 0.f, B1 = 0.f;
             const int i0 = P.echo0[c];
-            for (int e = 0; e < P.n_echoes[c]; ++e) {
-                const float q2 = -P.te[i0 + e] * r2;
-                const float s = t.s0 * expf(q2);
-                const float r = s - load_echo<XT>(x, (i0 + e) * N + n);
+            const int ne = P.n_echoes[c];
+            const XT* xp = x + (long long)i0 * N + n;
+            // equally spaced echoes: s_e = s_0 exp(-TE_0 r2) rho^e, rho = exp(-dTE r2)
+            const bool uni = P.te_uniform[c] != 0;
+            const float dq = -P.dte[c] * r2;
+            const float rho = uni ? expf(dq) : 0.0f;
+            float q2 = -P.te[i0] * r2;
+            float s = t.s0 * expf(q2);
+            for (int e = 0; e < ne; ++e) {
+                if (e > 0) {
+                    if (uni) {
+                        q2 += dq;
+                        s *= rho;
+                    } else {
+                        q2 = -P.te[i0 + e] * r2;
+                        s = t.s0 * expf(q2);
+                    }
+                }
+                const float r = s - load_echo<XT>(xp, 0);
+                xp += N;
                 const float ss = s * s;
                 S0 += ss;
                 S1 += ss * q2;
@@ -199,6 +234,7 @@ __global__ void __launch_bounds__(kBlock) k_grad_hess(DevProblem P, const XT* __
 // Block n of the preconditioner, M = H_n + diag(lambda_k d_n) with
 // d_n = sum_{m in N(n)} (w_n + w_m) / h^2, inverted in float64 through its
 // Cholesky factor: var_k = sum_j (L^-1)_{jk}^2, logdet = -2 sum log L_kk.
+template <int K>
 __global__ void __launch_bounds__(kBlock) k_uncertainty(DevProblem P, const float* __restrict__ h,
                                                         const float* __restrict__ w,
                                                         const float* __restrict__ y,
@@ -208,62 +244,75 @@ __global__ void __launch_bounds__(kBlock) k_uncertainty(DevProblem P, const floa
                                                         unsigned* status)
 {
     const long long N = P.N;
-    const int K = P.K;
     const long long sxy = (long long)P.nx * P.ny;
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
          n += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(n % P.nx);
         const int yy = (int)((n / P.nx) % P.ny);
         const int z = (int)(n / sxy);
-        const double wn = w[n];
+        const double wn = __ldg(w + n);
         double d = 0.0;
-        if (x > 0) d += (wn + w[n - 1]) * P.ihx2;
-        if (x < P.nx - 1) d += (wn + w[n + 1]) * P.ihx2;
-        if (yy > 0) d += (wn + w[n - P.nx]) * P.ihy2;
-        if (yy < P.ny - 1) d += (wn + w[n + P.nx]) * P.ihy2;
-        if (z > 0) d += (wn + w[n - sxy]) * P.ihz2;
-        if (z < P.nz - 1) d += (wn + w[n + sxy]) * P.ihz2;
-        double M[4][4], L[4][4];
+        if (x > 0) d += (wn + __ldg(w + n - 1)) * P.ihx2;
+        if (x < P.nx - 1) d += (wn + __ldg(w + n + 1)) * P.ihx2;
+        if (yy > 0) d += (wn + __ldg(w + n - P.nx)) * P.ihy2;
+        if (yy < P.ny - 1) d += (wn + __ldg(w + n + P.nx)) * P.ihy2;
+        if (z > 0) d += (wn + __ldg(w + n - sxy)) * P.ihz2;
+        if (z < P.nz - 1) d += (wn + __ldg(w + n + sxy)) * P.ihz2;
+        double M[K][K], L[K][K];
+#pragma unroll
         for (int a = 0; a < K; ++a)
-            for (int b = a; b < K; ++b) M[a][b] = M[b][a] = h[tri(K, a, b) * N + n];
+#pragma unroll
+            for (int b = a; b < K; ++b) M[a][b] = M[b][a] = __ldg(h + tri(K, a, b) * N + n);
+#pragma unroll
         for (int a = 0; a < K; ++a) M[a][a] += (double)P.lambda[a] * d;
         bool ok = true;
+        double ld = 0.0;
+#pragma unroll
         for (int j = 0; j < K; ++j) {
             double s = M[j][j];
+#pragma unroll
             for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
             if (!(s > 0.0)) { ok = false; s = 1e-300; }
             L[j][j] = sqrt(s);
+            ld += log(L[j][j]);
+            const double inv = 1.0 / L[j][j];
+#pragma unroll
             for (int i = j + 1; i < K; ++i) {
                 double v = M[i][j];
+#pragma unroll
                 for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
-                L[i][j] = v / L[j][j];
+                L[i][j] = v * inv;
             }
         }
         if (!ok && status) atomicOr(status, kStatusNotPD);
         // inverse of the lower factor, column by column
-        double Li[4][4];
+        double Li[K][K];
+#pragma unroll
         for (int j = 0; j < K; ++j) {
+#pragma unroll
             for (int i = 0; i < K; ++i) Li[i][j] = 0.0;
             Li[j][j] = 1.0 / L[j][j];
+#pragma unroll
             for (int i = j + 1; i < K; ++i) {
                 double v = 0.0;
+#pragma unroll
                 for (int k = j; k < i; ++k) v -= L[i][k] * Li[k][j];
                 Li[i][j] = v / L[i][i];
             }
         }
-        double ld = 0.0;
+        double var1 = 0.0;
+#pragma unroll
         for (int k = 0; k < K; ++k) {
             double v = 0.0;
+#pragma unroll
             for (int j = k; j < K; ++j) v += Li[j][k] * Li[j][k];
             var[k * N + n] = (float)v;
-            ld += log(L[k][k]);
+            if (k == 1) var1 = v;
         }
         if (logdet) logdet[n] = (float)(-2.0 * ld);
         if (moments && y) {
-            double s2 = 0.0;
-            for (int j = 1; j < K; ++j) s2 += Li[j][1] * Li[j][1];
-            const double lr1 = y[N + n];
-            const double es2 = exp(s2);
+            const double lr1 = __ldg(y + N + n);
+            const double es2 = exp(var1);
             moments[n] = (float)(sqrt(es2) * exp(lr1));
             moments[N + n] = (float)((es2 - 1.0) * es2 * exp(2.0 * lr1));
             moments[2 * N + n] = (float)(sqrt(es2) * exp(-lr1));
@@ -368,8 +417,12 @@ cudaError_t launch_uncertainty(const DevProblem& P, const float* h, const float*
                                unsigned* status, cudaStream_t st)
 {
     LaunchScope ls(MPM_KERNEL_UNCERTAINTY, st);
-    k_uncertainty<<<voxel_grid(P.N), kBlock, 0, st>>>(P, h, w, y, var, logdet, moments,
-                                                       status);
+    if (P.K == 4)
+        k_uncertainty<4><<<voxel_grid(P.N), kBlock, 0, st>>>(P, h, w, y, var, logdet, moments,
+                                                              status);
+    else
+        k_uncertainty<3><<<voxel_grid(P.N), kBlock, 0, st>>>(P, h, w, y, var, logdet, moments,
+                                                              status);
     return cudaGetLastError();
 }
 
