@@ -70,7 +70,7 @@ int voxel_grid(long long N)
 
 static thread_local std::string t_err;
 
-static mpm_status fail(mpm_status s, const char* fmt, ...)
+mpm_status fail(mpm_status s, const char* fmt, ...)
 {
     char buf[512];
     va_list ap;
@@ -98,7 +98,7 @@ static int n_images(const mpm_problem* p)
     return I;
 }
 
-static mpm_status check_problem(const mpm_problem* p)
+mpm_status check_problem(const mpm_problem* p)
 {
     if (!p) return fail(MPM_ERR_INVALID_ARG, "problem is NULL");
     if (p->nx < 0 || p->ny < 0 || p->nz < 0)
@@ -141,7 +141,7 @@ static mpm_status check_problem(const mpm_problem* p)
     return MPM_OK;
 }
 
-static mpm_status check_opts(const mpm_opts* o)
+mpm_status check_opts(const mpm_opts* o)
 {
     if (!o) return fail(MPM_ERR_INVALID_ARG, "opts is NULL");
     if (o->gn_iters < 0 || o->gn_iters > MPM_MAX_REPORT)
@@ -155,7 +155,7 @@ static mpm_status check_opts(const mpm_opts* o)
     return MPM_OK;
 }
 
-static DevProblem make_dev(const mpm_problem* p)
+DevProblem make_dev(const mpm_problem* p)
 {
     DevProblem P;
     memset(&P, 0, sizeof P);
@@ -201,7 +201,7 @@ static DevProblem make_dev(const mpm_problem* p)
 
 // Device (or managed) memory check: a host pointer handed to a kernel would
 // fault, so it is refused here.
-static mpm_status check_dev(const void* ptr, const char* name, bool optional, size_t align)
+mpm_status check_dev(const void* ptr, const char* name, bool optional, size_t align)
 {
     if (!ptr) {
         if (optional) return MPM_OK;
@@ -230,8 +230,6 @@ static mpm_status check_dev(const void* ptr, const char* name, bool optional, si
 
 static size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
 
-constexpr size_t kHeaderBytes = 4096;
-constexpr size_t kPartialBytes = sizeof(double) * 2 * kMaxBlocks;
 constexpr int kMeanBlocksHost = 304;   // must match the launcher's cap
 
 struct FitWs {

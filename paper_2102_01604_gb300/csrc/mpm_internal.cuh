@@ -255,4 +255,16 @@ cudaError_t launch_solve(const DevProblem& P, int cg_iters, double tol_cg, const
                          cudaStream_t st);
 size_t solve_ws_bytes(const DevProblem& P);
 
+// ------------------------------------------- host helpers of the entry points
+// (mpm_api.cu)
+
+constexpr size_t kHeaderBytes = 4096;                              // WsHeader, padded
+constexpr size_t kPartialBytes = sizeof(double) * 2 * kMaxBlocks;  // reduction partials
+
+mpm_status fail(mpm_status s, const char* fmt, ...);
+mpm_status check_problem(const mpm_problem* p);
+mpm_status check_opts(const mpm_opts* o);
+mpm_status check_dev(const void* ptr, const char* name, bool optional, size_t align);
+DevProblem make_dev(const mpm_problem* p);
+
 }  // namespace mpm
