@@ -159,6 +159,34 @@ mpm_status mpm_solve(const mpm_problem* problem, const mpm_opts* opts, const flo
                      const float* w, const float* g, const float* y, float* delta,
                      double* resid, void* ws, size_t ws_bytes, void* stream);
 
+/* mpm_solve without a caller workspace (the paper has no counterpart: this is
+ * an interface for callers that cannot allocate device memory).  Some callers
+ * cannot call cudaMalloc at all: code running inside another framework's
+ * memory pool that owns the whole device, real-time pipelines that reserve
+ * every byte up front, or paths that must not hit cudaMalloc's implicit device
+ * synchronisation.  This entry point takes the same arguments as mpm_solve
+ * minus (ws, ws_bytes), and keeps its scratch in a fixed 64 MiB device array
+ * owned by the library.  Every GPU that loads the library holds that array
+ * until the process exits.
+ *  - Size limit: problems whose solve scratch exceeds 64 MiB (about 550 000
+ *    voxels with four maps, e.g. 80^3) are refused with
+ *    MPM_ERR_WORKSPACE_TOO_SMALL and a message giving the bytes needed; use
+ *    mpm_solve with a workspace for those.
+ *  - Allocates nothing: no cudaMalloc, no cudaFree, no allocating library
+ *    routine.  The first call on each device looks up the array's device
+ *    address (cudaGetSymbolAddress, with that device current); make that
+ *    first call before any stream capture.
+ *  - Shared state: all calls on a device share the one array, which keeps the
+ *    last call's contents (the call clears what must start at zero).  Calls
+ *    whose work overlaps on the GPU (other streams, other threads) race on it
+ *    and must be serialised by the caller.
+ * Numeric failures are not readable through mpm_workspace_status here; a NaN
+ * or non positive definite block shows as non-finite entries of delta and
+ * resid. */
+mpm_status mpm_solve_static(const mpm_problem* problem, const mpm_opts* opts, const float* h,
+                            const float* w, const float* g, const float* y, float* delta,
+                            double* resid, void* stream);
+
 /* Laplace uncertainty (Sec. 3.6, Eqs. 43-47): var[K][N] = diagonal of
  * (H_n + diag(G'WG)_n lambda)^-1, computed in float64; logdet[N] (or NULL) =
  * log-determinant of that covariance block; moments[4][N] (or NULL; needs y)

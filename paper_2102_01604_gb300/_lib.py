@@ -78,6 +78,7 @@ PROTOTYPES = {
     "mpm_grad_hess": (ctypes.c_int, [_P, _V, _V, _V, _V, _V, _V, _V, _V, _S, _V]),
     "mpm_jtv_weights": (ctypes.c_int, [_P, _V, _V, _V, _V, _S, _V]),
     "mpm_solve": (ctypes.c_int, [_P, _O, _V, _V, _V, _V, _V, _V, _V, _S, _V]),
+    "mpm_solve_static": (ctypes.c_int, [_P, _O, _V, _V, _V, _V, _V, _V, _V]),
     "mpm_uncertainty": (ctypes.c_int, [_P, _V, _V, _V, _V, _V, _V, _V]),
     "mpm_fit": (ctypes.c_int, [_P, _O, _V, _V, _V, _V, _V, _V, _S, ctypes.POINTER(Report), _V]),
     "mpm_workspace_status": (ctypes.c_int, [_V, _S, _V]),
