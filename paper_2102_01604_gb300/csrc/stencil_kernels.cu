@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(kBlock) k_pcg_direction(long long total, int k
 constexpr int kMvX = 16, kMvY = 16;
 
 template <int K>
-__global__ void __launch_bounds__(kMvX * kMvY, 4) k_pcg_matvec(DevProblem P, int zc, int k_it,
+__global__ void __launch_bounds__(kMvX * kMvY, 3) k_pcg_matvec(DevProblem P, int zc, int k_it,
                                                               const float* __restrict__ h,
                                                               const float* __restrict__ w,
                                                               const float* __restrict__ pin,
@@ -378,14 +378,18 @@ __global__ void __launch_bounds__(kMvX * kMvY, 4) k_pcg_matvec(DevProblem P, int
             wn = __ldg(w + n0 + sxy);
         }
     }
+    float Hnext[T];
+    if (inside) {
+        const long long n0 = col + sxy * z0;
+#pragma unroll
+        for (int t = 0; t < T; ++t) Hnext[t] = __ldg(h + t * N + n0);
+    }
     Acc pq;
     for (int z = z0; z < z1; ++z) {
         const long long n = col + sxy * z;
         float Hn[T];
-        if (inside) {
 #pragma unroll
-            for (int t = 0; t < T; ++t) Hn[t] = __ldg(h + t * N + n);
-        }
+        for (int t = 0; t < T; ++t) Hn[t] = Hnext[t];
         // stage the current plane (own value and x / y halo) in shared memory
         __syncthreads();
         if (inside) {
@@ -412,6 +416,10 @@ __global__ void __launch_bounds__(kMvX * kMvY, 4) k_pcg_matvec(DevProblem P, int
 #pragma unroll
             for (int k = 0; k < K; ++k) pn_keep[k] = pn[k];
             const float wn_keep = wn;
+            if (more) {
+#pragma unroll
+                for (int t = 0; t < T; ++t) Hnext[t] = __ldg(h + t * N + n + sxy);
+            }
             if (more && z + 2 < nz) {
                 const long long n2 = n + 2 * sxy;
 #pragma unroll
