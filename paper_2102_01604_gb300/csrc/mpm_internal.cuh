@@ -3,6 +3,7 @@
 // C ABI (include/mpm.h).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -45,7 +46,7 @@ __host__ __device__ constexpr int tri(int K, int a, int b)
 }
 
 // Status bits recorded on the device.
-enum : unsigned { kStatusNotPD = 1u, kStatusNaN = 2u };
+enum : unsigned { kStatusNotPD = 1u, kStatusNaN = 2u, kStatusTimeout = 4u };
 
 // Device scalars of one PCG solve (lives in the workspace).
 struct SolveScalars {
@@ -254,6 +255,18 @@ cudaError_t launch_solve(const DevProblem& P, int cg_iters, double tol_cg, const
                          int* report_it, void* solve_ws, WsHeader* hdr, Reduce red,
                          cudaStream_t st);
 size_t solve_ws_bytes(const DevProblem& P);
+
+// TMA-staged stencil matvec (stencil_tma.cu).  make_tma_maps returns false
+// when the volume or the pointers do not meet the copy engine's alignment
+// rules; the shared-memory kernel is used then.
+struct TmaMaps {
+    CUtensorMap p[2], w, h;
+};
+bool make_tma_maps(const DevProblem& P, const float* h, const float* w, const float* p0,
+                   const float* p1, TmaMaps* out);
+StencilGrid tma_grid(const DevProblem& P);
+cudaError_t launch_matvec_tma(const DevProblem& P, const StencilGrid& g, const TmaMaps& m,
+                              int k_it, float* q, WsHeader* hdr, Reduce red, cudaStream_t st);
 
 // ------------------------------------------- host helpers of the entry points
 // (mpm_api.cu)

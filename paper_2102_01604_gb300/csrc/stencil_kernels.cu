@@ -655,6 +655,9 @@ static cudaError_t solve_k(const DevProblem& P, int cg_iters, double tol_cg, con
         k_pcg_init<K><<<sg.grid, sg.block, 0, st>>>(P, sg.zc, h, w, g, y, B, tol2, hdr, resid, red);
     }
     const StencilGrid mg = stencil_grid(P, kMvX, kMvY);
+    TmaMaps maps;
+    const bool tma = make_tma_maps(P, h, w, B.p[0], B.p[1], &maps);
+    const StencilGrid tg = tma ? tma_grid(P) : mg;
     // float4 streaming needs whole vectors per map and 16-byte aligned rows
     const bool vec4 = (P.N % 4 == 0) &&
                       ((reinterpret_cast<uintptr_t>(B.r) | reinterpret_cast<uintptr_t>(B.q) |
@@ -675,7 +678,12 @@ static cudaError_t solve_k(const DevProblem& P, int cg_iters, double tol_cg, con
         }
         {
             LaunchScope ls(MPM_KERNEL_PCG_MATVEC, st);
-            k_pcg_matvec<K><<<mg.grid, mg.block, 0, st>>>(P, mg.zc, k, h, w, pk, B.q, hdr, red);
+            if (tma) {
+                cudaError_t e = launch_matvec_tma(P, tg, maps, k, B.q, hdr, red, st);
+                if (e != cudaSuccess) return e;
+            } else {
+                k_pcg_matvec<K><<<mg.grid, mg.block, 0, st>>>(P, mg.zc, k, h, w, pk, B.q, hdr, red);
+            }
         }
         LaunchScope ls(MPM_KERNEL_PCG_UPDATE, st);
         if (vec4)
