@@ -37,6 +37,7 @@ if ROOT not in sys.path:
 METRIC = "Mvoxel·GN-iter/s, 1mm MPM JTV fit"
 UNIT = "Mvoxel·GN-iter/s"
 SHAPE = (176, 240, 256)
+VX = (1.0, 1.0, 1.0)
 GN_ITERS = 20
 CG_ITERS = 30
 LAMBDA = 10.0
@@ -60,9 +61,15 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--shape", default=None,
                     help="override the volume (nx,ny,nz) for profiling runs on a smaller case")
+    ap.add_argument("--echo-dtype", choices=["f32", "bf16"], default="f32",
+                    help="storage of the echo images (computation stays float32)")
+    ap.add_argument("--config", choices=["1mm", "0.8mm"], default="1mm",
+                    help="1mm: 176x240x256 at 1 mm; 0.8mm: 208x300x320 at 0.8 mm")
     args = ap.parse_args(argv)
+    global SHAPE, VX
+    if args.config == "0.8mm":
+        SHAPE, VX = (208, 300, 320), (0.8, 0.8, 0.8)
     if args.shape:
-        global SHAPE
         SHAPE = tuple(int(v) for v in args.shape.split(","))
         assert len(SHAPE) == 3
     return args
@@ -93,7 +100,7 @@ def aggregate(seconds: float, units: float, world: int, backend_device=None):
 
 # --------------------------------------------------------------- inputs
 
-def workload_inputs(seed: int, device):
+def workload_inputs(seed: int, device, echo_dtype: str = "f32"):
     """Phantom maps and B1 fields on the host, noise-free images from the
     library's own forward model on the GPU, Rician noise drawn on the GPU."""
     import torch
@@ -116,6 +123,8 @@ def workload_inputs(seed: int, device):
     prot["sigma2"] = sig2
     x = phantom.rician_torch(s, prot, seed + 1)
     del s
+    if echo_dtype == "bf16":
+        x = x.to(torch.bfloat16)
     torch.cuda.synchronize()
     return prot, ph, x, b1p, b1m
 
@@ -202,8 +211,9 @@ def algorithmic_bytes(K: int, C: int, I: int, echo_bytes: int = 4):
     }
 
 
-def kernel_roofline(prof: dict, n_vox: int, steps: int, K: int, C: int, I: int, peak_gbs: float):
-    ab = algorithmic_bytes(K, C, I)
+def kernel_roofline(prof: dict, n_vox: int, steps: int, K: int, C: int, I: int, peak_gbs: float,
+                    echo_bytes: int = 4):
+    ab = algorithmic_bytes(K, C, I, echo_bytes)
     solves = steps * GN_ITERS
     per_kernel = {}
     for kind, v in prof.items():
@@ -343,8 +353,9 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     seed = args.seed + 1000 * rank
 
-    prot, ph, x, b1p, b1m = workload_inputs(seed, dev)
-    problem = mpm.make_problem(prot, SHAPE, lam=LAMBDA, eps=EPS)
+    prot, ph, x, b1p, b1m = workload_inputs(seed, dev, args.echo_dtype)
+    problem = mpm.make_problem(prot, SHAPE, vx=VX, lam=LAMBDA, eps=EPS,
+                               echo_dtype=1 if args.echo_dtype == "bf16" else 0)
     opts = mpm.make_opts(gn_iters=GN_ITERS, cg_iters=CG_ITERS, newton_per_irls=1, init=True)
     K, C = problem.n_maps, problem.n_contrasts
     I = sum(prot["n_echoes"])
@@ -429,7 +440,8 @@ def run_ours(args):
         return 0
 
     peak, peak_src = measured_peak()
-    kern = kernel_roofline(prof, N, args.steps, K, C, I, peak)
+    kern = kernel_roofline(prof, N, args.steps, K, C, I, peak,
+                           echo_bytes=2 if args.echo_dtype == "bf16" else 4)
     dominant = max(kern, key=lambda k: kern[k]["ms_total"])
     dk = kern[dominant]
     traffic = measured_traffic(dominant, N)
@@ -445,12 +457,14 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(1000 * t_max / args.steps, 2), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"1 mm MPM JTV-MAP fit, {SHAPE[0]}x{SHAPE[1]}x{SHAPE[2]} voxels, "
-                               "PDw/T1w/MTw 8/8/6 echoes, Rician SNR 20, 20 updates x 30 PCG "
-                               "+ posterior variance",
+        "config": {"workload": f"{VX[0]:g} mm MPM JTV-MAP fit, {SHAPE[0]}x{SHAPE[1]}x{SHAPE[2]} "
+                               "voxels, PDw/T1w/MTw 8/8/6 echoes, Rician SNR 20, 20 updates x 30 "
+                               "PCG + posterior variance"
+                               + (", echoes stored bf16" if args.echo_dtype == "bf16" else ""),
+                   "echo_storage": args.echo_dtype,
                    "voxels": N, "gn_iters": GN_ITERS, "cg_iters": CG_ITERS, "lambda": LAMBDA,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "l2": f"inputs larger than L2 (images {x.numel() * 4 / 1e6:.0f} MB, L2 129 MB); "
+                   "l2": f"inputs larger than L2 (images {x.numel() * x.element_size() / 1e6:.0f} MB, L2 129 MB); "
                          "no flush",
                    "final_objective": final_F},
         "roofline": roofline,

@@ -1,0 +1,63 @@
+"""Precision variant: echo images stored as bfloat16, all arithmetic in float32
+(float64 for reductions and the uncertainty).
+
+The GPU fit is compared per map with the FP64 oracle run on the float32
+images, so the bfloat16 error includes the rounding of the data itself.  The
+float32 fit must meet the parity bound (1e-3 x max(1, |y|) in log space);
+for bfloat16 storage the error is reported per map and checked
+against a bound well below the noise-driven map error (the images' rounding
+is 2^-9 relative, the noise 1/SNR = 5%).
+"""
+import numpy as np
+import pytest
+
+import oracle as orc
+from cases import dataset, map_error, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+MAPS = ["log A", "log R1", "log R2*", "logit MTsat"]
+
+
+@pytest.fixture(scope="module")
+def mpm():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2102_01604_gb300 as m
+    m._lib.load()
+    return m
+
+
+def _gpu_fit(mpm, d, x, echo_dtype, gn, cg):
+    import torch
+    shape = d["shape"]
+    pg = mpm.make_problem(d["prot"], shape, echo_dtype=echo_dtype)
+    y = torch.zeros((pg.n_maps, int(np.prod(shape))), dtype=torch.float32, device="cuda")
+    st, rep = mpm.mpm_fit(pg, mpm.make_opts(gn_iters=gn, cg_iters=cg), x, y, to_dev(d["b1p"]),
+                          to_dev(d["b1m"]))
+    return to_np(y), np.array(rep.F[:rep.iters + 1])
+
+
+def test_per_map_error_float32_and_bfloat16_echoes(mpm):
+    import torch
+    shape, gn, cg = (64, 64, 24), 20, 30
+    d = dataset(shape, seed=71)
+    po = orc.make_problem(d["prot"], shape)
+    ref = orc.fit(po, d["x"], None, d["b1p"], d["b1m"], gn_iters=gn, cg_iters=cg)
+    x32 = to_dev(d["x"])
+    y32, F32 = _gpu_fit(mpm, d, x32, 0, gn, cg)
+    y16, F16 = _gpu_fit(mpm, d, x32.to(torch.bfloat16), 1, gn, cg)
+    e32 = map_error(y32, ref["y"])
+    e16 = np.abs(y16 - ref["y"])
+    noise = np.sqrt(np.mean((ref["y"] - d["y_true"]) ** 2, axis=1))
+    print("\nper-map error vs FP64 oracle after 20 updates (64x64x24):")
+    for k, name in enumerate(MAPS):
+        print(f"  {name:12s} f32 max {e32[k].max():.2e} | bf16 max {e16[k].max():.2e} "
+              f"rms {np.sqrt(np.mean(e16[k] ** 2)):.2e} | oracle-vs-truth rms {noise[k]:.2e}")
+    print(f"  objective: f32 rel {abs(F32[-1] - ref['F'][-1]) / ref['F'][-1]:.2e}, "
+          f"bf16 rel {abs(F16[-1] - ref['F'][-1]) / ref['F'][-1]:.2e}")
+    assert e32.max() <= 1e-3
+    np.testing.assert_allclose(F32, ref["F"], rtol=1e-5)
+    for k in range(4):
+        # bfloat16 rounding of the data moves the maps far less than the noise does
+        assert np.sqrt(np.mean(e16[k] ** 2)) <= 0.1 * noise[k]
