@@ -364,6 +364,9 @@ def run_ours(args):
     var = torch.empty((K, N), dtype=torch.float32, device=dev)
     ws = mpm.workspace(problem, opts, device=dev)
 
+    # stencil tile shape for this volume, chosen by timing (outside the timed region)
+    tile, tile_ms = mpm.mpm_autotune(problem, opts, ws=ws)
+
     def step():
         st, rep = mpm.mpm_fit(problem, opts, x, y, b1p, b1m, var=var, ws=ws)
         return rep
@@ -462,6 +465,8 @@ def run_ours(args):
                                "PCG + posterior variance"
                                + (", echoes stored bf16" if args.echo_dtype == "bf16" else ""),
                    "echo_storage": args.echo_dtype,
+                   "stencil_tile": ["16x16", "32x8", "64x4"][tile] if tile >= 0 else "smem",
+                   "tile_autotune_us": [round(1000 * t, 1) for t in tile_ms],
                    "voxels": N, "gn_iters": GN_ITERS, "cg_iters": CG_ITERS, "lambda": LAMBDA,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": f"inputs larger than L2 (images {x.numel() * x.element_size() / 1e6:.0f} MB, L2 129 MB); "

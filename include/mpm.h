@@ -206,6 +206,22 @@ mpm_status mpm_fit(const mpm_problem* problem, const mpm_opts* opts, const void*
                    const float* b1p, const float* b1m, float* y_inout, float* var_out,
                    void* ws, size_t ws_bytes, mpm_report* report, void* stream);
 
+/* Tile-shape autotuner for the stencil matvec of the solve.  The TMA-staged
+ * matvec can tile the (x, y) plane as 16 x 16, 32 x 8 or 64 x 4 voxels; this
+ * call times each applicable shape on this volume (zeroed operands in `ws`, a
+ * MPM_CALL_SOLVE-sized workspace or larger), keeps the fastest for every later
+ * solve of a volume of this size in the process, and writes its index to
+ * *tile (-1 when the TMA matvec does not apply: nx not a multiple of 4, or the
+ * volume smaller than a tile) and the mean time per launch of each shape to
+ * ms[0..MPM_TILE_SHAPES-1] (-1 for shapes that do not apply; may be NULL).
+ * If *tile >= 0 on entry, that shape is recorded without timing (ws may then
+ * be NULL).  Without either, a default shape is used.  A shape that does not
+ * fit a volume falls back to the shared-memory matvec.  Synchronises
+ * `stream` when timing. */
+#define MPM_TILE_SHAPES 3
+mpm_status mpm_autotune(const mpm_problem* problem, const mpm_opts* opts, void* ws,
+                        size_t ws_bytes, void* stream, int* tile, float* ms);
+
 /* Synchronises `stream` and returns MPM_ERR_NUMERIC if a kernel that used this
  * workspace recorded a numeric failure since the workspace was last cleared
  * (every mpm_solve / mpm_fit clears it), else MPM_OK. */

@@ -19,7 +19,7 @@ from ._lib import MPMError, Opts, Problem, Report
 __all__ = [
     "make_problem", "make_opts", "workspace", "mpm_workspace_size", "mpm_forward",
     "mpm_grad_hess", "mpm_jtv_weights", "mpm_solve", "mpm_uncertainty", "mpm_fit",
-    "mpm_workspace_status", "mpm_kernel_launches", "mpm_profile_enable", "mpm_profile_read",
+    "mpm_workspace_status", "mpm_autotune", "mpm_kernel_launches", "mpm_profile_enable", "mpm_profile_read",
     "MPMError", "Problem", "Opts", "Report",
 ]
 
@@ -206,6 +206,22 @@ def mpm_fit(problem, opts, x, y, b1p=None, b1m=None, var=None, ws=None, stream=N
                                 _ptr(ws, "ws"), ws.numel(), ctypes.byref(rep), _stream(stream)),
                     "mpm_fit", allow)
     return st, rep
+
+
+def mpm_autotune(problem, opts, ws=None, stream=None, tile=-1):
+    """Pick the stencil tile shape for this volume by timing each candidate
+    (or pin ``tile`` >= 0 without timing).  Returns (tile index or -1,
+    per-shape milliseconds)."""
+    lib = _lib.load()
+    if tile < 0 and ws is None:
+        ws = workspace(problem, opts, _lib.CALL_SOLVE)
+    tile = ctypes.c_int(tile)
+    ms = (ctypes.c_float * 3)()
+    _lib.check(lib.mpm_autotune(ctypes.byref(problem), ctypes.byref(opts),
+                                _ptr(ws, "ws", optional=True), ws.numel() if ws is not None else 0,
+                                _stream(stream), ctypes.byref(tile), ms),
+               "mpm_autotune")
+    return tile.value, list(ms)
 
 
 def mpm_workspace_status(ws, stream=None) -> int:

@@ -82,6 +82,8 @@ PROTOTYPES = {
     "mpm_uncertainty": (ctypes.c_int, [_P, _V, _V, _V, _V, _V, _V, _V]),
     "mpm_fit": (ctypes.c_int, [_P, _O, _V, _V, _V, _V, _V, _V, _S, ctypes.POINTER(Report), _V]),
     "mpm_workspace_status": (ctypes.c_int, [_V, _S, _V]),
+    "mpm_autotune": (ctypes.c_int, [_P, _O, _V, _S, _V, ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_float)]),
     "mpm_kernel_launches": (ctypes.c_ulonglong, []),
     "mpm_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "mpm_profile_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double),

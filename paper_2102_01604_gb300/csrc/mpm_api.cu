@@ -553,6 +553,34 @@ mpm_status mpm_uncertainty(const mpm_problem* problem, const float* h, const flo
     return MPM_OK;
 }
 
+mpm_status mpm_autotune(const mpm_problem* problem, const mpm_opts* opts, void* ws,
+                        size_t ws_bytes, void* stream, int* tile, float* ms)
+{
+    MPM_TRY(check_problem(problem));
+    MPM_TRY(check_opts(opts));
+    const DevProblem P = make_dev(problem);
+    const int want = tile ? *tile : -1;
+    if (want >= MPM_TILE_SHAPES) return fail(MPM_ERR_INVALID_ARG, "tile %d out of range", want);
+    if (tile) *tile = -1;
+    if (P.N == 0) return MPM_OK;
+    float t_ms[MPM_TILE_SHAPES];
+    int best = -1;
+    if (want >= 0) {
+        // pin the requested shape without timing
+        for (int i = 0; i < MPM_TILE_SHAPES; ++i) t_ms[i] = -1.0f;
+        tma_tile_set(P, want);
+        best = want;
+    } else {
+        FitWs L;
+        MPM_TRY(check_ws(P, MPM_CALL_SOLVE, ws, ws_bytes, L));
+        MPM_CUDA(tma_autotune(P, L.solve, L.hdr, L.red, (cudaStream_t)stream, &best, t_ms));
+    }
+    if (tile) *tile = best;
+    if (ms)
+        for (int i = 0; i < MPM_TILE_SHAPES; ++i) ms[i] = i < tma_tile_count() ? t_ms[i] : -1.0f;
+    return MPM_OK;
+}
+
 mpm_status mpm_workspace_status(const void* ws, size_t ws_bytes, void* stream)
 {
     if (ws_bytes < sizeof(WsHeader)) return fail(MPM_ERR_WORKSPACE_TOO_SMALL, "workspace too small");

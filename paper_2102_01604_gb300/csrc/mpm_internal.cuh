@@ -111,7 +111,7 @@ __device__ __forceinline__ double warp_sum(double v)
 }
 
 // Sum of v over the block, valid in thread 0.  Fixed order (deterministic).
-__device__ __forceinline__ double block_sum(double v, double* sh /* [kBlock/32] */)
+__device__ __forceinline__ double block_sum(double v, double* sh /* one per warp */)
 {
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     const int nw = (blockDim.x * blockDim.y + 31) >> 5;
@@ -141,7 +141,7 @@ __device__ __forceinline__ double warp_acc(Acc a)
     return (double)a.hi + (double)a.lo;
 }
 
-__device__ __forceinline__ double block_acc(Acc a, double* sh /* [kBlock/32] */)
+__device__ __forceinline__ double block_acc(Acc a, double* sh /* one per warp */)
 {
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     const int nw = (blockDim.x * blockDim.y + 31) >> 5;
@@ -164,7 +164,7 @@ __device__ __forceinline__ double block_acc(Acc a, double* sh /* [kBlock/32] */)
 template <int NV>
 __device__ __forceinline__ bool grid_reduce(const Acc (&v)[NV], Reduce red, double (&out)[NV])
 {
-    __shared__ double sh[kBlock / 32];
+    __shared__ double sh[32];          // one slot per warp of the block (up to 1024 threads)
     __shared__ bool am_last;
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     const int nthreads = blockDim.x * blockDim.y;
@@ -261,10 +261,20 @@ size_t solve_ws_bytes(const DevProblem& P);
 // rules; the shared-memory kernel is used then.
 struct TmaMaps {
     CUtensorMap p[2], w, h;
+    int tile;          // index of the tile shape the maps were encoded for
 };
+int tma_tile_count();
 bool make_tma_maps(const DevProblem& P, const float* h, const float* w, const float* p0,
-                   const float* p1, TmaMaps* out);
-StencilGrid tma_grid(const DevProblem& P);
+                   const float* p1, int tile, TmaMaps* out);
+StencilGrid tma_grid(const DevProblem& P, int tile);
+int tma_tile_choice(const DevProblem& P);   // tile shape for this volume (tuned or default)
+void tma_tile_set(const DevProblem& P, int tile);
+// Times every applicable tile shape of the TMA matvec on this volume (operands
+// taken from the solve workspace, zeroed), records the fastest for later
+// solves and returns it (-1 when TMA does not apply); ms[i] receives the mean
+// time of shape i (or -1).  Synchronises the stream.
+cudaError_t tma_autotune(const DevProblem& P, void* solve_ws, WsHeader* hdr, Reduce red,
+                         cudaStream_t st, int* best, float* ms);
 cudaError_t launch_matvec_tma(const DevProblem& P, const StencilGrid& g, const TmaMaps& m,
                               int k_it, float* q, WsHeader* hdr, Reduce red, cudaStream_t st);
 

@@ -656,8 +656,9 @@ static cudaError_t solve_k(const DevProblem& P, int cg_iters, double tol_cg, con
     }
     const StencilGrid mg = stencil_grid(P, kMvX, kMvY);
     TmaMaps maps;
-    const bool tma = make_tma_maps(P, h, w, B.p[0], B.p[1], &maps);
-    const StencilGrid tg = tma ? tma_grid(P) : mg;
+    const int tile = tma_tile_choice(P);
+    const bool tma = tile >= 0 && make_tma_maps(P, h, w, B.p[0], B.p[1], tile, &maps);
+    const StencilGrid tg = tma ? tma_grid(P, tile) : mg;
     // float4 streaming needs whole vectors per map and 16-byte aligned rows
     const bool vec4 = (P.N % 4 == 0) &&
                       ((reinterpret_cast<uintptr_t>(B.r) | reinterpret_cast<uintptr_t>(B.q) |
@@ -695,6 +696,52 @@ static cudaError_t solve_k(const DevProblem& P, int cg_iters, double tol_cg, con
     k_pcg_final<<<voxel_grid(P.N * K), kBlock, 0, st>>>(P.N * K, B, xacc, delta, y_update, hdr,
                                                         report_rel, report_it);
     return cudaGetLastError();
+}
+
+cudaError_t tma_autotune(const DevProblem& P, void* solve_ws, WsHeader* hdr, Reduce red,
+                         cudaStream_t st, int* best, float* ms)
+{
+    SolveBufs B = carve(P, solve_ws);
+    *best = -1;
+    // operands: R stands in for H (same size), r for w; all zero
+    const size_t vec = sizeof(float) * (size_t)P.K * P.N;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(B.R, 0, sizeof(float) * (size_t)P.T * P.N, st)) != cudaSuccess) return e;
+    for (float* v : {B.r, B.p[0], B.p[1]})
+        if ((e = cudaMemsetAsync(v, 0, vec, st)) != cudaSuccess) return e;
+    cudaEvent_t a, b;
+    if ((e = cudaEventCreate(&a)) != cudaSuccess) return e;
+    if ((e = cudaEventCreate(&b)) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return e;
+    }
+    float best_ms = 0.0f;
+    for (int t = 0; t < tma_tile_count(); ++t) {
+        ms[t] = -1.0f;
+        TmaMaps m;
+        if (!make_tma_maps(P, B.R, B.r, B.p[0], B.p[1], t, &m)) continue;
+        const StencilGrid g = tma_grid(P, t);
+        constexpr int reps = 5;
+        for (int i = 0; i <= reps && e == cudaSuccess; ++i) {
+            if (i == 1) e = cudaEventRecord(a, st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st);
+            if (e == cudaSuccess) e = launch_matvec_tma(P, g, m, 2, B.q, hdr, red, st);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(b, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float t_ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t_ms, a, b);
+        if (e != cudaSuccess) break;
+        ms[t] = t_ms / reps;
+        if (*best < 0 || ms[t] < best_ms) {
+            best_ms = ms[t];
+            *best = t;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (e == cudaSuccess && *best >= 0) tma_tile_set(P, *best);
+    return e;
 }
 
 cudaError_t launch_solve(const DevProblem& P, int cg_iters, double tol_cg, const float* h,

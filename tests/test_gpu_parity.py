@@ -233,3 +233,28 @@ def test_bf16_echoes(mpm):
                           to_dev(d["b1m"]))
     ref = orc.fit(po, d["x"], None, d["b1p"], d["b1m"], gn_iters=5, cg_iters=30)
     _check_fit(rep, to_np(yy), ref)
+
+
+@pytest.mark.parametrize("tile", [0, 1, 2])
+def test_solve_every_stencil_tile_shape(mpm, tile):
+    """The TMA matvec in each tile shape (16x16, 32x8, 64x4) on a volume with
+    ragged tiles in x and y, against the oracle."""
+    shape = (76, 21, 9)
+    d = dataset(shape, seed=81)
+    pg, po = _problems(mpm, d)
+    got, _ = mpm.mpm_autotune(pg, mpm.make_opts(), tile=tile)
+    assert got == tile
+    h, w, g, y = _system(d, po, 82)
+    delta, resid = mpm.mpm_solve(pg, mpm.make_opts(cg_iters=30), to_dev(h), to_dev(w), to_dev(g),
+                                 to_dev(y))
+    d_o, it, r_o = orc.solve(po, h, w, g, y, 30)
+    assert_close_scaled(to_np(delta), d_o, 2e-4, "delta")
+
+
+def test_autotune_times_the_shapes(mpm):
+    d = dataset((96, 48, 20), seed=83)
+    pg = mpm.make_problem(d["prot"], (96, 48, 20))
+    tile, ms = mpm.mpm_autotune(pg, mpm.make_opts())
+    assert tile in (0, 1, 2)
+    assert all(t > 0 for t in ms)
+    assert ms[tile] == min(ms)
