@@ -53,6 +53,7 @@ extern "C" {
 #define MPM_MAX_CONTRASTS 8
 #define MPM_MAX_IMAGES 64
 #define MPM_MAX_REPORT 256
+#define MPM_MAX_BATCH 64
 
 typedef int mpm_status;
 
@@ -104,6 +105,9 @@ typedef struct {
                               means; 0: y_inout holds the starting maps */
     double tol_gn;         /* stop when |F_prev - F| < tol_gn |F_prev| (0 = off) */
     double tol_cg;         /* stop PCG when |r_k| <= tol_cg |r_0| (0 = off) */
+    int graph;             /* 1: with tol_gn = 0, run all updates as one captured CUDA
+                              graph (instantiated on first use, cached per argument
+                              set, replayed afterwards); 0: direct launches */
 } mpm_opts;
 
 /* Per-update record filled by mpm_fit (host memory, caller-owned). */
@@ -221,6 +225,21 @@ mpm_status mpm_fit(const mpm_problem* problem, const mpm_opts* opts, const void*
 #define MPM_TILE_SHAPES 3
 mpm_status mpm_autotune(const mpm_problem* problem, const mpm_opts* opts, void* ws,
                         size_t ws_bytes, void* stream, int* tile, float* ms);
+
+/* Several subjects fitted together (batched fits; the paper fits one subject
+ * at a time).  Each subject i has its own problem (matrix size, contrasts and
+ * echo counts may all differ), images x[i], optional b1p[i] / b1m[i] (the
+ * arrays themselves may be NULL), maps y[i], optional var_out[i] and
+ * workspace ws[i] of ws_bytes[i]; opts and the report array (n entries, may
+ * be NULL) are shared.  With tol_gn = 0 and opts->graph = 1 the updates of all
+ * subjects are captured as parallel branches of one CUDA graph (cached per
+ * argument set) so uneven volumes share the GPU in one graph launch;
+ * otherwise subjects run one after another.  Each subject's result equals its
+ * mpm_fit result.  Synchronises `stream`.  1 <= n <= MPM_MAX_BATCH. */
+mpm_status mpm_fit_batch(int n, const mpm_problem* const* problems, const mpm_opts* opts,
+                         const void* const* x, const float* const* b1p, const float* const* b1m,
+                         float* const* y, float* const* var_out, void* const* ws,
+                         const size_t* ws_bytes, mpm_report* reports, void* stream);
 
 /* Synchronises `stream` and returns MPM_ERR_NUMERIC if a kernel that used this
  * workspace recorded a numeric failure since the workspace was last cleared

@@ -18,7 +18,7 @@ from ._lib import MPMError, Opts, Problem, Report
 
 __all__ = [
     "make_problem", "make_opts", "workspace", "mpm_workspace_size", "mpm_forward",
-    "mpm_grad_hess", "mpm_jtv_weights", "mpm_solve", "mpm_uncertainty", "mpm_fit",
+    "mpm_grad_hess", "mpm_jtv_weights", "mpm_solve", "mpm_uncertainty", "mpm_fit", "mpm_fit_batch",
     "mpm_workspace_status", "mpm_autotune", "mpm_kernel_launches", "mpm_profile_enable", "mpm_profile_read",
     "MPMError", "Problem", "Opts", "Report",
 ]
@@ -58,9 +58,9 @@ def make_problem(protocol: dict, shape, vx=(1.0, 1.0, 1.0), lam=10.0, eps=1e-3,
 
 
 def make_opts(gn_iters=10, cg_iters=30, newton_per_irls=1, init=True, tol_gn=0.0,
-              tol_cg=0.0) -> Opts:
+              tol_cg=0.0, graph=False) -> Opts:
     return Opts(int(gn_iters), int(cg_iters), int(newton_per_irls), 1 if init else 0,
-                float(tol_gn), float(tol_cg))
+                float(tol_gn), float(tol_cg), 1 if graph else 0)
 
 
 def _ptr(t, name, dtype=None, optional=False):
@@ -222,6 +222,37 @@ def mpm_autotune(problem, opts, ws=None, stream=None, tile=-1):
                                 _stream(stream), ctypes.byref(tile), ms),
                "mpm_autotune")
     return tile.value, list(ms)
+
+
+def mpm_fit_batch(problems, opts, xs, ys, b1ps=None, b1ms=None, vars=None, wss=None,
+                  stream=None, allow_not_converged=True):
+    """Fit several subjects together (see mpm_fit_batch in mpm.h).  Lists hold
+    one entry per subject; ``wss`` defaults to freshly allocated workspaces.
+    Returns (status, [Report])."""
+    import torch
+    lib = _lib.load()
+    n = len(problems)
+    if wss is None:
+        wss = [workspace(p, opts, _lib.CALL_FIT, y.device) for p, y in zip(problems, ys)]
+    V = ctypes.c_void_p
+    P = ctypes.POINTER(Problem)
+    parr = (P * n)(*[ctypes.pointer(p) for p in problems])
+    xdt = lambda p: torch.bfloat16 if p.echo_dtype == 1 else torch.float32
+    arr = lambda ts, name, dt=None, opt=False: (V * n)(*[
+        _ptr(t, f"{name}[{i}]", dt(problems[i]) if callable(dt) else dt, opt)
+        for i, t in enumerate(ts)])
+    xa = arr(xs, "x", xdt)
+    ya = arr(ys, "y", _f32())
+    bpa = arr(b1ps, "b1p", _f32(), True) if b1ps is not None else None
+    bma = arr(b1ms, "b1m", _f32(), True) if b1ms is not None else None
+    va = arr(vars, "var", _f32(), True) if vars is not None else None
+    wa = arr(wss, "ws")
+    wb = (ctypes.c_size_t * n)(*[w.numel() for w in wss])
+    reps = (Report * n)()
+    allow = (_lib.OK, _lib.WARN_NOT_CONVERGED) if allow_not_converged else (_lib.OK,)
+    st = _lib.check(lib.mpm_fit_batch(n, parr, ctypes.byref(opts), xa, bpa, bma, ya, va, wa, wb,
+                                      reps, _stream(stream)), "mpm_fit_batch", allow)
+    return st, list(reps)
 
 
 def mpm_workspace_status(ws, stream=None) -> int:

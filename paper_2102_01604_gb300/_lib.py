@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "libmpm.so")
 MAX_CONTRASTS = 8
 MAX_IMAGES = 64
 MAX_REPORT = 256
+MAX_BATCH = 64
 
 OK = 0
 WARN_NOT_CONVERGED = 1
@@ -51,6 +52,7 @@ class Opts(ctypes.Structure):
         ("gn_iters", ctypes.c_int), ("cg_iters", ctypes.c_int),
         ("newton_per_irls", ctypes.c_int), ("init", ctypes.c_int),
         ("tol_gn", ctypes.c_double), ("tol_cg", ctypes.c_double),
+        ("graph", ctypes.c_int),
     ]
 
 
@@ -81,6 +83,10 @@ PROTOTYPES = {
     "mpm_solve_static": (ctypes.c_int, [_P, _O, _V, _V, _V, _V, _V, _V, _V]),
     "mpm_uncertainty": (ctypes.c_int, [_P, _V, _V, _V, _V, _V, _V, _V]),
     "mpm_fit": (ctypes.c_int, [_P, _O, _V, _V, _V, _V, _V, _V, _S, ctypes.POINTER(Report), _V]),
+    "mpm_fit_batch": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_P), _O, ctypes.POINTER(_V),
+                                     ctypes.POINTER(_V), ctypes.POINTER(_V), ctypes.POINTER(_V),
+                                     ctypes.POINTER(_V), ctypes.POINTER(_V),
+                                     ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(Report), _V]),
     "mpm_workspace_status": (ctypes.c_int, [_V, _S, _V]),
     "mpm_autotune": (ctypes.c_int, [_P, _O, _V, _S, _V, ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_float)]),

@@ -23,6 +23,9 @@ struct ProfRecord {
 };
 
 static std::atomic<bool> g_prof_on{false};
+static thread_local bool t_capturing = false;
+
+void LaunchScope::capturing(bool on) { t_capturing = on; }
 static std::mutex g_prof_mu;
 static std::vector<ProfRecord> g_prof;
 static std::vector<cudaEvent_t> g_pool;
@@ -42,7 +45,7 @@ static cudaEvent_t pool_get()
 LaunchScope::LaunchScope(int k, cudaStream_t s) : kind(k), st(s), rec(nullptr)
 {
     g_launches.fetch_add(1, std::memory_order_relaxed);
-    if (!g_prof_on.load(std::memory_order_relaxed)) return;
+    if (t_capturing || !g_prof_on.load(std::memory_order_relaxed)) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     ProfRecord r{kind, pool_get(), pool_get()};
     if (!r.a || !r.b) return;
@@ -150,6 +153,7 @@ mpm_status check_opts(const mpm_opts* o)
         return fail(MPM_ERR_INVALID_ARG, "cg_iters = %d outside [1, 1e6]", o->cg_iters);
     if (o->newton_per_irls < 1) return fail(MPM_ERR_INVALID_ARG, "newton_per_irls must be >= 1");
     if (o->init != 0 && o->init != 1) return fail(MPM_ERR_INVALID_ARG, "init must be 0 or 1");
+    if (o->graph != 0 && o->graph != 1) return fail(MPM_ERR_INVALID_ARG, "graph must be 0 or 1");
     if (!(std::isfinite(o->tol_gn) && o->tol_gn >= 0.0) || !(std::isfinite(o->tol_cg) && o->tol_cg >= 0.0))
         return fail(MPM_ERR_INVALID_ARG, "tolerances must be finite and >= 0");
     return MPM_OK;
@@ -377,6 +381,342 @@ static void initial_maps(const mpm_problem* p, const double* mean, float out[4])
     out[3] = (float)std::log(delta / (1.0 - delta));
 }
 
+
+// ------------------------------------------------------------------ fits
+
+// One subject's fit: arguments checked, workspace carved.
+struct FitJob {
+    const mpm_problem* problem;
+    mpm_opts opts;
+    DevProblem P;
+    const void* x;
+    const float *b1p, *b1m;
+    float *y, *var;
+    void* ws;
+    size_t ws_bytes;
+    FitWs L;
+    bool empty;
+};
+
+static mpm_status fit_prepare(const mpm_problem* problem, const mpm_opts* opts, const void* x,
+                              const float* b1p, const float* b1m, float* y, float* var_out,
+                              void* ws, size_t ws_bytes, FitJob& job)
+{
+    MPM_TRY(check_problem(problem));
+    MPM_TRY(check_opts(opts));
+    job.problem = problem;
+    job.opts = *opts;
+    job.P = make_dev(problem);
+    job.x = x;
+    job.b1p = b1p;
+    job.b1m = b1m;
+    job.y = y;
+    job.var = var_out;
+    job.ws = ws;
+    job.ws_bytes = ws_bytes;
+    job.empty = job.P.N == 0;
+    if (job.empty) return MPM_OK;
+    MPM_TRY(check_dev(x, "x", false, problem->echo_dtype ? 2 : 4));
+    MPM_TRY(check_dev(b1p, "b1p", true, 4));
+    MPM_TRY(check_dev(b1m, "b1m", true, 4));
+    MPM_TRY(check_dev(y, "y_inout", false, 4));
+    MPM_TRY(check_dev(var_out, "var_out", true, 4));
+    MPM_TRY(check_ws(job.P, MPM_CALL_FIT, ws, ws_bytes, job.L));
+    return MPM_OK;
+}
+
+// The updates of a fit whose schedule needs no host decision (tol_gn = 0):
+// every launch of every update, the final evaluation and the uncertainty.
+// Enqueued on `st`; nothing here synchronises, so it can be captured.
+static cudaError_t fit_enqueue_updates(const FitJob& j, cudaStream_t st, int* iters_out)
+{
+    const DevProblem& P = j.P;
+    const FitWs& L = j.L;
+    const int npi = j.opts.newton_per_irls;
+    bool w_fresh = false;
+    cudaError_t e = cudaSuccess;
+    int it = 0;
+    for (;; ++it) {
+        w_fresh = (it % npi == 0);
+        if ((e = launch_jtv(P, j.y, w_fresh ? L.w : nullptr, L.jtv + it, L.red, st))) return e;
+        if ((e = launch_grad_hess(P, j.problem->echo_dtype, j.x, j.y, j.b1p, j.b1m, L.g, L.h,
+                                  L.nll + it, L.red, st)))
+            return e;
+        if (it >= j.opts.gn_iters) break;
+        if ((e = launch_solve(P, j.opts.cg_iters, j.opts.tol_cg, L.h, L.w, L.g, j.y, L.xbuf, j.y,
+                              nullptr, L.cg_rel + it, L.cg_it + it, L.solve, L.hdr, L.red, st)))
+            return e;
+    }
+    if (j.var) {
+        if (!w_fresh && (e = launch_jtv(P, j.y, L.w, L.jtv + MPM_MAX_REPORT + 1, L.red, st))) return e;
+        if ((e = launch_uncertainty(P, L.h, L.w, j.y, j.var, nullptr, nullptr, &L.hdr->status, st)))
+            return e;
+    }
+    *iters_out = it;
+    return e;
+}
+
+// Same with the host-side stopping test on the objective (tol_gn > 0).
+static mpm_status fit_run_adaptive(const FitJob& j, cudaStream_t st, int* iters_out, bool* converged)
+{
+    const DevProblem& P = j.P;
+    const FitWs& L = j.L;
+    const int npi = j.opts.newton_per_irls;
+    bool w_fresh = false;
+    double F_prev = 0.0;
+    int it = 0;
+    *converged = false;
+    for (;; ++it) {
+        w_fresh = (it % npi == 0);
+        MPM_CUDA(launch_jtv(P, j.y, w_fresh ? L.w : nullptr, L.jtv + it, L.red, st));
+        MPM_CUDA(launch_grad_hess(P, j.problem->echo_dtype, j.x, j.y, j.b1p, j.b1m, L.g, L.h,
+                                  L.nll + it, L.red, st));
+        if (it >= j.opts.gn_iters) break;
+        double v[2];
+        MPM_CUDA(cudaMemcpyAsync(&v[0], L.nll + it, sizeof(double), cudaMemcpyDeviceToHost, st));
+        MPM_CUDA(cudaMemcpyAsync(&v[1], L.jtv + it, sizeof(double), cudaMemcpyDeviceToHost, st));
+        MPM_CUDA(cudaStreamSynchronize(st));
+        const double F = v[0] + v[1];
+        if (it > 0 && std::fabs(F_prev - F) < j.opts.tol_gn * std::fabs(F_prev)) {
+            *converged = true;
+            break;
+        }
+        F_prev = F;
+        MPM_CUDA(launch_solve(P, j.opts.cg_iters, j.opts.tol_cg, L.h, L.w, L.g, j.y, L.xbuf, j.y,
+                              nullptr, L.cg_rel + it, L.cg_it + it, L.solve, L.hdr, L.red, st));
+    }
+    if (j.var) {
+        if (!w_fresh) MPM_CUDA(launch_jtv(P, j.y, L.w, L.jtv + MPM_MAX_REPORT + 1, L.red, st));
+        MPM_CUDA(launch_uncertainty(P, L.h, L.w, j.y, j.var, nullptr, nullptr, &L.hdr->status, st));
+    }
+    *iters_out = it;
+    return MPM_OK;
+}
+
+// ------------------------------------------------------- graph capture
+
+// Private streams used to capture graphs (created once, never destroyed).
+static std::mutex g_stream_mu;
+static std::vector<cudaStream_t> g_streams;
+
+static cudaError_t private_streams(int n, std::vector<cudaStream_t>& out)
+{
+    std::lock_guard<std::mutex> lk(g_stream_mu);
+    while ((int)g_streams.size() < n) {
+        cudaStream_t s;
+        cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+        g_streams.push_back(s);
+    }
+    out.assign(g_streams.begin(), g_streams.begin() + n);
+    return cudaSuccess;
+}
+
+// Instantiated graphs keyed by everything the captured launches depend on.
+struct GraphEntry {
+    std::string key;
+    cudaGraphExec_t exec;
+    std::vector<int> iters;
+    unsigned long long kernels;   // kernel launches captured (counted again on every replay)
+};
+static std::mutex g_graph_mu;
+static std::vector<GraphEntry> g_graphs;      // most recent last
+constexpr size_t kGraphCacheSize = 8;
+
+static std::string graph_key(const FitJob* jobs, int n)
+{
+    int dev = -1;
+    cudaGetDevice(&dev);
+    std::string k(reinterpret_cast<const char*>(&dev), sizeof dev);
+    for (int i = 0; i < n; ++i) {
+        const FitJob& j = jobs[i];
+        k.append(reinterpret_cast<const char*>(j.problem), sizeof(mpm_problem));
+        k.append(reinterpret_cast<const char*>(&j.opts), sizeof(mpm_opts));
+        const void* ptrs[7] = {j.x, j.b1p, j.b1m, j.y, j.var, j.ws, (const void*)j.ws_bytes};
+        k.append(reinterpret_cast<const char*>(ptrs), sizeof ptrs);
+    }
+    return k;
+}
+
+// Capture the updates of every job as parallel branches of one graph.
+static mpm_status capture_updates(FitJob* jobs, int n, GraphEntry& out)
+{
+    MPM_CUDA(prime_tma_kernels());
+    std::vector<cudaStream_t> ss;
+    MPM_CUDA(private_streams(n + 1, ss));
+    cudaStream_t root = ss[0];
+    cudaGraph_t graph = nullptr;
+    std::vector<cudaEvent_t> evs;
+    auto cleanup = [&]() {
+        for (cudaEvent_t e : evs) cudaEventDestroy(e);
+    };
+    cudaEvent_t fork;
+    MPM_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    evs.push_back(fork);
+    LaunchScope::capturing(true);
+    const unsigned long long before = g_launches.load();
+    cudaError_t e = cudaStreamBeginCapture(root, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = cudaEventRecord(fork, root);
+    out.iters.assign(n, 0);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        if (jobs[i].empty) continue;
+        cudaStream_t b = ss[i + 1];
+        e = cudaStreamWaitEvent(b, fork, 0);
+        if (e == cudaSuccess) e = fit_enqueue_updates(jobs[i], b, &out.iters[i]);
+        cudaEvent_t join;
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+        if (e == cudaSuccess) {
+            evs.push_back(join);
+            e = cudaEventRecord(join, b);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(root, join, 0);
+        }
+    }
+    cudaError_t e2 = cudaStreamEndCapture(root, &graph);
+    LaunchScope::capturing(false);
+    // launches made while capturing are not executed: count them at each replay
+    out.kernels = g_launches.load() - before;
+    g_launches.fetch_sub(out.kernels);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&out.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cleanup();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MPM_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+    }
+    return MPM_OK;
+}
+
+// Initial maps (host round trip for the image means), then the updates -- as
+// one graph launch when the schedule is fixed and opts.graph is set, else as
+// direct launches -- then one read-back of every report.
+static mpm_status fit_run(FitJob* jobs, int n, mpm_report* reports, cudaStream_t st)
+{
+    for (int i = 0; i < n; ++i)
+        if (reports) memset(&reports[i], 0, sizeof(mpm_report));
+    // clear status words and counters; image means for the constant maps
+    std::vector<double> means((size_t)n * MPM_MAX_IMAGES);
+    bool any_init = false;
+    for (int i = 0; i < n; ++i) {
+        FitJob& j = jobs[i];
+        if (j.empty) continue;
+        MPM_CUDA(cudaMemsetAsync(j.L.hdr, 0, sizeof(WsHeader), st));
+        if (j.opts.init) {
+            any_init = true;
+            MPM_CUDA(launch_image_means(j.P, j.problem->echo_dtype, j.x, j.L.mean_parts, j.L.means, st));
+            MPM_CUDA(cudaMemcpyAsync(&means[(size_t)i * MPM_MAX_IMAGES], j.L.means,
+                                     sizeof(double) * j.P.I, cudaMemcpyDeviceToHost, st));
+        }
+    }
+    if (any_init) {
+        MPM_CUDA(cudaStreamSynchronize(st));
+        for (int i = 0; i < n; ++i) {
+            FitJob& j = jobs[i];
+            if (j.empty || !j.opts.init) continue;
+            float vals[4];
+            initial_maps(j.problem, &means[(size_t)i * MPM_MAX_IMAGES], vals);
+            MPM_CUDA(launch_fill_maps(j.P, vals, j.y, st));
+        }
+    }
+
+    std::vector<int> iters(n, 0);
+    std::vector<char> converged(n, 0);
+    const bool fixed = jobs[0].opts.tol_gn == 0.0;
+    if (fixed && jobs[0].opts.graph) {
+        const std::string key = graph_key(jobs, n);
+        cudaGraphExec_t exec = nullptr;
+        unsigned long long kernels = 0;
+        {
+            std::lock_guard<std::mutex> lk(g_graph_mu);
+            for (size_t g = 0; g < g_graphs.size(); ++g)
+                if (g_graphs[g].key == key) {
+                    GraphEntry hit = g_graphs[g];
+                    g_graphs.erase(g_graphs.begin() + g);
+                    g_graphs.push_back(hit);
+                    exec = hit.exec;
+                    iters = hit.iters;
+                    kernels = hit.kernels;
+                    break;
+                }
+        }
+        if (!exec) {
+            GraphEntry ge;
+            ge.key = key;
+            MPM_TRY(capture_updates(jobs, n, ge));
+            exec = ge.exec;
+            iters = ge.iters;
+            kernels = ge.kernels;
+            std::lock_guard<std::mutex> lk(g_graph_mu);
+            g_graphs.push_back(ge);
+            if (g_graphs.size() > kGraphCacheSize) {
+                cudaGraphExecDestroy(g_graphs.front().exec);
+                g_graphs.erase(g_graphs.begin());
+            }
+        }
+        MPM_CUDA(cudaGraphLaunch(exec, st));
+        g_launches.fetch_add(kernels);
+    } else if (fixed) {
+        for (int i = 0; i < n; ++i)
+            if (!jobs[i].empty) MPM_CUDA(fit_enqueue_updates(jobs[i], st, &iters[i]));
+    } else {
+        for (int i = 0; i < n; ++i) {
+            if (jobs[i].empty) continue;
+            bool c = false;
+            MPM_TRY(fit_run_adaptive(jobs[i], st, &iters[i], &c));
+            converged[i] = c;
+        }
+    }
+
+    // read back every report with one synchronisation
+    struct Back {
+        double nll[MPM_MAX_REPORT + 1], jtv[MPM_MAX_REPORT + 1], cgr[MPM_MAX_REPORT];
+        int cgi[MPM_MAX_REPORT];
+        unsigned status;
+    };
+    std::vector<Back> back(n);
+    for (int i = 0; i < n; ++i) {
+        const FitJob& j = jobs[i];
+        if (j.empty) continue;
+        const int it = iters[i];
+        MPM_CUDA(cudaMemcpyAsync(back[i].nll, j.L.nll, sizeof(double) * (it + 1), cudaMemcpyDeviceToHost, st));
+        MPM_CUDA(cudaMemcpyAsync(back[i].jtv, j.L.jtv, sizeof(double) * (it + 1), cudaMemcpyDeviceToHost, st));
+        if (it > 0) {
+            MPM_CUDA(cudaMemcpyAsync(back[i].cgr, j.L.cg_rel, sizeof(double) * it, cudaMemcpyDeviceToHost, st));
+            MPM_CUDA(cudaMemcpyAsync(back[i].cgi, j.L.cg_it, sizeof(int) * it, cudaMemcpyDeviceToHost, st));
+        }
+        MPM_CUDA(cudaMemcpyAsync(&back[i].status, &j.L.hdr->status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    }
+    MPM_CUDA(cudaStreamSynchronize(st));
+    mpm_status result = MPM_OK;
+    for (int i = 0; i < n; ++i) {
+        const FitJob& j = jobs[i];
+        if (j.empty) continue;
+        const int it = iters[i];
+        if (reports) {
+            mpm_report& r = reports[i];
+            r.iters = it;
+            for (int k = 0; k <= it; ++k) {
+                r.nll[k] = back[i].nll[k];
+                r.jtv[k] = back[i].jtv[k];
+                r.F[k] = back[i].nll[k] + back[i].jtv[k];
+            }
+            for (int k = 0; k < it; ++k) {
+                r.cg_rel[k] = back[i].cgr[k];
+                r.cg_done[k] = back[i].cgi[k];
+            }
+        }
+        const unsigned status = back[i].status;
+        if (status && result >= 0)
+            result = fail(MPM_ERR_NUMERIC, "%sdevice status 0x%x (%s%s%s)",
+                          n > 1 ? "a subject reported " : "", status,
+                          status & kStatusNotPD ? "non positive definite block " : "",
+                          status & kStatusNaN ? "NaN in a reduction " : "",
+                          status & kStatusTimeout ? "copy wait timed out" : "");
+        if (j.opts.tol_gn > 0.0 && !converged[i] && result == MPM_OK) result = MPM_WARN_NOT_CONVERGED;
+    }
+    return result;
+}
+
 }  // namespace mpm
 
 using namespace mpm;
@@ -599,90 +939,28 @@ mpm_status mpm_fit(const mpm_problem* problem, const mpm_opts* opts, const void*
                    const float* b1p, const float* b1m, float* y, float* var_out, void* ws,
                    size_t ws_bytes, mpm_report* report, void* stream)
 {
-    MPM_TRY(check_problem(problem));
-    MPM_TRY(check_opts(opts));
-    const DevProblem P = make_dev(problem);
-    cudaStream_t st = (cudaStream_t)stream;
-    if (report) memset(report, 0, sizeof *report);
-    if (P.N == 0) return MPM_OK;
-    MPM_TRY(check_dev(x, "x", false, problem->echo_dtype ? 2 : 4));
-    MPM_TRY(check_dev(b1p, "b1p", true, 4));
-    MPM_TRY(check_dev(b1m, "b1m", true, 4));
-    MPM_TRY(check_dev(y, "y_inout", false, 4));
-    MPM_TRY(check_dev(var_out, "var_out", true, 4));
-    FitWs L;
-    MPM_TRY(check_ws(P, MPM_CALL_FIT, ws, ws_bytes, L));
-    MPM_CUDA(cudaMemsetAsync(L.hdr, 0, sizeof(WsHeader), st));
+    FitJob job;
+    MPM_TRY(fit_prepare(problem, opts, x, b1p, b1m, y, var_out, ws, ws_bytes, job));
+    return fit_run(&job, 1, report, (cudaStream_t)stream);
+}
 
-    if (opts->init) {
-        double means[MPM_MAX_IMAGES];
-        MPM_CUDA(launch_image_means(P, problem->echo_dtype, x, L.mean_parts, L.means, st));
-        MPM_CUDA(cudaMemcpyAsync(means, L.means, sizeof(double) * P.I, cudaMemcpyDeviceToHost, st));
-        MPM_CUDA(cudaStreamSynchronize(st));
-        float vals[4];
-        initial_maps(problem, means, vals);
-        MPM_CUDA(launch_fill_maps(P, vals, y, st));
+mpm_status mpm_fit_batch(int n, const mpm_problem* const* problems, const mpm_opts* opts,
+                         const void* const* x, const float* const* b1p, const float* const* b1m,
+                         float* const* y, float* const* var_out, void* const* ws,
+                         const size_t* ws_bytes, mpm_report* reports, void* stream)
+{
+    if (n < 0 || n > MPM_MAX_BATCH) return fail(MPM_ERR_INVALID_ARG, "batch size %d outside [0, %d]", n, MPM_MAX_BATCH);
+    if (n == 0) return MPM_OK;
+    if (!problems || !x || !y || !ws || !ws_bytes)
+        return fail(MPM_ERR_INVALID_ARG, "problems, x, y, ws and ws_bytes must not be NULL");
+    std::vector<FitJob> jobs(n);
+    for (int i = 0; i < n; ++i) {
+        mpm_status s = fit_prepare(problems[i], opts, x[i], b1p ? b1p[i] : nullptr,
+                                   b1m ? b1m[i] : nullptr, y[i], var_out ? var_out[i] : nullptr,
+                                   ws[i], ws_bytes[i], jobs[i]);
+        if (s != MPM_OK) return fail(s, "subject %d: %s", i, t_err.c_str());
     }
-
-    const int npi = opts->newton_per_irls;
-    int it = 0;
-    bool converged = false, w_fresh = false;
-    double F_prev = 0.0;
-    for (;; ++it) {
-        w_fresh = (it % npi == 0);
-        MPM_CUDA(launch_jtv(P, y, w_fresh ? L.w : nullptr, L.jtv + it, L.red, st));
-        MPM_CUDA(launch_grad_hess(P, problem->echo_dtype, x, y, b1p, b1m, L.g, L.h, L.nll + it,
-                                  L.red, st));
-        if (it >= opts->gn_iters) break;
-        if (opts->tol_gn > 0.0) {
-            double v[2];
-            MPM_CUDA(cudaMemcpyAsync(&v[0], L.nll + it, sizeof(double), cudaMemcpyDeviceToHost, st));
-            MPM_CUDA(cudaMemcpyAsync(&v[1], L.jtv + it, sizeof(double), cudaMemcpyDeviceToHost, st));
-            MPM_CUDA(cudaStreamSynchronize(st));
-            const double F = v[0] + v[1];
-            if (it > 0 && std::fabs(F_prev - F) < opts->tol_gn * std::fabs(F_prev)) {
-                converged = true;
-                break;
-            }
-            F_prev = F;
-        }
-        MPM_CUDA(launch_solve(P, opts->cg_iters, opts->tol_cg, L.h, L.w, L.g, y, L.xbuf, y,
-                              nullptr, L.cg_rel + it, L.cg_it + it, L.solve, L.hdr, L.red, st));
-    }
-    const int iters = it;
-    if (var_out) {
-        if (!w_fresh) MPM_CUDA(launch_jtv(P, y, L.w, L.jtv + MPM_MAX_REPORT + 1, L.red, st));
-        MPM_CUDA(launch_uncertainty(P, L.h, L.w, y, var_out, nullptr, nullptr, &L.hdr->status, st));
-    }
-    double nll[MPM_MAX_REPORT + 1], jtv[MPM_MAX_REPORT + 1], cgr[MPM_MAX_REPORT];
-    int cgi[MPM_MAX_REPORT];
-    unsigned status = 0;
-    MPM_CUDA(cudaMemcpyAsync(nll, L.nll, sizeof(double) * (iters + 1), cudaMemcpyDeviceToHost, st));
-    MPM_CUDA(cudaMemcpyAsync(jtv, L.jtv, sizeof(double) * (iters + 1), cudaMemcpyDeviceToHost, st));
-    if (iters > 0) {
-        MPM_CUDA(cudaMemcpyAsync(cgr, L.cg_rel, sizeof(double) * iters, cudaMemcpyDeviceToHost, st));
-        MPM_CUDA(cudaMemcpyAsync(cgi, L.cg_it, sizeof(int) * iters, cudaMemcpyDeviceToHost, st));
-    }
-    MPM_CUDA(cudaMemcpyAsync(&status, &L.hdr->status, sizeof status, cudaMemcpyDeviceToHost, st));
-    MPM_CUDA(cudaStreamSynchronize(st));
-    if (report) {
-        report->iters = iters;
-        for (int i = 0; i <= iters; ++i) {
-            report->nll[i] = nll[i];
-            report->jtv[i] = jtv[i];
-            report->F[i] = nll[i] + jtv[i];
-        }
-        for (int i = 0; i < iters; ++i) {
-            report->cg_rel[i] = cgr[i];
-            report->cg_done[i] = cgi[i];
-        }
-    }
-    if (status)
-        return fail(MPM_ERR_NUMERIC, "device status 0x%x (%s%s)", status,
-                    status & kStatusNotPD ? "non positive definite block " : "",
-                    status & kStatusNaN ? "NaN in a reduction" : "");
-    if (opts->tol_gn > 0.0 && !converged) return MPM_WARN_NOT_CONVERGED;
-    return MPM_OK;
+    return fit_run(jobs.data(), n, reports, (cudaStream_t)stream);
 }
 
 }  // extern "C"

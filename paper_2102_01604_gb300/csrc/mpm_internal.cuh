@@ -225,6 +225,7 @@ int voxel_grid(long long N);
 struct LaunchScope {
     LaunchScope(int kind, cudaStream_t st);
     ~LaunchScope();
+    static void capturing(bool on);   // no timing events while this thread captures a graph
     int kind;
     cudaStream_t st;
     void* rec;
@@ -267,6 +268,7 @@ int tma_tile_count();
 bool make_tma_maps(const DevProblem& P, const float* h, const float* w, const float* p0,
                    const float* p1, int tile, TmaMaps* out);
 StencilGrid tma_grid(const DevProblem& P, int tile);
+cudaError_t prime_tma_kernels();   // shared-memory opt-ins, done before any graph capture
 int tma_tile_choice(const DevProblem& P);   // tile shape for this volume (tuned or default)
 void tma_tile_set(const DevProblem& P, int tile);
 // Times every applicable tile shape of the TMA matvec on this volume (operands

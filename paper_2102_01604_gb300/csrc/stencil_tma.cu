@@ -390,6 +390,28 @@ static cudaError_t launch_tma_tile(const DevProblem& P, const StencilGrid& g, co
     }
 }
 
+template <int K, int TX, int TY>
+static cudaError_t prime_one()
+{
+    return cudaFuncSetAttribute(k_pcg_matvec_tma<K, TX, TY>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                TmaLayout<K, TX, TY>::SMEM);
+}
+
+cudaError_t prime_tma_kernels()
+{
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e = prime_one<4, 16, 16>();
+    if (!e) e = prime_one<4, 32, 8>();
+    if (!e) e = prime_one<4, 64, 4>();
+    if (!e) e = prime_one<3, 16, 16>();
+    if (!e) e = prime_one<3, 32, 8>();
+    if (!e) e = prime_one<3, 64, 4>();
+    if (!e) done = true;
+    return e;
+}
+
 cudaError_t launch_matvec_tma(const DevProblem& P, const StencilGrid& g, const TmaMaps& m,
                               int k_it, float* q, WsHeader* hdr, Reduce red, cudaStream_t st)
 {
