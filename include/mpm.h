@@ -241,6 +241,43 @@ mpm_status mpm_fit_batch(int n, const mpm_problem* const* problems, const mpm_op
                          float* const* y, float* const* var_out, void* const* ws,
                          const size_t* ws_bytes, mpm_report* reports, void* stream);
 
+/* Continuous batching of fit requests (a serving loop; the paper fits one
+ * subject at a time).  The server owns no device memory: every admitted
+ * request's fit workspace is carved from `arena` (caller-owned device memory,
+ * 256-byte aligned), so admission follows the free HBM the caller hands over.
+ * Requests are admitted first come first served while one of `max_slots`
+ * slots is free and their workspace fits; an active request keeps its maps,
+ * weights, gradient, Hessian and PCG state resident in the arena between
+ * rounds.  The server creates `max_slots` CUDA streams of its own (one per
+ * slot); `stream` is the caller's stream on which the request inputs are
+ * produced (each request waits for it at admission).
+ *  - mpm_server_submit: queue one fit (same arguments as mpm_fit minus the
+ *    workspace and report; x, b1p, b1m, y_inout, var_out stay caller-owned
+ *    and must stay valid until the request is done).  Returns a ticket.
+ *    Refuses requests larger than the whole arena.
+ *  - mpm_server_step: one round -- admit what fits, advance every active
+ *    request by one update (its pending PCG solve, then the objective at the
+ *    new maps) on its own stream so their kernels overlap, wait once, apply
+ *    the stopping rule of mpm_fit (tol_gn on the objective, or gn_iters), and
+ *    finish the requests that stop (uncertainty if var_out was given, report)
+ *    releasing their workspace.  Reports the active, queued and just-finished
+ *    counts (any pointer may be NULL).
+ *  - mpm_server_poll: state of a ticket (MPM_REQ_*), its final status and,
+ *    once done, its report.
+ * A request's result equals mpm_fit's with the same arguments.  The server is
+ * guarded by a mutex; calls from several threads are serialised. */
+enum { MPM_REQ_QUEUED = 0, MPM_REQ_ACTIVE = 1, MPM_REQ_DONE = 2, MPM_REQ_FAILED = 3 };
+typedef struct mpm_server mpm_server;
+mpm_status mpm_server_create(void* arena, size_t arena_bytes, int max_slots, void* stream,
+                             mpm_server** out);
+mpm_status mpm_server_submit(mpm_server* server, const mpm_problem* problem, const mpm_opts* opts,
+                             const void* x, const float* b1p, const float* b1m, float* y_inout,
+                             float* var_out, int* ticket);
+mpm_status mpm_server_step(mpm_server* server, int* n_active, int* n_queued, int* n_finished);
+mpm_status mpm_server_poll(mpm_server* server, int ticket, int* state, mpm_status* status,
+                           mpm_report* report);
+mpm_status mpm_server_destroy(mpm_server* server);
+
 /* Synchronises `stream` and returns MPM_ERR_NUMERIC if a kernel that used this
  * workspace recorded a numeric failure since the workspace was last cleared
  * (every mpm_solve / mpm_fit clears it), else MPM_OK. */

@@ -20,7 +20,7 @@ __all__ = [
     "make_problem", "make_opts", "workspace", "mpm_workspace_size", "mpm_forward",
     "mpm_grad_hess", "mpm_jtv_weights", "mpm_solve", "mpm_uncertainty", "mpm_fit", "mpm_fit_batch",
     "mpm_workspace_status", "mpm_autotune", "mpm_kernel_launches", "mpm_profile_enable", "mpm_profile_read",
-    "MPMError", "Problem", "Opts", "Report",
+    "MPMError", "Problem", "Opts", "Report", "Server",
 ]
 
 
@@ -253,6 +253,63 @@ def mpm_fit_batch(problems, opts, xs, ys, b1ps=None, b1ms=None, vars=None, wss=N
     st = _lib.check(lib.mpm_fit_batch(n, parr, ctypes.byref(opts), xa, bpa, bma, ya, va, wa, wb,
                                       reps, _stream(stream)), "mpm_fit_batch", allow)
     return st, list(reps)
+
+
+class Server:
+    """Continuous-batching fit server over a caller-provided device arena
+    (see mpm_server_* in mpm.h).  Keeps references to every submitted
+    request's tensors until it is done."""
+
+    def __init__(self, arena, max_slots=8, stream=None):
+        self._lib = _lib.load()
+        self.arena = arena
+        h = ctypes.c_void_p()
+        _lib.check(self._lib.mpm_server_create(_ptr(arena, "arena"), arena.numel(), int(max_slots),
+                                               _stream(stream), ctypes.byref(h)),
+                   "mpm_server_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, problem, opts, x, y, b1p=None, b1m=None, var=None) -> int:
+        import torch
+        t = ctypes.c_int()
+        xdt = torch.bfloat16 if problem.echo_dtype == 1 else torch.float32
+        _lib.check(self._lib.mpm_server_submit(
+            self._h, ctypes.byref(problem), ctypes.byref(opts), _ptr(x, "x", xdt),
+            _ptr(b1p, "b1p", _f32(), True), _ptr(b1m, "b1m", _f32(), True), _ptr(y, "y", _f32()),
+            _ptr(var, "var", _f32(), True), ctypes.byref(t)), "mpm_server_submit")
+        self._keep[t.value] = (problem, opts, x, y, b1p, b1m, var)
+        return t.value
+
+    def step(self):
+        """One scheduling round; returns (active, queued, finished)."""
+        a, q, f = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _lib.check(self._lib.mpm_server_step(self._h, ctypes.byref(a), ctypes.byref(q),
+                                             ctypes.byref(f)), "mpm_server_step")
+        return a.value, q.value, f.value
+
+    def poll(self, ticket):
+        """Returns (state, status, Report or None)."""
+        state, status = ctypes.c_int(), ctypes.c_int()
+        rep = Report()
+        _lib.check(self._lib.mpm_server_poll(self._h, int(ticket), ctypes.byref(state),
+                                             ctypes.byref(status), ctypes.byref(rep)),
+                   "mpm_server_poll")
+        done = state.value in (_lib.REQ_DONE, _lib.REQ_FAILED)
+        if done:
+            self._keep.pop(ticket, None)
+        return state.value, status.value, rep if done else None
+
+    def close(self):
+        if self._h:
+            self._lib.mpm_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def mpm_workspace_status(ws, stream=None) -> int:

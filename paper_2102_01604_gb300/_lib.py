@@ -26,6 +26,7 @@ ERR_NUMERIC = -4
 ERR_TIMEOUT = -5
 
 CALL_FIT, CALL_SOLVE, CALL_GRAD_HESS, CALL_JTV = 0, 1, 2, 3
+REQ_QUEUED, REQ_ACTIVE, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 
 
 class Problem(ctypes.Structure):
@@ -88,6 +89,14 @@ PROTOTYPES = {
                                      ctypes.POINTER(_V), ctypes.POINTER(_V),
                                      ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(Report), _V]),
     "mpm_workspace_status": (ctypes.c_int, [_V, _S, _V]),
+    "mpm_server_create": (ctypes.c_int, [_V, _S, ctypes.c_int, _V, ctypes.POINTER(_V)]),
+    "mpm_server_submit": (ctypes.c_int, [_V, _P, _O, _V, _V, _V, _V, _V,
+                                         ctypes.POINTER(ctypes.c_int)]),
+    "mpm_server_step": (ctypes.c_int, [_V, ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "mpm_server_poll": (ctypes.c_int, [_V, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(Report)]),
+    "mpm_server_destroy": (ctypes.c_int, [_V]),
     "mpm_autotune": (ctypes.c_int, [_P, _O, _V, _S, _V, ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_float)]),
     "mpm_kernel_launches": (ctypes.c_ulonglong, []),

@@ -236,24 +236,7 @@ static size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
 
 constexpr int kMeanBlocksHost = 304;   // must match the launcher's cap
 
-struct FitWs {
-    WsHeader* hdr;
-    Reduce red;
-    double* mean_parts;
-    double* means;
-    double* nll;       // [MPM_MAX_REPORT + 2]
-    double* jtv;       // [MPM_MAX_REPORT + 2]
-    double* cg_rel;    // [MPM_MAX_REPORT]
-    int* cg_it;        // [MPM_MAX_REPORT]
-    float* w;
-    float* g;
-    float* h;
-    float* xbuf;
-    void* solve;
-    size_t total;
-};
-
-static FitWs layout(const DevProblem& P, int call, void* base)
+FitWs layout(const DevProblem& P, int call, void* base)
 {
     FitWs L;
     memset(&L, 0, sizeof L);
@@ -285,7 +268,7 @@ static FitWs layout(const DevProblem& P, int call, void* base)
     return L;
 }
 
-static mpm_status check_ws(const DevProblem& P, int call, void* ws, size_t ws_bytes, FitWs& L)
+mpm_status check_ws(const DevProblem& P, int call, void* ws, size_t ws_bytes, FitWs& L)
 {
     const size_t need = layout(P, call, nullptr).total;
     if (ws_bytes < need)
@@ -308,7 +291,7 @@ static mpm_status check_ws(const DevProblem& P, int call, void* ws, size_t ws_by
 //  - clamps R2* >= 1e-3, E in [1e-6, 1 - 1e-6], delta in [1e-4, 0.5];
 //    fallbacks R1 = 1/s and A from the first contrast when fewer than two
 //    distinct non-MT flip angles exist, R2* = 20/s without multi-echo data.
-static void initial_maps(const mpm_problem* p, const double* mean, float out[4])
+void initial_maps(const mpm_problem* p, const double* mean, float out[4])
 {
     const int C = p->n_contrasts;
     double lm[MPM_MAX_IMAGES];

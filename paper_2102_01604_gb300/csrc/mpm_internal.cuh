@@ -286,6 +286,28 @@ cudaError_t launch_matvec_tma(const DevProblem& P, const StencilGrid& g, const T
 constexpr size_t kHeaderBytes = 4096;                              // WsHeader, padded
 constexpr size_t kPartialBytes = sizeof(double) * 2 * kMaxBlocks;  // reduction partials
 
+// Carving of a fit / solve workspace (mpm_api.cu).
+struct FitWs {
+    WsHeader* hdr;
+    Reduce red;
+    double* mean_parts;
+    double* means;
+    double* nll;       // [MPM_MAX_REPORT + 2]
+    double* jtv;       // [MPM_MAX_REPORT + 2]
+    double* cg_rel;    // [MPM_MAX_REPORT]
+    int* cg_it;        // [MPM_MAX_REPORT]
+    float* w;
+    float* g;
+    float* h;
+    float* xbuf;
+    void* solve;
+    size_t total;
+};
+
+FitWs layout(const DevProblem& P, int call, void* base);   // base NULL: sizes only
+mpm_status check_ws(const DevProblem& P, int call, void* ws, size_t ws_bytes, FitWs& L);
+void initial_maps(const mpm_problem* p, const double* mean, float out[4]);
+
 mpm_status fail(mpm_status s, const char* fmt, ...);
 mpm_status check_problem(const mpm_problem* p);
 mpm_status check_opts(const mpm_opts* o);

@@ -1,0 +1,94 @@
+"""Continuous batching (mpm_server_*): requests of different sizes, contrast
+and echo counts arrive while others are running, are admitted as arena space
+and slots free up, and each result equals the same request fitted alone with
+mpm_fit (bit for bit: the same launches on the same data)."""
+import numpy as np
+import pytest
+
+from cases import dataset, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+REQUESTS = [
+    ((40, 32, 20), 101, ("PDw", "T1w", "MTw"), (8, 8, 6)),
+    ((24, 24, 16), 102, ("PDw", "T1w"), (6, 5)),
+    ((64, 48, 24), 103, ("PDw", "T1w", "MTw", "VFA15"), (4, 6, 4, 5)),
+    ((32, 20, 12), 104, ("PDw", "T1w", "MTw"), (5, 5, 5)),
+    ((48, 36, 16), 105, ("PDw", "T1w", "MTw"), (7, 4, 6)),
+]
+
+
+@pytest.fixture(scope="module")
+def mpm():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2102_01604_gb300 as m
+    m._lib.load()
+    return m
+
+
+def _req(mpm, spec):
+    shape, seed, contrasts, echoes = spec
+    d = dataset(shape, seed=seed, contrasts=contrasts, n_echoes=echoes)
+    return d, mpm.make_problem(d["prot"], shape)
+
+
+def test_served_results_equal_solo_fits(mpm):
+    import torch
+    opts = mpm.make_opts(gn_iters=30, cg_iters=30, tol_gn=1e-4)
+    reqs = [_req(mpm, s) for s in REQUESTS]
+    # solo
+    solo = []
+    for d, pg in reqs:
+        N = int(np.prod(d["shape"]))
+        y = torch.zeros((pg.n_maps, N), device="cuda")
+        v = torch.zeros((pg.n_maps, N), device="cuda")
+        st, rep = mpm.mpm_fit(pg, opts, to_dev(d["x"]), y, to_dev(d["b1p"]), to_dev(d["b1m"]), var=v)
+        solo.append((y, v, rep, st))
+    # served: an arena that holds about two of the requests at a time, 3 slots
+    sizes = [mpm.mpm_workspace_size(pg, opts) for _, pg in reqs]
+    arena = torch.empty(int(sorted(sizes)[-1] + sorted(sizes)[-2] + (1 << 20)), dtype=torch.uint8,
+                        device="cuda")
+    srv = mpm.Server(arena, max_slots=3)
+    outs, tickets = {}, {}
+    pending = list(range(len(reqs)))
+    rounds = 0
+    max_active = 0
+    while pending or any(srv.poll(t)[0] < 2 for t in tickets.values()):
+        # one new request every other round, while others are running
+        if pending and rounds % 2 == 0:
+            i = pending.pop(0)
+            d, pg = reqs[i]
+            N = int(np.prod(d["shape"]))
+            y = torch.zeros((pg.n_maps, N), device="cuda")
+            v = torch.zeros((pg.n_maps, N), device="cuda")
+            x, bp, bm = to_dev(d["x"]), to_dev(d["b1p"]), to_dev(d["b1m"])
+            tickets[i] = srv.submit(pg, opts, x, y, bp, bm, v)
+            outs[i] = (y, v, x, bp, bm)
+        active, queued, _ = srv.step()
+        max_active = max(max_active, active)
+        rounds += 1
+        assert rounds < 1000
+    assert max_active >= 2                  # requests overlapped
+    for i, t in tickets.items():
+        state, status, rep = srv.poll(t)
+        y, v, rep_solo, st_solo = solo[i]
+        assert state == 2 and status == st_solo
+        assert rep.iters == rep_solo.iters
+        assert list(rep.F[:rep.iters + 1]) == list(rep_solo.F[:rep.iters + 1])
+        assert np.array_equal(to_np(outs[i][0]), to_np(y)), i
+        assert np.array_equal(to_np(outs[i][1]), to_np(v)), i
+    srv.close()
+
+
+def test_server_refuses_requests_larger_than_the_arena(mpm):
+    import torch
+    d, pg = _req(mpm, REQUESTS[2])
+    arena = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    srv = mpm.Server(arena, max_slots=2)
+    N = int(np.prod(d["shape"]))
+    y = torch.zeros((pg.n_maps, N), device="cuda")
+    with pytest.raises(mpm.MPMError) as e:
+        srv.submit(pg, mpm.make_opts(), to_dev(d["x"]), y)
+    assert e.value.status == mpm._lib.ERR_WORKSPACE_TOO_SMALL
+    srv.close()
