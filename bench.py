@@ -65,9 +65,12 @@ def parse_args(argv=None):
                     help="storage of the echo images (computation stays float32)")
     ap.add_argument("--config", choices=["1mm", "0.8mm"], default="1mm",
                     help="1mm: 176x240x256 at 1 mm; 0.8mm: 208x300x320 at 0.8 mm")
-    ap.add_argument("--workload", choices=["plain", "batched"], default="plain",
+    ap.add_argument("--workload", choices=["plain", "batched", "served"], default="plain",
                     help="plain: one subject per fit; batched: 16 uneven subjects per "
-                         "mpm_fit_batch call, compared with plain fits of the same subjects")
+                         "mpm_fit_batch call, compared with plain fits of the same subjects; "
+                         "served: Poisson arrivals through mpm_server_* vs FIFO plain fits")
+    ap.add_argument("--requests", type=int, default=24, help="served: number of requests")
+    ap.add_argument("--rate", type=float, default=3.0, help="served: arrivals per second")
     args = ap.parse_args(argv)
     global SHAPE, VX
     if args.config == "0.8mm":
@@ -615,12 +618,158 @@ def run_batched(args):
     return 0
 
 
+# ----------------------------------------------------------- served arm
+
+SERVED_SIZES = [((64, 64, 64), (1.0, 1.0, 1.0)), ((128, 128, 128), (1.0, 1.0, 1.0)),
+                ((176, 240, 256), (1.0, 1.0, 1.0)), ((208, 300, 320), (0.8, 0.8, 0.8))]
+
+
+def served_requests(n: int, rate: float, seed: int):
+    """Seeded Poisson arrivals; each request draws one of the four volumes,
+    3 or 4 contrasts (PDw, T1w, MTw[, VFA15]) and 4-8 echoes per contrast."""
+    rng = np.random.default_rng(seed + 777)
+    t, out = 0.0, []
+    for i in range(n):
+        t += rng.exponential(1.0 / rate)
+        dims, vx = SERVED_SIZES[int(rng.integers(0, len(SERVED_SIZES)))]
+        nc = int(rng.integers(3, 5))
+        contrasts = ("PDw", "T1w", "MTw", "VFA15")[:nc]
+        echoes = tuple(int(v) for v in rng.integers(4, 9, size=nc))
+        out.append({"arrival": t, "dims": dims, "vx": vx, "contrasts": contrasts, "echoes": echoes})
+    return out
+
+
+def run_served(args):
+    import time as _time
+
+    import torch
+
+    import paper_2102_01604_gb300 as mpm
+    from paper_2102_01604_gb300 import phantom
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    opts = mpm.make_opts(gn_iters=50, cg_iters=CG_ITERS, tol_gn=1e-4)
+    reqs = served_requests(args.requests, args.rate, args.seed + 1000 * rank)
+    for i, r in enumerate(reqs):           # inputs resident before the clock starts
+        prot = phantom.protocol(r["contrasts"], r["echoes"])
+        ph = phantom.phantom(r["dims"], seed=args.seed + 13 * i, n_contrasts=len(r["contrasts"]))
+        yt = torch.from_numpy(ph["y"].astype(np.float32)).to(dev)
+        bp = torch.from_numpy(ph["b1p"].astype(np.float32)).to(dev)
+        bm = torch.from_numpy(ph["b1m"].astype(np.float32)).to(dev)
+        s = mpm.mpm_forward(mpm.make_problem(prot, r["dims"], vx=r["vx"]), yt, bp, bm)
+        sig2, j = [], 0
+        for ne in prot["n_echoes"]:
+            m = s[j].double().mean().item() / SNR
+            sig2.append(m * m)
+            j += ne
+        prot["sigma2"] = sig2
+        r["x"] = phantom.rician_torch(s, prot, args.seed + 29 * i + 1)
+        del s, yt
+        r["problem"] = mpm.make_problem(prot, r["dims"], vx=r["vx"], lam=LAMBDA, eps=EPS)
+        r["b1p"], r["b1m"] = bp, bm
+        r["N"] = int(np.prod(r["dims"]))
+        K = r["problem"].n_maps
+        r["y"] = torch.empty((K, r["N"]), device=dev)
+        r["var"] = torch.empty((K, r["N"]), device=dev)
+        r["ws_bytes"] = mpm.mpm_workspace_size(r["problem"], opts)
+    torch.cuda.synchronize()
+    # one workspace as large as the biggest request for the plain arm; the
+    # served arm gets an arena of 24 GB (or what is free) and 8 slots
+    free, _ = torch.cuda.mem_get_info()
+    arena_bytes = int(min(24 << 30, free * 0.7))
+    arena = torch.empty(arena_bytes, dtype=torch.uint8, device=dev)
+    for r in reqs:                         # warm-up: tile shapes and first launches
+        mpm.mpm_autotune(r["problem"], opts, ws=arena[:max(r["ws_bytes"], 1)])
+    warm = reqs[0]
+    mpm.mpm_fit(warm["problem"], opts, warm["x"], warm["y"], warm["b1p"], warm["b1m"],
+                var=warm["var"], ws=arena[:warm["ws_bytes"]])
+    torch.cuda.synchronize()
+
+    def clock():
+        return _time.perf_counter()
+
+    # plain: one fit at a time, first come first served
+    t0 = clock()
+    lat_plain, units_plain = [], 0.0
+    for r in reqs:
+        now = clock() - t0
+        if now < r["arrival"]:
+            _time.sleep(r["arrival"] - now)
+        st, rep = mpm.mpm_fit(r["problem"], opts, r["x"], r["y"], r["b1p"], r["b1m"], var=r["var"],
+                              ws=arena[:r["ws_bytes"]])
+        lat_plain.append(clock() - t0 - r["arrival"])
+        units_plain += r["N"] * rep.iters
+    span_plain = clock() - t0
+
+    # served: continuous batching
+    launches0 = mpm.mpm_kernel_launches()
+    clocks = ClockSampler(local)
+    clocks.start()
+    srv = mpm.Server(arena, max_slots=8)
+    t0 = clock()
+    nxt, live, lat_srv, units_srv = 0, {}, [None] * len(reqs), 0.0
+    while nxt < len(reqs) or live:
+        now = clock() - t0
+        while nxt < len(reqs) and reqs[nxt]["arrival"] <= now:
+            r = reqs[nxt]
+            live[srv.submit(r["problem"], opts, r["x"], r["y"], r["b1p"], r["b1m"], r["var"])] = nxt
+            nxt += 1
+        if not live:
+            _time.sleep(max(0.0, reqs[nxt]["arrival"] - (clock() - t0)))
+            continue
+        srv.step()
+        for t in list(live):
+            state, status, rep = srv.poll(t)
+            if state >= 2:
+                i = live.pop(t)
+                lat_srv[i] = clock() - t0 - reqs[i]["arrival"]
+                units_srv += reqs[i]["N"] * rep.iters
+    span_srv = clock() - t0
+    clk = clocks.stop()
+    srv.close()
+    launches = mpm.mpm_kernel_launches() - launches0
+    pct = lambda a, q: float(np.percentile(np.array(a), q))
+    if rank == 0:
+        line = {
+            "metric": "Mvoxel·GN-iter/s, served MPM JTV fits (continuous batching); p50/p99 latency",
+            "value": round(units_srv / span_srv / 1e6, 3), "unit": UNIT, "n_gpus": world,
+            "steps": args.requests, "warmup": 1, "ms_per_step": round(1000 * span_srv / args.requests, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "latency_s": {"mean": round(float(np.mean(lat_srv)), 3), "p50": round(pct(lat_srv, 50), 3),
+                          "p99": round(pct(lat_srv, 99), 3)},
+            "plain": {"value": round(units_plain / span_plain / 1e6, 3),
+                      "latency_s": {"mean": round(float(np.mean(lat_plain)), 3),
+                                    "p50": round(pct(lat_plain, 50), 3),
+                                    "p99": round(pct(lat_plain, 99), 3)}},
+            "config": {"workload": f"{args.requests} requests, Poisson arrivals at {args.rate}/s, "
+                                   "volumes 64^3 / 128^3 / 176x240x256 (1 mm) / 208x300x320 (0.8 mm), "
+                                   "3-4 contrasts, 4-8 echoes, stop at |dF|/F < 1e-4 (<= 50 updates), "
+                                   "30 PCG, posterior variance; served: 8 slots, arena "
+                                   f"{arena_bytes / 2**30:.1f} GiB; plain: FIFO one fit at a time",
+                       "mix": [[*r["dims"], len(r["contrasts"])] for r in reqs],
+                       "steps_meaning": "requests"},
+            "gpu_launches": int(launches), "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "served":
+        return run_served(args)
     return run_ours(args)
 
 

@@ -245,23 +245,29 @@ mpm_status mpm_fit_batch(int n, const mpm_problem* const* problems, const mpm_op
  * subject at a time).  The server owns no device memory: every admitted
  * request's fit workspace is carved from `arena` (caller-owned device memory,
  * 256-byte aligned), so admission follows the free HBM the caller hands over.
- * Requests are admitted first come first served while one of `max_slots`
- * slots is free and their workspace fits; an active request keeps its maps,
- * weights, gradient, Hessian and PCG state resident in the arena between
- * rounds.  The server creates `max_slots` CUDA streams of its own (one per
- * slot); `stream` is the caller's stream on which the request inputs are
- * produced (each request waits for it at admission).
+ * Requests are admitted while one of `max_slots` slots is free and their
+ * workspace fits, smallest volume first (ties by arrival; when the smallest
+ * does not fit, the first in arrival order that does); a request overtaken by
+ * 2 x max_slots later ones goes before all others, so none starves.  An
+ * active request keeps its maps, weights, gradient, Hessian and PCG state
+ * resident in the arena until it is done.  The server creates CUDA streams of its own (per slot, one for each
+ * stream priority level of the device) and pinned host staging per slot;
+ * `stream` is the caller's stream on which the request inputs are produced
+ * (each request waits for the state of that stream at its submission).
  *  - mpm_server_submit: queue one fit (same arguments as mpm_fit minus the
  *    workspace and report; x, b1p, b1m, y_inout, var_out stay caller-owned
  *    and must stay valid until the request is done).  Returns a ticket.
  *    Refuses requests larger than the whole arena.
- *  - mpm_server_step: one round -- admit what fits, advance every active
- *    request by one update (its pending PCG solve, then the objective at the
- *    new maps) on its own stream so their kernels overlap, wait once, apply
- *    the stopping rule of mpm_fit (tol_gn on the objective, or gn_iters), and
- *    finish the requests that stop (uncertainty if var_out was given, report)
- *    releasing their workspace.  Reports the active, queued and just-finished
- *    counts (any pointer may be NULL).
+ *  - mpm_server_step: one non-blocking pass -- every active request whose
+ *    last enqueued work has completed moves on (initial maps; the stopping
+ *    rule of mpm_fit on its objective; then either its PCG solve, update and
+ *    next evaluation, or its uncertainty and report; finished requests
+ *    release their workspace), then queued requests are admitted into free
+ *    slots while the arena has room.  Requests run on their own streams and
+ *    advance independently, so their kernels overlap on the GPU; smaller
+ *    volumes get higher stream priorities (below 2^19 voxels the highest,
+ *    one level lower per doubling).  Call it in a loop; reports the active,
+ *    queued and just-finished counts (any pointer may be NULL).
  *  - mpm_server_poll: state of a ticket (MPM_REQ_*), its final status and,
  *    once done, its report.
  * A request's result equals mpm_fit's with the same arguments.  The server is

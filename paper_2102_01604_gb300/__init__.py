@@ -282,7 +282,9 @@ class Server:
         return t.value
 
     def step(self):
-        """One scheduling round; returns (active, queued, finished)."""
+        """One non-blocking pass: advances every request whose last enqueued
+        work has completed, admits queued ones; returns (active, queued,
+        finished).  Call it in a loop."""
         a, q, f = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _lib.check(self._lib.mpm_server_step(self._h, ctypes.byref(a), ctypes.byref(q),
                                              ctypes.byref(f)), "mpm_server_step")

@@ -1,20 +1,25 @@
 // server.cu -- continuous batching of fit requests (mpm_server_*).
 //
 // Requests (one subject each, any matrix size, contrasts and echo counts) are
-// queued by mpm_server_submit.  Each mpm_server_step is one scheduling round:
-//   1. admit queued requests, first come first served, while a slot is free
-//      and their fit workspace fits in the free part of the caller's device
-//      arena (the library allocates nothing);
-//   2. advance every active request by one update on its own stream -- the
-//      PCG solve of the previous update and the evaluation of the objective
-//      at the new maps -- so the requests' kernels overlap on the GPU;
-//   3. wait once for all slots and test convergence on the host
-//      (|F_prev - F| < tol_gn |F_prev|, or gn_iters reached);
-//   4. finish converged requests (uncertainty if asked, report), free their
-//      workspace.
-// Maps, JTV weights, gradients, Hessians and PCG state stay resident in the
-// arena between rounds.  Each request runs exactly the launches of mpm_fit
-// with the same schedule, so its result is the same alone and in the mix.
+// queued by mpm_server_submit and run asynchronously, each on its own slot
+// stream, through a small state machine driven by mpm_server_step:
+//   admitted  -> image means enqueued (constant initial maps need them on the
+//                host), workspace carved from the caller's device arena;
+//   init      -> when the means have landed: initial maps, first evaluation
+//                of the objective, its two doubles copied to pinned memory;
+//   evaluate  -> when that copy has landed: the stopping rule of mpm_fit
+//                (|F_prev - F| < tol_gn |F_prev|, or gn_iters); if it goes
+//                on, the PCG solve and update and the next evaluation are
+//                enqueued at once; otherwise
+//   finish    -> uncertainty (if asked) and the report copied out; when that
+//                has landed the request is done and its workspace is freed.
+// A step never blocks: it only queries CUDA events, so every request moves at
+// its own pace and the kernels of all active requests overlap on the GPU.
+// Smaller volumes run on higher-priority streams (shortest job first at the
+// block scheduler), so a small request is not held behind a large one.
+// Maps, JTV weights, gradient, Hessian and PCG state stay resident in the
+// arena.  Each request runs exactly the launches of mpm_fit, so its result is
+// the same alone and in the mix.
 #include <deque>
 #include <map>
 #include <mutex>
@@ -25,10 +30,12 @@
 namespace mpm {
 
 enum ReqState { kQueued = 0, kActive = 1, kDone = 2, kFailed = 3 };
+enum Phase { kInit = 0, kEval = 1, kFinish = 2 };
 
 struct Request {
     int ticket;
     int state;
+    int phase;
     mpm_problem problem;
     mpm_opts opts;
     DevProblem P;
@@ -38,12 +45,23 @@ struct Request {
     size_t ws_off, ws_bytes;
     FitWs L;
     int slot;
+    int overtaken;            // later requests admitted before this one
+    cudaStream_t stream;      // the slot's stream of this request's priority
     int it;
-    bool solve_pending, w_fresh;
+    bool w_fresh;
     double F_prev;
     mpm_report report;
     mpm_status status;
     cudaEvent_t ready;        // inputs ready on the caller's stream
+    cudaEvent_t landed;       // the slot's last enqueued host copy has completed
+};
+
+// Pinned host staging of one slot.
+struct SlotHost {
+    double f[2];              // nll, jtv of the latest evaluation
+    double means[MPM_MAX_IMAGES];
+    unsigned status;
+    mpm_report report;
 };
 
 struct Arena {
@@ -105,14 +123,13 @@ struct mpm_server {
     Arena arena;
     int max_slots;
     cudaStream_t user;
-    std::vector<cudaStream_t> slots;
+    int prio_hi, n_prio;               // greatest priority, number of levels
+    std::vector<cudaStream_t> slots;   // [slot * n_prio + level], level 0 highest
     std::vector<int> slot_owner;       // ticket or -1
     std::deque<int> queue;
     std::map<int, Request> reqs;
     int next_ticket = 1;
-    double* host_f;                    // pinned: nll, jtv per slot
-    double* host_means;                // pinned: image means per slot
-    unsigned* host_status;             // pinned: status word per slot
+    SlotHost* host;                    // pinned, one per slot
 };
 
 #define SRV_CUDA(call)                                                                   \
@@ -122,10 +139,44 @@ struct mpm_server {
             return fail(MPM_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));          \
     } while (0)
 
-static mpm_status srv_sync(mpm_server* s)
+// Evaluation of the objective at the current maps (same launches as mpm_fit),
+// its two doubles copied to the slot's pinned staging.
+static mpm_status srv_eval(mpm_server* s, Request& r)
 {
-    for (int k = 0; k < s->max_slots; ++k)
-        if (s->slot_owner[k] >= 0) SRV_CUDA(cudaStreamSynchronize(s->slots[k]));
+    cudaStream_t st = r.stream;
+    const FitWs& L = r.L;
+    r.w_fresh = (r.it % r.opts.newton_per_irls == 0);
+    SRV_CUDA(launch_jtv(r.P, r.y, r.w_fresh ? L.w : nullptr, L.jtv + r.it, L.red, st));
+    SRV_CUDA(launch_grad_hess(r.P, r.problem.echo_dtype, r.x, r.y, r.b1p, r.b1m, L.g, L.h,
+                              L.nll + r.it, L.red, st));
+    SlotHost& h = s->host[r.slot];
+    SRV_CUDA(cudaMemcpyAsync(&h.f[0], L.nll + r.it, sizeof(double), cudaMemcpyDeviceToHost, st));
+    SRV_CUDA(cudaMemcpyAsync(&h.f[1], L.jtv + r.it, sizeof(double), cudaMemcpyDeviceToHost, st));
+    SRV_CUDA(cudaEventRecord(r.landed, st));
+    r.phase = kEval;
+    return MPM_OK;
+}
+
+// Uncertainty (if asked) and the report, copied to the slot's staging.
+static mpm_status srv_finish(mpm_server* s, Request& r)
+{
+    cudaStream_t st = r.stream;
+    const FitWs& L = r.L;
+    const int it = r.it;
+    if (r.var) {
+        if (!r.w_fresh) SRV_CUDA(launch_jtv(r.P, r.y, L.w, L.jtv + MPM_MAX_REPORT + 1, L.red, st));
+        SRV_CUDA(launch_uncertainty(r.P, L.h, L.w, r.y, r.var, nullptr, nullptr, &L.hdr->status, st));
+    }
+    SlotHost& h = s->host[r.slot];
+    SRV_CUDA(cudaMemcpyAsync(h.report.nll, L.nll, sizeof(double) * (it + 1), cudaMemcpyDeviceToHost, st));
+    SRV_CUDA(cudaMemcpyAsync(h.report.jtv, L.jtv, sizeof(double) * (it + 1), cudaMemcpyDeviceToHost, st));
+    if (it > 0) {
+        SRV_CUDA(cudaMemcpyAsync(h.report.cg_rel, L.cg_rel, sizeof(double) * it, cudaMemcpyDeviceToHost, st));
+        SRV_CUDA(cudaMemcpyAsync(h.report.cg_done, L.cg_it, sizeof(int) * it, cudaMemcpyDeviceToHost, st));
+    }
+    SRV_CUDA(cudaMemcpyAsync(&h.status, &L.hdr->status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    SRV_CUDA(cudaEventRecord(r.landed, st));
+    r.phase = kFinish;
     return MPM_OK;
 }
 
@@ -144,20 +195,26 @@ mpm_status mpm_server_create(void* arena, size_t arena_bytes, int max_slots, voi
     s->arena.init(arena, arena_bytes);
     s->max_slots = max_slots;
     s->user = (cudaStream_t)stream;
-    s->slots.resize(max_slots);
+    int least = 0, greatest = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e != cudaSuccess) {
+        delete s;
+        return fail(MPM_ERR_CUDA, "cudaDeviceGetStreamPriorityRange: %s", cudaGetErrorString(e));
+    }
+    s->prio_hi = greatest;
+    s->n_prio = least - greatest + 1;      // greatest is numerically the smallest
+    s->slots.resize((size_t)max_slots * s->n_prio);
     s->slot_owner.assign(max_slots, -1);
-    for (int k = 0; k < max_slots; ++k) {
-        cudaError_t e = cudaStreamCreateWithFlags(&s->slots[k], cudaStreamNonBlocking);
+    for (size_t k = 0; k < s->slots.size(); ++k) {
+        e = cudaStreamCreateWithPriority(&s->slots[k], cudaStreamNonBlocking,
+                                         greatest + (int)(k % s->n_prio));
         if (e != cudaSuccess) {
-            for (int j = 0; j < k; ++j) cudaStreamDestroy(s->slots[j]);
+            for (size_t j = 0; j < k; ++j) cudaStreamDestroy(s->slots[j]);
             delete s;
-            return fail(MPM_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+            return fail(MPM_ERR_CUDA, "cudaStreamCreateWithPriority: %s", cudaGetErrorString(e));
         }
     }
-    cudaError_t e = cudaHostAlloc((void**)&s->host_f, sizeof(double) * 2 * max_slots, 0);
-    if (e == cudaSuccess)
-        e = cudaHostAlloc((void**)&s->host_means, sizeof(double) * MPM_MAX_IMAGES * max_slots, 0);
-    if (e == cudaSuccess) e = cudaHostAlloc((void**)&s->host_status, sizeof(unsigned) * max_slots, 0);
+    e = cudaHostAlloc((void**)&s->host, sizeof(SlotHost) * max_slots, 0);
     if (e != cudaSuccess) {
         for (auto st2 : s->slots) cudaStreamDestroy(st2);
         delete s;
@@ -202,6 +259,7 @@ mpm_status mpm_server_submit(mpm_server* s, const mpm_problem* problem, const mp
     r.ws_bytes = need;
     r.slot = -1;
     cudaError_t e = cudaEventCreateWithFlags(&r.ready, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r.landed, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventRecord(r.ready, s->user);
     if (e != cudaSuccess) return fail(MPM_ERR_CUDA, "event: %s", cudaGetErrorString(e));
     s->reqs[r.ticket] = r;
@@ -214,130 +272,123 @@ mpm_status mpm_server_step(mpm_server* s, int* n_active, int* n_queued, int* n_f
 {
     if (!s) return fail(MPM_ERR_INVALID_ARG, "server is NULL");
     std::lock_guard<std::mutex> lk(s->mu);
-    // 1. admission (first come first served)
-    std::vector<int> admitted;
+    int finished = 0;
+    // advance every active request whose last enqueued copy has landed
+    for (int k = 0; k < s->max_slots; ++k) {
+        if (s->slot_owner[k] < 0) continue;
+        Request& r = s->reqs[s->slot_owner[k]];
+        const cudaError_t q = cudaEventQuery(r.landed);
+        if (q == cudaErrorNotReady) continue;
+        if (q != cudaSuccess) return fail(MPM_ERR_CUDA, "cudaEventQuery: %s", cudaGetErrorString(q));
+        SlotHost& h = s->host[k];
+        if (r.phase == kInit) {
+            if (r.opts.init) {
+                float vals[4];
+                initial_maps(&r.problem, h.means, vals);
+                SRV_CUDA(launch_fill_maps(r.P, vals, r.y, r.stream));
+            }
+            mpm_status st = srv_eval(s, r);
+            if (st != MPM_OK) return st;
+        } else if (r.phase == kEval) {
+            const double F = h.f[0] + h.f[1];
+            bool stop = r.it >= r.opts.gn_iters;
+            bool converged = false;
+            if (!stop && r.opts.tol_gn > 0.0 && r.it > 0 &&
+                std::fabs(r.F_prev - F) < r.opts.tol_gn * std::fabs(r.F_prev)) {
+                stop = converged = true;
+            }
+            mpm_status st;
+            if (stop) {
+                r.report.iters = r.it;
+                r.status = (r.opts.tol_gn > 0.0 && !converged) ? MPM_WARN_NOT_CONVERGED : MPM_OK;
+                st = srv_finish(s, r);
+            } else {
+                r.F_prev = F;
+                const FitWs& L = r.L;
+                SRV_CUDA(launch_solve(r.P, r.opts.cg_iters, r.opts.tol_cg, L.h, L.w, L.g, r.y, L.xbuf,
+                                      r.y, nullptr, L.cg_rel + r.it, L.cg_it + r.it, L.solve, L.hdr,
+                                      L.red, r.stream));
+                r.it += 1;
+                st = srv_eval(s, r);
+            }
+            if (st != MPM_OK) return st;
+        } else {                              // kFinish: the report has landed
+            const int iters = r.report.iters;
+            memcpy(r.report.nll, h.report.nll, sizeof(double) * (iters + 1));
+            memcpy(r.report.jtv, h.report.jtv, sizeof(double) * (iters + 1));
+            memcpy(r.report.cg_rel, h.report.cg_rel, sizeof(double) * iters);
+            memcpy(r.report.cg_done, h.report.cg_done, sizeof(int) * iters);
+            for (int i = 0; i <= iters; ++i) r.report.F[i] = r.report.nll[i] + r.report.jtv[i];
+            if (h.status) r.status = MPM_ERR_NUMERIC;
+            r.state = r.status < 0 ? kFailed : kDone;
+            s->slot_owner[k] = -1;
+            s->arena.release(r.ws_off, r.ws_bytes);
+            cudaEventDestroy(r.ready);
+            cudaEventDestroy(r.landed);
+            r.slot = -1;
+            ++finished;
+        }
+    }
+    // admission into free slots while the arena has room: smallest volume
+    // first (ties by arrival); a queued request overtaken by 2 x max_slots
+    // later ones is admitted before anything else, so none starves
     while (!s->queue.empty()) {
         int k = 0;
         while (k < s->max_slots && s->slot_owner[k] >= 0) ++k;
         if (k == s->max_slots) break;
-        Request& r = s->reqs[s->queue.front()];
+        auto pick = s->queue.end();
+        bool urgent = false;
+        for (auto q = s->queue.begin(); q != s->queue.end(); ++q) {
+            const Request& c = s->reqs[*q];
+            if (c.overtaken >= 2 * s->max_slots) {
+                pick = q;
+                urgent = true;
+                break;
+            }
+            if (pick == s->queue.end() || c.P.N < s->reqs[*pick].P.N) pick = q;
+        }
         size_t off;
-        if (!s->arena.alloc(r.ws_bytes, &off)) break;
-        s->queue.pop_front();
-        r.ws_off = off;
-        r.L = layout(r.P, MPM_CALL_FIT, s->arena.base + off);
-        r.slot = k;
-        r.state = kActive;
-        r.it = 0;
-        r.solve_pending = false;
-        s->slot_owner[k] = r.ticket;
-        cudaStream_t st = s->slots[k];
-        SRV_CUDA(cudaStreamWaitEvent(st, r.ready, 0));
-        SRV_CUDA(cudaMemsetAsync(r.L.hdr, 0, sizeof(WsHeader), st));
-        if (r.opts.init) {
-            SRV_CUDA(launch_image_means(r.P, r.problem.echo_dtype, r.x, r.L.mean_parts, r.L.means, st));
-            SRV_CUDA(cudaMemcpyAsync(s->host_means + (size_t)k * MPM_MAX_IMAGES, r.L.means,
-                                     sizeof(double) * r.P.I, cudaMemcpyDeviceToHost, st));
+        if (!s->arena.alloc(s->reqs[*pick].ws_bytes, &off)) {
+            if (urgent) break;                // it waits for room, nothing overtakes it
+            // the smallest does not fit: the first in arrival order that does
+            pick = s->queue.end();
+            for (auto q = s->queue.begin(); q != s->queue.end(); ++q)
+                if (s->arena.alloc(s->reqs[*q].ws_bytes, &off)) {
+                    pick = q;
+                    break;
+                }
+            if (pick == s->queue.end()) break;
         }
-        admitted.push_back(r.ticket);
-    }
-    if (!admitted.empty()) {
-        mpm_status st = srv_sync(s);
-        if (st != MPM_OK) return st;
-        for (int t : admitted) {
-            Request& r = s->reqs[t];
-            if (!r.opts.init) continue;
-            float vals[4];
-            initial_maps(&r.problem, s->host_means + (size_t)r.slot * MPM_MAX_IMAGES, vals);
-            SRV_CUDA(launch_fill_maps(r.P, vals, r.y, s->slots[r.slot]));
+        Request& a = s->reqs[*pick];
+        for (auto q = s->queue.begin(); q != pick; ++q) s->reqs[*q].overtaken += 1;
+        s->queue.erase(pick);
+        a.ws_off = off;
+        a.L = layout(a.P, MPM_CALL_FIT, s->arena.base + off);
+        a.slot = k;
+        a.state = kActive;
+        a.phase = kInit;
+        a.it = 0;
+        s->slot_owner[k] = a.ticket;
+        // priority level by size: volumes below 2^19 voxels highest, one level
+        // lower per doubling, the rest at the lowest level
+        int lv = 0;
+        for (size_t n = a.P.N >> 19; n && lv < s->n_prio - 1; n >>= 1) ++lv;
+        a.stream = s->slots[(size_t)k * s->n_prio + lv];
+        cudaStream_t st = a.stream;
+        SRV_CUDA(cudaStreamWaitEvent(st, a.ready, 0));
+        SRV_CUDA(cudaMemsetAsync(a.L.hdr, 0, sizeof(WsHeader), st));
+        if (a.opts.init) {
+            SRV_CUDA(launch_image_means(a.P, a.problem.echo_dtype, a.x, a.L.mean_parts, a.L.means, st));
+            SRV_CUDA(cudaMemcpyAsync(s->host[k].means, a.L.means, sizeof(double) * a.P.I,
+                                     cudaMemcpyDeviceToHost, st));
         }
-    }
-    // 2. one update per active request, each on its own stream
-    for (int k = 0; k < s->max_slots; ++k) {
-        if (s->slot_owner[k] < 0) continue;
-        Request& r = s->reqs[s->slot_owner[k]];
-        cudaStream_t st = s->slots[k];
-        const DevProblem& P = r.P;
-        const FitWs& L = r.L;
-        if (r.solve_pending) {
-            SRV_CUDA(launch_solve(P, r.opts.cg_iters, r.opts.tol_cg, L.h, L.w, L.g, r.y, L.xbuf, r.y,
-                                  nullptr, L.cg_rel + r.it - 1, L.cg_it + r.it - 1, L.solve, L.hdr,
-                                  L.red, st));
-            r.solve_pending = false;
-        }
-        r.w_fresh = (r.it % r.opts.newton_per_irls == 0);
-        SRV_CUDA(launch_jtv(P, r.y, r.w_fresh ? L.w : nullptr, L.jtv + r.it, L.red, st));
-        SRV_CUDA(launch_grad_hess(P, r.problem.echo_dtype, r.x, r.y, r.b1p, r.b1m, L.g, L.h,
-                                  L.nll + r.it, L.red, st));
-        SRV_CUDA(cudaMemcpyAsync(s->host_f + 2 * k, L.nll + r.it, sizeof(double),
-                                 cudaMemcpyDeviceToHost, st));
-        SRV_CUDA(cudaMemcpyAsync(s->host_f + 2 * k + 1, L.jtv + r.it, sizeof(double),
-                                 cudaMemcpyDeviceToHost, st));
-    }
-    // 3. one wait, then the stopping test (same rule as mpm_fit)
-    mpm_status st = srv_sync(s);
-    if (st != MPM_OK) return st;
-    std::vector<int> finishing;
-    for (int k = 0; k < s->max_slots; ++k) {
-        if (s->slot_owner[k] < 0) continue;
-        Request& r = s->reqs[s->slot_owner[k]];
-        const double F = s->host_f[2 * k] + s->host_f[2 * k + 1];
-        bool stop = r.it >= r.opts.gn_iters;
-        bool converged = false;
-        if (!stop && r.opts.tol_gn > 0.0 && r.it > 0 &&
-            std::fabs(r.F_prev - F) < r.opts.tol_gn * std::fabs(r.F_prev)) {
-            stop = true;
-            converged = true;
-        }
-        if (stop) {
-            r.report.iters = r.it;
-            r.status = (r.opts.tol_gn > 0.0 && !converged) ? MPM_WARN_NOT_CONVERGED : MPM_OK;
-            finishing.push_back(r.ticket);
-        } else {
-            r.F_prev = F;
-            r.solve_pending = true;
-            r.it += 1;
-        }
-    }
-    // 4. finish: uncertainty, reports, free the workspace
-    if (!finishing.empty()) {
-        for (int t : finishing) {
-            Request& r = s->reqs[t];
-            cudaStream_t stm = s->slots[r.slot];
-            const int it = r.it;
-            if (r.var) {
-                if (!r.w_fresh)
-                    SRV_CUDA(launch_jtv(r.P, r.y, r.L.w, r.L.jtv + MPM_MAX_REPORT + 1, r.L.red, stm));
-                SRV_CUDA(launch_uncertainty(r.P, r.L.h, r.L.w, r.y, r.var, nullptr, nullptr,
-                                            &r.L.hdr->status, stm));
-            }
-            SRV_CUDA(cudaMemcpyAsync(r.report.nll, r.L.nll, sizeof(double) * (it + 1), cudaMemcpyDeviceToHost, stm));
-            SRV_CUDA(cudaMemcpyAsync(r.report.jtv, r.L.jtv, sizeof(double) * (it + 1), cudaMemcpyDeviceToHost, stm));
-            if (it > 0) {
-                SRV_CUDA(cudaMemcpyAsync(r.report.cg_rel, r.L.cg_rel, sizeof(double) * it, cudaMemcpyDeviceToHost, stm));
-                SRV_CUDA(cudaMemcpyAsync(r.report.cg_done, r.L.cg_it, sizeof(int) * it, cudaMemcpyDeviceToHost, stm));
-            }
-            SRV_CUDA(cudaMemcpyAsync(s->host_status + r.slot, &r.L.hdr->status, sizeof(unsigned),
-                                     cudaMemcpyDeviceToHost, stm));
-        }
-        st = srv_sync(s);
-        if (st != MPM_OK) return st;
-        for (int t : finishing) {
-            Request& r = s->reqs[t];
-            for (int i = 0; i <= r.it; ++i) r.report.F[i] = r.report.nll[i] + r.report.jtv[i];
-            if (s->host_status[r.slot]) r.status = MPM_ERR_NUMERIC;
-            r.state = r.status < 0 ? kFailed : kDone;
-            s->slot_owner[r.slot] = -1;
-            s->arena.release(r.ws_off, r.ws_bytes);
-            cudaEventDestroy(r.ready);
-            r.slot = -1;
-        }
+        SRV_CUDA(cudaEventRecord(a.landed, st));
     }
     int active = 0;
     for (int k = 0; k < s->max_slots; ++k) active += s->slot_owner[k] >= 0;
     if (n_active) *n_active = active;
     if (n_queued) *n_queued = (int)s->queue.size();
-    if (n_finished) *n_finished = (int)finishing.size();
+    if (n_finished) *n_finished = finished;
     return MPM_OK;
 }
 
@@ -365,10 +416,11 @@ mpm_status mpm_server_destroy(mpm_server* s)
             cudaStreamDestroy(st);
         }
         for (auto& kv : s->reqs)
-            if (kv.second.state == kQueued || kv.second.state == kActive) cudaEventDestroy(kv.second.ready);
-        cudaFreeHost(s->host_f);
-        cudaFreeHost(s->host_means);
-        cudaFreeHost(s->host_status);
+            if (kv.second.state == kQueued || kv.second.state == kActive) {
+                cudaEventDestroy(kv.second.ready);
+                cudaEventDestroy(kv.second.landed);
+            }
+        cudaFreeHost(s->host);
     }
     delete s;
     return MPM_OK;
