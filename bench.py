@@ -253,7 +253,7 @@ def measured_peak():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for name in ("stencil_kernels.cu", "voxel_kernels.cu", "mpm_internal.cuh"):
+    for name in ("stencil_kernels.cu", "stencil_tma.cu", "voxel_kernels.cu", "mpm_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2102_01604_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

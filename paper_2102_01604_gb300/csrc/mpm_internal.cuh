@@ -213,7 +213,7 @@ __device__ __forceinline__ float load_echo<__nv_bfloat16>(const __nv_bfloat16* p
 
 struct StencilGrid {
     dim3 grid, block;
-    int zc;           // z planes per block
+    int zc;           // z planes per block (TMA matvec: number of z ranges)
 };
 
 StencilGrid stencil_grid(const DevProblem& P, int tile_x, int tile_y);

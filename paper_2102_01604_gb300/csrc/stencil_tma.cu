@@ -3,20 +3,25 @@
 // Same operator as k_pcg_matvec (stencil_kernels.cu): per voxel
 //   q_k = sum_j H_kj p_j + lambda_k sum_{m in N(n)} (w_n + w_m)(p_k[n] - p_k[m]) / h^2,
 // but every operand reaches shared memory through the tensor memory
-// accelerator: for each z plane, one thread issues three bulk tensor copies
-//   p  box 24 x 18 x 1 x K  at (x0 - 4, y0 - 1, z, 0)   (tile plus x / y halo)
-//   w  box 24 x 18 x 1      at (x0 - 4, y0 - 1, z)
-//   H  box 16 x 16 x 1 x T  at (x0, y0, z, 0)           (only planes the block owns)
-// into a ring of kStages stage buffers.  A producer warp issues the copies; a
-// stage is refilled as soon as the eight compute warps have released it, so
-// while a warp computes plane z the copies for planes up to z + 3 can be in
-// flight and no compute thread holds loads in registers.  x coordinates are multiples of 4 floats (16 bytes); boxes that
-// leave the volume are zero-filled by the copy engine and masked by the
+// accelerator.  For a tile of TX x TY voxels and each z plane, one thread
+// issues bulk tensor copies
+//   p  box (TX+8) x (TY+2) x 1 x K  at (x0 - 4, y0 - 1, z, 0)   (tile plus x / y halo)
+//   w  box (TX+8) x (TY+2) x 1      at (x0 - 4, y0 - 1, z)
+//   H  box TX x TY x 1 x T          at (x0, y0, z, 0)           (only planes computed)
+// into two rings: p / w planes (kStagesPW deep; plane z needs z - 1, z and
+// z + 1) and H planes (kStagesH deep; plane z needs only its own).  A
+// producer warp issues the copies; a stage is refilled as soon as the eight
+// compute warps have released it, so both streams run two planes ahead of
+// the compute and no compute thread holds loads in registers.  The depth is
+// what sets the speed: the copies in flight per SM have to cover the loaded
+// DRAM latency.  x coordinates are multiples of 4 floats (16 bytes); boxes
+// that leave the volume are zero-filled by the copy engine and masked by the
 // boundary flags.  Every mbarrier wait is bounded: on timeout the block
 // records kStatusTimeout, stops computing, drains its outstanding copies
 // (bounded again) and still takes part in the grid reduction.
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -25,7 +30,8 @@
 
 namespace mpm {
 
-constexpr int kStages = 4;
+constexpr int kStagesPW = 5;                   // p / w ring
+constexpr int kStagesH = 3;                    // H ring
 constexpr int kTmaVoxels = 256;                // voxels per tile, one compute thread each
 constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
 
@@ -39,12 +45,14 @@ struct TmaLayout {
     static constexpr int W_FLOATS = BY * BX;
     static constexpr int H_FLOATS = T * TY * TX;
     static constexpr int align128(int bytes) { return (bytes + 127) / 128 * 128; }
+    // p / w stage: p then w; H stages follow the p / w ring
     static constexpr int P_OFF = 0;
     static constexpr int W_OFF = align128(P_FLOATS * 4);
-    static constexpr int H_OFF = W_OFF + align128(W_FLOATS * 4);
-    static constexpr int STAGE = H_OFF + align128(H_FLOATS * 4);
+    static constexpr int PW_STAGE = W_OFF + align128(W_FLOATS * 4);
+    static constexpr int H_STAGE = align128(H_FLOATS * 4);
+    static constexpr int H_BASE = kStagesPW * PW_STAGE;
     static constexpr int P_BYTES = P_FLOATS * 4, W_BYTES = W_FLOATS * 4, H_BYTES = H_FLOATS * 4;
-    static constexpr int SMEM = kStages * STAGE + 128;   // + alignment slack
+    static constexpr int SMEM = H_BASE + kStagesH * H_STAGE + 128;   // + alignment slack
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -63,15 +71,18 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
                  : "memory");
 }
 
+// One try: the thread may be suspended until the phase completes or about
+// 20 us pass (the suspend-time hint), so waiting warps do not spin on issue
+// slots the compute warps need.
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
 {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(20000u)
         : "memory");
     return ok != 0;
 }
@@ -117,9 +128,16 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 constexpr int kConsumerWarps = kTmaVoxels / 32;
 constexpr int kTmaThreads = kTmaVoxels + 32;
 
+// Work split: the launch is one wave of resident blocks.  The volume is cut
+// into items -- one tile column over one of `nchunk` z ranges -- numbered
+// i = chunk * tiles + tile, and block b takes items b, b + G, b + 2G, ...
+// (G = gridDim.x), so the blocks running at one time cover neighbouring
+// tiles of the same z ranges (their DRAM rows and halos are shared).  The
+// ring and its phases run on from one item to the next, so the copies of the
+// next item overlap the end of the current one.
 template <int K, int TX, int TY>
 __global__ void __launch_bounds__(kTmaThreads) k_pcg_matvec_tma(
-    DevProblem P, int zc, int k_it, const __grid_constant__ CUtensorMap tp,
+    DevProblem P, int nchunk, int k_it, const __grid_constant__ CUtensorMap tp,
     const __grid_constant__ CUtensorMap tw, const __grid_constant__ CUtensorMap th,
     float* __restrict__ qout, WsHeader* hdr, Reduce red)
 {
@@ -127,8 +145,8 @@ __global__ void __launch_bounds__(kTmaThreads) k_pcg_matvec_tma(
     constexpr int kTmaBoxX = L::BX, kTmaBoxY = L::BY, kTmaTX = TX, kTmaTY = TY;
     static_assert(TX * TY == kTmaVoxels, "one compute thread per voxel");
     extern __shared__ unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t full[kStages];
-    __shared__ __align__(8) uint64_t empty[kStages];
+    __shared__ __align__(8) uint64_t pw_full[kStagesPW], pw_empty[kStagesPW];
+    __shared__ __align__(8) uint64_t h_full[kStagesH], h_empty[kStagesH];
     __shared__ int s_done;
     __shared__ volatile int s_fail;
     unsigned char* smem =
@@ -140,110 +158,158 @@ __global__ void __launch_bounds__(kTmaThreads) k_pcg_matvec_tma(
     const int tx = tid % kTmaTX, ty = tid / kTmaTX;          // meaningful for compute warps
     const int nx = P.nx, ny = P.ny, nz = P.nz;
     const long long N = P.N;
-    const int x0 = blockIdx.x * kTmaTX, y0 = blockIdx.y * kTmaTY;
-    const int z0 = blockIdx.z * zc;
-    const int z1 = min(nz, z0 + zc);
-    const int j0 = max(z0 - 1, 0);          // first plane this block loads
-    const int jmax = min(z1, nz - 1);       // last plane this block loads
+    const int gx = (nx + TX - 1) / TX;
+    const int tiles = gx * ((ny + TY - 1) / TY);
+    const int items = tiles * nchunk;
 
     if (tid == 0) {
         s_done = hdr->sc.done;
         s_fail = 0;
-        for (int s = 0; s < kStages; ++s) {
-            mbar_init(smem_u32(&full[s]), 1);
-            mbar_init(smem_u32(&empty[s]), kConsumerWarps);
+        for (int s = 0; s < kStagesPW; ++s) {
+            mbar_init(smem_u32(&pw_full[s]), 1);
+            mbar_init(smem_u32(&pw_empty[s]), kConsumerWarps);
+        }
+        for (int s = 0; s < kStagesH; ++s) {
+            mbar_init(smem_u32(&h_full[s]), 1);
+            mbar_init(smem_u32(&h_empty[s]), kConsumerWarps);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     const bool done = s_done != 0;
 
-    auto stage_of = [&](int j) { return (j - j0) % kStages; };
-    auto fill_of = [&](int j) { return (j - j0) / kStages; };
+    // Load counters: c over the p / w planes this block loads, e over its H
+    // planes (one per computed plane), both in order -> ring stage and phase.
+    auto pw_stage = [](int c) { return (int)((unsigned)c % (unsigned)kStagesPW); };
+    auto pw_phase = [](int c) { return (uint32_t)(((unsigned)c / (unsigned)kStagesPW) & 1u); };
+    auto h_stage = [](int e) { return (int)((unsigned)e % (unsigned)kStagesH); };
+    auto h_phase = [](int e) { return (uint32_t)(((unsigned)e / (unsigned)kStagesH) & 1u); };
+    auto pw_ptr = [&](int c) { return smem + pw_stage(c) * L::PW_STAGE; };
 
     Acc pq;
-    int issued_to = j0 - 1;
+    int pw_issued = -1, h_issued = -1;  // last counters issued (producer lane 0)
     if (!done && producer) {
         if (lane == 0) {
-            for (int j = j0; j <= jmax; ++j) {
-                const int s = stage_of(j), f = fill_of(j);
-                // the plane that held this stage must be released by every compute warp
-                if (f >= 1 && !mbar_wait(smem_u32(&empty[s]), (uint32_t)((f - 1) & 1))) {
-                    s_fail = 1;
-                    break;
+            int cb = 0, eb = 0;         // counters of the item's first planes
+            for (int i = blockIdx.x; i < items && !s_fail; i += gridDim.x) {
+                const int t = i % tiles, ch = i / tiles;
+                const int za = (int)((long long)ch * nz / nchunk), zb = (int)((long long)(ch + 1) * nz / nchunk);
+                const int x0 = (t % gx) * kTmaTX, y0 = (t / gx) * kTmaTY;
+                const int ja = max(za - 1, 0), jb = min(zb, nz - 1);
+                for (int j = ja; j <= jb && !s_fail; ++j) {
+                    // p / w plane j; its stage must be released by every compute warp
+                    const int c = cb + (j - ja);
+                    const int s = pw_stage(c);
+                    if (c >= kStagesPW && !mbar_wait(smem_u32(&pw_empty[s]), pw_phase(c - kStagesPW))) {
+                        s_fail = 1;
+                        break;
+                    }
+                    unsigned char* st = smem + s * L::PW_STAGE;
+                    const uint32_t bar = smem_u32(&pw_full[s]);
+                    mbar_expect_tx(bar, L::P_BYTES + L::W_BYTES);
+                    tma_load_4d(smem_u32(st + L::P_OFF), &tp, x0 - 4, y0 - 1, j, 0, bar);
+                    tma_load_3d(smem_u32(st + L::W_OFF), &tw, x0 - 4, y0 - 1, j, bar);
+                    pw_issued = c;
+                    if (j < za || j >= zb) continue;
+                    // H plane j
+                    const int e = eb + (j - za);
+                    const int sh = h_stage(e);
+                    if (e >= kStagesH && !mbar_wait(smem_u32(&h_empty[sh]), h_phase(e - kStagesH))) {
+                        s_fail = 1;
+                        break;
+                    }
+                    const uint32_t hbar = smem_u32(&h_full[sh]);
+                    mbar_expect_tx(hbar, L::H_BYTES);
+                    tma_load_4d(smem_u32(smem + L::H_BASE + sh * L::H_STAGE), &th, x0, y0, j, 0, hbar);
+                    h_issued = e;
                 }
-                if (s_fail) break;
-                unsigned char* st = smem + s * L::STAGE;
-                const uint32_t bar = smem_u32(&full[s]);
-                const bool own = j >= z0 && j < z1;
-                mbar_expect_tx(bar, L::P_BYTES + L::W_BYTES + (own ? L::H_BYTES : 0));
-                tma_load_4d(smem_u32(st + L::P_OFF), &tp, x0 - 4, y0 - 1, j, 0, bar);
-                tma_load_3d(smem_u32(st + L::W_OFF), &tw, x0 - 4, y0 - 1, j, bar);
-                if (own) tma_load_4d(smem_u32(st + L::H_OFF), &th, x0, y0, j, 0, bar);
-                issued_to = j;
+                cb += jb - ja + 1;
+                eb += zb - za;
             }
         }
     } else if (!done) {
-        const int x = x0 + tx, y = y0 + ty;
-        const bool inside = x < nx && y < ny;
-        int waited_to = j0 - 1;               // planes [j0, waited_to] are visible to this thread
-        for (int z = z0; z < z1; ++z) {
-            const int need = min(z + 1, nz - 1);
-            bool ok = !s_fail;
-            for (int j = waited_to + 1; ok && j <= need; ++j)
-                ok = mbar_wait(smem_u32(&full[stage_of(j)]), (uint32_t)(fill_of(j) & 1));
-            waited_to = need;
-            if (!ok) s_fail = 1;
-            if (ok && inside) {
-                const float* pcur = reinterpret_cast<const float*>(smem + stage_of(z) * L::STAGE + L::P_OFF);
-                const float* wcur = reinterpret_cast<const float*>(smem + stage_of(z) * L::STAGE + L::W_OFF);
-                const float* hcur = reinterpret_cast<const float*>(smem + stage_of(z) * L::STAGE + L::H_OFF);
-                const int cc = (ty + 1) * kTmaBoxX + tx + 4;      // centre in a p / w plane
-                const bool okxm = x > 0, okxp = x + 1 < nx, okym = y > 0, okyp = y + 1 < ny;
-                const bool okzm = z > 0, okzp = z + 1 < nz;
-                const float* pdn = okzm ? reinterpret_cast<const float*>(smem + stage_of(z - 1) * L::STAGE + L::P_OFF) : pcur;
-                const float* wdn = okzm ? reinterpret_cast<const float*>(smem + stage_of(z - 1) * L::STAGE + L::W_OFF) : wcur;
-                const float* pup = okzp ? reinterpret_cast<const float*>(smem + stage_of(z + 1) * L::STAGE + L::P_OFF) : pcur;
-                const float* wup = okzp ? reinterpret_cast<const float*>(smem + stage_of(z + 1) * L::STAGE + L::W_OFF) : wcur;
-                const float wc = wcur[cc];
-                const float cxm = okxm ? (wc + wcur[cc - 1]) * P.ihx2 : 0.f;
-                const float cxp = okxp ? (wc + wcur[cc + 1]) * P.ihx2 : 0.f;
-                const float cym = okym ? (wc + wcur[cc - kTmaBoxX]) * P.ihy2 : 0.f;
-                const float cyp = okyp ? (wc + wcur[cc + kTmaBoxX]) * P.ihy2 : 0.f;
-                const float czm = okzm ? (wc + wdn[cc]) * P.ihz2 : 0.f;
-                const float czp = okzp ? (wc + wup[cc]) * P.ihz2 : 0.f;
-                constexpr int PS = kTmaBoxY * kTmaBoxX;             // map stride in a p plane
-                float pc[K];
+        int waited = -1;                // p / w counters [0, waited] are visible to this thread
+        int released = 0;               // next p / w counter this warp releases
+        int cb = 0, eb = 0;
+        for (int i = blockIdx.x; i < items; i += gridDim.x) {
+            const int t = i % tiles, ch = i / tiles;
+            const int za = (int)((long long)ch * nz / nchunk), zb = (int)((long long)(ch + 1) * nz / nchunk);
+            const int x = (t % gx) * kTmaTX + tx, y = (t / gx) * kTmaTY + ty;
+            const int ja = max(za - 1, 0), jb = min(zb, nz - 1);
+            const bool inside = x < nx && y < ny;
+            for (int z = za; z < zb; ++z) {
+                const int need = cb + (min(z + 1, nz - 1) - ja);
+                const int e = eb + (z - za);
+                bool ok = !s_fail;
+                for (int c = waited + 1; ok && c <= need; ++c)
+                    ok = mbar_wait(smem_u32(&pw_full[pw_stage(c)]), pw_phase(c));
+                waited = need;
+                if (ok) ok = mbar_wait(smem_u32(&h_full[h_stage(e)]), h_phase(e));
+                if (!ok) s_fail = 1;
+                if (ok && inside) {
+                    const int cz = cb + (z - ja);
+                    const float* pcur = reinterpret_cast<const float*>(pw_ptr(cz) + L::P_OFF);
+                    const float* wcur = reinterpret_cast<const float*>(pw_ptr(cz) + L::W_OFF);
+                    const float* hcur = reinterpret_cast<const float*>(smem + L::H_BASE + h_stage(e) * L::H_STAGE);
+                    const int cc = (ty + 1) * kTmaBoxX + tx + 4;      // centre in a p / w plane
+                    const bool okxm = x > 0, okxp = x + 1 < nx, okym = y > 0, okyp = y + 1 < ny;
+                    const bool okzm = z > 0, okzp = z + 1 < nz;
+                    const float* pdn = okzm ? reinterpret_cast<const float*>(pw_ptr(cz - 1) + L::P_OFF) : pcur;
+                    const float* wdn = okzm ? reinterpret_cast<const float*>(pw_ptr(cz - 1) + L::W_OFF) : wcur;
+                    const float* pup = okzp ? reinterpret_cast<const float*>(pw_ptr(cz + 1) + L::P_OFF) : pcur;
+                    const float* wup = okzp ? reinterpret_cast<const float*>(pw_ptr(cz + 1) + L::W_OFF) : wcur;
+                    // out-of-volume neighbours: the copy engine zero-fills the
+                    // x / y halo and the z neighbour falls back to the centre
+                    // plane, so a zero coefficient removes them without a branch
+                    const float wc = wcur[cc];
+                    const float cxm = okxm ? (wc + wcur[cc - 1]) * P.ihx2 : 0.f;
+                    const float cxp = okxp ? (wc + wcur[cc + 1]) * P.ihx2 : 0.f;
+                    const float cym = okym ? (wc + wcur[cc - kTmaBoxX]) * P.ihy2 : 0.f;
+                    const float cyp = okyp ? (wc + wcur[cc + kTmaBoxX]) * P.ihy2 : 0.f;
+                    const float czm = okzm ? (wc + wdn[cc]) * P.ihz2 : 0.f;
+                    const float czp = okzp ? (wc + wup[cc]) * P.ihz2 : 0.f;
+                    constexpr int PS = kTmaBoxY * kTmaBoxX;             // map stride in a p plane
+                    constexpr int HS = kTmaTX * kTmaTY;                 // entry stride in an H plane
+                    const int hc = ty * kTmaTX + tx;
+                    float hv[L::T];
 #pragma unroll
-                for (int k = 0; k < K; ++k) pc[k] = pcur[k * PS + cc];
-                const int hc = ty * kTmaTX + tx;
-                const long long n = (long long)x + (long long)nx * y + (long long)nx * ny * z;
-                float vpq = 0.0f;
+                    for (int m = 0; m < L::T; ++m) hv[m] = hcur[m * HS + hc];
+                    float pc[K];
 #pragma unroll
-                for (int a = 0; a < K; ++a) {
-                    const float v = pc[a];
-                    const float* pa = pcur + a * PS;
-                    float s = 0.f;
-                    if (okxm) s += cxm * (v - pa[cc - 1]);
-                    if (okxp) s += cxp * (v - pa[cc + 1]);
-                    if (okym) s += cym * (v - pa[cc - kTmaBoxX]);
-                    if (okyp) s += cyp * (v - pa[cc + kTmaBoxX]);
-                    if (okzm) s += czm * (v - pdn[a * PS + cc]);
-                    if (okzp) s += czp * (v - pup[a * PS + cc]);
-                    float acc = P.lambda[a] * s;
+                    for (int k = 0; k < K; ++k) pc[k] = pcur[k * PS + cc];
+                    float* qn = qout + ((long long)x + (long long)nx * y + (long long)nx * ny * z);
+                    float vpq = 0.0f;
 #pragma unroll
-                    for (int b = 0; b < K; ++b)
-                        acc += hcur[(a < b ? tri(K, a, b) : tri(K, b, a)) * (kTmaTX * kTmaTY) + hc] * pc[b];
-                    qout[a * N + n] = acc;
-                    vpq += v * acc;
+                    for (int a = 0; a < K; ++a) {
+                        const float* pa = pcur + a * PS;
+                        const float v = pc[a];
+                        float s = cxm * (v - pa[cc - 1]);
+                        s += cxp * (v - pa[cc + 1]);
+                        s += cym * (v - pa[cc - kTmaBoxX]);
+                        s += cyp * (v - pa[cc + kTmaBoxX]);
+                        s += czm * (v - pdn[a * PS + cc]);
+                        s += czp * (v - pup[a * PS + cc]);
+                        float acc = P.lambda[a] * s;
+#pragma unroll
+                        for (int b = 0; b < K; ++b) acc += hv[a < b ? tri(K, a, b) : tri(K, b, a)] * pc[b];
+                        qn[a * N] = acc;
+                        vpq += v * acc;
+                    }
+                    pq.add(vpq);
                 }
-                pq.add(vpq);
-            }
-            // this warp no longer needs plane z - 1
-            if (z - 1 >= j0) {
+                // this warp is done with H plane z and no longer needs the p / w
+                // planes below z; at the end of the item it releases all of
+                // the item's p / w planes
+                const int rel_to = z + 1 < zb ? cb + (z - 1 - ja) : cb + (jb - ja);
                 __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&empty[stage_of(z - 1)]));
+                if (lane == 0) {
+                    mbar_arrive(smem_u32(&h_empty[h_stage(e)]));
+                    for (int c = released; c <= rel_to; ++c) mbar_arrive(smem_u32(&pw_empty[pw_stage(c)]));
+                }
+                if (rel_to >= released) released = rel_to + 1;
             }
+            cb += jb - ja + 1;
+            eb += zb - za;
         }
     }
     __syncthreads();
@@ -252,8 +318,10 @@ __global__ void __launch_bounds__(kTmaThreads) k_pcg_matvec_tma(
         if (producer && lane == 0) {
             // the last fill of each stage (earlier fills have completed before
             // their stage could be refilled)
-            for (int j = max(j0, issued_to - kStages + 1); j <= issued_to; ++j)
-                mbar_wait(smem_u32(&full[stage_of(j)]), (uint32_t)(fill_of(j) & 1));
+            for (int c = max(0, pw_issued - kStagesPW + 1); c <= pw_issued; ++c)
+                mbar_wait(smem_u32(&pw_full[pw_stage(c)]), pw_phase(c));
+            for (int e = max(0, h_issued - kStagesH + 1); e <= h_issued; ++e)
+                mbar_wait(smem_u32(&h_full[h_stage(e)]), h_phase(e));
             atomicOr(&hdr->status, kStatusTimeout);
         }
         __syncthreads();
@@ -356,7 +424,7 @@ bool make_tma_maps(const DevProblem& P, const float* h, const float* w, const fl
 }
 
 template <int K, int TX, int TY>
-static cudaError_t launch_tma_k(const DevProblem& P, int zc, dim3 grid, const TmaMaps& m, int k_it,
+static cudaError_t launch_tma_k(const DevProblem& P, int nchunk, dim3 grid, const TmaMaps& m, int k_it,
                                 float* q, WsHeader* hdr, Reduce red, cudaStream_t st)
 {
     using L = TmaLayout<K, TX, TY>;
@@ -368,14 +436,75 @@ static cudaError_t launch_tma_k(const DevProblem& P, int zc, dim3 grid, const Tm
         attr = true;
     }
     k_pcg_matvec_tma<K, TX, TY><<<grid, dim3(kTmaThreads, 1, 1), L::SMEM, st>>>(
-        P, zc, k_it, m.p[k_it & 1], m.w, m.h, q, hdr, red);
+        P, nchunk, k_it, m.p[k_it & 1], m.w, m.h, q, hdr, red);
     return cudaGetLastError();
 }
 
+template <int K, int TX, int TY>
+static int resident_one()
+{
+    // the occupancy query needs the kernel's shared-memory opt-in first
+    int nb = 0;
+    if (cudaFuncSetAttribute(k_pcg_matvec_tma<K, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TmaLayout<K, TX, TY>::SMEM) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pcg_matvec_tma<K, TX, TY>, kTmaThreads,
+                                                      TmaLayout<K, TX, TY>::SMEM) != cudaSuccess) {
+        cudaGetLastError();
+        nb = 1;
+    }
+    return nb > 0 ? nb : 1;
+}
+
+// Resident blocks of the TMA matvec per SM for (K, tile) and the SM count of
+// the current device, looked up once per device.
+static int tma_wave(const DevProblem& P, int tile)
+{
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_tuple(dev, P.K, tile);
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int sms = kNumSm;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        sms = kNumSm;
+    }
+    int nb;
+    if (P.K == 4)
+        nb = tile == 1 ? resident_one<4, 32, 8>() : tile == 2 ? resident_one<4, 64, 4>() : resident_one<4, 16, 16>();
+    else
+        nb = tile == 1 ? resident_one<3, 32, 8>() : tile == 2 ? resident_one<3, 64, 4>() : resident_one<3, 16, 16>();
+    return cache[key] = nb * sms;
+}
+
+// One wave of resident blocks over tiles x nchunk items (StencilGrid::zc
+// carries nchunk).  nchunk minimises rounds x (planes per item + 2): the
+// last round should leave few slots idle, items should be long enough that
+// the two halo planes per item and the ring's start-up stay small.
 StencilGrid tma_grid(const DevProblem& P, int tile)
 {
-    StencilGrid g = stencil_grid(P, kTileShapes[tile][0], kTileShapes[tile][1]);
+    const int TX = kTileShapes[tile][0], TY = kTileShapes[tile][1];
+    const long long T = (long long)((P.nx + TX - 1) / TX) * ((P.ny + TY - 1) / TY);
+    const long long W = tma_wave(P, tile);
+    int best = 1;
+    long long best_cost = -1;
+    for (int c = 1; c <= P.nz; ++c) {
+        const long long per = (P.nz + c - 1) / c;
+        if (per < 4 && c > 1) break;
+        const long long rounds = (T * c + W - 1) / W;
+        const long long cost = rounds * (per + 2);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = c;
+        }
+    }
+    StencilGrid g;
+    g.grid = dim3((unsigned)std::min<long long>(T * best, W), 1, 1);
     g.block = dim3(kTmaThreads, 1, 1);
+    g.zc = best;
     return g;
 }
 
