@@ -62,6 +62,13 @@ class OrcProblem(ctypes.Structure):
     ]
 
 
+class OrcProjection(ctypes.Structure):
+    _fields_ = [
+        ("dims", (ctypes.c_int * 3) * MAX_CONTRASTS),
+        ("affine", (ctypes.c_double * 12) * MAX_CONTRASTS),
+    ]
+
+
 class OrcOpts(ctypes.Structure):
     _fields_ = [
         ("gn_iters", ctypes.c_int), ("cg_iters", ctypes.c_int),
@@ -72,6 +79,9 @@ class OrcOpts(ctypes.Structure):
 
 _D = ctypes.POINTER(ctypes.c_double)
 _P = ctypes.POINTER(OrcProblem)
+_Q = ctypes.POINTER(OrcProjection)
+_DD = ctypes.POINTER(_D)
+_U8 = ctypes.POINTER(ctypes.c_uint8)
 
 
 def _lib():
@@ -105,6 +115,17 @@ def _lib():
         lib.orc_init.restype = None
         lib.orc_fit.argtypes = [_P, ctypes.POINTER(OrcOpts), _D, _D, _D, _D, _D, _D, _D, _D]
         lib.orc_fit.restype = ctypes.c_int
+        lib.orc_pull.argtypes = [_P, ctypes.POINTER(ctypes.c_int), _D, ctypes.c_int, _D, _D, _U8]
+        lib.orc_pull.restype = None
+        lib.orc_push.argtypes = [_P, ctypes.POINTER(ctypes.c_int), _D, ctypes.c_int, _D, _D]
+        lib.orc_push.restype = None
+        lib.orc_grad_hess_proj.argtypes = [_P, _Q, _DD, _DD, _DD, _D, _D, _D]
+        lib.orc_grad_hess_proj.restype = ctypes.c_double
+        lib.orc_init_proj.argtypes = [_P, _Q, _DD, _D]
+        lib.orc_init_proj.restype = None
+        lib.orc_fit_proj.argtypes = [_P, _Q, ctypes.POINTER(OrcOpts), _DD, _DD, _DD, _D, _D, _D,
+                                     _D, _D]
+        lib.orc_fit_proj.restype = ctypes.c_int
         _lib_handle = lib
     return _lib_handle
 
@@ -272,6 +293,97 @@ def fit(p, x, y0=None, b1p=None, b1m=None, gn_iters=10, cg_iters=30, newton_per_
     cg = np.zeros(max(gn_iters, 1))
     it = _lib().orc_fit(ctypes.byref(p), ctypes.byref(o), _ptr(x), _ptr(b1p), _ptr(b1m),
                         _ptr(y), _ptr(F), _ptr(nll), _ptr(jt), _ptr(cg))
+    n = max(it, 0)
+    return {"y": y, "iters": it, "F": F[:n + 1], "nll": nll[:n + 1], "jtv": jt[:n + 1],
+            "cg_rel": cg[:n]}
+
+
+# ------------------------------------------------------------ spatial projection
+
+def make_projection(dims, affines) -> OrcProjection:
+    """Per contrast: acquisition grid ``dims[c] = (mx, my, mz)`` and the 3 x 4
+    (or 4 x 4) affine from its voxel coordinates to reconstruction voxel
+    coordinates."""
+    q = OrcProjection()
+    for c, (d, a) in enumerate(zip(dims, affines)):
+        a = np.asarray(a, dtype=np.float64)[:3, :4].reshape(12)
+        for k in range(3):
+            q.dims[c][k] = int(d[k])
+        for k in range(12):
+            q.affine[c][k] = float(a[k])
+    return q
+
+
+def _dims_aff(dims, A):
+    d = (ctypes.c_int * 3)(*(int(v) for v in dims))
+    a = np.ascontiguousarray(np.asarray(A, dtype=np.float64)[:3, :4].reshape(12))
+    return d, a
+
+
+def pull(p, dims, A, u):
+    """Psi u for u [ch][N] -> (out [ch][M], inside [M] bool)."""
+    u = _f64(np.atleast_2d(u))
+    d, a = _dims_aff(dims, A)
+    M = int(np.prod(dims))
+    out = np.zeros((u.shape[0], M))
+    inside = np.zeros(M, dtype=np.uint8)
+    _lib().orc_pull(ctypes.byref(p), d, _ptr(a), u.shape[0], _ptr(u), _ptr(out),
+                    inside.ctypes.data_as(_U8))
+    return out, inside.astype(bool)
+
+
+def push(p, dims, A, u):
+    """Psi' u for u [ch][M] -> [ch][N]."""
+    u = _f64(np.atleast_2d(u))
+    d, a = _dims_aff(dims, A)
+    out = np.zeros((u.shape[0], _nvox(p)))
+    _lib().orc_push(ctypes.byref(p), d, _ptr(a), u.shape[0], _ptr(u), _ptr(out))
+    return out
+
+
+def _ptr_list(arrs, C):
+    keep = [None if a is None else _f64(a) for a in (arrs if arrs is not None else [None] * C)]
+    arr = (_D * C)(*[_ptr(a) if a is not None else None for a in keep])
+    return arr, keep
+
+
+def grad_hess_proj(p, q, xs, y, b1ps=None, b1ms=None):
+    """Projected likelihood: xs[c] is [E_c][M_c].  Returns (nll, g, h)."""
+    C = p.n_contrasts
+    X, kx = _ptr_list(xs, C)
+    BP, kp = _ptr_list(b1ps, C)
+    BM, km = _ptr_list(b1ms, C)
+    y = _f64(y)
+    K = p.n_maps
+    g = np.zeros((K, _nvox(p)))
+    h = np.zeros((K * (K + 1) // 2, _nvox(p)))
+    nll = _lib().orc_grad_hess_proj(ctypes.byref(p), ctypes.byref(q), X, BP, BM, _ptr(y),
+                                    _ptr(g), _ptr(h))
+    return nll, g, h
+
+
+def init_proj(p, q, xs):
+    X, kx = _ptr_list(xs, p.n_contrasts)
+    y = np.zeros((p.n_maps, _nvox(p)))
+    _lib().orc_init_proj(ctypes.byref(p), ctypes.byref(q), X, _ptr(y))
+    return y
+
+
+def fit_proj(p, q, xs, y0=None, b1ps=None, b1ms=None, gn_iters=10, cg_iters=30,
+             newton_per_irls=1, tol_gn=0.0, tol_cg=0.0):
+    """fit() with the projected likelihood."""
+    C = p.n_contrasts
+    X, kx = _ptr_list(xs, C)
+    BP, kp = _ptr_list(b1ps, C)
+    BM, km = _ptr_list(b1ms, C)
+    o = OrcOpts(gn_iters, cg_iters, newton_per_irls, 1 if y0 is None else 0, tol_gn, tol_cg)
+    y = np.zeros((p.n_maps, _nvox(p))) if y0 is None else np.array(y0, dtype=np.float64)
+    F = np.zeros(gn_iters + 1)
+    nll = np.zeros(gn_iters + 1)
+    jt = np.zeros(gn_iters + 1)
+    cg = np.zeros(max(gn_iters, 1))
+    it = _lib().orc_fit_proj(ctypes.byref(p), ctypes.byref(q), ctypes.byref(o), X, BP, BM,
+                             _ptr(y), _ptr(F), _ptr(nll), _ptr(jt), _ptr(cg))
     n = max(it, 0)
     return {"y": y, "iters": it, "F": F[:n + 1], "nll": nll[:n + 1], "jtv": jt[:n + 1],
             "cg_rel": cg[:n]}

@@ -26,6 +26,13 @@
  *   orc_pcg/orc_solve dense Cholesky solve of H + L.
  *   orc_uncertainty   dense inverse / log-determinant; Monte-Carlo moments.
  *   orc_init          exact on a single noise-free voxel.
+ *   orc_pull/orc_push exact shifts and 90-degree rotations (index
+ *                     permutations); affine functions reproduced exactly by
+ *                     the interpolation; <Psi u, v> = <u, Psi' v>.
+ *   orc_grad_hess_proj
+ *                     identity reslicing gives orc_grad_hess; finite
+ *                     differences of the projected likelihood; the pushed
+ *                     Hessian majorises Psi' H Psi (Psi materialised).
  *   orc_fit           exact recovery from noise-free data (no prior); the
  *                     likelihood never increases over 1000 simulated voxels
  *                     (Sec. 3.1 protocol); the objective decreases under the
@@ -209,6 +216,36 @@ void orc_forward(const orc_problem* p, const double* y, const double* b1p,
 
 /* ------------------------------------------- likelihood, Eqs. 6, 24, 25 */
 
+/* Contribution of the echoes of contrast c in one voxel (Eqs. 6, 24, 25):
+ * adds to *nll, gn and P.  xv[e * xstride] is the observed echo e. */
+static void contrast_terms(const orc_problem* p, int c, int i0, const double yn[4], double bp,
+                           double bm, const double* xv, long xstride, double* nll, double gn[4],
+                           double P[4][4])
+{
+    int K = p->n_maps;
+    double is2 = 1.0 / p->sigma2[c];
+    for (int e = 0; e < p->n_echoes[c]; ++e) {
+        double s, ds[4], d2s[16];
+        orc_signal_jet(yn, p->alpha[c], p->tr[c], p->te[i0 + e], p->mt[c], bp, bm, &s, ds, d2s);
+        double r = s - xv[(long)e * xstride];
+        *nll += 0.5 * r * r * is2;
+        for (int k = 0; k < K; ++k) gn[k] += r * ds[k] * is2;
+        for (int k = 0; k < K; ++k)
+            for (int j = 0; j < K; ++j) P[k][j] += ds[k] * ds[j] * is2;
+        /* Loading of Eq. 24: |r| |H_f| (.) I (precond 0), or the
+         * row sums |H_f| 1 ("Proposed+", precond 1), or none (2). */
+        for (int k = 0; k < K; ++k) {
+            double load = 0.0;
+            if (p->precond == 0) {
+                load = fabs(d2s[4 * k + k]);
+            } else if (p->precond == 1) {
+                for (int j = 0; j < K; ++j) load += fabs(d2s[4 * k + j]);
+            }
+            P[k][k] += fabs(r) * load * is2;
+        }
+    }
+}
+
 double orc_grad_hess(const orc_problem* p, const double* x, const double* y,
                      const double* b1p, const double* b1m, double* g, double* h)
 {
@@ -225,33 +262,147 @@ double orc_grad_hess(const orc_problem* p, const double* x, const double* y,
         for (int c = 0; c < p->n_contrasts; ++c) {
             double bp = b1p ? b1p[n] : 1.0;
             double bm = b1m ? b1m[(long)c * N + n] : 1.0;
-            double is2 = 1.0 / p->sigma2[c];
-            for (int e = 0; e < p->n_echoes[c]; ++e, ++i) {
-                double s, ds[4], d2s[16];
-                orc_signal_jet(yn, p->alpha[c], p->tr[c], p->te[i], p->mt[c], bp, bm,
-                               &s, ds, d2s);
-                double r = s - x[(long)i * N + n];
-                nll += 0.5 * r * r * is2;
-                for (int k = 0; k < K; ++k) gn[k] += r * ds[k] * is2;
-                for (int k = 0; k < K; ++k)
-                    for (int j = 0; j < K; ++j) P[k][j] += ds[k] * ds[j] * is2;
-                /* Loading of Eq. 24: |r| |H_f| (.) I (precond 0), or the
-                 * row sums |H_f| 1 ("Proposed+", precond 1), or none (2). */
-                for (int k = 0; k < K; ++k) {
-                    double load = 0.0;
-                    if (p->precond == 0) {
-                        load = fabs(d2s[4 * k + k]);
-                    } else if (p->precond == 1) {
-                        for (int j = 0; j < K; ++j) load += fabs(d2s[4 * k + j]);
-                    }
-                    P[k][k] += fabs(r) * load * is2;
-                }
-            }
+            contrast_terms(p, c, i, yn, bp, bm, x + (long)i * N + n, N, &nll, gn, P);
+            i += p->n_echoes[c];
         }
         for (int k = 0; k < K; ++k) g[(long)k * N + n] = gn[k];
         for (int k = 0; k < K; ++k)
             for (int j = k; j < K; ++j)
                 h[(long)tri_index(K, k, j) * N + n] = P[k][j];
+    }
+    return nll;
+}
+
+/* ------------------------------------------- spatial projection, Sec. 2.4 */
+
+/* Reconstruction-space coordinate r = A (i, j, k, 1) of acquisition voxel
+ * (i, j, k); returns 1 when r lies inside the reconstruction grid,
+ * 0 <= r_d <= n_d - 1 on every axis (the voxel then has data that the model
+ * explains), else 0. */
+static int reslice_coord(const orc_problem* p, const double A[12], long i, long j, long k,
+                         double r[3])
+{
+    for (int d = 0; d < 3; ++d)
+        r[d] = A[4 * d + 0] * (double)i + A[4 * d + 1] * (double)j + A[4 * d + 2] * (double)k +
+               A[4 * d + 3];
+    return r[0] >= 0.0 && r[0] <= p->nx - 1 && r[1] >= 0.0 && r[1] <= p->ny - 1 &&
+           r[2] >= 0.0 && r[2] <= p->nz - 1;
+}
+
+/* The trilinear interpolation weights of r: up to 8 reconstruction voxels
+ * (corners of the cell holding r) and their weights; corners past the last
+ * voxel (which have weight 0) are left out.  Returns the count. */
+static int trilinear(const orc_problem* p, const double r[3], long idx[8], double wt[8])
+{
+    long b[3];
+    double f[3];
+    long n[3] = {p->nx, p->ny, p->nz};
+    for (int d = 0; d < 3; ++d) {
+        b[d] = (long)floor(r[d]);
+        f[d] = r[d] - (double)b[d];
+    }
+    int cnt = 0;
+    for (int cz = 0; cz < 2; ++cz)
+        for (int cy = 0; cy < 2; ++cy)
+            for (int cx = 0; cx < 2; ++cx) {
+                long ix = b[0] + cx, iy = b[1] + cy, iz = b[2] + cz;
+                if (ix > n[0] - 1 || iy > n[1] - 1 || iz > n[2] - 1) continue;
+                idx[cnt] = ix + n[0] * (iy + n[1] * iz);
+                wt[cnt] = (cx ? f[0] : 1.0 - f[0]) * (cy ? f[1] : 1.0 - f[1]) *
+                          (cz ? f[2] : 1.0 - f[2]);
+                ++cnt;
+            }
+    return cnt;
+}
+
+void orc_pull(const orc_problem* p, const int dims[3], const double A[12], int channels,
+              const double* u, double* out, unsigned char* inside)
+{
+    long N = n_vox(p);
+    long M = (long)dims[0] * dims[1] * dims[2];
+    long m = 0;
+    for (long k = 0; k < dims[2]; ++k)
+        for (long j = 0; j < dims[1]; ++j)
+            for (long i = 0; i < dims[0]; ++i, ++m) {
+                double r[3];
+                int in = reslice_coord(p, A, i, j, k, r);
+                if (inside) inside[m] = (unsigned char)in;
+                for (int ch = 0; ch < channels; ++ch) out[(long)ch * M + m] = 0.0;
+                if (!in) continue;
+                long idx[8];
+                double wt[8];
+                int cnt = trilinear(p, r, idx, wt);
+                for (int ch = 0; ch < channels; ++ch)
+                    for (int q = 0; q < cnt; ++q)
+                        out[(long)ch * M + m] += wt[q] * u[(long)ch * N + idx[q]];
+            }
+}
+
+void orc_push(const orc_problem* p, const int dims[3], const double A[12], int channels,
+              const double* u, double* out)
+{
+    long N = n_vox(p);
+    long M = (long)dims[0] * dims[1] * dims[2];
+    long m = 0;
+    for (long k = 0; k < dims[2]; ++k)
+        for (long j = 0; j < dims[1]; ++j)
+            for (long i = 0; i < dims[0]; ++i, ++m) {
+                double r[3];
+                if (!reslice_coord(p, A, i, j, k, r)) continue;
+                long idx[8];
+                double wt[8];
+                int cnt = trilinear(p, r, idx, wt);
+                for (int ch = 0; ch < channels; ++ch)
+                    for (int q = 0; q < cnt; ++q)
+                        out[(long)ch * N + idx[q]] += wt[q] * u[(long)ch * M + m];
+            }
+}
+
+/* Sec. 2.4: l_psi(y) = sum_c l_c(Psi_c y).  Per contrast the maps are pulled
+ * to its acquisition grid, the gradient and loaded Hessian of the contrast's
+ * echoes are formed there voxel by voxel (as in orc_grad_hess, acquisition
+ * voxels outside the reconstruction grid contribute nothing), and both are
+ * pushed back: g = sum_c Psi_c' g_c, h = sum_c Psi_c' h_c.  The latter is the
+ * block-diagonal majoriser of Psi_c' H_c Psi_c: with non-negative weights that
+ * sum to one per acquisition voxel, Jensen's inequality on each voxel's
+ * quadratic form bounds Psi' H Psi by diag(Psi' H) (the result the paper takes
+ * from Ashburner et al. 2018). */
+double orc_grad_hess_proj(const orc_problem* p, const orc_projection* q,
+                          const double* const* x, const double* const* b1p,
+                          const double* const* b1m, const double* y, double* g, double* h)
+{
+    long N = n_vox(p);
+    int K = p->n_maps, T = n_tri(K);
+    for (long i = 0; i < (long)K * N; ++i) g[i] = 0.0;
+    for (long i = 0; i < (long)T * N; ++i) h[i] = 0.0;
+    double nll = 0.0;
+    int i0 = 0;
+    for (int c = 0; c < p->n_contrasts; ++c) {
+        const int* dims = q->dims[c];
+        long M = (long)dims[0] * dims[1] * dims[2];
+        double* yc = malloc(sizeof(double) * K * M);
+        unsigned char* in = malloc(M);
+        double* gc = calloc((size_t)K * M, sizeof(double));
+        double* hc = calloc((size_t)T * M, sizeof(double));
+        orc_pull(p, dims, q->affine[c], K, y, yc, in);
+        for (long m = 0; m < M; ++m) {
+            if (!in[m]) continue;
+            double yn[4] = {0, 0, 0, 0};
+            for (int k = 0; k < K; ++k) yn[k] = yc[(long)k * M + m];
+            double gn[4] = {0, 0, 0, 0};
+            double P[4][4];
+            memset(P, 0, sizeof P);
+            double bp = b1p && b1p[c] ? b1p[c][m] : 1.0;
+            double bm = b1m && b1m[c] ? b1m[c][m] : 1.0;
+            contrast_terms(p, c, i0, yn, bp, bm, x[c] + m, M, &nll, gn, P);
+            for (int k = 0; k < K; ++k) gc[(long)k * M + m] = gn[k];
+            for (int k = 0; k < K; ++k)
+                for (int j = k; j < K; ++j) hc[(long)tri_index(K, k, j) * M + m] = P[k][j];
+        }
+        orc_push(p, dims, q->affine[c], K, gc, g);
+        orc_push(p, dims, q->affine[c], T, hc, h);
+        free(yc); free(in); free(gc); free(hc);
+        i0 += p->n_echoes[c];
     }
     return nll;
 }
@@ -462,10 +613,11 @@ int orc_uncertainty(const orc_problem* p, const double* h, const double* w,
  *   5. clamps: R2* >= 1e-3, E in [1e-6, 1 - 1e-6], delta in [1e-4, 0.5].
  * Fallbacks: fewer than two distinct non-MT flip angles -> R1 = 1/s and A from
  * the first contrast; no multi-echo contrast -> R2* = 20/s. */
+static void init_from_log_means(const orc_problem* p, const double* lmu, long N, double* y);
+
 void orc_init(const orc_problem* p, const double* x, double* y)
 {
     long N = n_vox(p);
-    int C = p->n_contrasts, K = p->n_maps;
     int I = n_images(p);
     double lmu[ORC_MAX_IMAGES];
     for (int i = 0; i < I; ++i) {
@@ -474,6 +626,30 @@ void orc_init(const orc_problem* p, const double* x, double* y)
         double mu = s / (double)N;
         lmu[i] = log(mu > 1e-30 ? mu : 1e-30);
     }
+    init_from_log_means(p, lmu, N, y);
+}
+
+/* The same rule with each image's mean taken over its own acquisition grid. */
+void orc_init_proj(const orc_problem* p, const orc_projection* q, const double* const* x,
+                   double* y)
+{
+    double lmu[ORC_MAX_IMAGES];
+    int i = 0;
+    for (int c = 0; c < p->n_contrasts; ++c) {
+        long M = (long)q->dims[c][0] * q->dims[c][1] * q->dims[c][2];
+        for (int e = 0; e < p->n_echoes[c]; ++e, ++i) {
+            double s = 0.0;
+            for (long m = 0; m < M; ++m) s += x[c][(long)e * M + m];
+            double mu = s / (double)M;
+            lmu[i] = log(mu > 1e-30 ? mu : 1e-30);
+        }
+    }
+    init_from_log_means(p, lmu, n_vox(p), y);
+}
+
+static void init_from_log_means(const orc_problem* p, const double* lmu, long N, double* y)
+{
+    int C = p->n_contrasts, K = p->n_maps;
     /* 2. shared slope, per-contrast intercepts */
     double te_mean[ORC_MAX_CONTRASTS], l_mean[ORC_MAX_CONTRASTS];
     double num = 0.0, den = 0.0;
@@ -552,9 +728,10 @@ void orc_init(const orc_problem* p, const double* x, double* y)
 /* Sec. 2.6-2.7: alternate the JTV weights (Eq. 40) and Newton updates
  * y <- y - (H + L)^-1 (g + L y) (Eq. 42) with the approximate Hessian of
  * Eq. 24, solved by PCG.  The objective is F = NLL (Eq. 25) + JTV_eps. */
-int orc_fit(const orc_problem* p, const orc_opts* o, const double* x,
-            const double* b1p, const double* b1m, double* y,
-            double* F, double* nll_out, double* jtv_out, double* cg_rel)
+static int fit_loop(const orc_problem* p, const orc_projection* q, const orc_opts* o,
+                    const double* x, const double* b1p, const double* b1m,
+                    const double* const* xs, const double* const* b1ps, const double* const* b1ms,
+                    double* y, double* F, double* nll_out, double* jtv_out, double* cg_rel)
 {
     long N = n_vox(p);
     int K = p->n_maps;
@@ -568,10 +745,14 @@ int orc_fit(const orc_problem* p, const orc_opts* o, const double* x,
     double F_prev = 0.0;
     int it;
 
-    if (o->init) orc_init(p, x, y);
+    if (o->init) {
+        if (q) orc_init_proj(p, q, xs, y);
+        else orc_init(p, x, y);
+    }
     for (it = 0;; ++it) {
         double jtv = orc_jtv(p, y, (it % npi == 0) ? w : NULL);
-        double nll = orc_grad_hess(p, x, y, b1p, b1m, g, h);
+        double nll = q ? orc_grad_hess_proj(p, q, xs, b1ps, b1ms, y, g, h)
+                       : orc_grad_hess(p, x, y, b1p, b1m, g, h);
         double Fi = nll + jtv;
         if (F) F[it] = Fi;
         if (nll_out) nll_out[it] = nll;
@@ -586,4 +767,18 @@ int orc_fit(const orc_problem* p, const orc_opts* o, const double* x,
     }
     free(w); free(g); free(h); free(delta); free(resid);
     return it;
+}
+
+int orc_fit(const orc_problem* p, const orc_opts* o, const double* x,
+            const double* b1p, const double* b1m, double* y,
+            double* F, double* nll_out, double* jtv_out, double* cg_rel)
+{
+    return fit_loop(p, NULL, o, x, b1p, b1m, NULL, NULL, NULL, y, F, nll_out, jtv_out, cg_rel);
+}
+
+int orc_fit_proj(const orc_problem* p, const orc_projection* q, const orc_opts* o,
+                 const double* const* x, const double* const* b1p, const double* const* b1m,
+                 double* y, double* F, double* nll_out, double* jtv_out, double* cg_rel)
+{
+    return fit_loop(p, q, o, NULL, NULL, NULL, x, b1p, b1m, y, F, nll_out, jtv_out, cg_rel);
 }

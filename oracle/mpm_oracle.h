@@ -69,6 +69,40 @@ void orc_forward(const orc_problem* p, const double* y, const double* b1p,
 double orc_grad_hess(const orc_problem* p, const double* x, const double* y,
                      const double* b1p, const double* b1m, double* g, double* h);
 
+/* Spatial projection (Sec. 2.4).  Contrast c was acquired on its own grid of
+ * dims[c] voxels (x fastest); affine[c] is the row-major 3 x 4 map from its
+ * voxel coordinates (i, j, k, 1) to reconstruction voxel coordinates. */
+typedef struct {
+    int dims[ORC_MAX_CONTRASTS][3];
+    double affine[ORC_MAX_CONTRASTS][12];
+} orc_projection;
+
+/* Psi u: trilinear interpolation of `channels` reconstruction-space images
+ * u[ch][N] at A m for every acquisition voxel m; out[ch][M].  inside[m] (may
+ * be NULL) is 1 when A m lies in the reconstruction grid, else 0 and out = 0. */
+void orc_pull(const orc_problem* p, const int dims[3], const double A[12], int channels,
+              const double* u, double* out, unsigned char* inside);
+
+/* out[ch][N] += Psi' u (the adjoint of orc_pull; u is [ch][M]). */
+void orc_push(const orc_problem* p, const int dims[3], const double A[12], int channels,
+              const double* u, double* out);
+
+/* NLL of the projected model (Sec. 2.4); g = sum_c Psi_c' g_c and
+ * h = sum_c Psi_c' h_c (block-diagonal majoriser).  x[c] is [E_c][M_c];
+ * b1p[c], b1m[c] are [M_c] (the arrays or their entries may be NULL). */
+double orc_grad_hess_proj(const orc_problem* p, const orc_projection* q,
+                          const double* const* x, const double* const* b1p,
+                          const double* const* b1m, const double* y, double* g, double* h);
+
+/* orc_init with each image's mean over its own acquisition grid. */
+void orc_init_proj(const orc_problem* p, const orc_projection* q, const double* const* x,
+                   double* y);
+
+/* orc_fit with the projected likelihood. */
+int orc_fit_proj(const orc_problem* p, const orc_projection* q, const orc_opts* o,
+                 const double* const* x, const double* const* b1p, const double* const* b1m,
+                 double* y, double* F, double* nll, double* jtv, double* cg_rel);
+
 /* Returns JTV_eps(y) = sum_n sqrt(u_n + eps^2); writes w when w != NULL. */
 double orc_jtv(const orc_problem* p, const double* y, double* w);
 
