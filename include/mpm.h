@@ -241,6 +241,61 @@ mpm_status mpm_fit_batch(int n, const mpm_problem* const* problems, const mpm_op
                          float* const* y, float* const* var_out, void* const* ws,
                          const size_t* ws_bytes, mpm_report* reports, void* stream);
 
+/* Spatial projection (Sec. 2.4, "Spatial projection"): contrast c was
+ * acquired on its own grid of dims[c] voxels (x fastest, M_c voxels) and
+ * affine[c] is the row-major 3 x 4 map from its voxel coordinates (i, j, k, 1)
+ * to reconstruction voxel coordinates (voxel centres at integer coordinates,
+ * both 0-based; a world-space pair of voxel-to-world matrices gives
+ * affine = inv(recon) * acq).  The paper's reslicing matrix Psi_c is
+ * trilinear interpolation at affine[c] * m; an acquisition voxel whose point
+ * lies outside [0, n_d - 1] on some axis of the reconstruction grid carries no
+ * data term.  Singular or non-finite affines are refused, and so are
+ * acquisition grids more than 4x finer than the reconstruction grid along an
+ * axis (the row sums of the inverse affine's linear part must be <= 4). */
+typedef struct {
+    int dims[MPM_MAX_CONTRASTS][3];
+    double affine[MPM_MAX_CONTRASTS][12];
+} mpm_projection;
+
+/* Workspace of the projected calls (call = MPM_CALL_FIT or
+ * MPM_CALL_GRAD_HESS): the plain size plus the per-contrast gradient and
+ * Hessian buffers on the acquisition grids. */
+mpm_status mpm_workspace_size_proj(const mpm_problem* problem, const mpm_projection* proj,
+                                   const mpm_opts* opts, int call, size_t* bytes);
+
+/* out[ch][M_c] = Psi_c u for `channels` reconstruction-space images
+ * u[ch][N] (the pull of Sec. 2.4). */
+mpm_status mpm_pull(const mpm_problem* problem, const mpm_projection* proj, int contrast,
+                    int channels, const float* u, float* out, void* stream);
+
+/* out[ch][N] = Psi_c' u (+ out if accumulate) for u[ch][M_c]: the adjoint of
+ * mpm_pull with the same weights (the push of Sec. 2.4).  Each output voxel
+ * gathers its terms in a fixed order, so results repeat bit for bit. */
+mpm_status mpm_push(const mpm_problem* problem, const mpm_projection* proj, int contrast,
+                    int channels, const float* u, float* out, int accumulate, void* stream);
+
+/* The projected voxel pass (Sec. 2.4 with Eqs. 6, 24-34): per contrast, the
+ * maps y[K][N] are pulled to its grid, the NLL, gradient g_c and loaded
+ * Hessian H_c of its echoes are formed per acquisition voxel, and
+ * g = sum_c Psi_c' g_c, h = sum_c Psi_c' H_c (the block-diagonal majoriser of
+ * Psi' H Psi, Ashburner et al. 2018 as cited there).  x[c] points to contrast
+ * c's echoes [E_c][M_c] (float32, or bfloat16 with echo_dtype = 1); b1p[c],
+ * b1m[c] to its B1 fields [M_c] (the arrays or their entries may be NULL: 1).
+ * x, b1p, b1m are host arrays of device pointers.  *nll (device) = the
+ * summed NLL.  ws: mpm_workspace_size_proj(..., MPM_CALL_GRAD_HESS) bytes. */
+mpm_status mpm_grad_hess_proj(const mpm_problem* problem, const mpm_projection* proj,
+                              const void* const* x, const float* const* b1p,
+                              const float* const* b1m, const float* y, float* g, float* h,
+                              double* nll, void* ws, size_t ws_bytes, void* stream);
+
+/* mpm_fit with the projected likelihood (the JTV prior and the solve stay on
+ * the reconstruction grid).  Constant initial maps use each image's mean over
+ * its own acquisition grid.  ws: mpm_workspace_size_proj(..., MPM_CALL_FIT). */
+mpm_status mpm_fit_proj(const mpm_problem* problem, const mpm_projection* proj,
+                        const mpm_opts* opts, const void* const* x, const float* const* b1p,
+                        const float* const* b1m, float* y_inout, float* var_out, void* ws,
+                        size_t ws_bytes, mpm_report* report, void* stream);
+
 /* Continuous batching of fit requests (a serving loop; the paper fits one
  * subject at a time).  The server owns no device memory: every admitted
  * request's fit workspace is carved from `arena` (caller-owned device memory,
@@ -304,7 +359,9 @@ enum {
     MPM_KERNEL_FORWARD = 7,
     MPM_KERNEL_INIT = 8,         /* image means and constant maps */
     MPM_KERNEL_PCG_DIRECTION = 9, /* p = z + beta p, x += alpha p */
-    MPM_KERNEL_KINDS = 10
+    MPM_KERNEL_GRAD_HESS_PROJ = 10, /* projected voxel pass, one contrast */
+    MPM_KERNEL_RESLICE = 11,     /* pull / push of the spatial projection */
+    MPM_KERNEL_KINDS = 12
 };
 
 /* Diagnostic timing.  While enabled (on != 0, process-wide), every kernel

@@ -14,13 +14,15 @@ from __future__ import annotations
 import ctypes
 
 from . import _lib
-from ._lib import MPMError, Opts, Problem, Report
+from ._lib import MPMError, Opts, Problem, Projection, Report
 
 __all__ = [
     "make_problem", "make_opts", "workspace", "mpm_workspace_size", "mpm_forward",
     "mpm_grad_hess", "mpm_jtv_weights", "mpm_solve", "mpm_uncertainty", "mpm_fit", "mpm_fit_batch",
     "mpm_workspace_status", "mpm_autotune", "mpm_kernel_launches", "mpm_profile_enable", "mpm_profile_read",
     "MPMError", "Problem", "Opts", "Report", "Server",
+    "Projection", "make_projection", "mpm_workspace_size_proj", "workspace_proj", "mpm_pull",
+    "mpm_push", "mpm_grad_hess_proj", "mpm_fit_proj",
 ]
 
 
@@ -253,6 +255,116 @@ def mpm_fit_batch(problems, opts, xs, ys, b1ps=None, b1ms=None, vars=None, wss=N
     st = _lib.check(lib.mpm_fit_batch(n, parr, ctypes.byref(opts), xa, bpa, bma, ya, va, wa, wb,
                                       reps, _stream(stream)), "mpm_fit_batch", allow)
     return st, list(reps)
+
+
+# ------------------------------------------------------------ spatial projection
+
+def make_projection(dims, affines) -> Projection:
+    """Per contrast: acquisition grid ``dims[c] = (mx, my, mz)`` and the
+    3 x 4 (or 4 x 4) affine from its voxel coordinates to reconstruction
+    voxel coordinates (see mpm_projection in mpm.h)."""
+    q = Projection()
+    for c, (d, a) in enumerate(zip(dims, affines)):
+        rows = [list(map(float, r[:4])) for r in list(a)[:3]]
+        for k in range(3):
+            q.dims[c][k] = int(d[k])
+        for r in range(3):
+            for k in range(4):
+                q.affine[c][4 * r + k] = rows[r][k]
+    return q
+
+
+def mpm_workspace_size_proj(problem, proj, opts=None, call=_lib.CALL_FIT) -> int:
+    lib = _lib.load()
+    n = ctypes.c_size_t()
+    _lib.check(lib.mpm_workspace_size_proj(ctypes.byref(problem), ctypes.byref(proj),
+                                           ctypes.byref(opts) if opts is not None else None,
+                                           int(call), ctypes.byref(n)), "mpm_workspace_size_proj")
+    return n.value
+
+
+def workspace_proj(problem, proj, opts=None, call=_lib.CALL_FIT, device="cuda"):
+    import torch
+    return torch.empty(max(mpm_workspace_size_proj(problem, proj, opts, call), 1),
+                       dtype=torch.uint8, device=device)
+
+
+def _ptr_array(ts, name, dtype, optional, C):
+    ts = list(ts) if ts is not None else [None] * C
+    return (ctypes.c_void_p * C)(*[_ptr(t, f"{name}[{c}]", dtype, optional)
+                                   for c, t in enumerate(ts)])
+
+
+def mpm_pull(problem, proj, contrast, u, stream=None):
+    """Psi_c u for u ``[ch, N]`` -> ``[ch, M_c]``."""
+    import torch
+    lib = _lib.load()
+    u2 = u.reshape(-1, u.shape[-1]) if u.dim() > 1 else u.reshape(1, -1)
+    d = proj.dims[contrast]
+    out = torch.empty((u2.shape[0], d[0] * d[1] * d[2]), dtype=torch.float32, device=u.device)
+    _lib.check(lib.mpm_pull(ctypes.byref(problem), ctypes.byref(proj), int(contrast), u2.shape[0],
+                            _ptr(u2, "u", _f32()), _ptr(out, "out", _f32()), _stream(stream)),
+               "mpm_pull")
+    return out
+
+
+def mpm_push(problem, proj, contrast, u, out=None, accumulate=False, stream=None):
+    """Psi_c' u for u ``[ch, M_c]`` -> ``[ch, N]`` (added to ``out`` if
+    ``accumulate``)."""
+    import torch
+    lib = _lib.load()
+    u2 = u.reshape(-1, u.shape[-1]) if u.dim() > 1 else u.reshape(1, -1)
+    N = problem.nx * problem.ny * problem.nz
+    if out is None:
+        out = torch.zeros((u2.shape[0], N), dtype=torch.float32, device=u.device)
+    _lib.check(lib.mpm_push(ctypes.byref(problem), ctypes.byref(proj), int(contrast), u2.shape[0],
+                            _ptr(u2, "u", _f32()), _ptr(out, "out", _f32()), int(accumulate),
+                            _stream(stream)), "mpm_push")
+    return out
+
+
+def mpm_grad_hess_proj(problem, proj, xs, y, b1ps=None, b1ms=None, ws=None, stream=None):
+    """Projected voxel pass.  ``xs[c]``: contrast c's echoes ``[E_c, M_c]``.
+    Returns (g ``[K, N]``, h ``[T, N]``, nll as a 0-d float64 CUDA tensor)."""
+    import torch
+    lib = _lib.load()
+    C = problem.n_contrasts
+    K = problem.n_maps
+    N = problem.nx * problem.ny * problem.nz
+    xdt = torch.bfloat16 if problem.echo_dtype == 1 else torch.float32
+    ws = workspace_proj(problem, proj, None, _lib.CALL_GRAD_HESS, y.device) if ws is None else ws
+    g = torch.empty((K, N), dtype=torch.float32, device=y.device)
+    h = torch.empty((K * (K + 1) // 2, N), dtype=torch.float32, device=y.device)
+    nll = torch.zeros((), dtype=torch.float64, device=y.device)
+    _lib.check(lib.mpm_grad_hess_proj(ctypes.byref(problem), ctypes.byref(proj),
+                                      _ptr_array(xs, "x", xdt, False, C),
+                                      _ptr_array(b1ps, "b1p", _f32(), True, C),
+                                      _ptr_array(b1ms, "b1m", _f32(), True, C),
+                                      _ptr(y, "y", _f32()), _ptr(g, "g", _f32()),
+                                      _ptr(h, "h", _f32()), _ptr(nll, "nll"), _ptr(ws, "ws"),
+                                      ws.numel(), _stream(stream)), "mpm_grad_hess_proj")
+    return g, h, nll
+
+
+def mpm_fit_proj(problem, proj, opts, xs, y, b1ps=None, b1ms=None, var=None, ws=None,
+                 stream=None, allow_not_converged=True):
+    """mpm_fit with the projected likelihood; ``xs[c]`` is ``[E_c, M_c]``.
+    Returns (status, Report)."""
+    import torch
+    lib = _lib.load()
+    C = problem.n_contrasts
+    xdt = torch.bfloat16 if problem.echo_dtype == 1 else torch.float32
+    ws = workspace_proj(problem, proj, opts, _lib.CALL_FIT, y.device) if ws is None else ws
+    rep = Report()
+    allow = (_lib.OK, _lib.WARN_NOT_CONVERGED) if allow_not_converged else (_lib.OK,)
+    st = _lib.check(lib.mpm_fit_proj(ctypes.byref(problem), ctypes.byref(proj), ctypes.byref(opts),
+                                     _ptr_array(xs, "x", xdt, False, C),
+                                     _ptr_array(b1ps, "b1p", _f32(), True, C),
+                                     _ptr_array(b1ms, "b1m", _f32(), True, C),
+                                     _ptr(y, "y", _f32()), _ptr(var, "var", _f32(), True),
+                                     _ptr(ws, "ws"), ws.numel(), ctypes.byref(rep),
+                                     _stream(stream)), "mpm_fit_proj", allow)
+    return st, rep
 
 
 class Server:

@@ -68,11 +68,20 @@ class Report(ctypes.Structure):
     ]
 
 
+class Projection(ctypes.Structure):
+    _fields_ = [
+        ("dims", (ctypes.c_int * 3) * MAX_CONTRASTS),
+        ("affine", (ctypes.c_double * 12) * MAX_CONTRASTS),
+    ]
+
+
 # Exported symbols and their prototypes (restype, argtypes).
 _P = ctypes.POINTER(Problem)
 _O = ctypes.POINTER(Opts)
 _V = ctypes.c_void_p
 _S = ctypes.c_size_t
+_Q = ctypes.POINTER(Projection)
+_VA = ctypes.POINTER(ctypes.c_void_p)
 PROTOTYPES = {
     "mpm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "mpm_last_error": (ctypes.c_char_p, []),
@@ -89,6 +98,13 @@ PROTOTYPES = {
                                      ctypes.POINTER(_V), ctypes.POINTER(_V),
                                      ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(Report), _V]),
     "mpm_workspace_status": (ctypes.c_int, [_V, _S, _V]),
+    "mpm_workspace_size_proj": (ctypes.c_int, [_P, _Q, _O, ctypes.c_int,
+                                               ctypes.POINTER(ctypes.c_size_t)]),
+    "mpm_pull": (ctypes.c_int, [_P, _Q, ctypes.c_int, ctypes.c_int, _V, _V, _V]),
+    "mpm_push": (ctypes.c_int, [_P, _Q, ctypes.c_int, ctypes.c_int, _V, _V, ctypes.c_int, _V]),
+    "mpm_grad_hess_proj": (ctypes.c_int, [_P, _Q, _VA, _VA, _VA, _V, _V, _V, _V, _V, _S, _V]),
+    "mpm_fit_proj": (ctypes.c_int, [_P, _Q, _O, _VA, _VA, _VA, _V, _V, _V, _S,
+                                    ctypes.POINTER(Report), _V]),
     "mpm_server_create": (ctypes.c_int, [_V, _S, ctypes.c_int, _V, ctypes.POINTER(_V)]),
     "mpm_server_submit": (ctypes.c_int, [_V, _P, _O, _V, _V, _V, _V, _V,
                                          ctypes.POINTER(ctypes.c_int)]),
@@ -106,7 +122,7 @@ PROTOTYPES = {
 }
 
 KERNEL_KINDS = ["grad_hess", "jtv", "pcg_init", "pcg_matvec", "pcg_update", "pcg_final",
-                "uncertainty", "forward", "init", "pcg_direction"]
+                "uncertainty", "forward", "init", "pcg_direction", "grad_hess_proj", "reslice"]
 
 _handle = None
 

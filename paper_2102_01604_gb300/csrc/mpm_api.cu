@@ -84,14 +84,6 @@ mpm_status fail(mpm_status s, const char* fmt, ...)
     return s;
 }
 
-#define MPM_CUDA(call)                                                                   \
-    do {                                                                                 \
-        cudaError_t e_ = (call);                                                         \
-        if (e_ != cudaSuccess)                                                           \
-            return fail(MPM_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),   \
-                        __FILE__, __LINE__);                                             \
-    } while (0)
-
 static bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 
 static int n_images(const mpm_problem* p)
@@ -223,12 +215,6 @@ mpm_status check_dev(const void* ptr, const char* name, bool optional, size_t al
         return fail(MPM_ERR_INVALID_ARG, "%s is not device memory", name);
     return MPM_OK;
 }
-
-#define MPM_TRY(expr)                     \
-    do {                                  \
-        mpm_status s_ = (expr);           \
-        if (s_ != MPM_OK) return s_;      \
-    } while (0)
 
 // ----------------------------------------------------------- workspace
 
@@ -379,7 +365,19 @@ struct FitJob {
     size_t ws_bytes;
     FitWs L;
     bool empty;
+    bool proj;        // spatial projection (mpm_fit_proj): pj holds it
+    ProjJob pj;
 };
+
+// The likelihood pieces of update `it`: the fused voxel pass, or its
+// projected form (per-contrast passes on the acquisition grids and the push).
+static cudaError_t launch_lik(const FitJob& j, int it, cudaStream_t st)
+{
+    const FitWs& L = j.L;
+    if (j.proj) return launch_grad_hess_proj(j.P, j.pj, j.y, L.g, L.h, L.nll + it, L.red, st);
+    return launch_grad_hess(j.P, j.problem->echo_dtype, j.x, j.y, j.b1p, j.b1m, L.g, L.h,
+                            L.nll + it, L.red, st);
+}
 
 static mpm_status fit_prepare(const mpm_problem* problem, const mpm_opts* opts, const void* x,
                               const float* b1p, const float* b1m, float* y, float* var_out,
@@ -398,6 +396,7 @@ static mpm_status fit_prepare(const mpm_problem* problem, const mpm_opts* opts, 
     job.ws = ws;
     job.ws_bytes = ws_bytes;
     job.empty = job.P.N == 0;
+    job.proj = false;
     if (job.empty) return MPM_OK;
     MPM_TRY(check_dev(x, "x", false, problem->echo_dtype ? 2 : 4));
     MPM_TRY(check_dev(b1p, "b1p", true, 4));
@@ -422,9 +421,7 @@ static cudaError_t fit_enqueue_updates(const FitJob& j, cudaStream_t st, int* it
     for (;; ++it) {
         w_fresh = (it % npi == 0);
         if ((e = launch_jtv(P, j.y, w_fresh ? L.w : nullptr, L.jtv + it, L.red, st))) return e;
-        if ((e = launch_grad_hess(P, j.problem->echo_dtype, j.x, j.y, j.b1p, j.b1m, L.g, L.h,
-                                  L.nll + it, L.red, st)))
-            return e;
+        if ((e = launch_lik(j, it, st))) return e;
         if (it >= j.opts.gn_iters) break;
         if ((e = launch_solve(P, j.opts.cg_iters, j.opts.tol_cg, L.h, L.w, L.g, j.y, L.xbuf, j.y,
                               nullptr, L.cg_rel + it, L.cg_it + it, L.solve, L.hdr, L.red, st)))
@@ -452,8 +449,7 @@ static mpm_status fit_run_adaptive(const FitJob& j, cudaStream_t st, int* iters_
     for (;; ++it) {
         w_fresh = (it % npi == 0);
         MPM_CUDA(launch_jtv(P, j.y, w_fresh ? L.w : nullptr, L.jtv + it, L.red, st));
-        MPM_CUDA(launch_grad_hess(P, j.problem->echo_dtype, j.x, j.y, j.b1p, j.b1m, L.g, L.h,
-                                  L.nll + it, L.red, st));
+        MPM_CUDA(launch_lik(j, it, st));
         if (it >= j.opts.gn_iters) break;
         double v[2];
         MPM_CUDA(cudaMemcpyAsync(&v[0], L.nll + it, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -517,6 +513,8 @@ static std::string graph_key(const FitJob* jobs, int n)
         k.append(reinterpret_cast<const char*>(&j.opts), sizeof(mpm_opts));
         const void* ptrs[7] = {j.x, j.b1p, j.b1m, j.y, j.var, j.ws, (const void*)j.ws_bytes};
         k.append(reinterpret_cast<const char*>(ptrs), sizeof ptrs);
+        k.push_back(j.proj ? 1 : 0);
+        if (j.proj) proj_key(j.pj, k);
     }
     return k;
 }
@@ -586,7 +584,10 @@ static mpm_status fit_run(FitJob* jobs, int n, mpm_report* reports, cudaStream_t
         MPM_CUDA(cudaMemsetAsync(j.L.hdr, 0, sizeof(WsHeader), st));
         if (j.opts.init) {
             any_init = true;
-            MPM_CUDA(launch_image_means(j.P, j.problem->echo_dtype, j.x, j.L.mean_parts, j.L.means, st));
+            if (j.proj)
+                MPM_CUDA(proj_image_means(j.P, j.pj, j.L.mean_parts, j.L.means, st));
+            else
+                MPM_CUDA(launch_image_means(j.P, j.problem->echo_dtype, j.x, j.L.mean_parts, j.L.means, st));
             MPM_CUDA(cudaMemcpyAsync(&means[(size_t)i * MPM_MAX_IMAGES], j.L.means,
                                      sizeof(double) * j.P.I, cudaMemcpyDeviceToHost, st));
         }
@@ -925,6 +926,38 @@ mpm_status mpm_fit(const mpm_problem* problem, const mpm_opts* opts, const void*
     FitJob job;
     MPM_TRY(fit_prepare(problem, opts, x, b1p, b1m, y, var_out, ws, ws_bytes, job));
     return fit_run(&job, 1, report, (cudaStream_t)stream);
+}
+
+mpm_status mpm_fit_proj(const mpm_problem* problem, const mpm_projection* proj,
+                        const mpm_opts* opts, const void* const* x, const float* const* b1p,
+                        const float* const* b1m, float* y, float* var_out, void* ws,
+                        size_t ws_bytes, mpm_report* report, void* stream)
+{
+    FitJob job;
+    MPM_TRY(check_problem(problem));
+    MPM_TRY(check_opts(opts));
+    job.problem = problem;
+    job.opts = *opts;
+    job.P = make_dev(problem);
+    job.x = nullptr;
+    job.b1p = job.b1m = nullptr;
+    job.y = y;
+    job.var = var_out;
+    job.ws = ws;
+    job.ws_bytes = ws_bytes;
+    job.empty = job.P.N == 0;
+    job.proj = true;
+    memset(&job.pj, 0, sizeof job.pj);
+    if (job.empty) {
+        if (report) memset(report, 0, sizeof *report);
+        return MPM_OK;
+    }
+    MPM_TRY(check_dev(y, "y_inout", false, 4));
+    MPM_TRY(check_dev(var_out, "var_out", true, 4));
+    mpm_status s = proj_prepare(problem, proj, x, b1p, b1m, ws, ws_bytes, job.pj, job.L);
+    if (s == MPM_OK) s = fit_run(&job, 1, report, (cudaStream_t)stream);
+    proj_release(job.pj);
+    return s;
 }
 
 mpm_status mpm_fit_batch(int n, const mpm_problem* const* problems, const mpm_opts* opts,

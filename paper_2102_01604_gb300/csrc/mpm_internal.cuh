@@ -8,6 +8,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "../../include/mpm.h"
 
 namespace mpm {
@@ -305,10 +307,50 @@ struct FitWs {
 };
 
 FitWs layout(const DevProblem& P, int call, void* base);   // base NULL: sizes only
+
+// Spatial projection (projection.cu): per-contrast inputs on the acquisition
+// grids, and the opaque projection and workspace of one projected fit.
+struct ProjIn {
+    int echo_dtype;
+    const void* x[MPM_MAX_CONTRASTS];
+    const float* b1p[MPM_MAX_CONTRASTS];
+    const float* b1m[MPM_MAX_CONTRASTS];
+};
+struct ProjJob {
+    void* Q;          // DevProj
+    void* W;          // ProjWs
+    ProjIn in;
+};
+cudaError_t launch_grad_hess_proj(const DevProblem& P, const ProjJob& pj, const float* y, float* g,
+                                  float* h, double* nll, Reduce red, cudaStream_t st);
+mpm_status proj_prepare(const mpm_problem* problem, const mpm_projection* proj, const void* const* x,
+                        const float* const* b1p, const float* const* b1m, void* ws, size_t ws_bytes,
+                        ProjJob& pj, FitWs& L);
+void proj_release(ProjJob& pj);
+size_t proj_key_bytes();
+void proj_key(const ProjJob& pj, std::string& k);
+cudaError_t proj_image_means(const DevProblem& P, const ProjJob& pj, double* parts, double* means,
+                             cudaStream_t st);
 mpm_status check_ws(const DevProblem& P, int call, void* ws, size_t ws_bytes, FitWs& L);
 void initial_maps(const mpm_problem* p, const double* mean, float out[4]);
 
 mpm_status fail(mpm_status s, const char* fmt, ...);
+
+// Return the status of a failing call (with the CUDA error text).
+#define MPM_CUDA(call)                                                                   \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(MPM_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),   \
+                        __FILE__, __LINE__);                                             \
+    } while (0)
+
+#define MPM_TRY(expr)                     \
+    do {                                  \
+        mpm_status s_ = (expr);           \
+        if (s_ != MPM_OK) return s_;      \
+    } while (0)
+
 mpm_status check_problem(const mpm_problem* p);
 mpm_status check_opts(const mpm_opts* o);
 mpm_status check_dev(const void* ptr, const char* name, bool optional, size_t align);

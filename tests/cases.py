@@ -78,3 +78,51 @@ def assert_close_scaled(got, ref, rtol, what=""):
 def map_error(y_got, y_ref):
     """Per-voxel error in log space relative to max(1, |y|)."""
     return np.abs(y_got - y_ref) / np.maximum(1.0, np.abs(y_ref))
+
+
+# ------------------------------------------------------------ spatial projection
+
+def sub_protocol(prot, c):
+    """The protocol of contrast c alone."""
+    i0 = sum(prot["n_echoes"][:c])
+    out = {k: (v[c:c + 1] if isinstance(v, list) else v) for k, v in prot.items()}
+    out["te"] = list(prot["te"][i0:i0 + prot["n_echoes"][c]])
+    return out
+
+
+def moved_dataset(shape, grids, affines, seed=0, contrasts=("PDw", "T1w", "MTw"),
+                  n_echoes=(6, 6, 5), snr=20.0):
+    """Phantom maps on the reconstruction grid ``shape``; contrast c acquired
+    on ``grids[c]`` with ``affines[c]`` (acquisition voxel -> reconstruction
+    voxel coordinates).  The images of each contrast are the oracle's forward
+    model of the pulled (interpolated) maps, with Rician noise at first-echo
+    SNR ``snr``, rounded to float32; B1 fields are drawn on each acquisition
+    grid."""
+    prot = phantom.protocol(contrasts, n_echoes)
+    with_mt = any(prot["mt"])
+    ph = phantom.phantom(shape, seed=seed, n_contrasts=len(contrasts), with_mt=with_mt)
+    prot = round_protocol(prot)
+    K = 4 if with_mt else 3
+    p0 = orc.make_problem(prot, shape)
+    s_list, bps, bms = [], [], []
+    for c in range(len(contrasts)):
+        yc, _ = orc.pull(p0, grids[c], affines[c], ph["y"])
+        fc = phantom.phantom(grids[c], seed=seed + 101 + c, n_contrasts=1, with_mt=with_mt)
+        bp, bm = f32(fc["b1p"]), f32(fc["b1m"][0])
+        sub = orc.make_problem(sub_protocol(prot, c), grids[c], n_maps=K)
+        s_list.append(orc.forward(sub, yc, bp, bm[None]))
+        bps.append(bp)
+        bms.append(bm)
+    sig2 = []
+    for c, s in enumerate(s_list):
+        m = float(np.mean(s[0])) / snr
+        sig2.append(float(np.float32(m * m)))
+    prot["sigma2"] = sig2
+    prot = round_protocol(prot)
+    xs = []
+    for c, s in enumerate(s_list):
+        sp = sub_protocol(prot, c)
+        xs.append(f32(phantom.rician(s, sp, seed=seed + 7 + c)))
+    return {"prot": prot, "shape": tuple(shape), "y_true": ph["y"], "xs": xs, "b1ps": bps,
+            "b1ms": bms, "grids": [tuple(g) for g in grids],
+            "affines": [np.asarray(a, dtype=np.float64) for a in affines]}

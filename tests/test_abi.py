@@ -47,7 +47,8 @@ def test_struct_layout_matches_header(lib):
 #include <stddef.h>
 #include "mpm.h"
 int main(void) {
-  printf("%zu %zu %zu\n", sizeof(mpm_problem), sizeof(mpm_opts), sizeof(mpm_report));
+  printf("%zu %zu %zu %zu %zu\n", sizeof(mpm_problem), sizeof(mpm_opts), sizeof(mpm_report),
+         sizeof(mpm_projection), offsetof(mpm_projection, affine));
   printf("%zu %zu %zu %zu %zu %zu\n", offsetof(mpm_problem, te), offsetof(mpm_problem, n_maps),
          offsetof(mpm_problem, lambda), offsetof(mpm_problem, echo_dtype),
          offsetof(mpm_report, cg_rel), offsetof(mpm_report, cg_done));
@@ -63,7 +64,8 @@ int main(void) {
     sizes = [int(v) for v in out]
     P, O, R = _lib.Problem, _lib.Opts, _lib.Report
     assert sizes[:3] == [ctypes.sizeof(P), ctypes.sizeof(O), ctypes.sizeof(R)]
-    assert sizes[3:] == [P.te.offset, P.n_maps.offset, P.lam.offset, P.echo_dtype.offset,
+    assert sizes[3:5] == [ctypes.sizeof(_lib.Projection), _lib.Projection.affine.offset]
+    assert sizes[5:] == [P.te.offset, P.n_maps.offset, P.lam.offset, P.echo_dtype.offset,
                          R.cg_rel.offset, R.cg_done.offset]
 
 
@@ -117,3 +119,47 @@ def test_host_pointers_are_refused(lib):
 def test_status_strings(lib):
     for s in (0, 1, -1, -2, -3, -4, -5):
         assert lib.mpm_status_string(s).decode()
+
+
+def _eye_proj(mpm, dims, C=3):
+    return mpm.make_projection([dims] * C, [[[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 1, 0]]] * C)
+
+
+def test_projection_validation(lib):
+    """Spatial projection: singular or non-finite affines, empty grids and host
+    pointers are refused before anything is enqueued; the workspace grows with
+    the acquisition grids."""
+    import numpy as np
+    import paper_2102_01604_gb300 as mpm
+    p = _problem((16, 12, 8))
+    o = mpm.make_opts()
+    q = _eye_proj(mpm, (16, 12, 8))
+    base = mpm.mpm_workspace_size_proj(p, q, o)
+    assert base > mpm.mpm_workspace_size(p, o)
+    q2 = _eye_proj(mpm, (32, 24, 8))
+    assert mpm.mpm_workspace_size_proj(p, q2, o) > base
+    n = ctypes.c_size_t()
+    for mutate in ("singular", "nan", "dims", "fine"):
+        qb = _eye_proj(mpm, (16, 12, 8))
+        if mutate == "singular":
+            for k in range(12):
+                qb.affine[1][k] = 0.0
+        elif mutate == "nan":
+            qb.affine[2][5] = float("nan")
+        elif mutate == "fine":
+            for r in range(3):
+                qb.affine[1][5 * r] = 0.2           # 5x smaller acquisition voxels
+        else:
+            qb.dims[0][2] = 0
+        st = lib.mpm_workspace_size_proj(ctypes.byref(p), ctypes.byref(qb), ctypes.byref(o), 0,
+                                         ctypes.byref(n))
+        assert st == _lib.ERR_INVALID_ARG, mutate
+        assert lib.mpm_last_error().decode()
+    # a host pointer among the per-contrast images
+    x = np.zeros((8, 16 * 12 * 8), dtype=np.float32)
+    xs = (ctypes.c_void_p * 3)(x.ctypes.data, x.ctypes.data, x.ctypes.data)
+    y = np.zeros((4, 16 * 12 * 8), dtype=np.float32)
+    st = lib.mpm_grad_hess_proj(ctypes.byref(p), ctypes.byref(q), xs, None, None, y.ctypes.data,
+                                y.ctypes.data, y.ctypes.data, y.ctypes.data, None, 0, None)
+    assert st == _lib.ERR_INVALID_ARG
+    assert "x[0]" in lib.mpm_last_error().decode()
