@@ -117,19 +117,6 @@ __device__ __forceinline__ void interpolate(const Cell& c, const float* __restri
     }
 }
 
-// Weight with which acquisition voxel (i, j, k) of contrast q pulls
-// reconstruction voxel (x, y, z); 0 when it does not.
-__device__ __forceinline__ float pull_weight(const ProjC& q, int i, int j, int k, int x, int y,
-                                             int z, int nx, int ny, int nz)
-{
-    float r[3];
-    if (!reslice(q, i, j, k, nx, ny, nz, r)) return 0.0f;
-    const Cell c = cell_of(r);
-    const int dx = x - c.b[0], dy = y - c.b[1], dz = z - c.b[2];
-    if ((unsigned)dx > 1u || (unsigned)dy > 1u || (unsigned)dz > 1u) return 0.0f;
-    return corner_weight(c, dx, dy, dz);
-}
-
 // Box of acquisition voxels that can pull reconstruction voxel (x, y, z).
 __device__ __forceinline__ void candidate_box(const ProjC& q, int x, int y, int z, int lo[3],
                                               int hi[3])
@@ -142,6 +129,47 @@ __device__ __forceinline__ void candidate_box(const ProjC& q, int x, int y, int 
         lo[d] = max(0, (int)ceilf(a - e));
         hi[d] = min(md[d] - 1, (int)floorf(a + e));
     }
+}
+
+// Calls f(w, m) for every acquisition voxel m of contrast q that pulls
+// reconstruction voxel (x, y, z), with the weight the pull uses, in a fixed
+// order (f is taken by value and returned).  Each coordinate is built with
+// the same fused multiply-adds as reslice(), so every weight is bit-identical
+// to the pull's; axes are tested one at a time and most candidates are
+// rejected on the first.
+template <typename F>
+__device__ __forceinline__ F gather_pullers(const ProjC& q, int x, int y, int z, int nx, int ny,
+                                            int nz, F f)
+{
+    int lo[3], hi[3];
+    candidate_box(q, x, y, z, lo, hi);
+    for (int k = lo[2]; k <= hi[2]; ++k)
+        for (int j = lo[1]; j <= hi[1]; ++j)
+            for (int i = lo[0]; i <= hi[0]; ++i) {
+                const float r0 = fmaf(q.A[0], (float)i, fmaf(q.A[1], (float)j, fmaf(q.A[2], (float)k, q.A[3])));
+                if (!(r0 >= 0.0f && r0 <= (float)(nx - 1))) continue;
+                const float b0 = floorf(r0);
+                const int dx = x - (int)b0;
+                if ((unsigned)dx > 1u) continue;
+                const float r1 = fmaf(q.A[4], (float)i, fmaf(q.A[5], (float)j, fmaf(q.A[6], (float)k, q.A[7])));
+                if (!(r1 >= 0.0f && r1 <= (float)(ny - 1))) continue;
+                const float b1 = floorf(r1);
+                const int dy = y - (int)b1;
+                if ((unsigned)dy > 1u) continue;
+                const float r2 = fmaf(q.A[8], (float)i, fmaf(q.A[9], (float)j, fmaf(q.A[10], (float)k, q.A[11])));
+                if (!(r2 >= 0.0f && r2 <= (float)(nz - 1))) continue;
+                const float b2 = floorf(r2);
+                const int dz = z - (int)b2;
+                if ((unsigned)dz > 1u) continue;
+                Cell c;
+                c.f[0] = r0 - b0;
+                c.f[1] = r1 - b1;
+                c.f[2] = r2 - b2;
+                const float w = corner_weight(c, dx, dy, dz);
+                if (w == 0.0f) continue;
+                f(w, (long long)i + (long long)q.mx * (j + (long long)q.my * k));
+            }
+    return f;
 }
 
 // ------------------------------------------------- projected voxel pass
@@ -216,22 +244,21 @@ __global__ void __launch_bounds__(kBlock) k_push_all(DevProblem P, DevProj Q, Pr
         for (int t = 0; t < K; ++t) G[t] = 0.0f;
 #pragma unroll
         for (int t = 0; t < T; ++t) H[t] = 0.0f;
-        for (int c = 0; c < Q.C; ++c) {
+        // unrolled, so each contrast's affine is read as constant operands
+#pragma unroll
+        for (int c = 0; c < MPM_MAX_CONTRASTS; ++c) {
+            if (c >= Q.C) break;
             const ProjC& q = Q.c[c];
             const long long M = q.M;
-            int lo[3], hi[3];
-            candidate_box(q, x, y, z, lo, hi);
-            for (int k = lo[2]; k <= hi[2]; ++k)
-                for (int j = lo[1]; j <= hi[1]; ++j)
-                    for (int i = lo[0]; i <= hi[0]; ++i) {
-                        const float w = pull_weight(q, i, j, k, x, y, z, P.nx, P.ny, P.nz);
-                        if (w == 0.0f) continue;
-                        const long long m = (long long)i + (long long)q.mx * (j + (long long)q.my * k);
+            const float* __restrict__ gs = B.gc[c];
+            const float* __restrict__ hs = B.hc[c];
+            auto add = [&](float w, long long m) {
 #pragma unroll
-                        for (int t = 0; t < K; ++t) G[t] = fmaf(w, __ldg(B.gc[c] + t * M + m), G[t]);
+                for (int t = 0; t < K; ++t) G[t] = fmaf(w, __ldg(gs + t * M + m), G[t]);
 #pragma unroll
-                        for (int t = 0; t < T; ++t) H[t] = fmaf(w, __ldg(B.hc[c] + t * M + m), H[t]);
-                    }
+                for (int t = 0; t < T; ++t) H[t] = fmaf(w, __ldg(hs + t * M + m), H[t]);
+            };
+            gather_pullers(q, x, y, z, P.nx, P.ny, P.nz, add);
         }
 #pragma unroll
         for (int t = 0; t < K; ++t) g[t * N + n] = G[t];
@@ -262,29 +289,27 @@ __global__ void __launch_bounds__(kBlock) k_pull(DevProblem P, ProjC q, int chan
     }
 }
 
+// Running sum of w * u[m] for one channel.
+struct SumInto {
+    float s;
+    const float* __restrict__ u;
+    __device__ __forceinline__ void operator()(float w, long long m) { s = fmaf(w, __ldg(u + m), s); }
+};
+
 __global__ void __launch_bounds__(kBlock) k_push(DevProblem P, ProjC q, int channels,
                                                  const float* __restrict__ u,
                                                  float* __restrict__ out, int accumulate)
 {
     const long long N = P.N, M = q.M;
     const long long sxy = (long long)P.nx * P.ny;
-    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
-         n += (long long)gridDim.x * blockDim.x) {
+    const long long total = N * channels;
+    for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+         id += (long long)gridDim.x * blockDim.x) {
+        const long long ch = id / N, n = id - ch * N;
         const int x = (int)(n % P.nx), y = (int)((n / P.nx) % P.ny), z = (int)(n / sxy);
-        int lo[3], hi[3];
-        candidate_box(q, x, y, z, lo, hi);
-        for (int ch = 0; ch < channels; ++ch) {
-            float s = accumulate ? out[ch * N + n] : 0.0f;
-            for (int k = lo[2]; k <= hi[2]; ++k)
-                for (int j = lo[1]; j <= hi[1]; ++j)
-                    for (int i = lo[0]; i <= hi[0]; ++i) {
-                        const float w = pull_weight(q, i, j, k, x, y, z, P.nx, P.ny, P.nz);
-                        if (w == 0.0f) continue;
-                        const long long m = (long long)i + (long long)q.mx * (j + (long long)q.my * k);
-                        s = fmaf(w, __ldg(u + ch * M + m), s);
-                    }
-            out[ch * N + n] = s;
-        }
+        SumInto acc{accumulate ? out[id] : 0.0f, u + ch * M};
+        acc = gather_pullers(q, x, y, z, P.nx, P.ny, P.nz, acc);
+        out[id] = acc.s;
     }
 }
 
