@@ -251,9 +251,28 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
-def kernel_source_hash():
+# Source files that define each kernel kind (besides device_common.cuh,
+# which every kernel includes).
+KIND_SOURCES = {
+    "grad_hess": ["voxel_kernels.cu", "voxel_model.cuh"],
+    "uncertainty": ["voxel_kernels.cu"],
+    "jtv": ["stencil_kernels.cu"],
+    "pcg_init": ["stencil_kernels.cu"],
+    "pcg_direction": ["stencil_kernels.cu"],
+    "pcg_matvec": ["stencil_kernels.cu", "stencil_tma.cu"],
+    "pcg_update": ["stencil_kernels.cu"],
+    "pcg_final": ["stencil_kernels.cu"],
+    "grad_hess_proj": ["projection.cu", "voxel_model.cuh"],
+    "reslice": ["projection.cu"],
+}
+
+
+def kernel_source_hash(kind: str):
+    """Hash of the sources of one kernel kind, or None for an unknown kind."""
+    if kind not in KIND_SOURCES:
+        return None
     h = hashlib.sha256()
-    for name in ("stencil_kernels.cu", "stencil_tma.cu", "voxel_kernels.cu", "mpm_internal.cuh"):
+    for name in ["device_common.cuh"] + KIND_SOURCES[kind]:
         with open(os.path.join(ROOT, "paper_2102_01604_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -261,16 +280,14 @@ def kernel_source_hash():
 
 def measured_traffic(kind: str, n_vox: int):
     """DRAM bytes per launch from the committed ncu capture, scaled to this
-    volume; None when the kernels changed since the capture."""
+    volume; None when the kernel's sources changed since the capture."""
     try:
         with open(TRAFFIC_FILE) as f:
             tr = json.load(f)
     except (OSError, ValueError):
         return None
-    if tr.get("source_hash") != kernel_source_hash():
-        return None
     k = tr.get("kernels", {}).get(kind)
-    if not k:
+    if not k or k.get("source_hash") != kernel_source_hash(kind):
         return None
     return int(k["dram_bytes_per_voxel"] * n_vox)
 
