@@ -200,19 +200,27 @@ class ClockSampler:
 def algorithmic_bytes(K: int, C: int, I: int, echo_bytes: int = 4):
     """Bytes each kernel must move per voxel (reads + writes of its operands,
     float32, every array touched once); the PCG direction bytes are per solve
-    (its first launch reads no x)."""
+    (odd passes read z and p_{k-1} and write p_k; even passes also read
+    p_{k-2} and, after the first, x, and write x)."""
     T = K * (K + 1) // 2
     f = 4
-    dir1 = 2 * K * f + 2 * K * f                        # k = 1: read z, p_old; write p, x
-    dirk = dir1 + K * f                                 # k >= 2: + read x
+    direction = 0
+    for k in range(1, CG_ITERS):
+        if k % 2:
+            direction += 3 * K * f
+        else:
+            direction += (5 if k == 2 else 6) * K * f
+    xcount = max((k for k in range(2, CG_ITERS, 2)), default=0)
+    pend = CG_ITERS - xcount                            # directions folded by the final pass
+    final = (K * f if xcount else 0) + pend * K * f + 2 * K * f
     return {
         "grad_hess": I * echo_bytes + K * f + f + C * f + K * f + T * f,
         "jtv": K * f + f,
         "pcg_init": f + 2 * K * f + T * f + T * f + 3 * K * f,
-        "pcg_direction_per_solve": (dir1 + dirk * max(CG_ITERS - 2, 0)) if CG_ITERS > 1 else 0,
+        "pcg_direction_per_solve": direction,
         "pcg_matvec": K * f + T * f + f + K * f,
         "pcg_update": 2 * K * f + T * f + 2 * K * f,
-        "pcg_final": 4 * K * f,
+        "pcg_final": final,
         "uncertainty": T * f + f + K * f,
     }
 

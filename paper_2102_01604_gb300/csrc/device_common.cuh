@@ -55,10 +55,11 @@ struct SolveScalars {
     double rr0;       // |r_0|^2
     double rr;        // |r_k|^2 of the current residual
     double alpha;     // step of the latest completed matvec
+    double alpha_prev;  // step of the matvec before it
     double beta;      // coefficient of the next direction update
     double tol2;      // (tol_cg)^2, 0 = off
     int it;           // PCG iterations completed
-    int xcount;       // iterations already folded into x
+    int xcount;       // iterations already folded into x (x is updated every other iteration)
     int done;         // 1 = no further iterations
     int pad;
 };

@@ -1,7 +1,8 @@
 // stencil_kernels.cu -- the prior and the Newton-system solve (sm_103a):
 //   k_jtv          JTV weights w_n = (u_n + eps^2)^-1/2 and JTV_eps (Eqs. 38-40)
 //   k_pcg_init     r_0 = g + L y, preconditioner factor, z_0 = M^-1 r_0 (Eq. 42)
-//   k_pcg_direction p_k = z_k + beta p_{k-1}; x += alpha p_{k-1}
+//   k_pcg_direction p_k = z_k + beta p_{k-1}; every other k also
+//                  x += alpha_{k-2} p_{k-2} + alpha_{k-1} p_{k-1}
 //   k_pcg_matvec   q = (H + L) p_k; p.q
 //   k_pcg_update   r -= alpha q; z = M^-1 r; r.z, r.r
 //   k_pcg_final    delta = x + alpha p (or y <- y - delta)
@@ -245,6 +246,7 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(DevProblem P, int zc, const
         sc.rr0 = out[1];
         sc.rr = out[1];
         sc.alpha = 0.0;
+        sc.alpha_prev = 0.0;
         sc.beta = 0.0;
         sc.it = 0;
         sc.xcount = 0;
@@ -258,27 +260,34 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(DevProblem P, int zc, const
 
 // ---------------------------------------------------------- PCG direction
 
-// p_k = z_k + beta_{k-1} p_{k-1} and x += alpha_{k-1} p_{k-1} (k >= 1), a
-// streaming pass over the K*N entries (float4 when VPT = 4).
+// p_k = z_k + beta_{k-1} p_{k-1} (k >= 1), a streaming pass over the K*N
+// entries (float4 when VPT = 4).  x is brought up to date only at even k:
+// x += alpha_{k-2} p_{k-2} + alpha_{k-1} p_{k-1}, with p_{k-2} read from the
+// buffer that p_k is about to replace.  The two additions happen in the order
+// of two single updates (bit for bit the same x); the odd passes skip x, which
+// saves reading and writing it every other iteration.
 template <int VPT>
 __global__ void __launch_bounds__(kBlock) k_pcg_direction(long long total, int k_it,
                                                           const float* __restrict__ zv,
                                                           const float* __restrict__ pold,
                                                           float* __restrict__ pnew,
                                                           float* __restrict__ xacc,
-                                                          const WsHeader* hdr)
+                                                          WsHeader* hdr)
 {
     using V = typename std::conditional<VPT == 4, float4, float>::type;
-    __shared__ float s_beta, s_alpha;
+    __shared__ float s_beta, s_alpha, s_alpha_prev;
     __shared__ int s_done;
     if (threadIdx.x == 0) {
         s_done = hdr->sc.done;
         s_beta = (float)hdr->sc.beta;
         s_alpha = (float)hdr->sc.alpha;
+        s_alpha_prev = (float)hdr->sc.alpha_prev;
     }
     __syncthreads();
     if (s_done) return;
-    const float beta = s_beta, alpha = s_alpha;
+    const bool fold = (k_it & 1) == 0;                  // x update at even k (k >= 2)
+    if (fold && blockIdx.x == 0 && threadIdx.x == 0) hdr->sc.xcount = k_it;
+    const float beta = s_beta, alpha = s_alpha, alpha_prev = s_alpha_prev;
     const long long nv = total / VPT;
     const V* __restrict__ z4 = reinterpret_cast<const V*>(zv);
     const V* __restrict__ o4 = reinterpret_cast<const V*>(pold);
@@ -288,18 +297,28 @@ __global__ void __launch_bounds__(kBlock) k_pcg_direction(long long total, int k
          i += (long long)gridDim.x * blockDim.x) {
         const V zz = __ldg(z4 + i);
         const V o = __ldg(o4 + i);
-        V xo;
-        if (k_it > 1) xo = x4[i];
-        V pv, xv;
+        V pv;
+        if (fold) {
+            const V o2 = p4[i];                             // p_{k-2}, before it is replaced
+            V xo;
+            if (k_it > 2) xo = x4[i];
+            V xv;
 #pragma unroll
-        for (int j = 0; j < VPT; ++j) {
-            const float oj = reinterpret_cast<const float*>(&o)[j];
-            reinterpret_cast<float*>(&pv)[j] = reinterpret_cast<const float*>(&zz)[j] + beta * oj;
-            const float xj = k_it > 1 ? reinterpret_cast<const float*>(&xo)[j] : 0.0f;
-            reinterpret_cast<float*>(&xv)[j] = xj + alpha * oj;
+            for (int j = 0; j < VPT; ++j) {
+                const float oj = reinterpret_cast<const float*>(&o)[j];
+                const float xj = k_it > 2 ? reinterpret_cast<const float*>(&xo)[j] : 0.0f;
+                const float t = fmaf(alpha_prev, reinterpret_cast<const float*>(&o2)[j], xj);
+                reinterpret_cast<float*>(&xv)[j] = fmaf(alpha, oj, t);
+                reinterpret_cast<float*>(&pv)[j] = fmaf(beta, oj, reinterpret_cast<const float*>(&zz)[j]);
+            }
+            x4[i] = xv;
+        } else {
+#pragma unroll
+            for (int j = 0; j < VPT; ++j)
+                reinterpret_cast<float*>(&pv)[j] =
+                    fmaf(beta, reinterpret_cast<const float*>(&o)[j], reinterpret_cast<const float*>(&zz)[j]);
         }
         p4[i] = pv;
-        x4[i] = xv;
     }
 }
 
@@ -467,11 +486,11 @@ __global__ void __launch_bounds__(kMvX * kMvY, 3) k_pcg_matvec(DevProblem P, int
     double out[1];
     if (grid_reduce<1>(v, red, out) && tid == 0) {
         SolveScalars& sc = hdr->sc;
-        if (k_it > 0) sc.xcount = k_it;
         if (!(out[0] == out[0])) atomicOr(&hdr->status, kStatusNaN);
         if (!(out[0] > 0.0)) {
-            sc.done = 1;                 // no further step; alpha keeps the previous value
+            sc.done = 1;                 // no further step; the alphas keep their values
         } else {
+            sc.alpha_prev = sc.alpha;
             sc.alpha = sc.rz / out[0];
         }
     }
@@ -568,13 +587,15 @@ __global__ void __launch_bounds__(kBlock) k_pcg_final(long long total, SolveBufs
 {
     const SolveScalars sc = hdr->sc;
     const bool have_x = sc.xcount > 0;
-    const bool pend = sc.xcount < sc.it;
-    const float alpha = (float)sc.alpha;
+    const int pend = sc.it - sc.xcount;        // directions not yet in x: 0, 1 or 2
+    const float alpha = (float)sc.alpha, alpha_prev = (float)sc.alpha_prev;
     const float* __restrict__ pp = B.p[(sc.it - 1) & 1];
+    const float* __restrict__ pp2 = B.p[sc.it & 1];   // p_{it-2} when pend == 2
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
         float v = have_x ? xacc[i] : 0.0f;
-        if (pend) v += alpha * pp[i];
+        if (pend == 2) v = fmaf(alpha_prev, pp2[i], v);
+        if (pend >= 1) v = fmaf(alpha, pp[i], v);
         if (y_update)
             y_update[i] -= v;
         else

@@ -330,11 +330,11 @@ __global__ void __launch_bounds__(kTmaThreads) k_pcg_matvec_tma(
     double out[1];
     if (grid_reduce<1>(v, red, out) && tid == 0 && !done) {
         SolveScalars& sc = hdr->sc;
-        if (k_it > 0) sc.xcount = k_it;
         if (!(out[0] == out[0])) atomicOr(&hdr->status, kStatusNaN);
         if (!(out[0] > 0.0)) {
-            sc.done = 1;                 // no further step; alpha keeps the previous value
+            sc.done = 1;                 // no further step; the alphas keep their values
         } else {
+            sc.alpha_prev = sc.alpha;
             sc.alpha = sc.rz / out[0];
         }
     }
