@@ -216,7 +216,7 @@ def algorithmic_bytes(K: int, C: int, I: int, echo_bytes: int = 4):
     return {
         "grad_hess": I * echo_bytes + K * f + f + C * f + K * f + T * f,
         "jtv": K * f + f,
-        "pcg_init": f + 2 * K * f + T * f + T * f + 3 * K * f,
+        "pcg_init": f + 2 * K * f + T * f + T * f + 2 * K * f,
         "pcg_direction_per_solve": direction,
         "pcg_matvec": K * f + T * f + f + K * f,
         "pcg_update": 2 * K * f + T * f + 2 * K * f,

@@ -1,6 +1,6 @@
 // stencil_kernels.cu -- the prior and the Newton-system solve (sm_103a):
 //   k_jtv          JTV weights w_n = (u_n + eps^2)^-1/2 and JTV_eps (Eqs. 38-40)
-//   k_pcg_init     r_0 = g + L y, preconditioner factor, z_0 = M^-1 r_0 (Eq. 42)
+//   k_pcg_init     r_0 = g + L y, preconditioner factor, p_0 = z_0 = M^-1 r_0 (Eq. 42)
 //   k_pcg_direction p_k = z_k + beta p_{k-1}; every other k also
 //                  x += alpha_{k-2} p_{k-2} + alpha_{k-1} p_{k-1}
 //   k_pcg_matvec   q = (H + L) p_k; p.q
@@ -228,8 +228,7 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(DevProblem P, int zc, const
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 B.r[k * N + n] = r[k];
-                B.z[k * N + n] = zz[k];
-                B.p[0][k * N + n] = zz[k];                // p_0 = z_0
+                B.p[0][k * N + n] = zz[k];                // p_0 = z_0 (z_0 itself is never read again)
                 vrz += r[k] * zz[k];
                 vrr += r[k] * r[k];
             }

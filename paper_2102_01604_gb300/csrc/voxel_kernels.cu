@@ -118,7 +118,8 @@ __global__ void __launch_bounds__(kBlock) k_uncertainty(DevProblem P, const floa
 #pragma unroll
         for (int a = 0; a < K; ++a) M[a][a] += (double)P.lambda[a] * d;
         bool ok = true;
-        double ld = 0.0;
+        double ld = 0.0;                // log det L, only when asked (log in float64 is costly)
+        double inv[K];                  // 1 / L_jj, one division per diagonal entry
 #pragma unroll
         for (int j = 0; j < K; ++j) {
             double s = M[j][j];
@@ -126,14 +127,14 @@ __global__ void __launch_bounds__(kBlock) k_uncertainty(DevProblem P, const floa
             for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
             if (!(s > 0.0)) { ok = false; s = 1e-300; }
             L[j][j] = sqrt(s);
-            ld += log(L[j][j]);
-            const double inv = 1.0 / L[j][j];
+            if (logdet) ld += log(L[j][j]);
+            inv[j] = 1.0 / L[j][j];
 #pragma unroll
             for (int i = j + 1; i < K; ++i) {
                 double v = M[i][j];
 #pragma unroll
                 for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
-                L[i][j] = v * inv;
+                L[i][j] = v * inv[j];
             }
         }
         if (!ok && status) atomicOr(status, kStatusNotPD);
@@ -143,13 +144,13 @@ __global__ void __launch_bounds__(kBlock) k_uncertainty(DevProblem P, const floa
         for (int j = 0; j < K; ++j) {
 #pragma unroll
             for (int i = 0; i < K; ++i) Li[i][j] = 0.0;
-            Li[j][j] = 1.0 / L[j][j];
+            Li[j][j] = inv[j];
 #pragma unroll
             for (int i = j + 1; i < K; ++i) {
                 double v = 0.0;
 #pragma unroll
                 for (int k = j; k < i; ++k) v -= L[i][k] * Li[k][j];
-                Li[i][j] = v / L[i][i];
+                Li[i][j] = v * inv[i];
             }
         }
         double var1 = 0.0;
