@@ -213,3 +213,46 @@ def test_acquisition_grids_partly_or_wholly_outside(mpm):
                                           [to_dev(b) for b in d["b1ms"]])
     assert float(nll2) == float(nll)
     assert np.array_equal(to_np(g2), to_np(g)) and np.array_equal(to_np(h2), to_np(h))
+
+
+def test_projected_fit_adaptive_stop_matches_the_oracle(mpm, moved):
+    """The host-side stopping rule (tol_gn > 0) on the projected fit: same
+    number of updates and objective as the oracle's rule."""
+    import torch
+    d = moved
+    pg, qg, po, qo = _problems(mpm, d)
+    ref = orc.fit_proj(po, qo, d["xs"], b1ps=d["b1ps"], b1ms=d["b1ms"], gn_iters=30, cg_iters=30,
+                       tol_gn=1e-3)
+    N = int(np.prod(d["shape"]))
+    y = torch.zeros((4, N), device="cuda")
+    st, rep = mpm.mpm_fit_proj(pg, qg, mpm.make_opts(gn_iters=30, cg_iters=30, tol_gn=1e-3),
+                               [to_dev(x) for x in d["xs"]], y, [to_dev(b) for b in d["b1ps"]],
+                               [to_dev(b) for b in d["b1ms"]])
+    assert 0 < rep.iters < 30 and rep.iters == ref["iters"]
+    np.testing.assert_allclose(np.array(rep.F[:rep.iters + 1]), ref["F"], rtol=1e-5)
+    assert map_error(to_np(y), ref["y"]).max() <= 1e-3
+
+
+def test_projected_fit_three_maps_and_bfloat16_echoes(mpm):
+    """Two contrasts without MT (K = 3 maps), echoes stored as bfloat16: the
+    oracle sees the same bfloat16-rounded images."""
+    import torch
+    grids = [(30, 28, 10), (26, 24, 10)]
+    affs = [np.eye(4), _aff([[0.9375, 0.25, 0.0], [-0.25, 0.9375, 0.0], [0.0, 0.0, 1.0]],
+                            [1.5, 2.75, 0.0])]
+    d = moved_dataset((28, 26, 10), grids, affs, seed=17, contrasts=("PDw", "T1w"),
+                      n_echoes=(6, 5))
+    xs16 = [torch.from_numpy(x).cuda().to(torch.bfloat16) for x in d["xs"]]
+    xs_rounded = [x.float().cpu().numpy() for x in xs16]
+    pg = mpm.make_problem(d["prot"], d["shape"], echo_dtype=1)
+    assert pg.n_maps == 3
+    qg = mpm.make_projection(d["grids"], d["affines"])
+    po = orc.make_problem(d["prot"], d["shape"])
+    qo = orc.make_projection(d["grids"], d["affines"])
+    ref = orc.fit_proj(po, qo, xs_rounded, b1ps=d["b1ps"], b1ms=d["b1ms"], gn_iters=6, cg_iters=30)
+    N = int(np.prod(d["shape"]))
+    y = torch.zeros((3, N), device="cuda")
+    st, rep = mpm.mpm_fit_proj(pg, qg, mpm.make_opts(gn_iters=6, cg_iters=30), xs16, y,
+                               [to_dev(b) for b in d["b1ps"]], [to_dev(b) for b in d["b1ms"]])
+    np.testing.assert_allclose(np.array(rep.F[:7]), ref["F"], rtol=1e-5)
+    assert map_error(to_np(y), ref["y"]).max() <= 1e-3
