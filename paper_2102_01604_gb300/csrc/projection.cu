@@ -11,8 +11,8 @@
 //
 //   k_grad_hess_proj  per acquisition voxel of one contrast: interpolate the
 //                     maps (8 corners), then the same per-contrast voxel model
-//                     as k_grad_hess (voxel_model.cuh); writes g_c, H_c and
-//                     the contrast's NLL
+//                     as k_grad_hess (voxel_model.cuh); writes g_c and H_c
+//                     (interleaved per acquisition voxel) and the contrast's NLL
 //   k_push_all        per reconstruction voxel: gathers, over every contrast,
 //                     the acquisition voxels whose interpolation stencil holds
 //                     it (a box around A_c^-1 n) with the pull's own weights,
@@ -45,10 +45,21 @@ struct DevProj {
     ProjC c[MPM_MAX_CONTRASTS];
 };
 
-// Per-contrast buffers of the projected voxel pass.
+// g_c and H_c of one acquisition voxel are stored together, K + T floats
+// padded to a multiple of 4 (16 for K = 4, 12 for K = 3), so the push reads
+// them as whole 16-byte vectors from one line.
+template <int K>
+struct GhStride {
+    static constexpr int T = K * (K + 1) / 2;
+    static constexpr int S = (K + T + 3) / 4 * 4;     // floats per voxel
+    static constexpr int V = S / 4;                    // float4 per voxel
+};
+
+__host__ __device__ constexpr int gh_floats(int K) { return (K + K * (K + 1) / 2 + 3) / 4 * 4; }
+
+// Per-contrast g_c / H_c buffers of the projected voxel pass.
 struct ProjBufs {
-    const float* gc[MPM_MAX_CONTRASTS];
-    const float* hc[MPM_MAX_CONTRASTS];
+    const float4* gh[MPM_MAX_CONTRASTS];
 };
 
 // Reconstruction coordinate of acquisition voxel (i, j, k); true when it lies
@@ -180,16 +191,24 @@ __global__ void __launch_bounds__(kBlock) k_grad_hess_proj(DevProblem P, ProjC q
                                                            const XT* __restrict__ x,
                                                            const float* __restrict__ b1p,
                                                            const float* __restrict__ b1m,
-                                                           float* __restrict__ gc,
-                                                           float* __restrict__ hc, double* nll,
+                                                           float4* __restrict__ gh, double* nll,
                                                            Reduce red)
 {
     constexpr int T = K * (K + 1) / 2;
+    using GS = GhStride<K>;
+    // each warp's 32 voxels are staged here and written as one contiguous run
+    __shared__ float4 stage[kBlock / 32][32 * GS::V];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const long long M = q.M;
     const long long sxy = (long long)q.mx * q.my;
     Acc nll_acc;
-    for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < M;
-         m += (long long)gridDim.x * blockDim.x) {
+    // the loop runs whole warps (all lanes the same number of times)
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long trips = (M + stride - 1) / stride;
+    for (long long it = 0; it < trips; ++it) {
+        const long long m0 = it * stride + blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31);
+        const long long m = m0 + lane;
+        const bool live = m < M;
         const int i = (int)(m % q.mx), j = (int)((m / q.mx) % q.my), k = (int)(m / sxy);
         float G[K], H[T];
 #pragma unroll
@@ -198,7 +217,7 @@ __global__ void __launch_bounds__(kBlock) k_grad_hess_proj(DevProblem P, ProjC q
         for (int t = 0; t < T; ++t) H[t] = 0.0f;
         float nll_v = 0.0f;
         float r[3];
-        if (reslice(q, i, j, k, P.nx, P.ny, P.nz, r)) {
+        if (live && reslice(q, i, j, k, P.nx, P.ny, P.nz, r)) {
             float yv[K];
             interpolate<K>(cell_of(r), y, P.N, P.nx, P.ny, P.nz, yv);
             float yk[4] = {0.f, 0.f, 0.f, 0.f};
@@ -211,10 +230,24 @@ __global__ void __launch_bounds__(kBlock) k_grad_hess_proj(DevProblem P, ProjC q
             const ContrastTerms ct = contrast_terms(P, c, a, relax(P.tr[c], r1), dl, mm, bp, bm);
             accumulate_contrast<K, PRE, XT>(P, c, ct, r2, x + m, M, G, H, nll_v);
         }
+        float o[GS::S];
 #pragma unroll
-        for (int t = 0; t < K; ++t) gc[t * M + m] = G[t];
+        for (int t = 0; t < K; ++t) o[t] = G[t];
 #pragma unroll
-        for (int t = 0; t < T; ++t) hc[t * M + m] = H[t];
+        for (int t = 0; t < T; ++t) o[K + t] = H[t];
+#pragma unroll
+        for (int t = K + T; t < GS::S; ++t) o[t] = 0.0f;
+#pragma unroll
+        for (int v = 0; v < GS::V; ++v)
+            stage[wp][lane * GS::V + v] = make_float4(o[4 * v], o[4 * v + 1], o[4 * v + 2], o[4 * v + 3]);
+        __syncwarp();
+        const long long end = M * GS::V;                 // float4 entries of the buffer
+#pragma unroll
+        for (int v = 0; v < GS::V; ++v) {
+            const long long e = m0 * GS::V + v * 32 + lane;
+            if (e < end) gh[e] = stage[wp][v * 32 + lane];
+        }
+        __syncwarp();
         nll_acc.add(nll_v);
     }
     Acc v[1] = {nll_acc};
@@ -222,13 +255,20 @@ __global__ void __launch_bounds__(kBlock) k_grad_hess_proj(DevProblem P, ProjC q
     if (grid_reduce<1>(v, red, out) && threadIdx.x == 0) *nll = out[0];
 }
 
+__device__ __forceinline__ float lane4(const float4& e, int u)
+{
+    return u == 0 ? e.x : u == 1 ? e.y : u == 2 ? e.z : e.w;
+}
+
 // g = sum_c Psi_c' g_c, h = sum_c Psi_c' H_c; nll = sum_c nll_c (fixed order).
 template <int K>
-__global__ void __launch_bounds__(kBlock) k_push_all(DevProblem P, DevProj Q, ProjBufs B,
+__global__ void __launch_bounds__(kBlock, 4) k_push_all(DevProblem P, DevProj Q, ProjBufs B,
                                                      float* __restrict__ g, float* __restrict__ h,
                                                      const double* nll_parts, double* nll)
 {
+    using GS = GhStride<K>;
     constexpr int T = K * (K + 1) / 2;
+    constexpr int CH = K + T;                     // channels: g, then the packed H
     const long long N = P.N;
     const long long sxy = (long long)P.nx * P.ny;
     if (blockIdx.x == 0 && threadIdx.x == 0 && nll) {
@@ -239,31 +279,30 @@ __global__ void __launch_bounds__(kBlock) k_push_all(DevProblem P, DevProj Q, Pr
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
          n += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(n % P.nx), y = (int)((n / P.nx) % P.ny), z = (int)(n / sxy);
-        float G[K], H[T];
+        float A[CH];
 #pragma unroll
-        for (int t = 0; t < K; ++t) G[t] = 0.0f;
-#pragma unroll
-        for (int t = 0; t < T; ++t) H[t] = 0.0f;
+        for (int t = 0; t < CH; ++t) A[t] = 0.0f;
         // unrolled, so each contrast's affine is read as constant operands
 #pragma unroll
         for (int c = 0; c < MPM_MAX_CONTRASTS; ++c) {
             if (c >= Q.C) break;
             const ProjC& q = Q.c[c];
-            const long long M = q.M;
-            const float* __restrict__ gs = B.gc[c];
-            const float* __restrict__ hs = B.hc[c];
+            const float4* __restrict__ src = B.gh[c];
             auto add = [&](float w, long long m) {
 #pragma unroll
-                for (int t = 0; t < K; ++t) G[t] = fmaf(w, __ldg(gs + t * M + m), G[t]);
+                for (int v = 0; v < GS::V; ++v) {
+                    const float4 e = __ldg(src + m * GS::V + v);
 #pragma unroll
-                for (int t = 0; t < T; ++t) H[t] = fmaf(w, __ldg(hs + t * M + m), H[t]);
+                    for (int u = 0; u < 4; ++u)
+                        if (4 * v + u < CH) A[4 * v + u] = fmaf(w, lane4(e, u), A[4 * v + u]);
+                }
             };
             gather_pullers(q, x, y, z, P.nx, P.ny, P.nz, add);
         }
 #pragma unroll
-        for (int t = 0; t < K; ++t) g[t * N + n] = G[t];
+        for (int t = 0; t < K; ++t) g[t * N + n] = A[t];
 #pragma unroll
-        for (int t = 0; t < T; ++t) h[t * N + n] = H[t];
+        for (int t = 0; t < T; ++t) h[t * N + n] = A[K + t];
     }
 }
 
@@ -372,8 +411,7 @@ static mpm_status make_proj(const mpm_problem* p, const mpm_projection* proj, De
 struct ProjWs {
     FitWs L;
     double* nll_parts;
-    float* gc[MPM_MAX_CONTRASTS];
-    float* hc[MPM_MAX_CONTRASTS];
+    float4* gh[MPM_MAX_CONTRASTS];
     size_t total;
 };
 
@@ -391,8 +429,7 @@ static ProjWs proj_layout(const DevProblem& P, const DevProj& Q, int call, void*
     };
     W.nll_parts = reinterpret_cast<double*>(take(sizeof(double) * MPM_MAX_CONTRASTS));
     for (int c = 0; c < Q.C; ++c) {
-        W.gc[c] = reinterpret_cast<float*>(take(sizeof(float) * (size_t)P.K * Q.c[c].M));
-        W.hc[c] = reinterpret_cast<float*>(take(sizeof(float) * (size_t)P.T * Q.c[c].M));
+        W.gh[c] = reinterpret_cast<float4*>(take(sizeof(float) * (size_t)gh_floats(P.K) * Q.c[c].M));
     }
     W.total = off;
     return W;
@@ -409,19 +446,18 @@ static cudaError_t grad_hess_proj_k(const DevProblem& P, const DevProj& Q, const
         if (in.echo_dtype == 1)
             k_grad_hess_proj<K, PRE, __nv_bfloat16><<<grid, kBlock, 0, st>>>(
                 P, Q.c[c], c, y, static_cast<const __nv_bfloat16*>(in.x[c]), in.b1p[c], in.b1m[c],
-                W.gc[c], W.hc[c], W.nll_parts + c, red);
+                W.gh[c], W.nll_parts + c, red);
         else
             k_grad_hess_proj<K, PRE, float><<<grid, kBlock, 0, st>>>(
                 P, Q.c[c], c, y, static_cast<const float*>(in.x[c]), in.b1p[c], in.b1m[c],
-                W.gc[c], W.hc[c], W.nll_parts + c, red);
+                W.gh[c], W.nll_parts + c, red);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     ProjBufs B;
     memset(&B, 0, sizeof B);
     for (int c = 0; c < Q.C; ++c) {
-        B.gc[c] = W.gc[c];
-        B.hc[c] = W.hc[c];
+        B.gh[c] = W.gh[c];
     }
     LaunchScope ls(MPM_KERNEL_RESLICE, st);
     k_push_all<K><<<voxel_grid(P.N), kBlock, 0, st>>>(P, Q, B, g, h, W.nll_parts, nll);
