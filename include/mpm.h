@@ -28,12 +28,14 @@
  *    Host pointers are rejected with MPM_ERR_INVALID_ARG.
  *  - Device scalars (nll, jtv) are caller-owned device doubles, overwritten.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
- *    stream).  Every call except mpm_fit and mpm_workspace_size only enqueues
- *    work on it and returns without synchronising.
+ *    stream).  The fits (mpm_fit, mpm_fit_batch, mpm_fit_proj), mpm_autotune
+ *    and the server calls synchronise as their comments say; every other call
+ *    only enqueues work on it and returns without synchronising.
  *  - Scratch memory: calls that need it take a caller-owned device workspace
  *    (ws, ws_bytes) of at least mpm_workspace_size() bytes.  The library
- *    itself allocates no device memory.  Two calls that run concurrently must
- *    not share a workspace.
+ *    allocates no device memory at run time (mpm_solve_static uses a fixed
+ *    array compiled into the library instead).  Two calls that run
+ *    concurrently must not share a workspace.
  *  - Errors: every call returns an mpm_status; argument errors are detected on
  *    the host before anything is enqueued.  Kernels never trap: numeric
  *    failures (a preconditioner block that is not positive definite, a NaN in
@@ -64,7 +66,9 @@ enum {
     MPM_ERR_WORKSPACE_TOO_SMALL = -2,
     MPM_ERR_CUDA = -3,
     MPM_ERR_NUMERIC = -4,
-    MPM_ERR_TIMEOUT = -5              /* reserved: no call spins on the device */
+    MPM_ERR_TIMEOUT = -5              /* reserved; a bounded copy wait that runs out
+                                         inside a kernel is reported as
+                                         MPM_ERR_NUMERIC (see mpm_workspace_status) */
 };
 
 /* Which call a workspace is sized for (mpm_workspace_size). */
@@ -340,8 +344,10 @@ mpm_status mpm_server_poll(mpm_server* server, int ticket, int* state, mpm_statu
 mpm_status mpm_server_destroy(mpm_server* server);
 
 /* Synchronises `stream` and returns MPM_ERR_NUMERIC if a kernel that used this
- * workspace recorded a numeric failure since the workspace was last cleared
- * (every mpm_solve / mpm_fit clears it), else MPM_OK. */
+ * workspace recorded a failure since the workspace was last cleared (every
+ * mpm_solve / mpm_fit clears it): a preconditioner block that is not positive
+ * definite, a NaN in a reduction, or a bounded copy wait of the stencil matvec
+ * that ran out (mpm_last_error() names which).  Otherwise MPM_OK. */
 mpm_status mpm_workspace_status(const void* ws, size_t ws_bytes, void* stream);
 
 /* Diagnostic: number of kernels this library has launched in this process. */

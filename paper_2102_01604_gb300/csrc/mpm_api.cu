@@ -913,9 +913,10 @@ mpm_status mpm_workspace_status(const void* ws, size_t ws_bytes, void* stream)
     unsigned status = 0;
     MPM_CUDA(cudaMemcpyAsync(&status, ws, sizeof status, cudaMemcpyDeviceToHost, st));
     MPM_CUDA(cudaStreamSynchronize(st));
-    if (status) return fail(MPM_ERR_NUMERIC, "device status 0x%x (%s%s)", status,
+    if (status) return fail(MPM_ERR_NUMERIC, "device status 0x%x (%s%s%s)", status,
                             status & kStatusNotPD ? "non positive definite block " : "",
-                            status & kStatusNaN ? "NaN in a reduction" : "");
+                            status & kStatusNaN ? "NaN in a reduction " : "",
+                            status & kStatusTimeout ? "copy wait timed out" : "");
     return MPM_OK;
 }
 
