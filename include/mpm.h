@@ -304,10 +304,15 @@ mpm_status mpm_fit_proj(const mpm_problem* problem, const mpm_projection* proj,
  * subject at a time).  The server owns no device memory: every admitted
  * request's fit workspace is carved from `arena` (caller-owned device memory,
  * 256-byte aligned), so admission follows the free HBM the caller hands over.
- * Requests are admitted while one of `max_slots` slots is free and their
- * workspace fits, smallest volume first (ties by arrival; when the smallest
- * does not fit, the first in arrival order that does); a request overtaken by
- * 2 x max_slots later ones goes before all others, so none starves.  An
+ * Requests are admitted while one of `max_slots` slots is free, their
+ * workspace fits and the GPU load allows: a request's load is
+ * min(1, voxels / 2^21) (about 2^21 voxels keep every kernel of a fit at a full
+ * wave) and the active requests' loads may sum to at most 1.5, so one large
+ * fit runs with small ones beside it but never two large fits at once.  Among
+ * those, the smallest volume goes first (ties by arrival; when the smallest
+ * does not fit the arena, the first in arrival order that does); a request
+ * overtaken by 2 x max_slots later ones goes before all others, so none
+ * starves.  An
  * active request keeps its maps, weights, gradient, Hessian and PCG state
  * resident in the arena until it is done.  The server creates CUDA streams of its own (per slot, one for each
  * stream priority level of the device) and pinned host staging per slot;

@@ -29,6 +29,10 @@
 
 namespace mpm {
 
+// Share of the GPU one fit keeps busy (see the admission rule).
+constexpr double kMaxLoad = 1.5;
+inline double gpu_load(long long n_vox) { return n_vox >= (1LL << 21) ? 1.0 : (double)n_vox / (1LL << 21); }
+
 enum ReqState { kQueued = 0, kActive = 1, kDone = 2, kFailed = 3 };
 enum Phase { kInit = 0, kEval = 1, kFinish = 2 };
 
@@ -329,36 +333,50 @@ mpm_status mpm_server_step(mpm_server* s, int* n_active, int* n_queued, int* n_f
             ++finished;
         }
     }
-    // admission into free slots while the arena has room: smallest volume
-    // first (ties by arrival); a queued request overtaken by 2 x max_slots
-    // later ones is admitted before anything else, so none starves
+    // admission into free slots while the arena has room and the GPU load
+    // allows: smallest volume first (ties by arrival); a queued request
+    // overtaken by 2 x max_slots later ones is admitted before anything else,
+    // so none starves.  A request's load is min(1, N / 2^21): about 2^21
+    // voxels keep every kernel of a fit at a full wave, so two such fits side
+    // by side only interleave their kernels; requests are admitted while the
+    // active load stays <= 1.5 (one large fit and small ones beside it).
+    double load = 0.0;
+    for (int k = 0; k < s->max_slots; ++k)
+        if (s->slot_owner[k] >= 0) load += gpu_load(s->reqs[s->slot_owner[k]].P.N);
     while (!s->queue.empty()) {
         int k = 0;
         while (k < s->max_slots && s->slot_owner[k] >= 0) ++k;
         if (k == s->max_slots) break;
+        auto fits = [&](const Request& c) { return load == 0.0 || load + gpu_load(c.P.N) <= kMaxLoad; };
         auto pick = s->queue.end();
         bool urgent = false;
-        for (auto q = s->queue.begin(); q != s->queue.end(); ++q) {
-            const Request& c = s->reqs[*q];
-            if (c.overtaken >= 2 * s->max_slots) {
+        for (auto q = s->queue.begin(); q != s->queue.end(); ++q)
+            if (s->reqs[*q].overtaken >= 2 * s->max_slots) {
                 pick = q;
                 urgent = true;
                 break;
             }
-            if (pick == s->queue.end() || c.P.N < s->reqs[*pick].P.N) pick = q;
-        }
-        size_t off;
-        if (!s->arena.alloc(s->reqs[*pick].ws_bytes, &off)) {
-            if (urgent) break;                // it waits for room, nothing overtakes it
-            // the smallest does not fit: the first in arrival order that does
-            pick = s->queue.end();
+        size_t off = 0;
+        if (urgent) {
+            // it waits for load and room; nothing overtakes it
+            if (!fits(s->reqs[*pick]) || !s->arena.alloc(s->reqs[*pick].ws_bytes, &off)) break;
+        } else {
             for (auto q = s->queue.begin(); q != s->queue.end(); ++q)
-                if (s->arena.alloc(s->reqs[*q].ws_bytes, &off)) {
+                if (fits(s->reqs[*q]) && (pick == s->queue.end() || s->reqs[*q].P.N < s->reqs[*pick].P.N))
                     pick = q;
-                    break;
-                }
             if (pick == s->queue.end()) break;
+            if (!s->arena.alloc(s->reqs[*pick].ws_bytes, &off)) {
+                // the smallest does not fit the arena: the first in arrival order that does
+                pick = s->queue.end();
+                for (auto q = s->queue.begin(); q != s->queue.end(); ++q)
+                    if (fits(s->reqs[*q]) && s->arena.alloc(s->reqs[*q].ws_bytes, &off)) {
+                        pick = q;
+                        break;
+                    }
+                if (pick == s->queue.end()) break;
+            }
         }
+        load += gpu_load(s->reqs[*pick].P.N);
         Request& a = s->reqs[*pick];
         for (auto q = s->queue.begin(); q != pick; ++q) s->reqs[*q].overtaken += 1;
         s->queue.erase(pick);
