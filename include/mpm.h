@@ -236,8 +236,10 @@ mpm_status mpm_autotune(const mpm_problem* problem, const mpm_opts* opts, void* 
  * arrays themselves may be NULL), maps y[i], optional var_out[i] and
  * workspace ws[i] of ws_bytes[i]; opts and the report array (n entries, may
  * be NULL) are shared.  With tol_gn = 0 and opts->graph = 1 the updates of all
- * subjects are captured as parallel branches of one CUDA graph (cached per
- * argument set) so uneven volumes share the GPU in one graph launch;
+ * subjects are captured into one CUDA graph (cached per argument set) in two
+ * lanes: subjects of about 2^21 voxels or more one after another, the smaller
+ * ones one after another beside them, so uneven volumes share the GPU in one
+ * graph launch;
  * otherwise subjects run one after another.  Each subject's result equals its
  * mpm_fit result.  Synchronises `stream`.  1 <= n <= MPM_MAX_BATCH. */
 mpm_status mpm_fit_batch(int n, const mpm_problem* const* problems, const mpm_opts* opts,

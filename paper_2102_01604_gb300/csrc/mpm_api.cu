@@ -523,8 +523,12 @@ static std::string graph_key(const FitJob* jobs, int n)
 static mpm_status capture_updates(FitJob* jobs, int n, GraphEntry& out)
 {
     MPM_CUDA(prime_tma_kernels());
+    // Two lanes: subjects that fill the GPU on their own (gpu_load = 1) run one
+    // after another on the first; the smaller ones run, also one after
+    // another, on the second, beside them.  Side by side, two large fits only
+    // interleave their one-wave kernels.
     std::vector<cudaStream_t> ss;
-    MPM_CUDA(private_streams(n + 1, ss));
+    MPM_CUDA(private_streams(3, ss));
     cudaStream_t root = ss[0];
     cudaGraph_t graph = nullptr;
     std::vector<cudaEvent_t> evs;
@@ -539,17 +543,23 @@ static mpm_status capture_updates(FitJob* jobs, int n, GraphEntry& out)
     cudaError_t e = cudaStreamBeginCapture(root, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) e = cudaEventRecord(fork, root);
     out.iters.assign(n, 0);
-    for (int i = 0; i < n && e == cudaSuccess; ++i) {
-        if (jobs[i].empty) continue;
-        cudaStream_t b = ss[i + 1];
-        e = cudaStreamWaitEvent(b, fork, 0);
-        if (e == cudaSuccess) e = fit_enqueue_updates(jobs[i], b, &out.iters[i]);
-        cudaEvent_t join;
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
-        if (e == cudaSuccess) {
-            evs.push_back(join);
-            e = cudaEventRecord(join, b);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(root, join, 0);
+    bool used[2] = {false, false};
+    for (int lane = 0; lane < 2 && e == cudaSuccess; ++lane) {
+        cudaStream_t b = ss[1 + lane];
+        for (int i = 0; i < n && e == cudaSuccess; ++i) {
+            if (jobs[i].empty || (gpu_load(jobs[i].P.N) >= 1.0) != (lane == 0)) continue;
+            if (!used[lane]) e = cudaStreamWaitEvent(b, fork, 0);
+            used[lane] = true;
+            if (e == cudaSuccess) e = fit_enqueue_updates(jobs[i], b, &out.iters[i]);
+        }
+        if (used[lane] && e == cudaSuccess) {
+            cudaEvent_t join;
+            e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+            if (e == cudaSuccess) {
+                evs.push_back(join);
+                e = cudaEventRecord(join, b);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(root, join, 0);
+            }
         }
     }
     cudaError_t e2 = cudaStreamEndCapture(root, &graph);

@@ -29,9 +29,8 @@
 
 namespace mpm {
 
-// Share of the GPU one fit keeps busy (see the admission rule).
+// Active fits may keep at most this much of the GPU busy (see gpu_load).
 constexpr double kMaxLoad = 1.5;
-inline double gpu_load(long long n_vox) { return n_vox >= (1LL << 21) ? 1.0 : (double)n_vox / (1LL << 21); }
 
 enum ReqState { kQueued = 0, kActive = 1, kDone = 2, kFailed = 3 };
 enum Phase { kInit = 0, kEval = 1, kFinish = 2 };
