@@ -46,6 +46,11 @@ __device__ __forceinline__ void make_edges(const DevProblem& P, int x, int y, in
 
 // ------------------------------------------------------------- JTV weights
 
+// Each thread marches up its z range with the centre values of planes z - 1,
+// z and z + 1 in registers; the centre of plane z + 2 is loaded one plane
+// ahead, so the only far (next-plane) load is in flight while plane z is
+// computed.  The x / y neighbours come from the current plane (L1).  The six
+// terms are summed in the order x-, x+, y-, y+, z-, z+.
 template <int K>
 __global__ void __launch_bounds__(kBlock) k_jtv(DevProblem P, int zc, const float* __restrict__ y,
                                                 float* __restrict__ w, double* jtv, Reduce red)
@@ -57,30 +62,49 @@ __global__ void __launch_bounds__(kBlock) k_jtv(DevProblem P, int zc, const floa
     const int z0 = blockIdx.z * zc;
     const int z1 = min(P.nz, z0 + zc);
     Acc acc;
-    if (x < P.nx && yy < P.ny) {
-        const float ih[6] = {P.ihx2, P.ihx2, P.ihy2, P.ihy2, P.ihz2, P.ihz2};
+    if (x < P.nx && yy < P.ny && z0 < z1) {
+        const long long base = x + (long long)P.nx * yy;
+        const bool okx0 = x > 0, okx1 = x < P.nx - 1, oky0 = yy > 0, oky1 = yy < P.ny - 1;
+        float dn[K], cu[K], up[K], nx2[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const float* yk = y + k * N + base;
+            cu[k] = __ldg(yk + sxy * z0);
+            dn[k] = z0 > 0 ? __ldg(yk + sxy * (z0 - 1)) : 0.0f;
+            up[k] = z0 + 1 < P.nz ? __ldg(yk + sxy * (z0 + 1)) : 0.0f;
+        }
         for (int z = z0; z < z1; ++z) {
-            const long long n = x + (long long)P.nx * yy + sxy * z;
-            const long long off[6] = {-1, 1, -P.nx, P.nx, -sxy, sxy};
-            const bool ok[6] = {x > 0, x < P.nx - 1, yy > 0, yy < P.ny - 1, z > 0, z < P.nz - 1};
+            const long long n = base + sxy * z;
+            const bool okz0 = z > 0, okz1 = z < P.nz - 1;
+            // the centre two planes up, for the next step
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                nx2[k] = (z + 2 < P.nz && z + 1 < z1) ? __ldg(y + k * N + n + 2 * sxy) : 0.0f;
             float u = 0.0f;
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                const float* yk = y + k * N;
-                const float v = __ldg(yk + n);
+                const float* yk = y + k * N + n;
+                const float v = cu[k];
                 float s = 0.0f;
-#pragma unroll
-                for (int j = 0; j < 6; ++j)
-                    if (ok[j]) {
-                        const float d = __ldg(yk + n + off[j]) - v;
-                        s += d * d * ih[j];
-                    }
+                float d;
+                if (okx0) { d = __ldg(yk - 1) - v; s += d * d * P.ihx2; }
+                if (okx1) { d = __ldg(yk + 1) - v; s += d * d * P.ihx2; }
+                if (oky0) { d = __ldg(yk - P.nx) - v; s += d * d * P.ihy2; }
+                if (oky1) { d = __ldg(yk + P.nx) - v; s += d * d * P.ihy2; }
+                if (okz0) { d = dn[k] - v; s += d * d * P.ihz2; }
+                if (okz1) { d = up[k] - v; s += d * d * P.ihz2; }
                 u += P.lambda[k] * s;
             }
             const float val = u + P.eps2;
             const float sq = sqrtf(val);
             if (w) w[n] = 1.0f / sq;
             acc.add(sq);
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                dn[k] = cu[k];
+                cu[k] = up[k];
+                up[k] = nx2[k];
+            }
         }
     }
     Acc v[1] = {acc};
