@@ -236,9 +236,11 @@ mpm_status mpm_autotune(const mpm_problem* problem, const mpm_opts* opts, void* 
  * arrays themselves may be NULL), maps y[i], optional var_out[i] and
  * workspace ws[i] of ws_bytes[i]; opts and the report array (n entries, may
  * be NULL) are shared.  With tol_gn = 0 and opts->graph = 1 the updates of all
- * subjects are captured into one CUDA graph (cached per argument set) in two
- * lanes: subjects of about 2^21 voxels or more one after another, the smaller
- * ones one after another beside them, so uneven volumes share the GPU in one
+ * subjects are captured into one CUDA graph (cached per argument set) as
+ * lanes run side by side: subjects of about 2^21 voxels or more one after
+ * another in one lane, the smaller ones dealt over as many lanes as keep the
+ * load of the lanes running together within 1.5 (0.5 beside the large lane;
+ * a subject's load is voxels / 2^21), so uneven volumes share the GPU in one
  * graph launch;
  * otherwise subjects run one after another.  Each subject's result equals its
  * mpm_fit result.  Synchronises `stream`.  1 <= n <= MPM_MAX_BATCH. */

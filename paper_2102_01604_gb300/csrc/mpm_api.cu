@@ -1,6 +1,7 @@
 // mpm_api.cu -- the C ABI declared in include/mpm.h: argument checking,
 // workspace layout, constant initial maps and the host loop of the fit.
 #include <atomic>
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -523,12 +524,37 @@ static std::string graph_key(const FitJob* jobs, int n)
 static mpm_status capture_updates(FitJob* jobs, int n, GraphEntry& out)
 {
     MPM_CUDA(prime_tma_kernels());
-    // Two lanes: subjects that fill the GPU on their own (gpu_load = 1) run one
-    // after another on the first; the smaller ones run, also one after
-    // another, on the second, beside them.  Side by side, two large fits only
-    // interleave their one-wave kernels.
+    // Lanes of the graph, each a chain of subjects on one stream, all lanes
+    // side by side.  Subjects that fill the GPU on their own (gpu_load = 1)
+    // form one lane: side by side, two such fits only interleave their
+    // one-wave kernels.  The smaller subjects, largest first, are dealt
+    // round-robin to as many lanes as keep the load of the lanes running
+    // together within 1.5 (0.5 beside the large lane).
+    std::vector<int> large, small;
+    double max_small = 0.0;
+    for (int i = 0; i < n; ++i) {
+        if (jobs[i].empty) continue;
+        const double l = gpu_load(jobs[i].P.N);
+        if (l >= 1.0) {
+            large.push_back(i);
+        } else {
+            small.push_back(i);
+            max_small = std::max(max_small, l);
+        }
+    }
+    std::stable_sort(small.begin(), small.end(),
+                     [&](int a, int b) { return jobs[a].P.N > jobs[b].P.N; });
+    const double budget = large.empty() ? 1.5 : 0.5;
+    int n_small = small.empty() ? 0 : (int)std::floor(budget / max_small);
+    n_small = std::max(1, std::min(n_small, (int)small.size()));
+    std::vector<std::vector<int>> lanes;
+    if (!large.empty()) lanes.push_back(large);
+    for (int l = 0; l < n_small; ++l) lanes.emplace_back();
+    for (size_t k = 0; k < small.size(); ++k)
+        lanes[(large.empty() ? 0 : 1) + k % n_small].push_back(small[k]);
+
     std::vector<cudaStream_t> ss;
-    MPM_CUDA(private_streams(3, ss));
+    MPM_CUDA(private_streams((int)lanes.size() + 1, ss));
     cudaStream_t root = ss[0];
     cudaGraph_t graph = nullptr;
     std::vector<cudaEvent_t> evs;
@@ -543,23 +569,17 @@ static mpm_status capture_updates(FitJob* jobs, int n, GraphEntry& out)
     cudaError_t e = cudaStreamBeginCapture(root, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) e = cudaEventRecord(fork, root);
     out.iters.assign(n, 0);
-    bool used[2] = {false, false};
-    for (int lane = 0; lane < 2 && e == cudaSuccess; ++lane) {
-        cudaStream_t b = ss[1 + lane];
-        for (int i = 0; i < n && e == cudaSuccess; ++i) {
-            if (jobs[i].empty || (gpu_load(jobs[i].P.N) >= 1.0) != (lane == 0)) continue;
-            if (!used[lane]) e = cudaStreamWaitEvent(b, fork, 0);
-            used[lane] = true;
-            if (e == cudaSuccess) e = fit_enqueue_updates(jobs[i], b, &out.iters[i]);
-        }
-        if (used[lane] && e == cudaSuccess) {
-            cudaEvent_t join;
-            e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
-            if (e == cudaSuccess) {
-                evs.push_back(join);
-                e = cudaEventRecord(join, b);
-                if (e == cudaSuccess) e = cudaStreamWaitEvent(root, join, 0);
-            }
+    for (size_t l = 0; l < lanes.size() && e == cudaSuccess; ++l) {
+        cudaStream_t b = ss[1 + l];
+        e = cudaStreamWaitEvent(b, fork, 0);
+        for (size_t k = 0; k < lanes[l].size() && e == cudaSuccess; ++k)
+            e = fit_enqueue_updates(jobs[lanes[l][k]], b, &out.iters[lanes[l][k]]);
+        cudaEvent_t join;
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+        if (e == cudaSuccess) {
+            evs.push_back(join);
+            e = cudaEventRecord(join, b);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(root, join, 0);
         }
     }
     cudaError_t e2 = cudaStreamEndCapture(root, &graph);
