@@ -525,33 +525,16 @@ static mpm_status capture_updates(FitJob* jobs, int n, GraphEntry& out)
 {
     MPM_CUDA(prime_tma_kernels());
     // Lanes of the graph, each a chain of subjects on one stream, all lanes
-    // side by side.  Subjects that fill the GPU on their own (gpu_load = 1)
-    // form one lane: side by side, two such fits only interleave their
-    // one-wave kernels.  The smaller subjects, largest first, are dealt
-    // round-robin to as many lanes as keep the load of the lanes running
-    // together within 1.5 (0.5 beside the large lane).
-    std::vector<int> large, small;
-    double max_small = 0.0;
+    // side by side (lane_plan).  Subjects that fill the GPU on their own run
+    // in one lane: side by side, two such fits only interleave their one-wave
+    // kernels.
+    std::vector<long long> voxels(n);
+    std::vector<char> empty(n);
     for (int i = 0; i < n; ++i) {
-        if (jobs[i].empty) continue;
-        const double l = gpu_load(jobs[i].P.N);
-        if (l >= 1.0) {
-            large.push_back(i);
-        } else {
-            small.push_back(i);
-            max_small = std::max(max_small, l);
-        }
+        voxels[i] = jobs[i].P.N;
+        empty[i] = jobs[i].empty ? 1 : 0;
     }
-    std::stable_sort(small.begin(), small.end(),
-                     [&](int a, int b) { return jobs[a].P.N > jobs[b].P.N; });
-    const double budget = large.empty() ? 1.5 : 0.5;
-    int n_small = small.empty() ? 0 : (int)std::floor(budget / max_small);
-    n_small = std::max(1, std::min(n_small, (int)small.size()));
-    std::vector<std::vector<int>> lanes;
-    if (!large.empty()) lanes.push_back(large);
-    for (int l = 0; l < n_small; ++l) lanes.emplace_back();
-    for (size_t k = 0; k < small.size(); ++k)
-        lanes[(large.empty() ? 0 : 1) + k % n_small].push_back(small[k]);
+    const std::vector<std::vector<int>> lanes = lane_plan(voxels, empty);
 
     std::vector<cudaStream_t> ss;
     MPM_CUDA(private_streams((int)lanes.size() + 1, ss));

@@ -7,6 +7,7 @@
 #include <string>
 
 #include "device_common.cuh"
+#include "host_logic.h"
 
 namespace mpm {
 
@@ -16,13 +17,6 @@ struct StencilGrid {
     dim3 grid, block;
     int zc;           // z planes per block (TMA matvec: number of z ranges)
 };
-
-// Share of the GPU one fit keeps busy: about 2^21 voxels keep every kernel
-// of a fit at a full wave, so larger volumes count as 1, smaller ones pro rata.
-inline double gpu_load(long long n_vox)
-{
-    return n_vox >= (1LL << 21) ? 1.0 : (double)n_vox / (double)(1LL << 21);
-}
 
 StencilGrid stencil_grid(const DevProblem& P, int tile_x, int tile_y);
 int voxel_grid(long long N);

@@ -29,9 +29,6 @@
 
 namespace mpm {
 
-// Active fits may keep at most this much of the GPU busy (see gpu_load).
-constexpr double kMaxLoad = 1.5;
-
 enum ReqState { kQueued = 0, kActive = 1, kDone = 2, kFailed = 3 };
 enum Phase { kInit = 0, kEval = 1, kFinish = 2 };
 
@@ -65,56 +62,6 @@ struct SlotHost {
     double means[MPM_MAX_IMAGES];
     unsigned status;
     mpm_report report;
-};
-
-struct Arena {
-    char* base;
-    size_t bytes;
-    std::map<size_t, size_t> free_;   // offset -> size, coalesced
-
-    void init(void* b, size_t n)
-    {
-        base = static_cast<char*>(b);
-        bytes = n;
-        free_.clear();
-        free_[0] = n;
-    }
-    bool alloc(size_t n, size_t* off)
-    {
-        n = (n + 255) & ~(size_t)255;
-        for (auto it = free_.begin(); it != free_.end(); ++it)
-            if (it->second >= n) {
-                *off = it->first;
-                const size_t rest = it->second - n, at = it->first + n;
-                free_.erase(it);
-                if (rest) free_[at] = rest;
-                return true;
-            }
-        return false;
-    }
-    void release(size_t off, size_t n)
-    {
-        n = (n + 255) & ~(size_t)255;
-        auto it = free_.emplace(off, n).first;
-        auto nx = std::next(it);
-        if (nx != free_.end() && it->first + it->second == nx->first) {
-            it->second += nx->second;
-            free_.erase(nx);
-        }
-        if (it != free_.begin()) {
-            auto pv = std::prev(it);
-            if (pv->first + pv->second == it->first) {
-                pv->second += it->second;
-                free_.erase(it);
-            }
-        }
-    }
-    size_t largest() const
-    {
-        size_t m = 0;
-        for (auto& f : free_) m = f.second > m ? f.second : m;
-        return m;
-    }
 };
 
 }  // namespace mpm
@@ -332,8 +279,8 @@ mpm_status mpm_server_step(mpm_server* s, int* n_active, int* n_queued, int* n_f
             ++finished;
         }
     }
-    // admission into free slots while the arena has room and the GPU load
-    // allows: smallest volume first (ties by arrival); a queued request
+    // admission into free slots (admit_pick) while the arena has room and the
+    // GPU load allows: smallest volume first (ties by arrival); a queued request
     // overtaken by 2 x max_slots later ones is admitted before anything else,
     // so none starves.  A request's load is min(1, N / 2^21): about 2^21
     // voxels keep every kernel of a fit at a full wave, so two such fits side
@@ -342,39 +289,20 @@ mpm_status mpm_server_step(mpm_server* s, int* n_active, int* n_queued, int* n_f
     double load = 0.0;
     for (int k = 0; k < s->max_slots; ++k)
         if (s->slot_owner[k] >= 0) load += gpu_load(s->reqs[s->slot_owner[k]].P.N);
+    std::vector<Queued> view;
     while (!s->queue.empty()) {
         int k = 0;
         while (k < s->max_slots && s->slot_owner[k] >= 0) ++k;
         if (k == s->max_slots) break;
-        auto fits = [&](const Request& c) { return load == 0.0 || load + gpu_load(c.P.N) <= kMaxLoad; };
-        auto pick = s->queue.end();
-        bool urgent = false;
-        for (auto q = s->queue.begin(); q != s->queue.end(); ++q)
-            if (s->reqs[*q].overtaken >= 2 * s->max_slots) {
-                pick = q;
-                urgent = true;
-                break;
-            }
-        size_t off = 0;
-        if (urgent) {
-            // it waits for load and room; nothing overtakes it
-            if (!fits(s->reqs[*pick]) || !s->arena.alloc(s->reqs[*pick].ws_bytes, &off)) break;
-        } else {
-            for (auto q = s->queue.begin(); q != s->queue.end(); ++q)
-                if (fits(s->reqs[*q]) && (pick == s->queue.end() || s->reqs[*q].P.N < s->reqs[*pick].P.N))
-                    pick = q;
-            if (pick == s->queue.end()) break;
-            if (!s->arena.alloc(s->reqs[*pick].ws_bytes, &off)) {
-                // the smallest does not fit the arena: the first in arrival order that does
-                pick = s->queue.end();
-                for (auto q = s->queue.begin(); q != s->queue.end(); ++q)
-                    if (fits(s->reqs[*q]) && s->arena.alloc(s->reqs[*q].ws_bytes, &off)) {
-                        pick = q;
-                        break;
-                    }
-                if (pick == s->queue.end()) break;
-            }
+        view.clear();
+        for (int t : s->queue) {
+            const Request& c = s->reqs[t];
+            view.push_back({c.P.N, c.ws_bytes, c.overtaken});
         }
+        size_t off = 0;
+        const int pi = admit_pick(view, load, s->max_slots, s->arena, &off);
+        if (pi < 0) break;
+        auto pick = s->queue.begin() + pi;
         load += gpu_load(s->reqs[*pick].P.N);
         Request& a = s->reqs[*pick];
         for (auto q = s->queue.begin(); q != pick; ++q) s->reqs[*q].overtaken += 1;

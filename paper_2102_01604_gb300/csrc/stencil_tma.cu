@@ -481,26 +481,13 @@ static int tma_wave(const DevProblem& P, int tile)
 }
 
 // One wave of resident blocks over tiles x nchunk items (StencilGrid::zc
-// carries nchunk).  nchunk minimises rounds x (planes per item + 2): the
-// last round should leave few slots idle, items should be long enough that
-// the two halo planes per item and the ring's start-up stay small.
+// carries nchunk, chosen by tma_chunks).
 StencilGrid tma_grid(const DevProblem& P, int tile)
 {
     const int TX = kTileShapes[tile][0], TY = kTileShapes[tile][1];
     const long long T = (long long)((P.nx + TX - 1) / TX) * ((P.ny + TY - 1) / TY);
     const long long W = tma_wave(P, tile);
-    int best = 1;
-    long long best_cost = -1;
-    for (int c = 1; c <= P.nz; ++c) {
-        const long long per = (P.nz + c - 1) / c;
-        if (per < 4 && c > 1) break;
-        const long long rounds = (T * c + W - 1) / W;
-        const long long cost = rounds * (per + 2);
-        if (best_cost < 0 || cost < best_cost) {
-            best_cost = cost;
-            best = c;
-        }
-    }
+    const int best = tma_chunks(T, P.nz, W);
     StencilGrid g;
     g.grid = dim3((unsigned)std::min<long long>(T * best, W), 1, 1);
     g.block = dim3(kTmaThreads, 1, 1);
