@@ -1,7 +1,8 @@
 """Parity of every C-ABI call against the FP64 oracle, element by element, on
 seeded inputs spanning several stencil tiles and ragged tails.
 
-Tolerances (derived in the design doc from float32 arithmetic):
+Tolerances, from float32 rounding (2^-24 relative per operation) grown over
+the sums and solves each output goes through:
   forward, gradient, Hessian   1e-4 x (|ref| + rms of the row)
   likelihood, JTV energy       2e-6 relative
   JTV weights                  1e-5 relative

@@ -4,7 +4,7 @@
 The GPU fit is compared per map with the FP64 oracle run on the float32
 images, so the bfloat16 error includes the rounding of the data itself.  The
 float32 fit must meet the parity bound (1e-3 x max(1, |y|) in log space);
-for bfloat16 storage the error is reported per map and checked
+for bfloat16 storage the error is printed per map and checked
 against a bound well below the noise-driven map error (the images' rounding
 is 2^-9 relative, the noise 1/SNR = 5%).
 """
