@@ -209,6 +209,11 @@ __global__ void __launch_bounds__(kBlock) k_grad_hess_proj(DevProblem P, ProjC q
         const long long m0 = it * stride + blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31);
         const long long m = m0 + lane;
         const bool live = m < M;
+        if (m + stride < M) {   // the next trip's echoes and B1 values into L2
+            for (int e = 0; e < P.n_echoes[c]; ++e) prefetch_l2(x + e * M + m + stride);
+            if (b1p) prefetch_l2(b1p + m + stride);
+            if (b1m) prefetch_l2(b1m + m + stride);
+        }
         const int i = (int)(m % q.mx), j = (int)((m / q.mx) % q.my), k = (int)(m / sxy);
         float G[K], H[T];
 #pragma unroll

@@ -38,9 +38,24 @@ __global__ void __launch_bounds__(kBlock) k_forward(DevProblem P, const float* _
 
 // ------------------------------------------------------ fused voxel pass
 
+// Hint voxel n (the next one of this thread's grid-stride loop, n < N) into
+// L2: its echoes, maps and B1 values, so that their DRAM latency overlaps the
+// arithmetic of the current voxel.
+template <typename XT>
+__device__ __forceinline__ void prefetch_voxel(const DevProblem& P, const XT* x, const float* y,
+                                               const float* b1p, const float* b1m, long long n)
+{
+    const long long N = P.N;
+    for (int i = 0; i < P.I; ++i) prefetch_l2(x + i * N + n);
+    for (int k = 0; k < P.K; ++k) prefetch_l2(y + k * N + n);
+    if (b1p) prefetch_l2(b1p + n);
+    if (b1m)
+        for (int c = 0; c < P.C; ++c) prefetch_l2(b1m + c * N + n);
+}
+
 // The fused voxel pass: per voxel, accumulate_contrast for every contrast.
 template <int K, int PRE, typename XT>
-__global__ void __launch_bounds__(kBlock) k_grad_hess(DevProblem P, const XT* __restrict__ x,
+__global__ void __launch_bounds__(kBlock, 4) k_grad_hess(DevProblem P, const XT* __restrict__ x,
                                                       const float* __restrict__ y,
                                                       const float* __restrict__ b1p,
                                                       const float* __restrict__ b1m,
@@ -53,6 +68,8 @@ __global__ void __launch_bounds__(kBlock) k_grad_hess(DevProblem P, const XT* __
     Acc nll_acc;
     for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
          n += (long long)gridDim.x * blockDim.x) {
+        const long long next = n + (long long)gridDim.x * blockDim.x;
+        if (next < N) prefetch_voxel<XT>(P, x, y, b1p, b1m, next);
         float a, r1, r2, dl, m;
         map_params(y, N, n, K, a, r1, r2, dl, m);
         const float bp = b1p ? __ldg(b1p + n) : 1.0f;

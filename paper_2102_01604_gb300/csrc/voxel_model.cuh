@@ -8,6 +8,13 @@
 
 namespace mpm {
 
+// Hint the line holding p into L2 (the voxel passes fetch their next voxel's
+// operands this way while they compute the current one).
+__device__ __forceinline__ void prefetch_l2(const void* p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // Per-contrast factors shared by every echo of contrast c in one voxel.  With
 // q_k = (ds/dy_k) / s  (Eqs. 27-30):
 //   q_A = 1, q_R1 = q1, q_R2* = -TE r2 (echo dependent), q_delta = qd,
@@ -107,37 +114,16 @@ __device__ __forceinline__ void map_params_v(const float* yv, int K, float& a, f
 // give, with v = (1, q1, 0, qd) and e2 the log R2* axis,
 //   g += (R0 v + R1 e2) / sigma^2
 //   P += (S0 v v' + S1 (v e2' + e2 v') + S2 e2 e2' + loading) / sigma^2
-// which is Eq. 24 summed over the echoes of the contrast.  xp points at the first echo of contrast c in this voxel; echo e is at
-// xp[e * stride].
-template <int K, int PRE, typename XT>
-__device__ __forceinline__ void accumulate_contrast(const DevProblem& P, int c,
-                                                    const ContrastTerms& t, float r2,
-                                                    const XT* xp, long long stride,
-                                                    float (&G)[K], float (&H)[K * (K + 1) / 2],
-                                                    float& nll_v)
-{
+// which is Eq. 24 summed over the echoes of the contrast.  xp points at the
+// first echo of contrast c in this voxel; echo e is at xp[e * stride].
+template <int PRE>
+struct EchoSums {
     float S0 = 0.f, S1 = 0.f, S2 = 0.f, R0 = 0.f, R1 = 0.f, N2 = 0.f;
     float A0 = 0.f, A2 = 0.f, B1 = 0.f;
-    const int i0 = P.echo0[c];
-    const int ne = P.n_echoes[c];
-    // equally spaced echoes: s_e = s_0 exp(-TE_0 r2) rho^e, rho = exp(-dTE r2)
-    const bool uni = P.te_uniform[c] != 0;
-    const float dq = -P.dte[c] * r2;
-    const float rho = uni ? expf(dq) : 0.0f;
-    float q2 = -P.te[i0] * r2;
-    float s = t.s0 * expf(q2);
-    for (int e = 0; e < ne; ++e) {
-        if (e > 0) {
-            if (uni) {
-                q2 += dq;
-                s *= rho;
-            } else {
-                q2 = -P.te[i0 + e] * r2;
-                s = t.s0 * expf(q2);
-            }
-        }
-        const float r = s - load_echo<XT>(xp, 0);
-        xp += stride;
+    // one echo: signal s, q2 = -TE r2, measured value xv
+    __device__ __forceinline__ void add(float s, float q2, float xv)
+    {
+        const float r = s - xv;
         const float ss = s * s;
         S0 += ss;
         S1 += ss * q2;
@@ -153,6 +139,40 @@ __device__ __forceinline__ void accumulate_contrast(const DevProblem& P, int c,
             if (PRE == 1) B1 += ars * fabsf(q2);
         }
     }
+};
+
+template <int K, int PRE, typename XT>
+__device__ __forceinline__ void accumulate_contrast(const DevProblem& P, int c,
+                                                    const ContrastTerms& t, float r2,
+                                                    const XT* xp, long long stride,
+                                                    float (&G)[K], float (&H)[K * (K + 1) / 2],
+                                                    float& nll_v)
+{
+    EchoSums<PRE> es;
+    const int i0 = P.echo0[c];
+    const int ne = P.n_echoes[c];
+    float q2 = -P.te[i0] * r2;
+    float s = t.s0 * expf(q2);
+    if (P.te_uniform[c] != 0) {
+        // equally spaced echoes: s_e = s_0 exp(-TE_0 r2) rho^e, rho = exp(-dTE r2)
+        const float dq = -P.dte[c] * r2;
+        const float rho = expf(dq);
+#pragma unroll 4
+        for (int e = 0; e < ne; ++e) {
+            es.add(s, q2, load_echo<XT>(xp, e * stride));
+            q2 += dq;
+            s *= rho;
+        }
+    } else {
+        es.add(s, q2, load_echo<XT>(xp, 0));
+#pragma unroll 4
+        for (int e = 1; e < ne; ++e) {
+            q2 = -P.te[i0 + e] * r2;
+            es.add(t.s0 * expf(q2), q2, load_echo<XT>(xp, e * stride));
+        }
+    }
+    const float S0 = es.S0, S1 = es.S1, S2 = es.S2, R0 = es.R0, R1 = es.R1, N2 = es.N2;
+    const float A0 = es.A0, A2 = es.A2, B1 = es.B1;
     const float is2 = P.isig2[c];
     const float q1 = t.q1, qd = t.qd;
     G[0] += is2 * R0;
