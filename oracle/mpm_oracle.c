@@ -36,9 +36,13 @@
  *   orc_fit           exact recovery from noise-free data (no prior); the
  *                     likelihood never increases over 1000 simulated voxels
  *                     (Sec. 3.1 protocol); the objective decreases under the
- *                     JTV majorise-minimise loop with accurate inner solves.
- *   The full prior-regularised fit after a fixed iteration count has no value
- *   printed in the paper: beyond the pins of its parts it is "parity
+ *                     JTV majorise-minimise loop with accurate inner solves;
+ *                     with the prior, constant noise-free maps are recovered
+ *                     from a perturbed start with F = N eps (the closed-form
+ *                     optimum); the fit commutes with mirroring any axis and
+ *                     with swapping x and y together with their voxel sizes.
+ *   The prior-regularised fit of noisy data after a fixed iteration count has
+ *   no value printed in the paper: beyond the pins above it is "parity
  *   unpinned".
  */
 #include "mpm_oracle.h"

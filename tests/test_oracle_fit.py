@@ -1,6 +1,8 @@
 """Pins of the oracle's fit: initial maps, exact recovery, the step-size
 condition of the proposed preconditioner, the convergence experiment of
-Sec. 3.1 / 4.1, and the JTV majorise-minimise loop (Sec. 2.5-2.7)."""
+Sec. 3.1 / 4.1, the JTV majorise-minimise loop (Sec. 2.5-2.7), the closed-form
+optimum of the regularised fit on constant noise-free maps, and the fit's
+equivariance under mirroring and axis swaps."""
 import math
 
 import numpy as np
@@ -178,3 +180,81 @@ def test_gain_tolerance_stops_early(orc):
     F = r["F"]
     assert abs(F[k - 1] - F[k]) < 1e-4 * abs(F[k - 1])
     assert all(abs(F[i - 1] - F[i]) >= 1e-4 * abs(F[i - 1]) for i in range(1, k))
+
+
+def _constant_truth(orc, shape, seed):
+    """Constant maps (one phantom voxel's values everywhere) imaged through
+    spatially varying B1 fields, without noise."""
+    N = int(np.prod(shape))
+    prot = phantom.protocol()
+    ph = phantom.phantom(shape, seed=seed)
+    truth = np.tile(ph["y"][:, :1], (1, N))
+    s = orc.forward(orc.make_problem(prot, shape), truth, ph["b1p"], ph["b1m"])
+    prot["sigma2"] = phantom.noise_sigma2(s, prot)
+    return prot, truth, s, ph["b1p"], ph["b1m"]
+
+
+def test_map_fit_reaches_the_closed_form_optimum(orc):
+    """With constant true maps and noise-free data, NLL = 0 and JTV_eps =
+    sum_n sqrt(0 + eps^2) = N eps are both at their minimum at the truth, so
+    the regularised objective's optimum is the truth with F* = N eps (Eqs.
+    38-40).  Started from a random perturbation, the fit must get there: with
+    accurate inner solves to rounding, with the fixed 30-iteration PCG closely."""
+    shape = (6, 5, 4)
+    N, eps = int(np.prod(shape)), 1e-3
+    prot, truth, s, b1p, b1m = _constant_truth(orc, shape, seed=2)
+    p = orc.make_problem(prot, shape, lam=10.0, eps=eps)
+    y0 = truth + np.random.default_rng(7).uniform(-0.1, 0.1, truth.shape)
+    r = orc.fit(p, s, y0, b1p, b1m, gn_iters=30, cg_iters=300, tol_cg=1e-12)
+    assert np.abs(r["y"] - truth).max() < 1e-10
+    assert abs(r["F"][-1] - N * eps) < 1e-12 * N * eps
+    assert r["nll"][-1] < 1e-20
+    assert np.all(np.diff(r["F"]) <= 1e-12 * r["F"][0])
+    r = orc.fit(p, s, y0, b1p, b1m, gn_iters=20, cg_iters=30)
+    assert np.abs(r["y"] - truth).max() < 1e-3
+    assert abs(r["F"][-1] - N * eps) < 1e-4 * N * eps
+
+
+def _vol(a, shape):
+    nx, ny, nz = shape
+    return a.reshape(a.shape[:-1] + (nz, ny, nx))
+
+
+def _flat(v):
+    return np.ascontiguousarray(v).reshape(v.shape[:-3] + (-1,))
+
+
+@pytest.mark.parametrize("axis", [-1, -2, -3])
+def test_map_fit_commutes_with_mirroring(orc, axis):
+    """Neumann boundaries and the symmetric 6-neighbour stencil make the fit
+    equivariant under mirroring any axis: fit(mirror(data)) = mirror(fit(data))
+    to rounding.  An asymmetric stencil or boundary breaks it."""
+    shape = (7, 5, 4)
+    prot, ph, b1p, b1m, x = _data(orc, shape, 4)
+    p = orc.make_problem(prot, shape, vx=(1.0, 1.3, 0.8), lam=10.0, eps=1e-3)
+    m = lambda a: _flat(np.flip(_vol(a, shape), axis=axis))
+    r = orc.fit(p, x, None, b1p, b1m, gn_iters=8, cg_iters=30)
+    rm = orc.fit(p, m(x), None, m(b1p), m(b1m), gn_iters=8, cg_iters=30)
+    assert np.abs(m(r["y"]) - rm["y"]).max() < 1e-10
+    assert np.abs(r["F"] - rm["F"]).max() < 1e-12 * r["F"][-1]
+
+
+def test_map_fit_commutes_with_swapping_axes(orc):
+    """Swapping the x and y axes of the data together with their voxel sizes
+    swaps the fitted maps (Eq. 38 weighs each axis by its own voxel size).
+    Swapping the data alone must not: that control shows the test sees an
+    axis mix-up of the voxel sizes."""
+    shape = (7, 5, 4)
+    vx = (1.0, 1.3, 0.8)
+    prot, ph, b1p, b1m, x = _data(orc, shape, 4)
+    sw = lambda a: _flat(np.swapaxes(_vol(a, shape), -1, -2))
+    r = orc.fit(orc.make_problem(prot, shape, vx=vx, lam=10.0, eps=1e-3), x, None, b1p, b1m,
+                gn_iters=8, cg_iters=30)
+    shape_t = (shape[1], shape[0], shape[2])
+    rt = orc.fit(orc.make_problem(prot, shape_t, vx=(vx[1], vx[0], vx[2]), lam=10.0, eps=1e-3),
+                 sw(x), None, sw(b1p), sw(b1m), gn_iters=8, cg_iters=30)
+    assert np.abs(sw(r["y"]) - rt["y"]).max() < 1e-10
+    assert np.abs(r["F"] - rt["F"]).max() < 1e-12 * r["F"][-1]
+    rw = orc.fit(orc.make_problem(prot, shape_t, vx=vx, lam=10.0, eps=1e-3),
+                 sw(x), None, sw(b1p), sw(b1m), gn_iters=8, cg_iters=30)
+    assert np.abs(sw(r["y"]) - rw["y"]).max() > 1e-3
