@@ -510,8 +510,17 @@ static std::string graph_key(const FitJob* jobs, int n)
     std::string k(reinterpret_cast<const char*>(&dev), sizeof dev);
     for (int i = 0; i < n; ++i) {
         const FitJob& j = jobs[i];
-        k.append(reinterpret_cast<const char*>(j.problem), sizeof(mpm_problem));
-        k.append(reinterpret_cast<const char*>(&j.opts), sizeof(mpm_opts));
+        // The kernels' view of the problem (make_dev zero-fills it before
+        // setting its fields, so entries past n_contrasts or the image count
+        // do not split the cache as the caller's struct could), the echo
+        // type, the schedule field by field (mpm_opts has tail padding), and
+        // every pointer the launches use.
+        k.append(reinterpret_cast<const char*>(&j.P), sizeof(DevProblem));
+        const long long sched[6] = {j.problem->echo_dtype, j.opts.gn_iters, j.opts.cg_iters,
+                                    j.opts.newton_per_irls, j.opts.init, j.opts.graph};
+        const double tols[2] = {j.opts.tol_gn, j.opts.tol_cg};
+        k.append(reinterpret_cast<const char*>(sched), sizeof sched);
+        k.append(reinterpret_cast<const char*>(tols), sizeof tols);
         const void* ptrs[7] = {j.x, j.b1p, j.b1m, j.y, j.var, j.ws, (const void*)j.ws_bytes};
         k.append(reinterpret_cast<const char*>(ptrs), sizeof ptrs);
         k.push_back(j.proj ? 1 : 0);
