@@ -243,7 +243,8 @@ mpm_status mpm_autotune(const mpm_problem* problem, const mpm_opts* opts, void* 
  * a subject's load is voxels / 2^21), so uneven volumes share the GPU in one
  * graph launch;
  * otherwise subjects run one after another.  Each subject's result equals its
- * mpm_fit result.  Synchronises `stream`.  1 <= n <= MPM_MAX_BATCH. */
+ * mpm_fit result.  Synchronises `stream`.  0 <= n <= MPM_MAX_BATCH; n = 0
+ * returns MPM_OK at once, without touching any argument or the stream. */
 mpm_status mpm_fit_batch(int n, const mpm_problem* const* problems, const mpm_opts* opts,
                          const void* const* x, const float* const* b1p, const float* const* b1m,
                          float* const* y, float* const* var_out, void* const* ws,
@@ -316,10 +317,10 @@ mpm_status mpm_fit_proj(const mpm_problem* problem, const mpm_projection* proj,
  * those, the smallest volume goes first (ties by arrival; when the smallest
  * does not fit the arena, the first in arrival order that does); a request
  * overtaken by 2 x max_slots later ones goes before all others, so none
- * starves.  An
- * active request keeps its maps, weights, gradient, Hessian and PCG state
- * resident in the arena until it is done.  The server creates CUDA streams of its own (per slot, one for each
- * stream priority level of the device) and pinned host staging per slot;
+ * starves.  An active request keeps its maps, weights, gradient, Hessian and
+ * PCG state resident in the arena until it is done.  The server creates CUDA streams
+ * of its own (per slot, one for each stream priority level of the device) and
+ * pinned host staging per slot;
  * `stream` is the caller's stream on which the request inputs are produced
  * (each request waits for the state of that stream at its submission).
  *  - mpm_server_submit: queue one fit (same arguments as mpm_fit minus the
@@ -338,6 +339,10 @@ mpm_status mpm_fit_proj(const mpm_problem* problem, const mpm_projection* proj,
  *    queued and just-finished counts (any pointer may be NULL).
  *  - mpm_server_poll: state of a ticket (MPM_REQ_*), its final status and,
  *    once done, its report.
+ *  - mpm_server_destroy: waits for the work already enqueued on the server's
+ *    streams, then frees its streams, events and staging; requests not yet
+ *    done are dropped (their outputs are undefined).  NULL is a no-op that
+ *    returns MPM_OK.
  * A request's result equals mpm_fit's with the same arguments.  The server is
  * guarded by a mutex; calls from several threads are serialised. */
 enum { MPM_REQ_QUEUED = 0, MPM_REQ_ACTIVE = 1, MPM_REQ_DONE = 2, MPM_REQ_FAILED = 3 };

@@ -163,3 +163,67 @@ def test_projection_validation(lib):
                                 y.ctypes.data, y.ctypes.data, y.ctypes.data, None, 0, None)
     assert st == _lib.ERR_INVALID_ARG
     assert "x[0]" in lib.mpm_last_error().decode()
+
+
+def test_every_compute_call_refuses_host_memory_and_null_problems(lib):
+    """Each entry point that takes device arrays names the first host array it
+    is given, and a NULL problem, before it enqueues anything."""
+    import numpy as np
+    import paper_2102_01604_gb300 as mpm
+    shape = (8, 8, 4)
+    p = _problem(shape)
+    o = mpm.make_opts(gn_iters=2, cg_iters=4)
+    q = _eye_proj(mpm, shape)
+    N = 8 * 8 * 4
+    host = np.zeros(64 * N, dtype=np.float32)        # large enough for any array here
+    hp = host.ctypes.data
+    d = ctypes.c_double()
+    rep = _lib.Report()
+    arr = (ctypes.c_void_p * 3)(hp, hp, hp)
+    P, O, Q = ctypes.byref(p), ctypes.byref(o), ctypes.byref(q)
+    calls = {
+        "mpm_forward": lambda pp: lib.mpm_forward(pp, hp, None, None, hp, None),
+        "mpm_grad_hess": lambda pp: lib.mpm_grad_hess(pp, hp, hp, None, None, hp, hp,
+                                                      ctypes.addressof(d), hp, 1 << 20, None),
+        "mpm_jtv_weights": lambda pp: lib.mpm_jtv_weights(pp, hp, hp, ctypes.addressof(d), hp,
+                                                          1 << 20, None),
+        "mpm_solve": lambda pp: lib.mpm_solve(pp, O, hp, hp, hp, hp, hp, None, hp, 1 << 20, None),
+        "mpm_solve_static": lambda pp: lib.mpm_solve_static(pp, O, hp, hp, hp, hp, hp, None, None),
+        "mpm_uncertainty": lambda pp: lib.mpm_uncertainty(pp, hp, hp, hp, hp, None, None, None),
+        "mpm_fit": lambda pp: lib.mpm_fit(pp, O, hp, None, None, hp, None, hp, 1 << 20,
+                                          ctypes.byref(rep), None),
+        "mpm_pull": lambda pp: lib.mpm_pull(pp, Q, 0, 4, hp, hp, None),
+        "mpm_push": lambda pp: lib.mpm_push(pp, Q, 0, 4, hp, hp, 0, None),
+        "mpm_grad_hess_proj": lambda pp: lib.mpm_grad_hess_proj(pp, Q, arr, None, None, hp, hp,
+                                                                hp, ctypes.addressof(d), hp,
+                                                                1 << 20, None),
+        "mpm_fit_proj": lambda pp: lib.mpm_fit_proj(pp, Q, O, arr, None, None, hp, None, hp,
+                                                    1 << 20, ctypes.byref(rep), None),
+    }
+    for name, call in calls.items():
+        assert call(P) == _lib.ERR_INVALID_ARG, name
+        assert lib.mpm_last_error().decode(), name
+        assert call(None) == _lib.ERR_INVALID_ARG, name + " (NULL problem)"
+    # batched fit: a host image array of the second subject
+    pa = (ctypes.POINTER(_lib.Problem) * 2)(ctypes.pointer(p), ctypes.pointer(p))
+    V2 = ctypes.c_void_p * 2
+    st = lib.mpm_fit_batch(2, pa, O, V2(hp, hp), None, None, V2(hp, hp), None, V2(hp, hp),
+                           (ctypes.c_size_t * 2)(1 << 20, 1 << 20), None, None)
+    assert st == _lib.ERR_INVALID_ARG and lib.mpm_last_error().decode()
+    # an empty batch is a no-op; negative or oversized batches are refused
+    assert lib.mpm_fit_batch(0, None, O, None, None, None, None, None, None, None, None,
+                             None) == _lib.OK
+    for bad in (-1, _lib.MAX_BATCH + 1):
+        assert lib.mpm_fit_batch(bad, pa, O, V2(hp, hp), None, None, V2(hp, hp), None,
+                                 V2(hp, hp), (ctypes.c_size_t * 2)(1 << 20, 1 << 20), None,
+                                 None) == _lib.ERR_INVALID_ARG
+    # the server: host arena, bad slot count, NULL handles
+    out = ctypes.c_void_p()
+    assert lib.mpm_server_create(hp, 1 << 20, 2, None, ctypes.byref(out)) == _lib.ERR_INVALID_ARG
+    assert not out.value
+    assert lib.mpm_server_create(hp, 1 << 20, 0, None, ctypes.byref(out)) == _lib.ERR_INVALID_ARG
+    n = ctypes.c_int()
+    assert lib.mpm_server_step(None, ctypes.byref(n), ctypes.byref(n), ctypes.byref(n)) == _lib.ERR_INVALID_ARG
+    assert lib.mpm_server_poll(None, 1, ctypes.byref(n), ctypes.byref(n), None) == _lib.ERR_INVALID_ARG
+    assert lib.mpm_server_destroy(None) == _lib.OK            # like free(NULL)
+    assert lib.mpm_workspace_status(hp, 1 << 20, None) == _lib.ERR_INVALID_ARG
