@@ -259,3 +259,52 @@ def test_autotune_times_the_shapes(mpm):
     assert tile in (0, 1, 2)
     assert all(t > 0 for t in ms)
     assert ms[tile] == min(ms)
+
+
+def _irregular_dataset(shape, seed):
+    """Eight contrasts (the maximum), two with an MT pulse, 1 to 12 echoes each
+    (46 images), three TRs, and irregular echo times in four contrasts: the
+    echo loop's general branch, next to equally spaced and single-echo ones."""
+    import math
+    from cases import f32, round_protocol
+    from paper_2102_01604_gb300 import phantom
+    rng = np.random.default_rng(seed)
+    n_echoes = [8, 1, 6, 3, 12, 2, 5, 9]
+    te = []
+    for c, ne in enumerate(n_echoes):
+        if c in (0, 3):
+            te += [0.0023 * (k + 1) for k in range(ne)]
+        else:
+            te += list(np.sort(rng.uniform(0.002, 0.03, ne)))
+    prot = round_protocol({
+        "names": [f"c{c}" for c in range(8)],
+        "alpha": [math.radians(a) for a in (6, 21, 6, 15, 10, 30, 4, 18)],
+        "tr": [0.025, 0.025, 0.025, 0.030, 0.018, 0.025, 0.040, 0.025],
+        "mt": [0, 0, 1, 0, 1, 0, 0, 0], "n_echoes": n_echoes, "te": te, "sigma2": [1.0] * 8})
+    ph = phantom.phantom(shape, seed=seed, n_contrasts=8)
+    bp, bm = f32(ph["b1p"]), f32(ph["b1m"])
+    s = orc.forward(orc.make_problem(prot, shape), ph["y"], bp, bm)
+    prot["sigma2"] = [float(np.float32(v)) for v in phantom.noise_sigma2(s, prot)]
+    prot = round_protocol(prot)
+    x = f32(phantom.rician(s, prot, seed=seed + 1))
+    return {"prot": prot, "shape": tuple(shape), "y_true": ph["y"], "b1p": bp, "b1m": bm, "x": x}
+
+
+def test_irregular_echoes_and_most_contrasts(mpm):
+    d = _irregular_dataset((19, 13, 5), seed=41)
+    assert len(d["prot"]["te"]) == 46
+    for precond in (0, 1):
+        pg, po = _problems(mpm, d, precond=precond)
+        y = (d["y_true"] + 0.05 * np.random.default_rng(5).standard_normal(d["y_true"].shape)
+             ).astype(np.float32)
+        if precond == 0:
+            s = mpm.mpm_forward(pg, to_dev(y), to_dev(d["b1p"]), to_dev(d["b1m"]))
+            assert_close_scaled(to_np(s), orc.forward(po, y, d["b1p"], d["b1m"]), 1e-5, "forward")
+        g, h, nll = mpm.mpm_grad_hess(pg, to_dev(d["x"]), to_dev(y), to_dev(d["b1p"]),
+                                      to_dev(d["b1m"]))
+        nll_o, g_o, h_o = orc.grad_hess(po, d["x"], y, d["b1p"], d["b1m"])
+        assert_close_scaled(to_np(g), g_o, 1e-4, "g")
+        assert_close_scaled(to_np(h), h_o, 1e-4, "h")
+        assert abs(nll.item() - nll_o) <= 2e-6 * abs(nll_o)
+    st, rep, y, var, ref, _ = _fit_both(mpm, d, gn_iters=4, cg_iters=20)
+    _check_fit(rep, y, ref)
