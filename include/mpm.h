@@ -15,7 +15,13 @@
  * --------------------------------
  *  - Grid: nx * ny * nz = N voxels, voxel n = x + nx*(y + ny*z) (x fastest).
  *  - Arrays are caller-owned DEVICE pointers (cudaMalloc / torch CUDA
- *    tensors), contiguous, 16-byte aligned, planar:
+ *    tensors), contiguous, aligned to their element size (a misaligned one is
+ *    rejected with MPM_ERR_INVALID_ARG), planar.  With 16-byte alignment, as
+ *    cudaMalloc and torch give, the solver streams float4 vectors and stages
+ *    the stencil operands by TMA.  Otherwise it takes its scalar and
+ *    shared-memory kernels.  Both paths meet the same parity bounds against
+ *    the reference; their reductions group the sums differently, so the two
+ *    agree to rounding, not bit for bit:
  *        y, g, delta, var      [K][N] float   K = n_maps
  *        h                     [T][N] float   T = K(K+1)/2, upper triangle row
  *                              by row: 00,01,02,03,11,12,13,22,23,33 (K=4) or
