@@ -344,7 +344,11 @@ mpm_status mpm_fit_proj(const mpm_problem* problem, const mpm_projection* proj,
  *    one level lower per doubling).  Call it in a loop; reports the active,
  *    queued and just-finished counts (any pointer may be NULL).
  *  - mpm_server_poll: state of a ticket (MPM_REQ_*), its final status and,
- *    once done, its report.
+ *    once done, its report.  The server keeps a finished request's state and
+ *    report (about 10 KB of host memory) until mpm_server_release.
+ *  - mpm_server_release: forgets a finished ticket (MPM_REQ_DONE or
+ *    MPM_REQ_FAILED), after which polling it is an error.  A ticket that is
+ *    still queued or active is refused with MPM_ERR_INVALID_ARG.
  *  - mpm_server_destroy: waits for the work already enqueued on the server's
  *    streams, then frees its streams, events and staging; requests not yet
  *    done are dropped (their outputs are undefined).  NULL is a no-op that
@@ -361,6 +365,7 @@ mpm_status mpm_server_submit(mpm_server* server, const mpm_problem* problem, con
 mpm_status mpm_server_step(mpm_server* server, int* n_active, int* n_queued, int* n_finished);
 mpm_status mpm_server_poll(mpm_server* server, int ticket, int* state, mpm_status* status,
                            mpm_report* report);
+mpm_status mpm_server_release(mpm_server* server, int ticket);
 mpm_status mpm_server_destroy(mpm_server* server);
 
 /* Synchronises `stream` and returns MPM_ERR_NUMERIC if a kernel that used this

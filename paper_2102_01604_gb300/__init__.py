@@ -414,6 +414,10 @@ class Server:
             self._keep.pop(ticket, None)
         return state.value, status.value, rep if done else None
 
+    def release(self, ticket):
+        """Forget a finished ticket (its state and report)."""
+        _lib.check(self._lib.mpm_server_release(self._h, int(ticket)), "mpm_server_release")
+
     def close(self):
         if self._h:
             self._lib.mpm_server_destroy(self._h)

@@ -112,6 +112,7 @@ PROTOTYPES = {
                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "mpm_server_poll": (ctypes.c_int, [_V, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(Report)]),
+    "mpm_server_release": (ctypes.c_int, [_V, ctypes.c_int]),
     "mpm_server_destroy": (ctypes.c_int, [_V]),
     "mpm_autotune": (ctypes.c_int, [_P, _O, _V, _S, _V, ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_float)]),

@@ -209,9 +209,16 @@ mpm_status mpm_server_submit(mpm_server* s, const mpm_problem* problem, const mp
     r.ws_bytes = need;
     r.slot = -1;
     cudaError_t e = cudaEventCreateWithFlags(&r.ready, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r.landed, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventRecord(r.ready, s->user);
     if (e != cudaSuccess) return fail(MPM_ERR_CUDA, "event: %s", cudaGetErrorString(e));
+    e = cudaEventCreateWithFlags(&r.landed, cudaEventDisableTiming);
+    if (e == cudaSuccess) {
+        e = cudaEventRecord(r.ready, s->user);
+        if (e != cudaSuccess) cudaEventDestroy(r.landed);
+    }
+    if (e != cudaSuccess) {
+        cudaEventDestroy(r.ready);
+        return fail(MPM_ERR_CUDA, "event: %s", cudaGetErrorString(e));
+    }
     s->reqs[r.ticket] = r;
     s->queue.push_back(r.ticket);
     *ticket = r.ticket;
@@ -348,6 +355,19 @@ mpm_status mpm_server_poll(mpm_server* s, int ticket, int* state, mpm_status* st
     *state = r.state;
     if (status) *status = r.status;
     if (report && (r.state == kDone || r.state == kFailed)) *report = r.report;
+    return MPM_OK;
+}
+
+mpm_status mpm_server_release(mpm_server* s, int ticket)
+{
+    if (!s) return fail(MPM_ERR_INVALID_ARG, "server is NULL");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return fail(MPM_ERR_INVALID_ARG, "unknown ticket %d", ticket);
+    // a finished request holds no slot, event or arena space any more
+    if (it->second.state != kDone && it->second.state != kFailed)
+        return fail(MPM_ERR_INVALID_ARG, "ticket %d is not finished", ticket);
+    s->reqs.erase(it);
     return MPM_OK;
 }
 

@@ -225,5 +225,6 @@ def test_every_compute_call_refuses_host_memory_and_null_problems(lib):
     n = ctypes.c_int()
     assert lib.mpm_server_step(None, ctypes.byref(n), ctypes.byref(n), ctypes.byref(n)) == _lib.ERR_INVALID_ARG
     assert lib.mpm_server_poll(None, 1, ctypes.byref(n), ctypes.byref(n), None) == _lib.ERR_INVALID_ARG
+    assert lib.mpm_server_release(None, 1) == _lib.ERR_INVALID_ARG
     assert lib.mpm_server_destroy(None) == _lib.OK            # like free(NULL)
     assert lib.mpm_workspace_status(hp, 1 << 20, None) == _lib.ERR_INVALID_ARG
