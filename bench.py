@@ -65,6 +65,9 @@ def parse_args(argv=None):
                     help="storage of the echo images (computation stays float32)")
     ap.add_argument("--config", choices=["1mm", "0.8mm"], default="1mm",
                     help="1mm: 176x240x256 at 1 mm; 0.8mm: 208x300x320 at 0.8 mm")
+    ap.add_argument("--write-traffic", nargs="+", metavar="CSV", default=None,
+                    help="write profiles/dram_traffic.json from an ncu --csv capture of the "
+                         "plain bench (and optionally one of --workload moved); runs no GPU work")
     ap.add_argument("--workload", choices=["plain", "batched", "served", "moved"], default="plain",
                     help="plain: one subject per fit; batched: 16 uneven subjects per "
                          "mpm_fit_batch call, compared with plain fits of the same subjects; "
@@ -298,6 +301,91 @@ def measured_traffic(kind: str, n_vox: int):
     if not k or k.get("source_hash") != kernel_source_hash(kind):
         return None
     return int(k["dram_bytes_per_voxel"] * n_vox)
+
+
+# Kernel kind of each kernel function (the name before its template arguments).
+KERNEL_KIND = {
+    "k_pcg_update": "pcg_update", "k_pcg_matvec_tma": "pcg_matvec", "k_pcg_matvec": "pcg_matvec",
+    "k_pcg_direction": "pcg_direction", "k_pcg_init": "pcg_init", "k_jtv": "jtv",
+    "k_pcg_final": "pcg_final", "k_grad_hess": "grad_hess", "k_uncertainty": "uncertainty",
+    "k_grad_hess_proj": "grad_hess_proj", "k_push_all": "reslice",
+}
+
+
+def read_ncu_csv(path: str):
+    """Launches of an `ncu --csv` metrics log in launch order: for each, the
+    kernel function name and its metric values."""
+    import csv
+    with open(path) as f:
+        lines = [l for l in f if l.startswith('"')]
+    launches = {}
+    for r in csv.DictReader(lines):
+        d = launches.setdefault(int(r["ID"]), {"name": r["Kernel Name"], "metrics": {}})
+        d["metrics"][r["Metric Name"]] = float(r["Metric Value"].replace(",", ""))
+    out = []
+    for i in sorted(launches):
+        name = launches[i]["name"]
+        name = name[5:] if name.startswith("void ") else name
+        out.append((name.split("(")[0].split("<")[0].strip(), launches[i]["metrics"]))
+    return out
+
+
+def last_fit(launches):
+    """The launches of the last whole fit: after the second-to-last
+    k_uncertainty, through the last one (the whole list if there are fewer)."""
+    ends = [i for i, (name, _) in enumerate(launches) if name == "k_uncertainty"]
+    if not ends:
+        return launches
+    start = ends[-2] + 1 if len(ends) > 1 else 0
+    return launches[start:ends[-1] + 1]
+
+
+# The captures write_traffic reads, and the call that turns them into the file.
+TRAFFIC_COMMANDS = [
+    "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
+    "--clock-control none -k regex:^k_ -c 5000 --csv --log-file launches_full.csv "
+    "python bench.py --steps 1 --warmup 1 --no-cpu-baseline --no-e2e",
+    "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
+    "--clock-control none -k regex:\"k_grad_hess_proj|k_push_all\" -c 400 --csv "
+    "--log-file moved_full.csv python bench.py --workload moved --steps 1 --warmup 1",
+    "python bench.py --write-traffic launches_full.csv moved_full.csv",
+]
+
+
+def write_traffic(plain_csv: str, moved_csv=None, n_vox: int = None, out: str = TRAFFIC_FILE,
+                  commands=()):
+    """Per kernel kind, the DRAM bytes per launch of the timed fit of an ncu
+    capture (`dram__bytes_read.sum + dram__bytes_write.sum`), with the hash of
+    the kind's sources, into `out`.  The plain capture holds the warm-up and
+    the timed fit (its last fit is used); the moved-scan capture holds only
+    the projection kernels of a warm-up and a timed fit (its second half is
+    used)."""
+    n_vox = n_vox or int(np.prod(SHAPE))
+    sets = [last_fit(read_ncu_csv(plain_csv))]
+    if moved_csv:
+        moved = read_ncu_csv(moved_csv)
+        sets.append(moved[len(moved) // 2:])
+    agg = {}
+    for launches in sets:
+        for name, m in launches:
+            kind = KERNEL_KIND.get(name)
+            if kind is None:
+                continue
+            a = agg.setdefault(kind, [0, 0.0])
+            a[0] += 1
+            a[1] += m.get("dram__bytes_read.sum", 0.0) + m.get("dram__bytes_write.sum", 0.0)
+    doc = {"workload": f"{'x'.join(str(v) for v in SHAPE)} fit, timed fit of each capture",
+           "capture": list(commands),
+           "per_voxel_of": "reconstruction voxels (k_grad_hess_proj: acquisition voxels of one "
+                           "contrast, here the same count)",
+           "kernels": {}}
+    for kind, (n, b) in sorted(agg.items()):
+        doc["kernels"][kind] = {"launches": n, "dram_bytes_per_launch": int(b / n),
+                                "dram_bytes_per_voxel": round(b / n / n_vox, 3),
+                                "source_hash": kernel_source_hash(kind)}
+    with open(out, "w") as f:
+        json.dump(doc, f, indent=1)
+    return doc
 
 
 # ---------------------------------------------------------- CPU oracle
@@ -961,6 +1049,13 @@ def run_served(args):
 
 def main(argv=None):
     args = parse_args(argv)
+    if args.write_traffic:
+        doc = write_traffic(args.write_traffic[0],
+                            args.write_traffic[1] if len(args.write_traffic) > 1 else None,
+                            commands=TRAFFIC_COMMANDS)
+        for kind, k in doc["kernels"].items():
+            print(f"{kind:16s} {k['launches']:5d} launches {k['dram_bytes_per_voxel']:9.3f} B/voxel")
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":

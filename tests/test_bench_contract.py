@@ -58,3 +58,53 @@ def test_reference_arm_other_ranks_are_silent(monkeypatch, capsys):
     monkeypatch.setenv("LOCAL_RANK", "1")
     assert bench.main(["--impl", "reference", "--steps", "1", "--warmup", "0"]) == 0
     assert capsys.readouterr().out == ""
+
+
+def _ncu_csv(path, launches):
+    """A log in `ncu --csv --metrics ...` form: one row per launch and metric,
+    between the profiler's own lines and the program's output."""
+    head = ('"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream",'
+            '"Block Size","Grid Size","Device","CC","Section Name","Metric Name","Metric Unit",'
+            '"Metric Value"\n')
+    with open(path, "w") as f:
+        f.write("==PROF== Connected to process 1\n")
+        f.write('{"metric": "the program\'s own output"}\n')
+        f.write(head)
+        for i, (name, rd, wr) in enumerate(launches):
+            for metric, val in (("dram__bytes_read.sum", rd), ("dram__bytes_write.sum", wr),
+                                ("gpu__time_duration.sum", 1000)):
+                f.write(f'"{i}","1","python3","127.0.0.1","{name}","1","7","(256, 1, 1)",'
+                        f'"(1216, 1, 1)","0","10.3","Command line profiler metrics","{metric}",'
+                        f'"byte","{val:,}"\n')
+
+
+def test_write_traffic_takes_the_timed_fit(tmp_path):
+    """DRAM bytes per launch come from the last whole fit of the plain capture
+    (after the second-to-last k_uncertainty) and from the second half of the
+    moved-scan capture; warm-up and autotuning launches do not count."""
+    upd = "void k_pcg_update<4, 4>(DevProblem, int, float *, Reduce)"
+    unc = "void k_uncertainty<4>(DevProblem, const float *, float *)"
+    plain = [("void k_pcg_matvec_tma<4, 16, 16>(DevProblem, int)", 9e9, 9e9),   # autotuner
+             (upd, 5e9, 5e9), (unc, 7e9, 7e9),                                 # warm-up fit
+             ("void k_jtv<4>(DevProblem, const float *)", 100, 20),              # timed fit
+             (upd, 1000, 200), (upd, 1100, 300), (unc, 600, 40)]
+    moved = [("void k_grad_hess_proj<4, 0, float>(DevProblem)", 8e9, 8e9),
+             ("void k_push_all<4>(DevProblem)", 8e9, 8e9),
+             ("void k_grad_hess_proj<4, 0, float>(DevProblem)", 500, 70),
+             ("void k_push_all<4>(DevProblem)", 900, 100)]
+    _ncu_csv(tmp_path / "plain.csv", plain)
+    _ncu_csv(tmp_path / "moved.csv", moved)
+    out = tmp_path / "traffic.json"
+    doc = bench.write_traffic(str(tmp_path / "plain.csv"), str(tmp_path / "moved.csv"),
+                              n_vox=10, out=str(out), commands=["cmd"])
+    k = json.load(open(out))["kernels"]
+    assert doc["kernels"] == k and json.load(open(out))["capture"] == ["cmd"]
+    assert k["pcg_update"]["launches"] == 2 and k["pcg_update"]["dram_bytes_per_launch"] == 1300
+    assert k["pcg_update"]["dram_bytes_per_voxel"] == 130.0
+    assert k["jtv"]["dram_bytes_per_launch"] == 120
+    assert k["uncertainty"] == {"launches": 1, "dram_bytes_per_launch": 640,
+                                "dram_bytes_per_voxel": 64.0,
+                                "source_hash": bench.kernel_source_hash("uncertainty")}
+    assert "pcg_matvec" not in k
+    assert k["grad_hess_proj"]["dram_bytes_per_launch"] == 570
+    assert k["reslice"]["dram_bytes_per_launch"] == 1000
