@@ -340,6 +340,23 @@ def last_fit(launches):
     return launches[start:ends[-1] + 1]
 
 
+def launch_table(launches) -> str:
+    """Per kernel function: launches, total ncu time, share of the total and
+    DRAM bytes per launch, largest total first."""
+    agg = {}
+    for name, m in launches:
+        a = agg.setdefault(name, [0, 0.0, 0.0])
+        a[0] += 1
+        a[1] += m.get("gpu__time_duration.sum", 0.0)
+        a[2] += m.get("dram__bytes_read.sum", 0.0) + m.get("dram__bytes_write.sum", 0.0)
+    total = sum(a[1] for a in agg.values()) or 1.0
+    rows = [f"{len(launches)} launches, {total / 1e6:.1f} ms"]
+    for name, (n, t, b) in sorted(agg.items(), key=lambda kv: -kv[1][1]):
+        rows.append(f"{name:24s} {n:5d} {t / 1e6:9.2f} ms {100 * t / total:5.1f}% "
+                    f"{b / n / 1e6:9.1f} MB/launch")
+    return "\n".join(rows)
+
+
 # The captures write_traffic reads, and the call that turns them into the file.
 TRAFFIC_COMMANDS = [
     "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
@@ -1053,6 +1070,7 @@ def main(argv=None):
         doc = write_traffic(args.write_traffic[0],
                             args.write_traffic[1] if len(args.write_traffic) > 1 else None,
                             commands=TRAFFIC_COMMANDS)
+        print(launch_table(last_fit(read_ncu_csv(args.write_traffic[0]))))
         for kind, k in doc["kernels"].items():
             print(f"{kind:16s} {k['launches']:5d} launches {k['dram_bytes_per_voxel']:9.3f} B/voxel")
         return 0

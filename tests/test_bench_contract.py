@@ -108,3 +108,12 @@ def test_write_traffic_takes_the_timed_fit(tmp_path):
     assert "pcg_matvec" not in k
     assert k["grad_hess_proj"]["dram_bytes_per_launch"] == 570
     assert k["reslice"]["dram_bytes_per_launch"] == 1000
+
+
+def test_launch_table_shares(tmp_path):
+    _ncu_csv(tmp_path / "t.csv", [("void k_a<1>(int)", 10, 0), ("void k_b(int)", 20, 0),
+                                  ("void k_a<1>(int)", 30, 0)])
+    rows = bench.launch_table(bench.read_ncu_csv(str(tmp_path / "t.csv"))).splitlines()
+    assert rows[0].startswith("3 launches")
+    assert rows[1].split()[:2] == ["k_a", "2"] and "66.7%" in rows[1]   # 2 of 3 us
+    assert rows[2].split()[:2] == ["k_b", "1"] and "33.3%" in rows[2]
