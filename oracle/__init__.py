@@ -22,26 +22,52 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mpm_oracle.c")
 _SO = os.path.join(_HERE, "libmpm_oracle.so")
+_SO_OMP = os.path.join(_HERE, "libmpm_oracle_omp.so")
 
 MAX_CONTRASTS = 8
 MAX_IMAGES = 128
 
-_lib_handle = None
+_handles = {}
+_variant = "serial"
+
+
+def _compile(out: str, extra) -> None:
+    fd, tmp = tempfile.mkstemp(suffix=".so", dir=_HERE)
+    os.close(fd)
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", *extra,
+           "-o", tmp, _SRC, "-lm"]
+    try:
+        subprocess.run(cmd, check=True)
+    except BaseException:
+        os.unlink(tmp)
+        raise
+    os.replace(tmp, out)
+
+
+def _fresh(path: str) -> bool:
+    return os.path.exists(path) and os.path.getmtime(path) >= max(
+        os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "mpm_oracle.h")))
 
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (plain C11, no FP contraction so that x86
-    and Arm hosts round identically).  Returns the library path."""
-    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= max(
-            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "mpm_oracle.h"))):
-        return _SO
-    fd, tmp = tempfile.mkstemp(suffix=".so", dir=_HERE)
-    os.close(fd)
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-           "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _SO)
+    and Arm hosts round identically): the serial library and, from the same
+    source with -fopenmp, the threaded one.  Returns the serial library's
+    path."""
+    if force or not _fresh(_SO):
+        _compile(_SO, [])
+    if force or not _fresh(_SO_OMP):
+        _compile(_SO_OMP, ["-fopenmp"])
     return _SO
+
+
+def use_threads(n: int) -> int:
+    """Run the following oracle calls serially (n == 1) or on n OpenMP threads
+    (n > 1; n <= 0: all host cores).  The results are bit-identical either
+    way.  Returns the thread count in use."""
+    global _variant
+    _variant = "serial" if n == 1 else "omp"
+    return _lib().orc_threads(n if n > 1 else 0)
 
 
 class OrcProblem(ctypes.Structure):
@@ -85,9 +111,12 @@ _U8 = ctypes.POINTER(ctypes.c_uint8)
 
 
 def _lib():
-    global _lib_handle
-    if _lib_handle is None:
-        lib = ctypes.CDLL(build())
+    lib = _handles.get(_variant)
+    if lib is None:
+        build()
+        lib = ctypes.CDLL(_SO if _variant == "serial" else _SO_OMP)
+        lib.orc_threads.restype = ctypes.c_int
+        lib.orc_threads.argtypes = [ctypes.c_int]
         lib.orc_signal.restype = ctypes.c_double
         lib.orc_signal.argtypes = [_D, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_int, ctypes.c_double, ctypes.c_double]
@@ -126,8 +155,8 @@ def _lib():
         lib.orc_fit_proj.argtypes = [_P, _Q, ctypes.POINTER(OrcOpts), _DD, _DD, _DD, _D, _D, _D,
                                      _D, _D]
         lib.orc_fit_proj.restype = ctypes.c_int
-        _lib_handle = lib
-    return _lib_handle
+        _handles[_variant] = lib
+    return lib
 
 
 def _ptr(a):

@@ -44,16 +44,56 @@
  *   The prior-regularised fit of noisy data after a fixed iteration count has
  *   no value printed in the paper: beyond the pins above it is "parity
  *   unpinned".
+ *
+ * Threads.  The same source builds serial and, with -fopenmp, threaded over
+ * voxels (the timing host's cores).  Every volume-wide sum is taken in fixed
+ * chunks of ORC_CHUNK voxels, each chunk summed in voxel order and the chunk
+ * sums added in chunk order, so both builds round identically for any thread
+ * count.  Per-voxel arithmetic is the same statement in both.  The spatial
+ * projection functions stay serial.
  */
 #include "mpm_oracle.h"
 
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* ---------------------------------------------------------------- helpers */
 
 static long n_vox(const orc_problem* p) { return (long)p->nx * p->ny * p->nz; }
+
+/* Volume-wide sums: chunks of ORC_CHUNK voxels summed in order, then the
+ * chunk sums in chunk order (the same rounding with or without threads). */
+#define ORC_CHUNK 4096L
+
+static long n_chunks(long n) { return (n + ORC_CHUNK - 1) / ORC_CHUNK; }
+
+static long chunk_end(long c, long n)
+{
+    long e = (c + 1) * ORC_CHUNK;
+    return e < n ? e : n;
+}
+
+static double sum_chunks(const double* part, long nc)
+{
+    double s = 0.0;
+    for (long c = 0; c < nc; ++c) s += part[c];
+    return s;
+}
+
+int orc_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 static int n_images(const orc_problem* p)
 {
@@ -204,6 +244,7 @@ void orc_forward(const orc_problem* p, const double* y, const double* b1p,
 {
     long N = n_vox(p);
     int K = p->n_maps;
+#pragma omp parallel for schedule(static)
     for (long n = 0; n < N; ++n) {
         double yn[4] = {0, 0, 0, 0};
         for (int k = 0; k < K; ++k) yn[k] = y[(long)k * N + n];
@@ -255,25 +296,33 @@ double orc_grad_hess(const orc_problem* p, const double* x, const double* y,
 {
     long N = n_vox(p);
     int K = p->n_maps;
-    double nll = 0.0;
-    for (long n = 0; n < N; ++n) {
-        double yn[4] = {0, 0, 0, 0};
-        for (int k = 0; k < K; ++k) yn[k] = y[(long)k * N + n];
-        double gn[4] = {0, 0, 0, 0};
-        double P[4][4];
-        memset(P, 0, sizeof P);
-        int i = 0;
-        for (int c = 0; c < p->n_contrasts; ++c) {
-            double bp = b1p ? b1p[n] : 1.0;
-            double bm = b1m ? b1m[(long)c * N + n] : 1.0;
-            contrast_terms(p, c, i, yn, bp, bm, x + (long)i * N + n, N, &nll, gn, P);
-            i += p->n_echoes[c];
+    long nc = n_chunks(N);
+    double* part = malloc(sizeof(double) * (nc > 0 ? nc : 1));
+#pragma omp parallel for schedule(static)
+    for (long ch = 0; ch < nc; ++ch) {
+        double nll = 0.0;
+        for (long n = ch * ORC_CHUNK; n < chunk_end(ch, N); ++n) {
+            double yn[4] = {0, 0, 0, 0};
+            for (int k = 0; k < K; ++k) yn[k] = y[(long)k * N + n];
+            double gn[4] = {0, 0, 0, 0};
+            double P[4][4];
+            memset(P, 0, sizeof P);
+            int i = 0;
+            for (int c = 0; c < p->n_contrasts; ++c) {
+                double bp = b1p ? b1p[n] : 1.0;
+                double bm = b1m ? b1m[(long)c * N + n] : 1.0;
+                contrast_terms(p, c, i, yn, bp, bm, x + (long)i * N + n, N, &nll, gn, P);
+                i += p->n_echoes[c];
+            }
+            for (int k = 0; k < K; ++k) g[(long)k * N + n] = gn[k];
+            for (int k = 0; k < K; ++k)
+                for (int j = k; j < K; ++j)
+                    h[(long)tri_index(K, k, j) * N + n] = P[k][j];
         }
-        for (int k = 0; k < K; ++k) g[(long)k * N + n] = gn[k];
-        for (int k = 0; k < K; ++k)
-            for (int j = k; j < K; ++j)
-                h[(long)tri_index(K, k, j) * N + n] = P[k][j];
+        part[ch] = nll;
     }
+    double nll = sum_chunks(part, nc);
+    free(part);
     return nll;
 }
 
@@ -419,24 +468,32 @@ double orc_jtv(const orc_problem* p, const double* y, double* w)
 {
     long N = n_vox(p);
     int K = p->n_maps;
-    double jtv = 0.0;
-    for (long n = 0; n < N; ++n) {
-        long m[6];
-        double ih2[6];
-        int cnt = neighbours(p, n, m, ih2);
-        double u = 0.0;
-        for (int k = 0; k < K; ++k) {
-            double acc = 0.0;
-            for (int j = 0; j < cnt; ++j) {
-                double dlt = y[(long)k * N + m[j]] - y[(long)k * N + n];
-                acc += dlt * dlt * ih2[j];
+    long nc = n_chunks(N);
+    double* part = malloc(sizeof(double) * (nc > 0 ? nc : 1));
+#pragma omp parallel for schedule(static)
+    for (long ch = 0; ch < nc; ++ch) {
+        double jtv = 0.0;
+        for (long n = ch * ORC_CHUNK; n < chunk_end(ch, N); ++n) {
+            long m[6];
+            double ih2[6];
+            int cnt = neighbours(p, n, m, ih2);
+            double u = 0.0;
+            for (int k = 0; k < K; ++k) {
+                double acc = 0.0;
+                for (int j = 0; j < cnt; ++j) {
+                    double dlt = y[(long)k * N + m[j]] - y[(long)k * N + n];
+                    acc += dlt * dlt * ih2[j];
+                }
+                u += p->lambda[k] * acc;
             }
-            u += p->lambda[k] * acc;
+            double v = u + p->eps * p->eps;
+            if (w) w[n] = 1.0 / sqrt(v);
+            jtv += sqrt(v);
         }
-        double v = u + p->eps * p->eps;
-        if (w) w[n] = 1.0 / sqrt(v);
-        jtv += sqrt(v);
+        part[ch] = jtv;
     }
+    double jtv = sum_chunks(part, nc);
+    free(part);
     return jtv;
 }
 
@@ -445,6 +502,7 @@ void orc_membrane(const orc_problem* p, const double* w, const double* v, double
 {
     long N = n_vox(p);
     int K = p->n_maps;
+#pragma omp parallel for schedule(static)
     for (long n = 0; n < N; ++n) {
         long m[6];
         double ih2[6];
@@ -461,6 +519,7 @@ void orc_membrane(const orc_problem* p, const double* w, const double* v, double
 void orc_membrane_diag(const orc_problem* p, const double* w, double* d)
 {
     long N = n_vox(p);
+#pragma omp parallel for schedule(static)
     for (long n = 0; n < N; ++n) {
         long m[6];
         double ih2[6];
@@ -479,6 +538,7 @@ static void apply_system(const orc_problem* p, const double* h, const double* w,
     long N = n_vox(p);
     int K = p->n_maps;
     orc_membrane(p, w, v, out);
+#pragma omp parallel for schedule(static)
     for (long n = 0; n < N; ++n)
         for (int k = 0; k < K; ++k) {
             double acc = 0.0;
@@ -493,21 +553,31 @@ static int apply_precond_inverse(const orc_problem* p, const double* h, const do
 {
     long N = n_vox(p);
     int K = p->n_maps;
+    int bad = 0;
+#pragma omp parallel for schedule(static) reduction(|:bad)
     for (long n = 0; n < N; ++n) {
         double M[4][4], L[4][4], b[4], x[4];
         precond_block(p, h, d, n, M);
-        if (cholesky(K, M, L)) return -1;
+        if (cholesky(K, M, L)) { bad = 1; continue; }
         for (int k = 0; k < K; ++k) b[k] = r[(long)k * N + n];
         chol_solve(K, L, b, x);
         for (int k = 0; k < K; ++k) z[(long)k * N + n] = x[k];
     }
-    return 0;
+    return bad ? -1 : 0;
 }
 
 static double dot(long n, const double* a, const double* b)
 {
-    double s = 0.0;
-    for (long i = 0; i < n; ++i) s += a[i] * b[i];
+    long nc = n_chunks(n);
+    double* part = malloc(sizeof(double) * (nc > 0 ? nc : 1));
+#pragma omp parallel for schedule(static)
+    for (long c = 0; c < nc; ++c) {
+        double s = 0.0;
+        for (long i = c * ORC_CHUNK; i < chunk_end(c, n); ++i) s += a[i] * b[i];
+        part[c] = s;
+    }
+    double s = sum_chunks(part, nc);
+    free(part);
     return s;
 }
 
@@ -524,6 +594,7 @@ int orc_pcg(const orc_problem* p, const double* h, const double* w, const double
     int it = 0;
 
     orc_membrane_diag(p, w, d);
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < L; ++i) { x[i] = 0.0; r[i] = b[i]; }
     if (apply_precond_inverse(p, h, d, r, z)) { it = -1; goto done; }
     memcpy(pv, z, sizeof(double) * L);
@@ -537,11 +608,13 @@ int orc_pcg(const orc_problem* p, const double* h, const double* w, const double
         double pq = dot(L, pv, q);
         if (!(pq > 0.0)) break;
         double alpha = rz / pq;
+#pragma omp parallel for schedule(static)
         for (long i = 0; i < L; ++i) { x[i] += alpha * pv[i]; r[i] -= alpha * q[i]; }
         if (apply_precond_inverse(p, h, d, r, z)) { it = -1; goto done; }
         double rz_new = dot(L, r, z);
         double beta = rz_new / rz;
         rz = rz_new;
+#pragma omp parallel for schedule(static)
         for (long i = 0; i < L; ++i) pv[i] = z[i] + beta * pv[i];
         if (resid) resid[it + 1] = sqrt(dot(L, r, r));
     }
@@ -556,6 +629,7 @@ int orc_solve(const orc_problem* p, const double* h, const double* w, const doub
     long L = (long)p->n_maps * n_vox(p);
     double* b = malloc(sizeof(double) * L);
     orc_membrane(p, w, y, b);                       /* b = g + L y (Eq. 42) */
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < L; ++i) b[i] += g[i];
     int it = orc_pcg(p, h, w, b, delta, max_iters, tol, resid);
     free(b);
@@ -570,12 +644,13 @@ int orc_uncertainty(const orc_problem* p, const double* h, const double* w,
     long N = n_vox(p);
     int K = p->n_maps;
     double* d = malloc(sizeof(double) * N);
-    int status = 0;
+    int bad = 0;
     orc_membrane_diag(p, w, d);
+#pragma omp parallel for schedule(static) reduction(|:bad)
     for (long n = 0; n < N; ++n) {
         double M[4][4], L[4][4];
         precond_block(p, h, d, n, M);
-        if (cholesky(K, M, L)) { status = -1; continue; }
+        if (cholesky(K, M, L)) { bad = 1; continue; }
         for (int k = 0; k < K; ++k) {
             double e[4] = {0, 0, 0, 0}, col[4];
             e[k] = 1.0;
@@ -598,7 +673,7 @@ int orc_uncertainty(const orc_problem* p, const double* h, const double* w,
         }
     }
     free(d);
-    return status;
+    return bad ? -1 : 0;
 }
 
 /* ---------------------------------------------------- initial maps */
@@ -624,12 +699,19 @@ void orc_init(const orc_problem* p, const double* x, double* y)
     long N = n_vox(p);
     int I = n_images(p);
     double lmu[ORC_MAX_IMAGES];
+    long nc = n_chunks(N);
+    double* part = malloc(sizeof(double) * (nc > 0 ? nc : 1));
     for (int i = 0; i < I; ++i) {
-        double s = 0.0;
-        for (long n = 0; n < N; ++n) s += x[(long)i * N + n];
-        double mu = s / (double)N;
+#pragma omp parallel for schedule(static)
+        for (long c = 0; c < nc; ++c) {
+            double s = 0.0;
+            for (long n = c * ORC_CHUNK; n < chunk_end(c, N); ++n) s += x[(long)i * N + n];
+            part[c] = s;
+        }
+        double mu = sum_chunks(part, nc) / (double)N;
         lmu[i] = log(mu > 1e-30 ? mu : 1e-30);
     }
+    free(part);
     init_from_log_means(p, lmu, N, y);
 }
 
@@ -767,6 +849,7 @@ static int fit_loop(const orc_problem* p, const orc_projection* q, const orc_opt
         int cg = orc_solve(p, h, w, g, y, delta, o->cg_iters, o->tol_cg, resid);
         if (cg < 0) { it = -1; break; }
         if (cg_rel) cg_rel[it] = resid[0] > 0.0 ? resid[cg] / resid[0] : 0.0;
+#pragma omp parallel for schedule(static)
         for (long i = 0; i < L; ++i) y[i] -= delta[i];
     }
     free(w); free(g); free(h); free(delta); free(resid);

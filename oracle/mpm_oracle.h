@@ -141,4 +141,9 @@ int orc_fit(const orc_problem* p, const orc_opts* o, const double* x,
             const double* b1p, const double* b1m, double* y,
             double* F, double* nll, double* jtv, double* cg_rel);
 
+/* Threads of the OpenMP build (the serial build ignores n and returns 1).
+ * n > 0 sets the count; returns the count in use.  Results do not depend on
+ * it: volume-wide sums are taken in fixed voxel chunks. */
+int orc_threads(int n);
+
 #endif
