@@ -66,8 +66,12 @@ def parse_args(argv=None):
     ap.add_argument("--config", choices=["1mm", "0.8mm"], default="1mm",
                     help="1mm: 176x240x256 at 1 mm; 0.8mm: 208x300x320 at 0.8 mm")
     ap.add_argument("--write-traffic", nargs="+", metavar="CSV", default=None,
-                    help="write profiles/dram_traffic.json from an ncu --csv capture of the "
-                         "plain bench (and optionally one of --workload moved); runs no GPU work")
+                    help="write profiles/dram_traffic.json from the per-kernel ncu captures "
+                         "of TRAFFIC_COMMANDS; runs no GPU work")
+    ap.add_argument("--print-hashes", action="store_true",
+                    help="print the source hash of every kernel kind (stderr) before running")
+    ap.add_argument("--launch-table", metavar="CSV", default=None,
+                    help="print the per-kernel launch table of an ncu --csv capture; runs no GPU work")
     ap.add_argument("--workload", choices=["plain", "batched", "served", "moved"], default="plain",
                     help="plain: one subject per fit; batched: 16 uneven subjects per "
                          "mpm_fit_batch call, compared with plain fits of the same subjects; "
@@ -200,29 +204,37 @@ class ClockSampler:
 
 # ------------------------------------------------------------ roofline
 
-def algorithmic_bytes(K: int, C: int, I: int, echo_bytes: int = 4):
-    """Bytes each kernel must move per voxel (reads + writes of its operands,
-    float32, every array touched once); the PCG direction bytes are per solve
-    (odd passes read z and p_{k-1} and write p_k; even passes also read
-    p_{k-2} and, after the first, x, and write x)."""
+def step_bytes(j: int, K: int, cg_iters: int = None) -> int:
+    """Bytes PCG iteration j moves per voxel (pcg_step.cuh): j = 0 reads z_0, w,
+    H and writes p_0, v_0; later iterations read z, v, p, w, H and write z, v,
+    p; even j >= 2 also read p_{j-2} and write x, and read x when j > 2."""
     T = K * (K + 1) // 2
     f = 4
-    direction = 0
-    for k in range(1, CG_ITERS):
-        if k % 2:
-            direction += 3 * K * f
-        else:
-            direction += (5 if k == 2 else 6) * K * f
-    xcount = max((k for k in range(2, CG_ITERS, 2)), default=0)
-    pend = CG_ITERS - xcount                            # directions folded by the final pass
+    if j == 0:
+        return K * f + f + T * f + 2 * K * f
+    b = 3 * K * f + f + T * f + 3 * K * f
+    if j >= 2 and j % 2 == 0:
+        b += 2 * K * f + (K * f if j > 2 else 0)
+    return b
+
+
+def algorithmic_bytes(K: int, C: int, I: int, echo_bytes: int = 4, cg_iters: int = None):
+    """Bytes each kernel must move per voxel (reads + writes of its operands,
+    float32, every array touched once).  pcg_step_per_solve sums step_bytes
+    over the iterations of one solve; pcg_step is its mean per launch."""
+    cg = cg_iters or CG_ITERS
+    T = K * (K + 1) // 2
+    f = 4
+    per_solve = sum(step_bytes(j, K) for j in range(cg))
+    xcount = max((j for j in range(2, cg, 2)), default=0)
+    pend = cg - xcount                                  # directions folded by the final pass
     final = (K * f if xcount else 0) + pend * K * f + 2 * K * f
     return {
         "grad_hess": I * echo_bytes + K * f + f + C * f + K * f + T * f,
         "jtv": K * f + f,
-        "pcg_init": f + 2 * K * f + T * f + T * f + 2 * K * f,
-        "pcg_direction_per_solve": direction,
-        "pcg_matvec": K * f + T * f + f + K * f,
-        "pcg_update": 2 * K * f + T * f + 2 * K * f,
+        "pcg_init": f + 2 * K * f + T * f + K * f,
+        "pcg_step_per_solve": per_solve,
+        "pcg_step": per_solve / cg,
         "pcg_final": final,
         "uncertainty": T * f + f + K * f,
     }
@@ -236,8 +248,8 @@ def kernel_roofline(prof: dict, n_vox: int, steps: int, K: int, C: int, I: int, 
     for kind, v in prof.items():
         if not v["launches"]:
             continue
-        if kind == "pcg_direction":
-            total_bytes = ab["pcg_direction_per_solve"] * n_vox * solves
+        if kind == "pcg_step" and v["launches"] % CG_ITERS == 0:
+            total_bytes = ab["pcg_step_per_solve"] * n_vox * (v["launches"] // CG_ITERS)
         elif kind in ab:
             total_bytes = ab[kind] * n_vox * v["launches"]
         else:
@@ -268,11 +280,9 @@ KIND_SOURCES = {
     "grad_hess": ["voxel_kernels.cu", "voxel_model.cuh"],
     "uncertainty": ["voxel_kernels.cu"],
     "jtv": ["stencil_kernels.cu"],
-    "pcg_init": ["stencil_kernels.cu"],
-    "pcg_direction": ["stencil_kernels.cu"],
-    "pcg_matvec": ["stencil_kernels.cu", "stencil_tma.cu"],
-    "pcg_update": ["stencil_kernels.cu"],
-    "pcg_final": ["stencil_kernels.cu"],
+    "pcg_init": ["stencil_kernels.cu", "pcg_step.cuh"],
+    "pcg_step": ["stencil_kernels.cu", "stencil_tma.cu", "pcg_step.cuh"],
+    "pcg_final": ["stencil_kernels.cu", "pcg_step.cuh"],
     "grad_hess_proj": ["projection.cu", "voxel_model.cuh"],
     "reslice": ["projection.cu"],
 }
@@ -290,8 +300,9 @@ def kernel_source_hash(kind: str):
 
 
 def measured_traffic(kind: str, n_vox: int):
-    """DRAM bytes per launch from the committed ncu capture, scaled to this
-    volume; None when the kernel's sources changed since the capture."""
+    """DRAM bytes per launch from the committed ncu capture of this kernel kind
+    (on a smaller volume), scaled to n_vox voxels; None when the kernel's
+    sources changed since the capture."""
     try:
         with open(TRAFFIC_FILE) as f:
             tr = json.load(f)
@@ -305,10 +316,9 @@ def measured_traffic(kind: str, n_vox: int):
 
 # Kernel kind of each kernel function (the name before its template arguments).
 KERNEL_KIND = {
-    "k_pcg_update": "pcg_update", "k_pcg_matvec_tma": "pcg_matvec", "k_pcg_matvec": "pcg_matvec",
-    "k_pcg_direction": "pcg_direction", "k_pcg_init": "pcg_init", "k_jtv": "jtv",
-    "k_pcg_final": "pcg_final", "k_grad_hess": "grad_hess", "k_uncertainty": "uncertainty",
-    "k_grad_hess_proj": "grad_hess_proj", "k_push_all": "reslice",
+    "k_pcg_step_tma": "pcg_step", "k_pcg_step": "pcg_step", "k_pcg_init": "pcg_init",
+    "k_jtv": "jtv", "k_pcg_final": "pcg_final", "k_grad_hess": "grad_hess",
+    "k_uncertainty": "uncertainty", "k_grad_hess_proj": "grad_hess_proj", "k_push_all": "reslice",
 }
 
 
@@ -330,14 +340,20 @@ def read_ncu_csv(path: str):
     return out
 
 
-def last_fit(launches):
-    """The launches of the last whole fit: after the second-to-last
-    k_uncertainty, through the last one (the whole list if there are fewer)."""
-    ends = [i for i, (name, _) in enumerate(launches) if name == "k_uncertainty"]
-    if not ends:
-        return launches
-    start = ends[-2] + 1 if len(ends) > 1 else 0
-    return launches[start:ends[-1] + 1]
+def read_log_json(path: str, key: str):
+    """The first JSON object with `key` that the program printed into an ncu
+    log (None if there is none)."""
+    with open(path) as f:
+        for line in f:
+            line = line.strip()
+            if line.startswith("{") and key in line:
+                try:
+                    d = json.loads(line)
+                except ValueError:
+                    continue
+                if key in d:
+                    return d
+    return None
 
 
 def launch_table(launches) -> str:
@@ -357,52 +373,86 @@ def launch_table(launches) -> str:
     return "\n".join(rows)
 
 
-# The captures write_traffic reads, and the call that turns them into the file.
-TRAFFIC_COMMANDS = [
-    "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
-    "--clock-control none -k regex:^k_ -c 5000 --csv --log-file launches_full.csv "
-    "python bench.py --steps 1 --warmup 1 --no-cpu-baseline --no-e2e",
-    "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
-    "--clock-control none -k regex:\"k_grad_hess_proj|k_push_all\" -c 400 --csv "
-    "--log-file moved_full.csv python bench.py --workload moved --steps 1 --warmup 1",
-    "python bench.py --write-traffic launches_full.csv moved_full.csv",
-]
+# DRAM traffic captures: one ncu run per kernel kind, on a 176 x 240 x 128
+# volume (images 476 MB and every solver vector 86 MB, so the operands do not
+# fit the 129 MB L2), one kernel (-k), the launches after -s of it only.  The
+# metrics (DRAM bytes read and written, duration) take one pass.  Each run
+# writes ncu's CSV and the bench's own output (its voxel count and the source
+# hash of every kernel kind) into one file, which --write-traffic reads.
+TRAFFIC_SHAPE = (176, 240, 128)
+TRAFFIC_CAPTURES = {
+    # kind: (kernel name regex, launches skipped, launches captured, workload)
+    "pcg_step": ("k_pcg_step", 48, 30, "plain"),     # after the autotuner's 18 and one solve
+    "pcg_init": ("k_pcg_init", 1, 2, "plain"),
+    "pcg_final": ("k_pcg_final", 1, 2, "plain"),
+    "jtv": ("k_jtv", 1, 2, "plain"),
+    "grad_hess": ("k_grad_hess", 1, 2, "plain"),
+    "uncertainty": ("k_uncertainty", 0, 1, "plain"),
+    "grad_hess_proj": ("k_grad_hess_proj", 3, 3, "moved"),
+    "reslice": ("k_push_all", 1, 2, "moved"),
+}
 
 
-def write_traffic(plain_csv: str, moved_csv=None, n_vox: int = None, out: str = TRAFFIC_FILE,
-                  commands=()):
-    """Per kernel kind, the DRAM bytes per launch of the timed fit of an ncu
-    capture (`dram__bytes_read.sum + dram__bytes_write.sum`), with the hash of
-    the kind's sources, into `out`.  The plain capture holds the warm-up and
-    the timed fit (its last fit is used); the moved-scan capture holds only
-    the projection kernels of a warm-up and a timed fit (its second half is
-    used)."""
-    n_vox = n_vox or int(np.prod(SHAPE))
-    sets = [last_fit(read_ncu_csv(plain_csv))]
-    if moved_csv:
-        moved = read_ncu_csv(moved_csv)
-        sets.append(moved[len(moved) // 2:])
-    agg = {}
-    for launches in sets:
-        for name, m in launches:
+def traffic_command(kind: str) -> str:
+    rx, skip, count, workload = TRAFFIC_CAPTURES[kind]
+    shape = ",".join(str(v) for v in TRAFFIC_SHAPE)
+    return (f"ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
+            f"--clock-control none -k regex:{rx} -s {skip} -c {count} --csv "
+            f"python bench.py --workload {workload} --shape {shape} --steps 1 --warmup 0 "
+            f"--no-cpu-baseline --no-e2e --print-hashes > traffic_{kind}.csv 2>&1")
+
+
+TRAFFIC_COMMANDS = [traffic_command(k) for k in TRAFFIC_CAPTURES] + [
+    "python bench.py --write-traffic " + " ".join(f"traffic_{k}.csv" for k in TRAFFIC_CAPTURES)]
+
+
+def write_traffic(paths, out: str = TRAFFIC_FILE, commands=()):
+    """Per kernel kind, the mean DRAM bytes per launch and per voxel
+    (`dram__bytes_read.sum + dram__bytes_write.sum` of the captured launches,
+    divided by the capture's voxel count) into `out`, with the source hash of
+    the kind that the captured program printed.  Refuses (ValueError) when a
+    log lacks the program's hashes or voxel count, or when a captured kind's
+    sources have changed since the capture."""
+    doc = {"workload": f"{'x'.join(str(v) for v in TRAFFIC_SHAPE)} volume, one capture per "
+                       "kernel kind; per-voxel bytes are scaled to other volumes by the voxel count",
+           "capture": list(commands),
+           "per_voxel_of": "reconstruction voxels (k_grad_hess_proj: acquisition voxels of one "
+                           "contrast, here the same count)",
+           "kernels": {}}
+    for path in paths:
+        hashes = read_log_json(path, "kernel_source_hashes")
+        line = read_log_json(path, "config")
+        if not hashes or not line or "voxels" not in line["config"]:
+            raise ValueError(f"{path}: no source hashes or voxel count from the captured program")
+        n_vox = int(line["config"]["voxels"])
+        agg = {}
+        for name, m in read_ncu_csv(path):
             kind = KERNEL_KIND.get(name)
             if kind is None:
                 continue
             a = agg.setdefault(kind, [0, 0.0])
             a[0] += 1
             a[1] += m.get("dram__bytes_read.sum", 0.0) + m.get("dram__bytes_write.sum", 0.0)
-    doc = {"workload": f"{'x'.join(str(v) for v in SHAPE)} fit, timed fit of each capture",
-           "capture": list(commands),
-           "per_voxel_of": "reconstruction voxels (k_grad_hess_proj: acquisition voxels of one "
-                           "contrast, here the same count)",
-           "kernels": {}}
-    for kind, (n, b) in sorted(agg.items()):
-        doc["kernels"][kind] = {"launches": n, "dram_bytes_per_launch": int(b / n),
-                                "dram_bytes_per_voxel": round(b / n / n_vox, 3),
-                                "source_hash": kernel_source_hash(kind)}
+        for kind, (n, b) in agg.items():
+            captured = hashes["kernel_source_hashes"].get(kind)
+            if captured != kernel_source_hash(kind):
+                raise ValueError(f"{path}: {kind} was captured from sources {captured}, "
+                                 f"now {kernel_source_hash(kind)}")
+            doc["kernels"][kind] = {"launches": n, "voxels": n_vox,
+                                    "dram_bytes_per_launch": int(b / n),
+                                    "dram_bytes_per_voxel": round(b / n / n_vox, 3),
+                                    "source_hash": captured}
+    doc["kernels"] = dict(sorted(doc["kernels"].items()))
     with open(out, "w") as f:
         json.dump(doc, f, indent=1)
     return doc
+
+
+def print_source_hashes():
+    """One JSON line on stderr naming the source hash of every kernel kind
+    (read back from ncu logs by --write-traffic)."""
+    print(json.dumps({"kernel_source_hashes": {k: kernel_source_hash(k) for k in KIND_SOURCES}}),
+          file=sys.stderr, flush=True)
 
 
 # ---------------------------------------------------------- CPU oracle
@@ -610,7 +660,11 @@ def run_ours(args):
                 "frac": dk.get("frac_of_measured_hbm"), "traffic": traffic,
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
                 else "fallback 6.8 TB/s",
-                "share_of_step": round(dk["ms_total"] / (1000 * seconds), 3)}
+                "share_of_step": round(dk["ms_total"] / (1000 * seconds), 3),
+                "traffic_source": "ncu DRAM bytes of the kernel at "
+                                  f"{'x'.join(str(v) for v in TRAFFIC_SHAPE)} (profiles/dram_traffic.json), "
+                                  "scaled by the voxel count" if traffic is not None else
+                                  "no capture of the current kernel sources"}
     cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline(args.seed)
     line = {
         "metric": METRIC, "value": round(value / 1e6, 3), "unit": UNIT, "n_gpus": world,
@@ -1067,15 +1121,17 @@ def run_served(args):
 def main(argv=None):
     args = parse_args(argv)
     if args.write_traffic:
-        doc = write_traffic(args.write_traffic[0],
-                            args.write_traffic[1] if len(args.write_traffic) > 1 else None,
-                            commands=TRAFFIC_COMMANDS)
-        print(launch_table(last_fit(read_ncu_csv(args.write_traffic[0]))))
+        doc = write_traffic(args.write_traffic, commands=TRAFFIC_COMMANDS)
         for kind, k in doc["kernels"].items():
             print(f"{kind:16s} {k['launches']:5d} launches {k['dram_bytes_per_voxel']:9.3f} B/voxel")
         return 0
+    if args.launch_table:
+        print(launch_table(read_ncu_csv(args.launch_table)))
+        return 0
     if args.impl == "reference":
         return run_reference(args)
+    if args.print_hashes:
+        print_source_hashes()
     if args.workload == "batched":
         return run_batched(args)
     if args.workload == "served":

@@ -220,17 +220,18 @@ mpm_status mpm_fit(const mpm_problem* problem, const mpm_opts* opts, const void*
                    const float* b1p, const float* b1m, float* y_inout, float* var_out,
                    void* ws, size_t ws_bytes, mpm_report* report, void* stream);
 
-/* Tile-shape autotuner for the stencil matvec of the solve.  The TMA-staged
- * matvec can tile the (x, y) plane as 16 x 16, 32 x 8 or 64 x 4 voxels; this
+/* Tile-shape autotuner for the PCG iteration kernel of the solve.  The
+ * TMA-staged iteration can tile the (x, y) plane as 16 x 16, 32 x 8 or
+ * 64 x 4 voxels; this
  * call times each applicable shape on this volume (zeroed operands in `ws`, a
  * MPM_CALL_SOLVE-sized workspace or larger), keeps the fastest for every later
  * solve of a volume of this size in the process, and writes its index to
- * *tile (-1 when the TMA matvec does not apply: nx not a multiple of 4, or the
+ * *tile (-1 when the TMA kernel does not apply: nx not a multiple of 4, or the
  * volume smaller than a tile) and the mean time per launch of each shape to
  * ms[0..MPM_TILE_SHAPES-1] (-1 for shapes that do not apply; may be NULL).
  * If *tile >= 0 on entry, that shape is recorded without timing (ws may then
  * be NULL).  Without either, a default shape is used.  A shape that does not
- * fit a volume falls back to the shared-memory matvec.  Synchronises
+ * fit a volume falls back to the plain iteration kernel.  Synchronises
  * `stream` when timing. */
 #define MPM_TILE_SHAPES 3
 mpm_status mpm_autotune(const mpm_problem* problem, const mpm_opts* opts, void* ws,
@@ -371,9 +372,22 @@ mpm_status mpm_server_destroy(mpm_server* server);
 /* Synchronises `stream` and returns MPM_ERR_NUMERIC if a kernel that used this
  * workspace recorded a failure since the workspace was last cleared (every
  * mpm_solve / mpm_fit clears it): a preconditioner block that is not positive
- * definite, a NaN in a reduction, or a bounded copy wait of the stencil matvec
+ * definite, a NaN in a reduction, or a bounded copy wait of the PCG iteration
  * that ran out (mpm_last_error() names which).  Otherwise MPM_OK. */
 mpm_status mpm_workspace_status(const void* ws, size_t ws_bytes, void* stream);
+
+/* Test hook for the bounded waits of the TMA-staged PCG iteration (the paper
+ * has no counterpart; tests use it to drive the timeout path without a
+ * fault).  withhold != 0: from the next launch on, the iteration's producer
+ * issues no copies, so every copy wait of its compute warps runs out.
+ * wait_us > 0 sets the bound of every such wait (converted to clock cycles
+ * at the current device's clock rate); 0 restores the default of about 2 s.
+ * A launch whose wait ran out skips its work, drains its own copies, records
+ * the failure in the workspace status (mpm_workspace_status reports
+ * MPM_ERR_NUMERIC, "copy wait timed out") and returns; the solve then stops
+ * without a step.  Process-wide.  Returns MPM_ERR_INVALID_ARG for
+ * wait_us < 0. */
+mpm_status mpm_test_copy_timeout(int withhold, double wait_us);
 
 /* Diagnostic: number of kernels this library has launched in this process. */
 unsigned long long mpm_kernel_launches(void);
@@ -382,17 +396,15 @@ unsigned long long mpm_kernel_launches(void);
 enum {
     MPM_KERNEL_GRAD_HESS = 0,    /* fused voxel pass */
     MPM_KERNEL_JTV = 1,          /* JTV weights */
-    MPM_KERNEL_PCG_INIT = 2,     /* r0 = g + L y, preconditioner factor, z0 */
-    MPM_KERNEL_PCG_MATVEC = 3,   /* q = (H + L) p */
-    MPM_KERNEL_PCG_UPDATE = 4,   /* r update, z = M^-1 r */
-    MPM_KERNEL_PCG_FINAL = 5,    /* delta or y update */
-    MPM_KERNEL_UNCERTAINTY = 6,
-    MPM_KERNEL_FORWARD = 7,
-    MPM_KERNEL_INIT = 8,         /* image means and constant maps */
-    MPM_KERNEL_PCG_DIRECTION = 9, /* p = z + beta p, x += alpha p */
-    MPM_KERNEL_GRAD_HESS_PROJ = 10, /* projected voxel pass, one contrast */
-    MPM_KERNEL_RESLICE = 11,     /* pull / push of the spatial projection */
-    MPM_KERNEL_KINDS = 12
+    MPM_KERNEL_PCG_INIT = 2,     /* r0 = g + L y, z0 = M^-1 r0 */
+    MPM_KERNEL_PCG_STEP = 3,     /* one PCG iteration: z, p, q = (H + L) p, v = M^-1 q, x */
+    MPM_KERNEL_PCG_FINAL = 4,    /* delta or y update */
+    MPM_KERNEL_UNCERTAINTY = 5,
+    MPM_KERNEL_FORWARD = 6,
+    MPM_KERNEL_INIT = 7,         /* image means and constant maps */
+    MPM_KERNEL_GRAD_HESS_PROJ = 8, /* projected voxel pass, one contrast */
+    MPM_KERNEL_RESLICE = 9,      /* pull / push of the spatial projection */
+    MPM_KERNEL_KINDS = 10
 };
 
 /* Diagnostic timing.  While enabled (on != 0, process-wide), every kernel

@@ -19,7 +19,7 @@ from ._lib import MPMError, Opts, Problem, Projection, Report
 __all__ = [
     "make_problem", "make_opts", "workspace", "mpm_workspace_size", "mpm_forward",
     "mpm_grad_hess", "mpm_jtv_weights", "mpm_solve", "mpm_uncertainty", "mpm_fit", "mpm_fit_batch",
-    "mpm_workspace_status", "mpm_autotune", "mpm_kernel_launches", "mpm_profile_enable", "mpm_profile_read",
+    "mpm_workspace_status", "mpm_autotune", "mpm_test_copy_timeout", "mpm_kernel_launches", "mpm_profile_enable", "mpm_profile_read",
     "MPMError", "Problem", "Opts", "Report", "Server",
     "Projection", "make_projection", "mpm_workspace_size_proj", "workspace_proj", "mpm_pull",
     "mpm_push", "mpm_grad_hess_proj", "mpm_fit_proj",
@@ -433,6 +433,13 @@ class Server:
 def mpm_workspace_status(ws, stream=None) -> int:
     lib = _lib.load()
     return lib.mpm_workspace_status(_ptr(ws, "ws"), ws.numel(), _stream(stream))
+
+
+def mpm_test_copy_timeout(withhold: bool, wait_us: float = 0.0) -> None:
+    """Test hook: the TMA PCG iteration's producer withholds its copies and
+    every copy wait gives up after ``wait_us`` microseconds (0: default)."""
+    _lib.check(_lib.load().mpm_test_copy_timeout(1 if withhold else 0, float(wait_us)),
+               "mpm_test_copy_timeout")
 
 
 def mpm_kernel_launches() -> int:

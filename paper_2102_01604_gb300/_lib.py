@@ -116,14 +116,15 @@ PROTOTYPES = {
     "mpm_server_destroy": (ctypes.c_int, [_V]),
     "mpm_autotune": (ctypes.c_int, [_P, _O, _V, _S, _V, ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_float)]),
+    "mpm_test_copy_timeout": (ctypes.c_int, [ctypes.c_int, ctypes.c_double]),
     "mpm_kernel_launches": (ctypes.c_ulonglong, []),
     "mpm_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "mpm_profile_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int]),
 }
 
-KERNEL_KINDS = ["grad_hess", "jtv", "pcg_init", "pcg_matvec", "pcg_update", "pcg_final",
-                "uncertainty", "forward", "init", "pcg_direction", "grad_hess_proj", "reslice"]
+KERNEL_KINDS = ["grad_hess", "jtv", "pcg_init", "pcg_step", "pcg_final", "uncertainty",
+                "forward", "init", "grad_hess_proj", "reslice"]
 
 _handle = None
 

@@ -51,11 +51,11 @@ enum : unsigned { kStatusNotPD = 1u, kStatusNaN = 2u, kStatusTimeout = 4u };
 
 // Device scalars of one PCG solve (lives in the workspace).
 struct SolveScalars {
-    double rz;        // r . z of the current residual
+    double rz;        // r . z of the next residual (expanded, pcg_step.cuh)
     double rr0;       // |r_0|^2
     double rr;        // |r_k|^2 of the current residual
-    double alpha;     // step of the latest completed matvec
-    double alpha_prev;  // step of the matvec before it
+    double alpha;     // step of the latest completed iteration
+    double alpha_prev;  // step of the iteration before it
     double beta;      // coefficient of the next direction update
     double tol2;      // (tol_cg)^2, 0 = off
     int it;           // PCG iterations completed

@@ -1,7 +1,7 @@
 // host_logic.h -- host-side decisions of the library that make no CUDA call:
 // the server's device arena and admission pick, the GPU-load rule shared by
 // the server and the batched graph, the lanes of a batched graph, and the z
-// split of the TMA matvec.  Plain C++17, so the CPU tests compile and check it directly.
+// split of the TMA PCG iteration.  Plain C++17, so the CPU tests compile and check it directly.
 #pragma once
 
 #include <algorithm>
@@ -143,7 +143,7 @@ inline std::vector<std::vector<int>> lane_plan(const std::vector<long long>& vox
     return lanes;
 }
 
-// Number of z ranges of the TMA matvec: the launch is one wave of `wave`
+// Number of z ranges of the TMA PCG iteration: the launch is one wave of `wave`
 // resident blocks over tiles x nchunk items, block b taking items b, b + G,
 // ...; nchunk minimises rounds x (planes per item + 2), so that the last
 // round leaves few slots idle and items stay long enough that their two halo

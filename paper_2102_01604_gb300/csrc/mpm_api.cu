@@ -749,6 +749,22 @@ const char* mpm_last_error(void) { return t_err.c_str(); }
 
 unsigned long long mpm_kernel_launches(void) { return g_launches.load(); }
 
+mpm_status mpm_test_copy_timeout(int withhold, double wait_us)
+{
+    if (!(wait_us >= 0.0) || !std::isfinite(wait_us))
+        return fail(MPM_ERR_INVALID_ARG, "wait_us must be finite and >= 0");
+    long long cycles = 0;
+    if (wait_us > 0.0) {
+        int dev = 0, khz = 0;
+        MPM_CUDA(cudaGetDevice(&dev));
+        MPM_CUDA(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev));
+        cycles = (long long)(wait_us * 1e-3 * (double)khz);
+        if (cycles < 1) cycles = 1;
+    }
+    set_copy_test(withhold, cycles);
+    return MPM_OK;
+}
+
 mpm_status mpm_profile_enable(int on)
 {
     g_prof_on.store(on != 0);

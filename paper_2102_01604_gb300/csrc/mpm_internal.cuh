@@ -8,6 +8,7 @@
 
 #include "device_common.cuh"
 #include "host_logic.h"
+#include "pcg_step.cuh"
 
 namespace mpm {
 
@@ -15,7 +16,7 @@ namespace mpm {
 
 struct StencilGrid {
     dim3 grid, block;
-    int zc;           // z planes per block (TMA matvec: number of z ranges)
+    int zc;           // z planes per block (TMA iteration: number of z ranges)
 };
 
 StencilGrid stencil_grid(const DevProblem& P, int tile_x, int tile_y);
@@ -59,34 +60,41 @@ cudaError_t launch_solve(const DevProblem& P, int cg_iters, double tol_cg, const
                          cudaStream_t st);
 size_t solve_ws_bytes(const DevProblem& P);
 
-// TMA-staged stencil matvec (stencil_tma.cu).  make_tma_maps returns false
+// TMA-staged PCG iteration (stencil_tma.cu).  make_step_maps returns false
 // when the volume or the pointers do not meet the copy engine's alignment
-// rules; the shared-memory kernel is used then.
-struct TmaMaps {
-    CUtensorMap p[2], w, h;
+// rules; the plain kernel is used then.
+struct StepMaps {
+    CUtensorMap z[2], v[2], p[3];   // halo boxes of the solve buffers
+    CUtensorMap p2[3], x;           // tile boxes (x fold)
+    CUtensorMap w, h;
+    SolveBufs B;
+    float* xacc;
     int tile;          // index of the tile shape the maps were encoded for
 };
 int tma_tile_count();
-bool make_tma_maps(const DevProblem& P, const float* h, const float* w, const float* p0,
-                   const float* p1, int tile, TmaMaps* out);
+bool make_step_maps(const DevProblem& P, const float* h, const float* w, const SolveBufs& B,
+                    float* xacc, int tile, StepMaps* out);
 StencilGrid tma_grid(const DevProblem& P, int tile);
 cudaError_t prime_tma_kernels();   // shared-memory opt-ins, done before any graph capture
 int tma_tile_choice(const DevProblem& P);   // tile shape for this volume (tuned or default)
 void tma_tile_set(const DevProblem& P, int tile);
-// Times every applicable tile shape of the TMA matvec on this volume (operands
-// taken from the solve workspace, zeroed), records the fastest for later
-// solves and returns it (-1 when TMA does not apply); ms[i] receives the mean
-// time of shape i (or -1).  Synchronises the stream.
+// Times every applicable tile shape of the TMA iteration on this volume
+// (operands taken from the solve workspace, zeroed), records the fastest for
+// later solves and returns it (-1 when TMA does not apply); ms[i] receives
+// the mean time of shape i (or -1).  Synchronises the stream.
 cudaError_t tma_autotune(const DevProblem& P, void* solve_ws, WsHeader* hdr, Reduce red,
                          cudaStream_t st, int* best, float* ms);
-cudaError_t launch_matvec_tma(const DevProblem& P, const StencilGrid& g, const TmaMaps& m,
-                              int k_it, float* q, WsHeader* hdr, Reduce red, cudaStream_t st);
+cudaError_t launch_step_tma(const DevProblem& P, const StencilGrid& g, const StepMaps& m, int j,
+                            int flags, WsHeader* hdr, double* resid, Reduce red, cudaStream_t st);
+// Test hook: with withhold set, the TMA iteration's producer issues no copies;
+// every bounded wait gives up after wait_cycles clock cycles (<= 0: default).
+void set_copy_test(int withhold, long long wait_cycles);
 
 // ------------------------------------------- host helpers of the entry points
 // (mpm_api.cu)
 
 constexpr size_t kHeaderBytes = 4096;                              // WsHeader, padded
-constexpr size_t kPartialBytes = sizeof(double) * 2 * kMaxBlocks;  // reduction partials
+constexpr size_t kPartialBytes = sizeof(double) * 8 * kMaxBlocks;  // reduction partials (8 sums)
 
 // Carving of a fit / solve workspace (mpm_api.cu).
 struct FitWs {

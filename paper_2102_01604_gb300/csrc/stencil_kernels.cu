@@ -1,11 +1,11 @@
 // stencil_kernels.cu -- the prior and the Newton-system solve (sm_103a):
 //   k_jtv          JTV weights w_n = (u_n + eps^2)^-1/2 and JTV_eps (Eqs. 38-40)
-//   k_pcg_init     r_0 = g + L y, preconditioner factor, p_0 = z_0 = M^-1 r_0 (Eq. 42)
-//   k_pcg_direction p_k = z_k + beta p_{k-1}; every other k also
-//                  x += alpha_{k-2} p_{k-2} + alpha_{k-1} p_{k-1}
-//   k_pcg_matvec   q = (H + L) p_k; p.q
-//   k_pcg_update   r -= alpha q; z = M^-1 r; r.z, r.r
-//   k_pcg_final    delta = x + alpha p (or y <- y - delta)
+//   k_pcg_init     r_0 = g + L y, z_0 = M^-1 r_0 (Eq. 42)
+//   k_pcg_step     one PCG iteration (pcg_step.cuh): z_j, p_j from the previous
+//                  iteration, q = (H + L) p_j, v = M^-1 q, the x fold and the
+//                  sums for alpha_j and beta_j -- the plain kernel used when the
+//                  TMA-staged one (stencil_tma.cu) does not apply
+//   k_pcg_final    delta = x + pending directions (or y <- y - delta)
 //
 // L = G'WG (x) diag(lambda) is applied as the 7-point weighted stencil
 //   (L v)_k[n] = lambda_k sum_{m in N(n)} (w_n + w_m)(v_k[n] - v_k[m]) / h^2,
@@ -13,9 +13,8 @@
 // (x, y) tile and march along z.  All CG scalars (alpha, beta, |r|) live in
 // device memory and are produced by the last block of each reducing launch,
 // so the whole PCG runs without a host round trip.
-#include <type_traits>
-
 #include "mpm_internal.cuh"
+#include "pcg_step.cuh"
 
 namespace mpm {
 
@@ -112,75 +111,14 @@ __global__ void __launch_bounds__(kBlock) k_jtv(DevProblem P, int zc, const floa
     if (grid_reduce<1>(v, red, out) && threadIdx.x == 0 && threadIdx.y == 0) *jtv = out[0];
 }
 
-// ------------------------------------------------ preconditioner helpers
-
-// Lower Cholesky factor of the K x K block, packed row by row
-// (00, 10, 11, 20, 21, 22, 30, 31, 32, 33) with reciprocal diagonal.
-__host__ __device__ constexpr int lo(int i, int j) { return i * (i + 1) / 2 + j; }
-
-template <int K>
-__device__ __forceinline__ bool cholesky_f32(const float (&M)[K][K], float (&L)[K * (K + 1) / 2])
-{
-    bool ok = true;
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-        float s = M[j][j];
-#pragma unroll
-        for (int k = 0; k < j; ++k) s -= L[lo(j, k)] * L[lo(j, k)];
-        if (!(s > 0.0f)) {
-            ok = false;
-            s = fmaxf(fabsf(M[j][j]), 1e-30f);
-        }
-        const float dj = sqrtf(s);
-        L[lo(j, j)] = 1.0f / dj;
-#pragma unroll
-        for (int i = j + 1; i < K; ++i) {
-            float v = M[i][j];
-#pragma unroll
-            for (int k = 0; k < j; ++k) v -= L[lo(i, k)] * L[lo(j, k)];
-            L[lo(i, j)] = v / dj;
-        }
-    }
-    return ok;
-}
-
-// z = (L L')^-1 r with the packed factor.
-template <int K>
-__device__ __forceinline__ void chol_apply(const float (&L)[K * (K + 1) / 2], const float (&r)[K],
-                                           float (&z)[K])
-{
-    float t[K];
-#pragma unroll
-    for (int i = 0; i < K; ++i) {
-        float v = r[i];
-#pragma unroll
-        for (int k = 0; k < i; ++k) v -= L[lo(i, k)] * t[k];
-        t[i] = v * L[lo(i, i)];
-    }
-#pragma unroll
-    for (int i = K - 1; i >= 0; --i) {
-        float v = t[i];
-#pragma unroll
-        for (int k = i + 1; k < K; ++k) v -= L[lo(k, i)] * z[k];
-        z[i] = v * L[lo(i, i)];
-    }
-}
-
-// Per-solve workspace layout (all [.][N] float, 256-byte aligned).
-struct SolveBufs {
-    float* R;       // [T][N] preconditioner factor
-    float* r;       // [K][N]
-    float* z;       // [K][N]
-    float* p[2];    // [K][N] directions, p_k in p[k & 1]
-    float* q;       // [K][N]
-};
+// ------------------------------------------------------ solve workspace
 
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 size_t solve_ws_bytes(const DevProblem& P)
 {
     const size_t vec = align256(sizeof(float) * (size_t)P.K * P.N);
-    return align256(sizeof(float) * (size_t)P.T * P.N) + 5 * vec;
+    return 7 * vec;
 }
 
 static SolveBufs carve(const DevProblem& P, void* ws)
@@ -188,13 +126,9 @@ static SolveBufs carve(const DevProblem& P, void* ws)
     SolveBufs b;
     char* c = static_cast<char*>(ws);
     const size_t vec = align256(sizeof(float) * (size_t)P.K * P.N);
-    b.R = reinterpret_cast<float*>(c);
-    c += align256(sizeof(float) * (size_t)P.T * P.N);
-    b.r = reinterpret_cast<float*>(c); c += vec;
-    b.z = reinterpret_cast<float*>(c); c += vec;
-    b.p[0] = reinterpret_cast<float*>(c); c += vec;
-    b.p[1] = reinterpret_cast<float*>(c); c += vec;
-    b.q = reinterpret_cast<float*>(c);
+    for (float*& v : b.z) { v = reinterpret_cast<float*>(c); c += vec; }
+    for (float*& v : b.v) { v = reinterpret_cast<float*>(c); c += vec; }
+    for (float*& v : b.p) { v = reinterpret_cast<float*>(c); c += vec; }
     return b;
 }
 
@@ -204,7 +138,7 @@ template <int K>
 __global__ void __launch_bounds__(kBlock) k_pcg_init(DevProblem P, int zc, const float* __restrict__ h,
                                                      const float* __restrict__ w,
                                                      const float* __restrict__ g,
-                                                     const float* __restrict__ y, SolveBufs B,
+                                                     const float* __restrict__ y, float* __restrict__ z0,
                                                      double tol2, WsHeader* hdr, double* resid,
                                                      Reduce red)
 {
@@ -213,20 +147,17 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(DevProblem P, int zc, const
     const long long sxy = (long long)P.nx * P.ny;
     const int x = blockIdx.x * kTileX + threadIdx.x;
     const int yy = blockIdx.y * kTileY + threadIdx.y;
-    const int z0 = blockIdx.z * zc;
-    const int z1 = min(P.nz, z0 + zc);
+    const int z0p = blockIdx.z * zc;
+    const int z1p = min(P.nz, z0p + zc);
     Acc rz, rr;
     bool pd = true;
     if (x < P.nx && yy < P.ny) {
-        for (int z = z0; z < z1; ++z) {
+        for (int z = z0p; z < z1p; ++z) {
             const long long n = x + (long long)P.nx * yy + sxy * z;
             const float wn = __ldg(w + n);
             Edges e;
             make_edges(P, x, yy, z, n, w, wn, e);
-            float d = 0.0f;
-#pragma unroll
-            for (int j = 0; j < 6; ++j) d += e.c[j];
-            float r[K], M[K][K];
+            float r[K];
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 const float* yk = y + k * N;
@@ -237,22 +168,17 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(DevProblem P, int zc, const
                     if (e.ok[j]) s += e.c[j] * (v - __ldg(yk + n + e.off[j]));
                 r[k] = __ldg(g + k * N + n) + P.lambda[k] * s;
             }
+            float hv[T], M[K][K];
 #pragma unroll
-            for (int a = 0; a < K; ++a)
-#pragma unroll
-                for (int b = a; b < K; ++b) M[a][b] = M[b][a] = __ldg(h + tri(K, a, b) * N + n);
-#pragma unroll
-            for (int a = 0; a < K; ++a) M[a][a] += P.lambda[a] * d;
+            for (int t = 0; t < T; ++t) hv[t] = __ldg(h + t * N + n);
+            precond_block<K>(P, hv, edge_sum(e.c), M);
             float L[T], zz[K];
             pd &= cholesky_f32<K>(M, L);
             chol_apply<K>(L, r, zz);
-#pragma unroll
-            for (int k = 0; k < T; ++k) B.R[k * N + n] = L[k];
             float vrz = 0.0f, vrr = 0.0f;
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                B.r[k * N + n] = r[k];
-                B.p[0][k * N + n] = zz[k];                // p_0 = z_0 (z_0 itself is never read again)
+                z0[k * N + n] = zz[k];
                 vrz += r[k] * zz[k];
                 vrr += r[k] * r[k];
             }
@@ -281,326 +207,106 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(DevProblem P, int zc, const
     }
 }
 
-// ---------------------------------------------------------- PCG direction
+// -------------------------------------------------------- PCG iteration
 
-// p_k = z_k + beta_{k-1} p_{k-1} (k >= 1), a streaming pass over the K*N
-// entries (float4 when VPT = 4).  x is brought up to date only at even k:
-// x += alpha_{k-2} p_{k-2} + alpha_{k-1} p_{k-1}, with p_{k-2} read from the
-// buffer that p_k is about to replace.  The two additions happen in the order
-// of two single updates (bit for bit the same x); the odd passes skip x, which
-// saves reading and writing it every other iteration.
-template <int VPT>
-__global__ void __launch_bounds__(kBlock) k_pcg_direction(long long total, int k_it,
-                                                          const float* __restrict__ zv,
-                                                          const float* __restrict__ pold,
-                                                          float* __restrict__ pnew,
-                                                          float* __restrict__ xacc,
-                                                          WsHeader* hdr)
+// Plain form of one PCG iteration (pcg_step.cuh): a thread per (x, y) column
+// marching a run of z planes; each neighbour's p_j is formed from its own
+// (z, v, p) read from memory.  Used for volumes or pointers the TMA kernel
+// cannot take (nx not a multiple of 4, a volume smaller than a tile).
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_pcg_step(DevProblem P, int zc, int j, int flags,
+                                                     const float* __restrict__ h,
+                                                     const float* __restrict__ w,
+                                                     const float* __restrict__ zin,
+                                                     const float* __restrict__ vin,
+                                                     const float* __restrict__ pin,
+                                                     const float* __restrict__ p2,
+                                                     float* __restrict__ zout, float* __restrict__ vout,
+                                                     float* __restrict__ pout, float* __restrict__ xacc,
+                                                     WsHeader* hdr, double* resid, Reduce red)
 {
-    using V = typename std::conditional<VPT == 4, float4, float>::type;
-    __shared__ float s_beta, s_alpha, s_alpha_prev;
+    constexpr int T = K * (K + 1) / 2;
+    __shared__ float s_alpha, s_alpha_prev, s_beta;
     __shared__ int s_done;
-    if (threadIdx.x == 0) {
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    if (tid == 0) {
         s_done = hdr->sc.done;
-        s_beta = (float)hdr->sc.beta;
         s_alpha = (float)hdr->sc.alpha;
         s_alpha_prev = (float)hdr->sc.alpha_prev;
+        s_beta = (float)hdr->sc.beta;
     }
     __syncthreads();
     if (s_done) return;
-    const bool fold = (k_it & 1) == 0;                  // x update at even k (k >= 2)
-    if (fold && blockIdx.x == 0 && threadIdx.x == 0) hdr->sc.xcount = k_it;
-    const float beta = s_beta, alpha = s_alpha, alpha_prev = s_alpha_prev;
-    const long long nv = total / VPT;
-    const V* __restrict__ z4 = reinterpret_cast<const V*>(zv);
-    const V* __restrict__ o4 = reinterpret_cast<const V*>(pold);
-    V* __restrict__ p4 = reinterpret_cast<V*>(pnew);
-    V* __restrict__ x4 = reinterpret_cast<V*>(xacc);
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nv;
-         i += (long long)gridDim.x * blockDim.x) {
-        const V zz = __ldg(z4 + i);
-        const V o = __ldg(o4 + i);
-        V pv;
-        if (fold) {
-            const V o2 = p4[i];                             // p_{k-2}, before it is replaced
-            V xo;
-            if (k_it > 2) xo = x4[i];
-            V xv;
-#pragma unroll
-            for (int j = 0; j < VPT; ++j) {
-                const float oj = reinterpret_cast<const float*>(&o)[j];
-                const float xj = k_it > 2 ? reinterpret_cast<const float*>(&xo)[j] : 0.0f;
-                const float t = fmaf(alpha_prev, reinterpret_cast<const float*>(&o2)[j], xj);
-                reinterpret_cast<float*>(&xv)[j] = fmaf(alpha, oj, t);
-                reinterpret_cast<float*>(&pv)[j] = fmaf(beta, oj, reinterpret_cast<const float*>(&zz)[j]);
-            }
-            x4[i] = xv;
-        } else {
-#pragma unroll
-            for (int j = 0; j < VPT; ++j)
-                reinterpret_cast<float*>(&pv)[j] =
-                    fmaf(beta, reinterpret_cast<const float*>(&o)[j], reinterpret_cast<const float*>(&zz)[j]);
-        }
-        p4[i] = pv;
-    }
-}
-
-// ------------------------------------------------------------- PCG matvec
-
-// q = (H + L) p with p already formed.  Tiled 2.5-D stencil: a block owns a
-// kMvX x kMvY (x, y) tile and marches up a run of z planes; the current plane
-// of p (with a one-voxel x / y halo) and of the JTV weights is staged in
-// shared memory, the planes below and above live in registers, so each
-// operand is read from memory about once per voxel.
-constexpr int kMvX = 16, kMvY = 16;
-
-template <int K>
-__global__ void __launch_bounds__(kMvX * kMvY, 3) k_pcg_matvec(DevProblem P, int zc, int k_it,
-                                                              const float* __restrict__ h,
-                                                              const float* __restrict__ w,
-                                                              const float* __restrict__ pin,
-                                                              float* __restrict__ qout,
-                                                              WsHeader* hdr, Reduce red)
-{
-    constexpr int T = K * (K + 1) / 2;
-    __shared__ float sp[K][kMvY + 2][kMvX + 2];
-    __shared__ float sw[kMvY + 2][kMvX + 2];
-    __shared__ int s_done;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int tid = tx + ty * kMvX;
-    if (tid == 0) s_done = hdr->sc.done;
-    __syncthreads();
-    if (s_done) return;
+    const bool first = flags & kStepFirst, fold = flags & kStepFold, readx = flags & kStepReadX;
+    const bool want_rr = flags & kStepResid;
+    if (fold && tid == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) hdr->sc.xcount = j;
+    const float alpha = s_alpha, alpha_prev = s_alpha_prev, beta = s_beta;
     const long long N = P.N;
-    const int nx = P.nx, ny = P.ny, nz = P.nz;
-    const long long sxy = (long long)nx * ny;
-    const int x = blockIdx.x * kMvX + tx;
-    const int y = blockIdx.y * kMvY + ty;
-    const int z0 = blockIdx.z * zc;
-    const int z1 = min(nz, z0 + zc);
-    const bool inside = x < nx && y < ny;
-    // Halo roles: border threads of the tile also load the neighbour just
-    // outside it (one plane ahead, so the loads overlap the compute).
-    const bool hx = inside && ((tx == 0 && x > 0) || (tx == kMvX - 1 && x + 1 < nx));
-    const bool hy = inside && ((ty == 0 && y > 0) || (ty == kMvY - 1 && y + 1 < ny));
-    const long long ox = tx == 0 ? -1 : 1;
-    const long long oy = ty == 0 ? -(long long)nx : (long long)nx;
-    const int sx = tx == 0 ? 0 : kMvX + 1;
-    const int sy = ty == 0 ? 0 : kMvY + 1;
-
-    const long long col = (long long)x + (long long)nx * y;   // (x, y) column offset
-    float pc[K], pp[K], pn[K], hxv[K + 1], hyv[K + 1];
-    float wc = 0.f, wp = 0.f, wn = 0.f;
-    auto load_halo = [&](long long n) {
-        if (hx) {
+    const long long sxy = (long long)P.nx * P.ny;
+    const int x = blockIdx.x * kTileX + threadIdx.x;
+    const int yy = blockIdx.y * kTileY + threadIdx.y;
+    const int z0p = blockIdx.z * zc;
+    const int z1p = min(P.nz, z0p + zc);
+    Acc acc[kStepSums];
+    auto point = [&](long long m, float (&zj)[K], float (&pj)[K]) {
+        float zz[K], vv[K], pp[K];
 #pragma unroll
-            for (int k = 0; k < K; ++k) hxv[k] = __ldg(pin + k * N + n + ox);
-            hxv[K] = __ldg(w + n + ox);
+        for (int a = 0; a < K; ++a) {
+            zz[a] = __ldg(zin + a * N + m);
+            vv[a] = first ? 0.0f : __ldg(vin + a * N + m);
+            pp[a] = first ? 0.0f : __ldg(pin + a * N + m);
         }
-        if (hy) {
-#pragma unroll
-            for (int k = 0; k < K; ++k) hyv[k] = __ldg(pin + k * N + n + oy);
-            hyv[K] = __ldg(w + n + oy);
-        }
+        step_point<K>(first, alpha, beta, zz, vv, pp, zj, pj);
     };
-    if (inside) {
-        const long long n0 = col + sxy * z0;
+    if (x < P.nx && yy < P.ny) {
+        for (int z = z0p; z < z1p; ++z) {
+            const long long n = x + (long long)P.nx * yy + sxy * z;
+            const float wn = __ldg(w + n);
+            Edges e;
+            make_edges(P, x, yy, z, n, w, wn, e);
+            float zj[K], pj[K], nb[6][K];
+            point(n, zj, pj);
 #pragma unroll
-        for (int k = 0; k < K; ++k) pc[k] = __ldg(pin + k * N + n0);
-        wc = __ldg(w + n0);
-        load_halo(n0);
-        if (z0 > 0) {
+            for (int m = 0; m < 6; ++m) {
+                float zm[K];
+                if (e.ok[m]) {
+                    point(n + e.off[m], zm, nb[m]);
+                } else {
 #pragma unroll
-            for (int k = 0; k < K; ++k) pp[k] = __ldg(pin + k * N + n0 - sxy);
-            wp = __ldg(w + n0 - sxy);
-        }
-        if (z0 + 1 < nz) {
-#pragma unroll
-            for (int k = 0; k < K; ++k) pn[k] = __ldg(pin + k * N + n0 + sxy);
-            wn = __ldg(w + n0 + sxy);
-        }
-    }
-    float Hnext[T];
-    if (inside) {
-        const long long n0 = col + sxy * z0;
-#pragma unroll
-        for (int t = 0; t < T; ++t) Hnext[t] = __ldg(h + t * N + n0);
-    }
-    Acc pq;
-    for (int z = z0; z < z1; ++z) {
-        const long long n = col + sxy * z;
-        float Hn[T];
-#pragma unroll
-        for (int t = 0; t < T; ++t) Hn[t] = Hnext[t];
-        // stage the current plane (own value and x / y halo) in shared memory
-        __syncthreads();
-        if (inside) {
-#pragma unroll
-            for (int k = 0; k < K; ++k) sp[k][ty + 1][tx + 1] = pc[k];
-            sw[ty + 1][tx + 1] = wc;
-            if (hx) {
-#pragma unroll
-                for (int k = 0; k < K; ++k) sp[k][ty + 1][sx] = hxv[k];
-                sw[ty + 1][sx] = hxv[K];
+                    for (int a = 0; a < K; ++a) nb[m][a] = pj[a];
+                }
             }
-            if (hy) {
+            float hv[T];
 #pragma unroll
-                for (int k = 0; k < K; ++k) sp[k][sy][tx + 1] = hyv[k];
-                sw[sy][tx + 1] = hyv[K];
-            }
-        }
-        __syncthreads();
-        if (inside) {
-            // prefetch the next plane's halo and the plane after it
-            const bool more = z + 1 < z1;
-            if (more) load_halo(n + sxy);
-            float pn_keep[K];
-#pragma unroll
-            for (int k = 0; k < K; ++k) pn_keep[k] = pn[k];
-            const float wn_keep = wn;
-            if (more) {
-#pragma unroll
-                for (int t = 0; t < T; ++t) Hnext[t] = __ldg(h + t * N + n + sxy);
-            }
-            if (more && z + 2 < nz) {
-                const long long n2 = n + 2 * sxy;
-#pragma unroll
-                for (int k = 0; k < K; ++k) pn[k] = __ldg(pin + k * N + n2);
-                wn = __ldg(w + n2);
-            }
-            // edge coefficients (w_n + w_m) / h^2 of the six neighbours
-            const bool okxm = x > 0, okxp = x + 1 < nx, okym = y > 0, okyp = y + 1 < ny;
-            const bool okzm = z > 0, okzp = z + 1 < nz;
-            const float cxm = okxm ? (wc + sw[ty + 1][tx]) * P.ihx2 : 0.f;
-            const float cxp = okxp ? (wc + sw[ty + 1][tx + 2]) * P.ihx2 : 0.f;
-            const float cym = okym ? (wc + sw[ty][tx + 1]) * P.ihy2 : 0.f;
-            const float cyp = okyp ? (wc + sw[ty + 2][tx + 1]) * P.ihy2 : 0.f;
-            const float czm = okzm ? (wc + wp) * P.ihz2 : 0.f;
-            const float czp = okzp ? (wc + wn_keep) * P.ihz2 : 0.f;
-            float vpq = 0.0f;
+            for (int t = 0; t < T; ++t) hv[t] = __ldg(h + t * N + n);
+            float v[K], sums[kStepSums];
+            step_voxel<K>(P, e.c, zj, pj, [&](int m, int a) { return nb[m][a]; }, hv, want_rr, v, sums);
 #pragma unroll
             for (int a = 0; a < K; ++a) {
-                const float v = pc[a];
-                float s = 0.f;
-                if (okxm) s += cxm * (v - sp[a][ty + 1][tx]);
-                if (okxp) s += cxp * (v - sp[a][ty + 1][tx + 2]);
-                if (okym) s += cym * (v - sp[a][ty][tx + 1]);
-                if (okyp) s += cyp * (v - sp[a][ty + 2][tx + 1]);
-                if (okzm) s += czm * (v - pp[a]);
-                if (okzp) s += czp * (v - pn_keep[a]);
-                float acc = P.lambda[a] * s;
-#pragma unroll
-                for (int b = 0; b < K; ++b) acc += Hn[a < b ? tri(K, a, b) : tri(K, b, a)] * pc[b];
-                qout[a * N + n] = acc;
-                vpq += v * acc;
+                if (!first) zout[a * N + n] = zj[a];
+                pout[a * N + n] = pj[a];
+                vout[a * N + n] = v[a];
             }
-            pq.add(vpq);
-            // march: the plane above becomes current
+            if (fold) {
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                pp[k] = pc[k];
-                pc[k] = pn_keep[k];
-            }
-            wp = wc;
-            wc = wn_keep;
-        }
-    }
-    Acc v[1] = {pq};
-    double out[1];
-    if (grid_reduce<1>(v, red, out) && tid == 0) {
-        SolveScalars& sc = hdr->sc;
-        if (!(out[0] == out[0])) atomicOr(&hdr->status, kStatusNaN);
-        if (!(out[0] > 0.0)) {
-            sc.done = 1;                 // no further step; the alphas keep their values
-        } else {
-            sc.alpha_prev = sc.alpha;
-            sc.alpha = sc.rz / out[0];
-        }
-    }
-}
-
-// ------------------------------------------------------------- PCG update
-
-// Streaming kernel: VPT consecutive voxels per thread (float4 loads when
-// VPT = 4), grid-stride over the volume.
-template <int K, int VPT>
-__global__ void __launch_bounds__(kBlock) k_pcg_update(DevProblem P, int k_it, SolveBufs B,
-                                                       WsHeader* hdr, double* resid, Reduce red)
-{
-    constexpr int T = K * (K + 1) / 2;
-    using V = typename std::conditional<VPT == 4, float4, float>::type;
-    __shared__ float s_alpha;
-    __shared__ int s_done;
-    if (threadIdx.x == 0) {
-        s_done = hdr->sc.done;
-        s_alpha = (float)hdr->sc.alpha;
-    }
-    __syncthreads();
-    if (s_done) return;
-    const float alpha = s_alpha;
-    const long long N = P.N;
-    const long long NV = N / VPT;           // vectors per map (N % VPT == 0)
-    const V* __restrict__ r4 = reinterpret_cast<const V*>(B.r);
-    const V* __restrict__ q4 = reinterpret_cast<const V*>(B.q);
-    const V* __restrict__ R4 = reinterpret_cast<const V*>(B.R);
-    V* __restrict__ rw = reinterpret_cast<V*>(B.r);
-    V* __restrict__ zw = reinterpret_cast<V*>(B.z);
-    Acc rz, rr;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < NV;
-         i += (long long)gridDim.x * blockDim.x) {
-        V rv[K], qv[K], Lv[T];
-#pragma unroll
-        for (int k = 0; k < K; ++k) rv[k] = r4[k * NV + i];
-#pragma unroll
-        for (int k = 0; k < K; ++k) qv[k] = __ldg(q4 + k * NV + i);
-#pragma unroll
-        for (int t = 0; t < T; ++t) Lv[t] = __ldg(R4 + t * NV + i);
-        V zo[K];
-#pragma unroll
-        for (int j = 0; j < VPT; ++j) {
-            float r[K], L[T], zz[K];
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                r[k] = reinterpret_cast<const float*>(&rv[k])[j] -
-                       alpha * reinterpret_cast<const float*>(&qv[k])[j];
-                reinterpret_cast<float*>(&rv[k])[j] = r[k];
+                for (int a = 0; a < K; ++a) {
+                    const float xo = readx ? xacc[a * N + n] : 0.0f;
+                    xacc[a * N + n] = fold_x(xo, alpha_prev, __ldg(p2 + a * N + n), alpha,
+                                             __ldg(pin + a * N + n));
+                }
             }
 #pragma unroll
-            for (int t = 0; t < T; ++t) L[t] = reinterpret_cast<const float*>(&Lv[t])[j];
-            chol_apply<K>(L, r, zz);
-            float vrz = 0.0f, vrr = 0.0f;
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                reinterpret_cast<float*>(&zo[k])[j] = zz[k];
-                vrz += r[k] * zz[k];
-                vrr += r[k] * r[k];
-            }
-            rz.add(vrz);
-            rr.add(vrr);
-        }
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            rw[k * NV + i] = rv[k];
-            zw[k * NV + i] = zo[k];
+            for (int i = 0; i < kStepSums; ++i) acc[i].add(sums[i]);
         }
     }
-    Acc v[2] = {rz, rr};
-    double out[2];
-    if (grid_reduce<2>(v, red, out) && threadIdx.x == 0) {
-        SolveScalars& sc = hdr->sc;
-        const bool bad = !(out[0] == out[0]) || !(out[1] == out[1]);
-        if (bad) atomicOr(&hdr->status, kStatusNaN);
-        sc.beta = out[0] / sc.rz;
-        sc.rz = out[0];
-        sc.rr = out[1];
-        sc.it = k_it + 1;
-        if (resid) resid[k_it + 1] = sqrt(out[1]);
-        if (bad || !(out[0] > 0.0) || (sc.tol2 > 0.0 && out[1] <= sc.tol2 * sc.rr0)) sc.done = 1;
-    }
+    double out[kStepSums];
+    if (grid_reduce<kStepSums>(acc, red, out) && tid == 0) step_scalars(out, j, want_rr, hdr, resid);
 }
 
 // -------------------------------------------------------------- PCG final
 
+// delta = x + the directions not yet folded into x (none, p_{it-1}, or
+// p_{it-2} and p_{it-1}), or y <- y - delta.
 __global__ void __launch_bounds__(kBlock) k_pcg_final(long long total, SolveBufs B,
                                                       const float* __restrict__ xacc,
                                                       float* __restrict__ delta,
@@ -612,8 +318,8 @@ __global__ void __launch_bounds__(kBlock) k_pcg_final(long long total, SolveBufs
     const bool have_x = sc.xcount > 0;
     const int pend = sc.it - sc.xcount;        // directions not yet in x: 0, 1 or 2
     const float alpha = (float)sc.alpha, alpha_prev = (float)sc.alpha_prev;
-    const float* __restrict__ pp = B.p[(sc.it - 1) & 1];
-    const float* __restrict__ pp2 = B.p[sc.it & 1];   // p_{it-2} when pend == 2
+    const float* __restrict__ pp = B.p[(sc.it + 2) % 3];    // p_{it-1}
+    const float* __restrict__ pp2 = B.p[(sc.it + 1) % 3];   // p_{it-2} when pend == 2
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
         float v = have_x ? xacc[i] : 0.0f;
@@ -631,25 +337,6 @@ __global__ void __launch_bounds__(kBlock) k_pcg_final(long long total, SolveBufs
 }
 
 // ------------------------------------------------------------- launchers
-
-// One wave of resident blocks for a grid-stride streaming kernel.
-template <int K, int VPT>
-static int update_grid(long long units)
-{
-    static int per_sm = 0;
-    if (per_sm == 0) {
-        int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pcg_update<K, VPT>, kBlock, 0) !=
-                cudaSuccess || b < 1)
-            b = 1;
-        per_sm = b;
-    }
-    long long g = (units + kBlock - 1) / kBlock;
-    const long long cap = (long long)per_sm * kNumSm;
-    if (g > cap) g = cap;
-    if (g < 1) g = 1;
-    return (int)g;
-}
 
 StencilGrid stencil_grid(const DevProblem& P, int tx, int ty)
 {
@@ -682,6 +369,17 @@ cudaError_t launch_jtv(const DevProblem& P, const float* y, float* w, double* jt
     return cudaGetLastError();
 }
 
+// Launch flags of iteration j of a solve of cg_iters iterations.
+static int step_flags(int j, int cg_iters, bool want_resid)
+{
+    int f = 0;
+    if (j == 0) f |= kStepFirst;
+    if (j >= 2 && j % 2 == 0) f |= kStepFold;
+    if (j > 2 && j % 2 == 0) f |= kStepReadX;
+    if (want_resid || j == cg_iters - 1) f |= kStepResid;
+    return f;
+}
+
 template <int K>
 static cudaError_t solve_k(const DevProblem& P, int cg_iters, double tol_cg, const float* h,
                            const float* w, const float* g, const float* y, float* delta,
@@ -696,45 +394,25 @@ static cudaError_t solve_k(const DevProblem& P, int cg_iters, double tol_cg, con
     const double tol2 = tol_cg > 0.0 ? tol_cg * tol_cg : 0.0;
     {
         LaunchScope ls(MPM_KERNEL_PCG_INIT, st);
-        k_pcg_init<K><<<sg.grid, sg.block, 0, st>>>(P, sg.zc, h, w, g, y, B, tol2, hdr, resid, red);
+        k_pcg_init<K><<<sg.grid, sg.block, 0, st>>>(P, sg.zc, h, w, g, y, B.z[0], tol2, hdr, resid, red);
     }
-    const StencilGrid mg = stencil_grid(P, kMvX, kMvY);
-    TmaMaps maps;
+    StepMaps maps;
     const int tile = tma_tile_choice(P);
-    const bool tma = tile >= 0 && make_tma_maps(P, h, w, B.p[0], B.p[1], tile, &maps);
-    const StencilGrid tg = tma ? tma_grid(P, tile) : mg;
-    // float4 streaming needs whole vectors per map and 16-byte aligned rows
-    const bool vec4 = (P.N % 4 == 0) &&
-                      ((reinterpret_cast<uintptr_t>(B.r) | reinterpret_cast<uintptr_t>(B.q) |
-                        reinterpret_cast<uintptr_t>(B.z) | reinterpret_cast<uintptr_t>(B.R) |
-                        reinterpret_cast<uintptr_t>(B.p[0]) | reinterpret_cast<uintptr_t>(B.p[1]) |
-                        reinterpret_cast<uintptr_t>(xacc)) % 16 == 0);
-    const int ugrid = vec4 ? update_grid<K, 4>(P.N / 4) : update_grid<K, 1>(P.N);
-    const long long KN = (long long)K * P.N;
-    const int dgrid = voxel_grid(vec4 ? KN / 4 : KN);
-    for (int k = 0; k < cg_iters; ++k) {
-        float* pk = B.p[k & 1];
-        if (k > 0) {
-            LaunchScope ls(MPM_KERNEL_PCG_DIRECTION, st);
-            if (vec4)
-                k_pcg_direction<4><<<dgrid, kBlock, 0, st>>>(KN, k, B.z, B.p[(k + 1) & 1], pk, xacc, hdr);
-            else
-                k_pcg_direction<1><<<dgrid, kBlock, 0, st>>>(KN, k, B.z, B.p[(k + 1) & 1], pk, xacc, hdr);
+    const bool tma = tile >= 0 && make_step_maps(P, h, w, B, xacc, tile, &maps);
+    const StencilGrid tg = tma ? tma_grid(P, tile) : sg;
+    const bool want_resid = resid != nullptr || tol2 > 0.0;
+    for (int j = 0; j < cg_iters; ++j) {
+        const int flags = step_flags(j, cg_iters, want_resid);
+        LaunchScope ls(MPM_KERNEL_PCG_STEP, st);
+        if (tma) {
+            cudaError_t e = launch_step_tma(P, tg, maps, j, flags, hdr, resid, red, st);
+            if (e != cudaSuccess) return e;
+        } else {
+            const int jm = j > 0 ? j - 1 : 0;
+            k_pcg_step<K><<<sg.grid, sg.block, 0, st>>>(
+                P, sg.zc, j, flags, h, w, B.z[jm & 1], B.v[jm & 1], B.p[(j + 2) % 3], B.p[(j + 1) % 3],
+                B.z[j & 1], B.v[j & 1], B.p[j % 3], xacc, hdr, resid, red);
         }
-        {
-            LaunchScope ls(MPM_KERNEL_PCG_MATVEC, st);
-            if (tma) {
-                cudaError_t e = launch_matvec_tma(P, tg, maps, k, B.q, hdr, red, st);
-                if (e != cudaSuccess) return e;
-            } else {
-                k_pcg_matvec<K><<<mg.grid, mg.block, 0, st>>>(P, mg.zc, k, h, w, pk, B.q, hdr, red);
-            }
-        }
-        LaunchScope ls(MPM_KERNEL_PCG_UPDATE, st);
-        if (vec4)
-            k_pcg_update<K, 4><<<ugrid, kBlock, 0, st>>>(P, k, B, hdr, resid, red);
-        else
-            k_pcg_update<K, 1><<<ugrid, kBlock, 0, st>>>(P, k, B, hdr, resid, red);
     }
     LaunchScope ls(MPM_KERNEL_PCG_FINAL, st);
     k_pcg_final<<<voxel_grid(P.N * K), kBlock, 0, st>>>(P.N * K, B, xacc, delta, y_update, hdr,
@@ -745,14 +423,22 @@ static cudaError_t solve_k(const DevProblem& P, int cg_iters, double tol_cg, con
 cudaError_t tma_autotune(const DevProblem& P, void* solve_ws, WsHeader* hdr, Reduce red,
                          cudaStream_t st, int* best, float* ms)
 {
-    SolveBufs B = carve(P, solve_ws);
     *best = -1;
-    // operands: R stands in for H (same size), r for w; all zero
-    const size_t vec = sizeof(float) * (size_t)P.K * P.N;
+    // Timed on zeroed operands carved from the solve workspace's seven vectors
+    // so that no buffer the launch writes is also read: iteration 3 reads z, v
+    // and p from vectors 0-2 and p_{j-2} from 3, writes z, v, p to 4-6; H and w
+    // alias the read-only vectors 0-3.
+    const size_t vec = align256(sizeof(float) * (size_t)P.K * P.N);
+    char* c = static_cast<char*>(solve_ws);
+    auto at = [&](int i) { return reinterpret_cast<float*>(c + i * vec); };
+    SolveBufs B;
+    B.z[0] = at(0); B.z[1] = at(4);
+    B.v[0] = at(1); B.v[1] = at(5);
+    B.p[2] = at(2); B.p[1] = at(3); B.p[0] = at(6);
+    const float* h = at(0);       // T N floats <= 3 K N (K = 3, 4)
+    const float* w = at(3);
     cudaError_t e;
-    if ((e = cudaMemsetAsync(B.R, 0, sizeof(float) * (size_t)P.T * P.N, st)) != cudaSuccess) return e;
-    for (float* v : {B.r, B.p[0], B.p[1]})
-        if ((e = cudaMemsetAsync(v, 0, vec, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(solve_ws, 0, solve_ws_bytes(P), st)) != cudaSuccess) return e;
     cudaEvent_t a, b;
     if ((e = cudaEventCreate(&a)) != cudaSuccess) return e;
     if ((e = cudaEventCreate(&b)) != cudaSuccess) {
@@ -762,14 +448,14 @@ cudaError_t tma_autotune(const DevProblem& P, void* solve_ws, WsHeader* hdr, Red
     float best_ms = 0.0f;
     for (int t = 0; t < tma_tile_count(); ++t) {
         ms[t] = -1.0f;
-        TmaMaps m;
-        if (!make_tma_maps(P, B.R, B.r, B.p[0], B.p[1], t, &m)) continue;
+        StepMaps m;
+        if (!make_step_maps(P, h, w, B, at(3), t, &m)) continue;
         const StencilGrid g = tma_grid(P, t);
         constexpr int reps = 5;
         for (int i = 0; i <= reps && e == cudaSuccess; ++i) {
             if (i == 1) e = cudaEventRecord(a, st);
             if (e == cudaSuccess) e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st);
-            if (e == cudaSuccess) e = launch_matvec_tma(P, g, m, 2, B.q, hdr, red, st);
+            if (e == cudaSuccess) e = launch_step_tma(P, g, m, 3, kStepResid, hdr, nullptr, red, st);
         }
         if (e == cudaSuccess) e = cudaEventRecord(b, st);
         if (e == cudaSuccess) e = cudaEventSynchronize(b);

@@ -1,58 +1,93 @@
-// stencil_tma.cu -- q = (H + L) p with TMA plane staging (sm_103a).
+// stencil_tma.cu -- one PCG iteration of the Newton system (Eq. 42) with
+// TMA plane staging (sm_103a).  The per-voxel arithmetic is pcg_step.cuh's,
+// shared with the plain kernel k_pcg_step (stencil_kernels.cu).
 //
-// Same operator as k_pcg_matvec (stencil_kernels.cu): per voxel
-//   q_k = sum_j H_kj p_j + lambda_k sum_{m in N(n)} (w_n + w_m)(p_k[n] - p_k[m]) / h^2,
-// but every operand reaches shared memory through the tensor memory
-// accelerator.  For a tile of TX x TY voxels and each z plane, one thread
-// issues bulk tensor copies
-//   p  box (TX+8) x (TY+2) x 1 x K  at (x0 - 4, y0 - 1, z, 0)   (tile plus x / y halo)
-//   w  box (TX+8) x (TY+2) x 1      at (x0 - 4, y0 - 1, z)
-//   H  box TX x TY x 1 x T          at (x0, y0, z, 0)           (only planes computed)
-// into two rings: p / w planes (kStagesPW deep; plane z needs z - 1, z and
-// z + 1) and H planes (kStagesH deep; plane z needs only its own).  A
-// producer warp issues the copies; a stage is refilled as soon as the eight
-// compute warps have released it, so both streams run two planes ahead of
-// the compute and no compute thread holds loads in registers.  The depth is
-// what sets the speed: the copies in flight per SM have to cover the loaded
-// DRAM latency.  x coordinates are multiples of 4 floats (16 bytes); boxes
-// that leave the volume are zero-filled by the copy engine and masked by the
-// boundary flags.  Every mbarrier wait is bounded: on timeout the block
-// records kStatusTimeout, stops computing, drains its outstanding copies
-// (bounded again) and still takes part in the grid reduction.
+// Iteration j reads z_{j-1}, v_{j-1} and p_{j-1} (with a one-voxel halo), the
+// JTV weights and H, and writes z_j, p_j and v_j once:
+//   z_j = z_{j-1} - alpha_{j-1} v_{j-1},  p_j = z_j + beta_{j-1} p_{j-1}
+//   q_j = (H + L) p_j,  v_j = M^-1 q_j,  and the sums for alpha_j and beta_j.
+// A block owns a TX x TY tile and marches up a run of z planes.  Per plane
+// one thread issues bulk tensor copies into a ring of "raw" stages:
+//   z, v, p   box (TX+8) x (TY+2) x 1 x K at (x0 - 4, y0 - 1, z, 0)
+//   w         box (TX+8) x (TY+2) x 1     (same origin)
+//   x, p_j-2  box TX x TY x 1 x K at (x0, y0, z, 0) (even j >= 2, x fold)
+// and H (box TX x TY x 1 x T) into a second ring.  x coordinates are
+// multiples of 4 floats (16 bytes); boxes that leave the volume are
+// zero-filled by the copy engine and masked by zero stencil coefficients.
+//
+// Eight compute warps (one voxel per thread) take each plane in two phases:
+//   A  form z_j and p_j of the plane's points (the tile and its x / y halo,
+//      recomputed from the staged z, v, p) into a shared "formed" plane (a
+//      ring of three), write z_j and p_j of the tile and fold x; the raw
+//      stage is then released;
+//   B  one plane behind A: q = (H + L) p_j from the formed plane (x / y
+//      neighbours) and the thread's own column (z neighbours, kept in
+//      registers), v = M^-1 q, r = M z_j, the voxel's terms of the sums.
+// One named barrier among the compute warps per plane separates A's writes
+// of a formed plane from B's reads of it; with three formed planes in the
+// ring, A never overwrites a plane B may still read.  A producer warp keeps
+// both rings full; a stage is refilled once all eight compute warps have
+// released it.
+//
+// Every mbarrier wait is bounded: on timeout the block records
+// kStatusTimeout, stops computing (its warps still pass the same named
+// barriers, so none waits forever), drains its outstanding copies (bounded
+// again) and still takes part in the grid reduction.
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <tuple>
 
 #include "mpm_internal.cuh"
+#include "pcg_step.cuh"
 
 namespace mpm {
 
-constexpr int kStagesPW = 5;                   // p / w ring
-constexpr int kStagesH = 3;                    // H ring
-constexpr int kTmaVoxels = 256;                // voxels per tile, one compute thread each
+constexpr int kStepRaw = 2;                    // raw (z, v, p, w, x, p_{j-2}) stages
+constexpr int kStepH = 2;                      // H stages
+constexpr int kStepVoxels = 256;               // voxels per tile, one compute thread each
+constexpr int kStepWarps = kStepVoxels / 32;   // compute warps
+constexpr int kStepThreads = kStepVoxels + 32; // plus the producer warp
 constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
 
-// Tile of TX x TY voxels; the p / w boxes add a one-voxel y halo and a
-// four-voxel x margin on each side (x0 - 4 keeps the copy 16-byte aligned).
+// Test hooks (mpm_test_copy_timeout): the producer issues no copies, and the
+// bound of every wait, in clock cycles.
+static std::atomic<int> g_withhold{0};
+static std::atomic<long long> g_wait_cycles{kWaitCycles};
+
+void set_copy_test(int withhold, long long wait_cycles)
+{
+    g_withhold.store(withhold ? 1 : 0);
+    g_wait_cycles.store(wait_cycles > 0 ? wait_cycles : kWaitCycles);
+}
+
 template <int K, int TX, int TY>
-struct TmaLayout {
-    static constexpr int BX = TX + 8, BY = TY + 2;
+struct StepLayout {
     static constexpr int T = K * (K + 1) / 2;
-    static constexpr int P_FLOATS = K * BY * BX;
-    static constexpr int W_FLOATS = BY * BX;
-    static constexpr int H_FLOATS = T * TY * TX;
-    static constexpr int align128(int bytes) { return (bytes + 127) / 128 * 128; }
-    // p / w stage: p then w; H stages follow the p / w ring
-    static constexpr int P_OFF = 0;
-    static constexpr int W_OFF = align128(P_FLOATS * 4);
-    static constexpr int PW_STAGE = W_OFF + align128(W_FLOATS * 4);
-    static constexpr int H_STAGE = align128(H_FLOATS * 4);
-    static constexpr int H_BASE = kStagesPW * PW_STAGE;
-    static constexpr int P_BYTES = P_FLOATS * 4, W_BYTES = W_FLOATS * 4, H_BYTES = H_FLOATS * 4;
-    static constexpr int SMEM = H_BASE + kStagesH * H_STAGE + 128;   // + alignment slack
+    static constexpr int BX = TX + 8, BY = TY + 2;      // halo box (x from x0 - 4, y from y0 - 1)
+    static constexpr int SX = TX + 2, SY = TY + 2;      // formed plane: tile plus one voxel
+    static constexpr int BOX = BX * BY, TILE = TX * TY, SPL = SX * SY;
+    static constexpr int NH = 2 * (TX + TY);            // halo points of a formed plane
+    static constexpr int a128(int b) { return (b + 127) / 128 * 128; }
+    static constexpr int HALO_BYTES = K * BOX * 4, W_BYTES = BOX * 4;
+    static constexpr int TILE_BYTES = K * TILE * 4, H_BYTES = T * TILE * 4;
+    static constexpr int Z_OFF = 0;
+    static constexpr int V_OFF = a128(HALO_BYTES);
+    static constexpr int P_OFF = V_OFF + a128(HALO_BYTES);
+    static constexpr int W_OFF = P_OFF + a128(HALO_BYTES);
+    static constexpr int X_OFF = W_OFF + a128(W_BYTES);
+    static constexpr int P2_OFF = X_OFF + a128(TILE_BYTES);
+    static constexpr int RAW = P2_OFF + a128(TILE_BYTES);
+    static constexpr int H_STAGE = a128(H_BYTES);
+    static constexpr int SLOT = a128(K * SPL * 4);
+    static constexpr int H_BASE = kStepRaw * RAW;
+    static constexpr int S_BASE = H_BASE + kStepH * H_STAGE;
+    static constexpr int SMEM = S_BASE + 3 * SLOT + 128;   // + alignment slack
+    static_assert(TX * TY == kStepVoxels, "one compute thread per voxel");
+    static_assert(NH <= kStepVoxels, "one halo point per thread at most");
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -71,6 +106,11 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
                  : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 // One try: the thread may be suspended until the phase completes or about
 // 20 us pass (the suspend-time hint), so waiting warps do not spin on issue
 // slots the compute warps need.
@@ -87,12 +127,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait: false after about kWaitCycles.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+// Bounded wait: false after about `cycles` clock cycles.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long cycles)
 {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > cycles) return false;
     return true;
 }
 
@@ -116,228 +156,302 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
-__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+// Barrier 1 among the eight compute warps (the producer warp never joins it).
+__device__ __forceinline__ void compute_warps_sync()
 {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+    asm volatile("bar.sync 1, %0;" ::"n"(kStepVoxels) : "memory");
 }
-
-// Warp-specialised pipeline: warps 0-7 compute one voxel per thread, warp 8
-// is the producer.  Per stage, `full` completes when the copies have landed
-// and `empty` when all eight compute warps have released the plane; nobody
-// waits at a block-wide barrier inside the plane loop.
-constexpr int kConsumerWarps = kTmaVoxels / 32;
-constexpr int kTmaThreads = kTmaVoxels + 32;
 
 // Work split: the launch is one wave of resident blocks.  The volume is cut
 // into items -- one tile column over one of `nchunk` z ranges -- numbered
 // i = chunk * tiles + tile, and block b takes items b, b + G, b + 2G, ...
 // (G = gridDim.x), so the blocks running at one time cover neighbouring
-// tiles of the same z ranges (their DRAM rows and halos are shared).  The
-// ring and its phases run on from one item to the next, so the copies of the
-// next item overlap the end of the current one.
+// tiles of the same z ranges (their DRAM rows and halos are shared).  An item
+// over planes [za, zb) loads planes za - 1 .. zb (those inside the volume);
+// the planes outside [za, zb) only supply the z neighbours of its own column.
+// The rings and their phases run on from one item to the next.
 template <int K, int TX, int TY>
-__global__ void __launch_bounds__(kTmaThreads) k_pcg_matvec_tma(
-    DevProblem P, int nchunk, int k_it, const __grid_constant__ CUtensorMap tp,
+__global__ void __launch_bounds__(kStepThreads, 2) k_pcg_step_tma(
+    DevProblem P, int nchunk, int j, int flags, const __grid_constant__ CUtensorMap tz,
+    const __grid_constant__ CUtensorMap tv, const __grid_constant__ CUtensorMap tp,
     const __grid_constant__ CUtensorMap tw, const __grid_constant__ CUtensorMap th,
-    float* __restrict__ qout, WsHeader* hdr, Reduce red)
+    const __grid_constant__ CUtensorMap txm, const __grid_constant__ CUtensorMap tp2,
+    float* __restrict__ zout, float* __restrict__ vout, float* __restrict__ pout,
+    float* __restrict__ xacc, WsHeader* hdr, double* resid, Reduce red, long long wait_cycles,
+    int withhold)
 {
-    using L = TmaLayout<K, TX, TY>;
-    constexpr int kTmaBoxX = L::BX, kTmaBoxY = L::BY, kTmaTX = TX, kTmaTY = TY;
-    static_assert(TX * TY == kTmaVoxels, "one compute thread per voxel");
+    using L = StepLayout<K, TX, TY>;
+    constexpr int T = L::T;
     extern __shared__ unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t pw_full[kStagesPW], pw_empty[kStagesPW];
-    __shared__ __align__(8) uint64_t h_full[kStagesH], h_empty[kStagesH];
+    __shared__ __align__(8) uint64_t raw_full[kStepRaw], raw_empty[kStepRaw];
+    __shared__ __align__(8) uint64_t h_full[kStepH], h_empty[kStepH];
     __shared__ int s_done;
+    __shared__ float s_alpha, s_alpha_prev, s_beta;
     __shared__ volatile int s_fail;
     unsigned char* smem =
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const bool producer = warp == kConsumerWarps;
-    const int tx = tid % kTmaTX, ty = tid / kTmaTX;          // meaningful for compute warps
+    const bool producer = warp == kStepWarps;
+    const int tx = tid % TX, ty = tid / TX;              // meaningful for compute threads
     const int nx = P.nx, ny = P.ny, nz = P.nz;
     const long long N = P.N;
     const int gx = (nx + TX - 1) / TX;
     const int tiles = gx * ((ny + TY - 1) / TY);
     const int items = tiles * nchunk;
+    const bool first = flags & kStepFirst, fold = flags & kStepFold;
+    const bool readx = flags & kStepReadX, want_rr = flags & kStepResid;
 
     if (tid == 0) {
         s_done = hdr->sc.done;
+        s_alpha = (float)hdr->sc.alpha;
+        s_alpha_prev = (float)hdr->sc.alpha_prev;
+        s_beta = (float)hdr->sc.beta;
         s_fail = 0;
-        for (int s = 0; s < kStagesPW; ++s) {
-            mbar_init(smem_u32(&pw_full[s]), 1);
-            mbar_init(smem_u32(&pw_empty[s]), kConsumerWarps);
+        for (int s = 0; s < kStepRaw; ++s) {
+            mbar_init(smem_u32(&raw_full[s]), 1);
+            mbar_init(smem_u32(&raw_empty[s]), kStepWarps);
         }
-        for (int s = 0; s < kStagesH; ++s) {
+        for (int s = 0; s < kStepH; ++s) {
             mbar_init(smem_u32(&h_full[s]), 1);
-            mbar_init(smem_u32(&h_empty[s]), kConsumerWarps);
+            mbar_init(smem_u32(&h_empty[s]), kStepWarps);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    const bool done = s_done != 0;
+    if (s_done) return;                                   // the same in every block
+    if (fold && tid == 0 && blockIdx.x == 0) hdr->sc.xcount = j;
+    const float alpha = s_alpha, alpha_prev = s_alpha_prev, beta = s_beta;
 
-    // Load counters: c over the p / w planes this block loads, e over its H
-    // planes (one per computed plane), both in order -> ring stage and phase.
-    auto pw_stage = [](int c) { return (int)((unsigned)c % (unsigned)kStagesPW); };
-    auto pw_phase = [](int c) { return (uint32_t)(((unsigned)c / (unsigned)kStagesPW) & 1u); };
-    auto h_stage = [](int e) { return (int)((unsigned)e % (unsigned)kStagesH); };
-    auto h_phase = [](int e) { return (uint32_t)(((unsigned)e / (unsigned)kStagesH) & 1u); };
-    auto pw_ptr = [&](int c) { return smem + pw_stage(c) * L::PW_STAGE; };
+    // Counters: c over the raw planes this block loads, e over its H planes
+    // (one per plane it computes), both in order -> ring stage and phase.
+    auto r_stage = [](int c) { return (int)((unsigned)c % (unsigned)kStepRaw); };
+    auto r_phase = [](int c) { return (uint32_t)(((unsigned)c / (unsigned)kStepRaw) & 1u); };
+    auto h_stage = [](int e) { return (int)((unsigned)e % (unsigned)kStepH); };
+    auto h_phase = [](int e) { return (uint32_t)(((unsigned)e / (unsigned)kStepH) & 1u); };
+    auto formed = [&](int c) {
+        return reinterpret_cast<float*>(smem + L::S_BASE + ((unsigned)c % 3u) * L::SLOT);
+    };
 
-    Acc pq;
-    int pw_issued = -1, h_issued = -1;  // last counters issued (producer lane 0)
-    if (!done && producer) {
-        if (lane == 0) {
-            int cb = 0, eb = 0;         // counters of the item's first planes
+    Acc acc[kStepSums];
+    int raw_issued = -1, h_issued = -1;   // last counters issued (producer lane 0)
+    if (producer) {
+        if (lane == 0 && !withhold) {
+            int cb = 0, eb = 0;           // counters of the item's first planes
             for (int i = blockIdx.x; i < items && !s_fail; i += gridDim.x) {
                 const int t = i % tiles, ch = i / tiles;
                 const int za = (int)((long long)ch * nz / nchunk), zb = (int)((long long)(ch + 1) * nz / nchunk);
-                const int x0 = (t % gx) * kTmaTX, y0 = (t / gx) * kTmaTY;
+                const int x0 = (t % gx) * TX, y0 = (t / gx) * TY;
                 const int ja = max(za - 1, 0), jb = min(zb, nz - 1);
-                for (int j = ja; j <= jb && !s_fail; ++j) {
-                    // p / w plane j; its stage must be released by every compute warp
-                    const int c = cb + (j - ja);
-                    const int s = pw_stage(c);
-                    if (c >= kStagesPW && !mbar_wait(smem_u32(&pw_empty[s]), pw_phase(c - kStagesPW))) {
+                for (int jj = ja; jj <= jb && !s_fail; ++jj) {
+                    const int c = cb + (jj - ja);
+                    const int s = r_stage(c);
+                    if (c >= kStepRaw &&
+                        !mbar_wait(smem_u32(&raw_empty[s]), r_phase(c - kStepRaw), wait_cycles)) {
                         s_fail = 1;
                         break;
                     }
-                    unsigned char* st = smem + s * L::PW_STAGE;
-                    const uint32_t bar = smem_u32(&pw_full[s]);
-                    mbar_expect_tx(bar, L::P_BYTES + L::W_BYTES);
-                    tma_load_4d(smem_u32(st + L::P_OFF), &tp, x0 - 4, y0 - 1, j, 0, bar);
-                    tma_load_3d(smem_u32(st + L::W_OFF), &tw, x0 - 4, y0 - 1, j, bar);
-                    pw_issued = c;
-                    if (j < za || j >= zb) continue;
-                    // H plane j
-                    const int e = eb + (j - za);
+                    const bool inner = jj >= za && jj < zb;
+                    unsigned char* st = smem + s * L::RAW;
+                    const uint32_t bar = smem_u32(&raw_full[s]);
+                    uint32_t bytes = L::HALO_BYTES + L::W_BYTES;
+                    if (!first) bytes += 2 * L::HALO_BYTES;
+                    if (fold && inner) bytes += L::TILE_BYTES * (readx ? 2 : 1);
+                    mbar_expect_tx(bar, bytes);
+                    tma_load_4d(smem_u32(st + L::Z_OFF), &tz, x0 - 4, y0 - 1, jj, 0, bar);
+                    if (!first) {
+                        tma_load_4d(smem_u32(st + L::V_OFF), &tv, x0 - 4, y0 - 1, jj, 0, bar);
+                        tma_load_4d(smem_u32(st + L::P_OFF), &tp, x0 - 4, y0 - 1, jj, 0, bar);
+                    }
+                    tma_load_3d(smem_u32(st + L::W_OFF), &tw, x0 - 4, y0 - 1, jj, bar);
+                    if (fold && inner) {
+                        tma_load_4d(smem_u32(st + L::P2_OFF), &tp2, x0, y0, jj, 0, bar);
+                        if (readx) tma_load_4d(smem_u32(st + L::X_OFF), &txm, x0, y0, jj, 0, bar);
+                    }
+                    raw_issued = c;
+                    if (!inner) continue;
+                    const int e = eb + (jj - za);
                     const int sh = h_stage(e);
-                    if (e >= kStagesH && !mbar_wait(smem_u32(&h_empty[sh]), h_phase(e - kStagesH))) {
+                    if (e >= kStepH &&
+                        !mbar_wait(smem_u32(&h_empty[sh]), h_phase(e - kStepH), wait_cycles)) {
                         s_fail = 1;
                         break;
                     }
                     const uint32_t hbar = smem_u32(&h_full[sh]);
                     mbar_expect_tx(hbar, L::H_BYTES);
-                    tma_load_4d(smem_u32(smem + L::H_BASE + sh * L::H_STAGE), &th, x0, y0, j, 0, hbar);
+                    tma_load_4d(smem_u32(smem + L::H_BASE + sh * L::H_STAGE), &th, x0, y0, jj, 0, hbar);
                     h_issued = e;
                 }
                 cb += jb - ja + 1;
                 eb += zb - za;
             }
         }
-    } else if (!done) {
-        int waited = -1;                // p / w counters [0, waited] are visible to this thread
-        int released = 0;               // next p / w counter this warp releases
+    } else {
         int cb = 0, eb = 0;
         for (int i = blockIdx.x; i < items; i += gridDim.x) {
             const int t = i % tiles, ch = i / tiles;
             const int za = (int)((long long)ch * nz / nchunk), zb = (int)((long long)(ch + 1) * nz / nchunk);
-            const int x = (t % gx) * kTmaTX + tx, y = (t / gx) * kTmaTY + ty;
+            const int x = (t % gx) * TX + tx, y = (t / gx) * TY + ty;
             const int ja = max(za - 1, 0), jb = min(zb, nz - 1);
             const bool inside = x < nx && y < ny;
-            for (int z = za; z < zb; ++z) {
-                const int need = cb + (min(z + 1, nz - 1) - ja);
-                const int e = eb + (z - za);
-                bool ok = !s_fail;
-                for (int c = waited + 1; ok && c <= need; ++c)
-                    ok = mbar_wait(smem_u32(&pw_full[pw_stage(c)]), pw_phase(c));
-                waited = need;
-                if (ok) ok = mbar_wait(smem_u32(&h_full[h_stage(e)]), h_phase(e));
+            const bool okxm = x > 0, okxp = x + 1 < nx, okym = y > 0, okyp = y + 1 < ny;
+            const int cc = (ty + 1) * L::BX + tx + 4;      // own point in a halo box
+            const int sc = (ty + 1) * L::SX + tx + 1;      // own point in a formed plane
+            const int tc = ty * TX + tx;                   // own point in a tile box
+            // own column: p_j of planes z - 1, z, z + 1, z_j of z and z + 1,
+            // the weights of z - 1, z, z + 1 and the x / y coefficients of z, z + 1
+            float pm[K], pc[K], pn[K], zc[K], zn[K], cxy[4], cxyn[4];
+            float wm = 0.f, wc = 0.f, wn = 0.f;
+#pragma unroll
+            for (int a = 0; a < K; ++a) pm[a] = pc[a] = pn[a] = zc[a] = zn[a] = 0.f;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) cxy[m] = cxyn[m] = 0.f;
+
+            // Phase B for plane z (counter cz of its formed plane, H counter e):
+            // `up` holds p_j of plane z + 1 (or of z itself at the top face).
+            auto phase_b = [&](int z, int cz, int e, const float (&up)[K], float wup) {
+                const bool ok = !s_fail && mbar_wait(smem_u32(&h_full[h_stage(e)]), h_phase(e), wait_cycles);
                 if (!ok) s_fail = 1;
                 if (ok && inside) {
-                    const int cz = cb + (z - ja);
-                    const float* pcur = reinterpret_cast<const float*>(pw_ptr(cz) + L::P_OFF);
-                    const float* wcur = reinterpret_cast<const float*>(pw_ptr(cz) + L::W_OFF);
-                    const float* hcur = reinterpret_cast<const float*>(smem + L::H_BASE + h_stage(e) * L::H_STAGE);
-                    const int cc = (ty + 1) * kTmaBoxX + tx + 4;      // centre in a p / w plane
-                    const bool okxm = x > 0, okxp = x + 1 < nx, okym = y > 0, okyp = y + 1 < ny;
-                    const bool okzm = z > 0, okzp = z + 1 < nz;
-                    const float* pdn = okzm ? reinterpret_cast<const float*>(pw_ptr(cz - 1) + L::P_OFF) : pcur;
-                    const float* wdn = okzm ? reinterpret_cast<const float*>(pw_ptr(cz - 1) + L::W_OFF) : wcur;
-                    const float* pup = okzp ? reinterpret_cast<const float*>(pw_ptr(cz + 1) + L::P_OFF) : pcur;
-                    const float* wup = okzp ? reinterpret_cast<const float*>(pw_ptr(cz + 1) + L::W_OFF) : wcur;
-                    // out-of-volume neighbours: the copy engine zero-fills the
-                    // x / y halo and the z neighbour falls back to the centre
-                    // plane, so a zero coefficient removes them without a branch
-                    const float wc = wcur[cc];
-                    const float cxm = okxm ? (wc + wcur[cc - 1]) * P.ihx2 : 0.f;
-                    const float cxp = okxp ? (wc + wcur[cc + 1]) * P.ihx2 : 0.f;
-                    const float cym = okym ? (wc + wcur[cc - kTmaBoxX]) * P.ihy2 : 0.f;
-                    const float cyp = okyp ? (wc + wcur[cc + kTmaBoxX]) * P.ihy2 : 0.f;
-                    const float czm = okzm ? (wc + wdn[cc]) * P.ihz2 : 0.f;
-                    const float czp = okzp ? (wc + wup[cc]) * P.ihz2 : 0.f;
-                    constexpr int PS = kTmaBoxY * kTmaBoxX;             // map stride in a p plane
-                    constexpr int HS = kTmaTX * kTmaTY;                 // entry stride in an H plane
-                    const int hc = ty * kTmaTX + tx;
-                    float hv[L::T];
+                    const float* hb = reinterpret_cast<const float*>(smem + L::H_BASE + h_stage(e) * L::H_STAGE);
+                    float hv[T];
 #pragma unroll
-                    for (int m = 0; m < L::T; ++m) hv[m] = hcur[m * HS + hc];
-                    float pc[K];
+                    for (int m = 0; m < T; ++m) hv[m] = hb[m * L::TILE + tc];
+                    const float* fp = formed(cz);
+                    const float c6[6] = {cxy[0], cxy[1], cxy[2], cxy[3],
+                                         z > 0 ? (wc + wm) * P.ihz2 : 0.f,
+                                         z + 1 < nz ? (wc + wup) * P.ihz2 : 0.f};
+                    auto nb = [&](int m, int a) -> float {
+                        switch (m) {
+                        case 0: return fp[a * L::SPL + sc - 1];
+                        case 1: return fp[a * L::SPL + sc + 1];
+                        case 2: return fp[a * L::SPL + sc - L::SX];
+                        case 3: return fp[a * L::SPL + sc + L::SX];
+                        case 4: return pm[a];
+                        default: return up[a];
+                        }
+                    };
+                    float v[K], sums[kStepSums];
+                    step_voxel<K>(P, c6, zc, pc, nb, hv, want_rr, v, sums);
+                    const long long n = (long long)x + (long long)nx * y + (long long)nx * ny * z;
 #pragma unroll
-                    for (int k = 0; k < K; ++k) pc[k] = pcur[k * PS + cc];
-                    float* qn = qout + ((long long)x + (long long)nx * y + (long long)nx * ny * z);
-                    float vpq = 0.0f;
+                    for (int a = 0; a < K; ++a) vout[a * N + n] = v[a];
+#pragma unroll
+                    for (int s = 0; s < kStepSums; ++s) acc[s].add(sums[s]);
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&h_empty[h_stage(e)]));
+            };
+
+            for (int jj = ja; jj <= jb; ++jj) {
+                const int c = cb + (jj - ja);
+                const bool inner = jj >= za && jj < zb;
+                const bool ok = !s_fail && mbar_wait(smem_u32(&raw_full[r_stage(c)]), r_phase(c), wait_cycles);
+                if (!ok) s_fail = 1;
+                if (ok) {
+                    // Phase A: z_j and p_j of this plane
+                    const unsigned char* st = smem + r_stage(c) * L::RAW;
+                    const float* bz = reinterpret_cast<const float*>(st + L::Z_OFF);
+                    const float* bv = reinterpret_cast<const float*>(st + L::V_OFF);
+                    const float* bp = reinterpret_cast<const float*>(st + L::P_OFF);
+                    const float* bw = reinterpret_cast<const float*>(st + L::W_OFF);
+                    float zz[K], vv[K], pp[K];
 #pragma unroll
                     for (int a = 0; a < K; ++a) {
-                        const float* pa = pcur + a * PS;
-                        const float v = pc[a];
-                        float s = cxm * (v - pa[cc - 1]);
-                        s += cxp * (v - pa[cc + 1]);
-                        s += cym * (v - pa[cc - kTmaBoxX]);
-                        s += cyp * (v - pa[cc + kTmaBoxX]);
-                        s += czm * (v - pdn[a * PS + cc]);
-                        s += czp * (v - pup[a * PS + cc]);
-                        float acc = P.lambda[a] * s;
-#pragma unroll
-                        for (int b = 0; b < K; ++b) acc += hv[a < b ? tri(K, a, b) : tri(K, b, a)] * pc[b];
-                        qn[a * N] = acc;
-                        vpq += v * acc;
+                        zz[a] = bz[a * L::BOX + cc];
+                        vv[a] = first ? 0.f : bv[a * L::BOX + cc];
+                        pp[a] = first ? 0.f : bp[a * L::BOX + cc];
                     }
-                    pq.add(vpq);
+                    step_point<K>(first, alpha, beta, zz, vv, pp, zn, pn);
+                    wn = bw[cc];
+                    cxyn[0] = okxm ? (wn + bw[cc - 1]) * P.ihx2 : 0.f;
+                    cxyn[1] = okxp ? (wn + bw[cc + 1]) * P.ihx2 : 0.f;
+                    cxyn[2] = okym ? (wn + bw[cc - L::BX]) * P.ihy2 : 0.f;
+                    cxyn[3] = okyp ? (wn + bw[cc + L::BX]) * P.ihy2 : 0.f;
+                    if (inner) {
+                        float* fp = formed(c);
+#pragma unroll
+                        for (int a = 0; a < K; ++a) fp[a * L::SPL + sc] = pn[a];
+                        if (tid < L::NH) {
+                            // halo point: y - 1 row, y + TY row, x - 1 column, x + TX column
+                            int sx, sy;
+                            if (tid < TX) { sx = tid + 1; sy = 0; }
+                            else if (tid < 2 * TX) { sx = tid - TX + 1; sy = TY + 1; }
+                            else if (tid < 2 * TX + TY) { sx = 0; sy = tid - 2 * TX + 1; }
+                            else { sx = TX + 1; sy = tid - 2 * TX - TY + 1; }
+                            const int hc = sy * L::BX + sx + 3;
+                            float hz[K], hv[K], hp[K], hzj[K], hpj[K];
+#pragma unroll
+                            for (int a = 0; a < K; ++a) {
+                                hz[a] = bz[a * L::BOX + hc];
+                                hv[a] = first ? 0.f : bv[a * L::BOX + hc];
+                                hp[a] = first ? 0.f : bp[a * L::BOX + hc];
+                            }
+                            step_point<K>(first, alpha, beta, hz, hv, hp, hzj, hpj);
+#pragma unroll
+                            for (int a = 0; a < K; ++a) fp[a * L::SPL + sy * L::SX + sx] = hpj[a];
+                        }
+                        if (inside) {
+                            const long long n = (long long)x + (long long)nx * y + (long long)nx * ny * jj;
+#pragma unroll
+                            for (int a = 0; a < K; ++a) {
+                                if (!first) zout[a * N + n] = zn[a];
+                                pout[a * N + n] = pn[a];
+                            }
+                            if (fold) {
+                                const float* bx = reinterpret_cast<const float*>(st + L::X_OFF);
+                                const float* b2 = reinterpret_cast<const float*>(st + L::P2_OFF);
+#pragma unroll
+                                for (int a = 0; a < K; ++a)
+                                    xacc[a * N + n] = fold_x(readx ? bx[a * L::TILE + tc] : 0.f, alpha_prev,
+                                                             b2[a * L::TILE + tc], alpha, pp[a]);
+                            }
+                        }
+                    }
                 }
-                // this warp is done with H plane z and no longer needs the p / w
-                // planes below z; at the end of the item it releases all of
-                // the item's p / w planes
-                const int rel_to = z + 1 < zb ? cb + (z - 1 - ja) : cb + (jb - ja);
                 __syncwarp();
-                if (lane == 0) {
-                    mbar_arrive(smem_u32(&h_empty[h_stage(e)]));
-                    for (int c = released; c <= rel_to; ++c) mbar_arrive(smem_u32(&pw_empty[pw_stage(c)]));
+                if (lane == 0) mbar_arrive(smem_u32(&raw_empty[r_stage(c)]));
+                compute_warps_sync();
+                if (jj - 1 >= za) {
+                    phase_b(jj - 1, c - 1, eb + (jj - 1 - za), pn, wn);
                 }
-                if (rel_to >= released) released = rel_to + 1;
+                // the plane above becomes current
+#pragma unroll
+                for (int a = 0; a < K; ++a) {
+                    pm[a] = pc[a];
+                    pc[a] = pn[a];
+                    zc[a] = zn[a];
+                }
+#pragma unroll
+                for (int m = 0; m < 4; ++m) cxy[m] = cxyn[m];
+                wm = wc;
+                wc = wn;
+            }
+            if (jb == zb - 1) {
+                // the item reaches the top face: its last plane has no plane above
+                phase_b(jb, cb + (jb - ja), eb + (jb - za), pc, wc);
             }
             cb += jb - ja + 1;
             eb += zb - za;
         }
     }
     __syncthreads();
-    if (!done && s_fail) {
+    if (s_fail) {
         // drain: no copy may still be writing this block's shared memory
         if (producer && lane == 0) {
             // the last fill of each stage (earlier fills have completed before
             // their stage could be refilled)
-            for (int c = max(0, pw_issued - kStagesPW + 1); c <= pw_issued; ++c)
-                mbar_wait(smem_u32(&pw_full[pw_stage(c)]), pw_phase(c));
-            for (int e = max(0, h_issued - kStagesH + 1); e <= h_issued; ++e)
-                mbar_wait(smem_u32(&h_full[h_stage(e)]), h_phase(e));
+            for (int c = max(0, raw_issued - kStepRaw + 1); c <= raw_issued; ++c)
+                mbar_wait(smem_u32(&raw_full[r_stage(c)]), r_phase(c), wait_cycles);
+            for (int e = max(0, h_issued - kStepH + 1); e <= h_issued; ++e)
+                mbar_wait(smem_u32(&h_full[h_stage(e)]), h_phase(e), wait_cycles);
             atomicOr(&hdr->status, kStatusTimeout);
         }
         __syncthreads();
     }
-    Acc v[1] = {pq};
-    double out[1];
-    if (grid_reduce<1>(v, red, out) && tid == 0 && !done) {
-        SolveScalars& sc = hdr->sc;
-        if (!(out[0] == out[0])) atomicOr(&hdr->status, kStatusNaN);
-        if (!(out[0] > 0.0)) {
-            sc.done = 1;                 // no further step; the alphas keep their values
-        } else {
-            sc.alpha_prev = sc.alpha;
-            sc.alpha = sc.rz / out[0];
-        }
-    }
+    double out[kStepSums];
+    if (grid_reduce<kStepSums>(acc, red, out) && tid == 0) step_scalars(out, j, want_rr, hdr, resid);
 }
 
 // ------------------------------------------------------------------ host
@@ -370,7 +484,7 @@ static bool encode(CUtensorMap* m, const float* base, int rank, const cuuint64_t
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Tile shapes the TMA matvec is compiled for (x by y voxels).
+// Tile shapes the TMA iteration is compiled for (x by y voxels).
 static const int kTileShapes[][2] = {{16, 16}, {32, 8}, {64, 4}};
 
 int tma_tile_count() { return 3; }
@@ -395,8 +509,8 @@ int tma_tile_choice(const DevProblem& P)
     return (P.nx >= 40 && P.ny >= 10) ? 1 : 0;    // 32 x 8 when it fits, else 16 x 16
 }
 
-bool make_tma_maps(const DevProblem& P, const float* h, const float* w, const float* p0,
-                   const float* p1, int tile, TmaMaps* out)
+bool make_step_maps(const DevProblem& P, const float* h, const float* w, const SolveBufs& B,
+                    float* xacc, int tile, StepMaps* out)
 {
     if (tile < 0 || tile >= tma_tile_count()) return false;
     const int TX = kTileShapes[tile][0], TY = kTileShapes[tile][1];
@@ -404,39 +518,53 @@ bool make_tma_maps(const DevProblem& P, const float* h, const float* w, const fl
     // TMA needs 16-byte aligned bases and row strides, and boxes no larger
     // than the volume in x and y.
     if (P.nx % 4 != 0 || P.nx < BX || P.ny < BY) return false;
-    if ((reinterpret_cast<uintptr_t>(h) | reinterpret_cast<uintptr_t>(w) |
-         reinterpret_cast<uintptr_t>(p0) | reinterpret_cast<uintptr_t>(p1)) % 16)
-        return false;
+    uintptr_t any = reinterpret_cast<uintptr_t>(h) | reinterpret_cast<uintptr_t>(w) |
+                    reinterpret_cast<uintptr_t>(xacc);
+    for (float* v : B.z) any |= reinterpret_cast<uintptr_t>(v);
+    for (float* v : B.v) any |= reinterpret_cast<uintptr_t>(v);
+    for (float* v : B.p) any |= reinterpret_cast<uintptr_t>(v);
+    if (any % 16) return false;
     if (!encode_fn()) return false;
     const cuuint64_t nx = P.nx, ny = P.ny, nz = P.nz;
     const cuuint64_t row = nx * 4, plane = nx * ny * 4, vol = (cuuint64_t)P.N * 4;
-    const cuuint64_t dp[4] = {nx, ny, nz, (cuuint64_t)P.K};
+    const cuuint64_t dk[4] = {nx, ny, nz, (cuuint64_t)P.K};
     const cuuint64_t dh[4] = {nx, ny, nz, (cuuint64_t)P.T};
     const cuuint64_t s4[3] = {row, plane, vol};
     const cuuint64_t d3[3] = {nx, ny, nz};
     const cuuint64_t s3[2] = {row, plane};
-    const cuuint32_t bp[4] = {(cuuint32_t)BX, (cuuint32_t)BY, 1, (cuuint32_t)P.K};
-    const cuuint32_t bw[3] = {(cuuint32_t)BX, (cuuint32_t)BY, 1};
-    const cuuint32_t bh[4] = {(cuuint32_t)TX, (cuuint32_t)TY, 1, (cuuint32_t)P.T};
+    const cuuint32_t halo[4] = {(cuuint32_t)BX, (cuuint32_t)BY, 1, (cuuint32_t)P.K};
+    const cuuint32_t halo_w[3] = {(cuuint32_t)BX, (cuuint32_t)BY, 1};
+    const cuuint32_t tile_k[4] = {(cuuint32_t)TX, (cuuint32_t)TY, 1, (cuuint32_t)P.K};
+    const cuuint32_t tile_h[4] = {(cuuint32_t)TX, (cuuint32_t)TY, 1, (cuuint32_t)P.T};
+    bool ok = encode(&out->w, w, 3, d3, s3, halo_w) && encode(&out->h, h, 4, dh, s4, tile_h) &&
+              encode(&out->x, xacc, 4, dk, s4, tile_k);
+    for (int i = 0; i < 2 && ok; ++i)
+        ok = encode(&out->z[i], B.z[i], 4, dk, s4, halo) && encode(&out->v[i], B.v[i], 4, dk, s4, halo);
+    for (int i = 0; i < 3 && ok; ++i)
+        ok = encode(&out->p[i], B.p[i], 4, dk, s4, halo) && encode(&out->p2[i], B.p[i], 4, dk, s4, tile_k);
+    out->B = B;
+    out->xacc = xacc;
     out->tile = tile;
-    return encode(&out->p[0], p0, 4, dp, s4, bp) && encode(&out->p[1], p1, 4, dp, s4, bp) &&
-           encode(&out->w, w, 3, d3, s3, bw) && encode(&out->h, h, 4, dh, s4, bh);
+    return ok;
 }
 
 template <int K, int TX, int TY>
-static cudaError_t launch_tma_k(const DevProblem& P, int nchunk, dim3 grid, const TmaMaps& m, int k_it,
-                                float* q, WsHeader* hdr, Reduce red, cudaStream_t st)
+static cudaError_t launch_step_k(const DevProblem& P, int nchunk, dim3 grid, const StepMaps& m, int j,
+                                 int flags, WsHeader* hdr, double* resid, Reduce red, cudaStream_t st)
 {
-    using L = TmaLayout<K, TX, TY>;
+    using L = StepLayout<K, TX, TY>;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_pcg_matvec_tma<K, TX, TY>,
+        cudaError_t e = cudaFuncSetAttribute(k_pcg_step_tma<K, TX, TY>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_pcg_matvec_tma<K, TX, TY><<<grid, dim3(kTmaThreads, 1, 1), L::SMEM, st>>>(
-        P, nchunk, k_it, m.p[k_it & 1], m.w, m.h, q, hdr, red);
+    const int jm = j > 0 ? j - 1 : 0;
+    k_pcg_step_tma<K, TX, TY><<<grid, dim3(kStepThreads, 1, 1), L::SMEM, st>>>(
+        P, nchunk, j, flags, m.z[jm & 1], m.v[jm & 1], m.p[(j + 2) % 3], m.w, m.h, m.x,
+        m.p2[(j + 1) % 3], m.B.z[j & 1], m.B.v[j & 1], m.B.p[j % 3], m.xacc, hdr, resid, red,
+        g_wait_cycles.load(std::memory_order_relaxed), g_withhold.load(std::memory_order_relaxed));
     return cudaGetLastError();
 }
 
@@ -445,18 +573,18 @@ static int resident_one()
 {
     // the occupancy query needs the kernel's shared-memory opt-in first
     int nb = 0;
-    if (cudaFuncSetAttribute(k_pcg_matvec_tma<K, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             TmaLayout<K, TX, TY>::SMEM) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pcg_matvec_tma<K, TX, TY>, kTmaThreads,
-                                                      TmaLayout<K, TX, TY>::SMEM) != cudaSuccess) {
+    if (cudaFuncSetAttribute(k_pcg_step_tma<K, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             StepLayout<K, TX, TY>::SMEM) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pcg_step_tma<K, TX, TY>, kStepThreads,
+                                                      StepLayout<K, TX, TY>::SMEM) != cudaSuccess) {
         cudaGetLastError();
         nb = 1;
     }
     return nb > 0 ? nb : 1;
 }
 
-// Resident blocks of the TMA matvec per SM for (K, tile) and the SM count of
-// the current device, looked up once per device.
+// Resident blocks of the TMA iteration per SM for (K, tile) times the SM
+// count of the current device, looked up once per device.
 static int tma_wave(const DevProblem& P, int tile)
 {
     static std::mutex mu;
@@ -490,28 +618,27 @@ StencilGrid tma_grid(const DevProblem& P, int tile)
     const int best = tma_chunks(T, P.nz, W);
     StencilGrid g;
     g.grid = dim3((unsigned)std::min<long long>(T * best, W), 1, 1);
-    g.block = dim3(kTmaThreads, 1, 1);
+    g.block = dim3(kStepThreads, 1, 1);
     g.zc = best;
     return g;
 }
 
 template <int K>
-static cudaError_t launch_tma_tile(const DevProblem& P, const StencilGrid& g, const TmaMaps& m,
-                                   int k_it, float* q, WsHeader* hdr, Reduce red, cudaStream_t st)
+static cudaError_t launch_step_tile(const DevProblem& P, const StencilGrid& g, const StepMaps& m, int j,
+                                    int flags, WsHeader* hdr, double* resid, Reduce red, cudaStream_t st)
 {
     switch (m.tile) {
-    case 1: return launch_tma_k<K, 32, 8>(P, g.zc, g.grid, m, k_it, q, hdr, red, st);
-    case 2: return launch_tma_k<K, 64, 4>(P, g.zc, g.grid, m, k_it, q, hdr, red, st);
-    default: return launch_tma_k<K, 16, 16>(P, g.zc, g.grid, m, k_it, q, hdr, red, st);
+    case 1: return launch_step_k<K, 32, 8>(P, g.zc, g.grid, m, j, flags, hdr, resid, red, st);
+    case 2: return launch_step_k<K, 64, 4>(P, g.zc, g.grid, m, j, flags, hdr, resid, red, st);
+    default: return launch_step_k<K, 16, 16>(P, g.zc, g.grid, m, j, flags, hdr, resid, red, st);
     }
 }
 
 template <int K, int TX, int TY>
 static cudaError_t prime_one()
 {
-    return cudaFuncSetAttribute(k_pcg_matvec_tma<K, TX, TY>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                TmaLayout<K, TX, TY>::SMEM);
+    return cudaFuncSetAttribute(k_pcg_step_tma<K, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                StepLayout<K, TX, TY>::SMEM);
 }
 
 cudaError_t prime_tma_kernels()
@@ -528,11 +655,11 @@ cudaError_t prime_tma_kernels()
     return e;
 }
 
-cudaError_t launch_matvec_tma(const DevProblem& P, const StencilGrid& g, const TmaMaps& m,
-                              int k_it, float* q, WsHeader* hdr, Reduce red, cudaStream_t st)
+cudaError_t launch_step_tma(const DevProblem& P, const StencilGrid& g, const StepMaps& m, int j,
+                            int flags, WsHeader* hdr, double* resid, Reduce red, cudaStream_t st)
 {
-    if (P.K == 4) return launch_tma_tile<4>(P, g, m, k_it, q, hdr, red, st);
-    return launch_tma_tile<3>(P, g, m, k_it, q, hdr, red, st);
+    if (P.K == 4) return launch_step_tile<4>(P, g, m, j, flags, hdr, resid, red, st);
+    return launch_step_tile<3>(P, g, m, j, flags, hdr, resid, red, st);
 }
 
 }  // namespace mpm

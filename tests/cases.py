@@ -126,3 +126,64 @@ def moved_dataset(shape, grids, affines, seed=0, contrasts=("PDw", "T1w", "MTw")
     return {"prot": prot, "shape": tuple(shape), "y_true": ph["y"], "xs": xs, "b1ps": bps,
             "b1ms": bms, "grids": [tuple(g) for g in grids],
             "affines": [np.asarray(a, dtype=np.float64) for a in affines]}
+
+
+# ------------------------------------------------------------ full-size fits
+
+FULLSIZE = {
+    # config: (shape, voxel size in mm)
+    "1mm": ((176, 240, 256), (1.0, 1.0, 1.0)),
+    "0.8mm": ((208, 300, 320), (0.8, 0.8, 0.8)),
+}
+FULLSIZE_FIT = {"gn_iters": 20, "cg_iters": 30, "lam": 10.0, "eps": 1e-3, "seed": 0}
+
+
+def bf16_round(x32):
+    """float32 -> nearest bfloat16 (ties to even), returned as float32: the
+    values a bfloat16 copy of the images holds."""
+    u = np.ascontiguousarray(x32, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32)
+
+
+def fullsize_case(config="1mm", echo="f32"):
+    """The headline workload's inputs at full size: the bench protocol and
+    phantom statistics, seeded host noise (so the oracle sees the same data),
+    float32 images (rounded once more to bfloat16 values with echo="bf16")."""
+    shape, vx = FULLSIZE[config]
+    d = dataset(shape, seed=FULLSIZE_FIT["seed"])
+    d.pop("s")
+    if echo == "bf16":
+        d["x"] = bf16_round(d["x"])
+    d["vx"] = vx
+    return d
+
+
+def sample_voxels(shape, n_inner=8192, n_face=4096, seed=12345):
+    """Seeded voxel indices for sampled comparisons: uniform over the volume,
+    plus voxels on its six faces (where the prior's boundary rule acts)."""
+    nx, ny, nz = shape
+    rng = np.random.default_rng(seed)
+    inner = rng.choice(nx * ny * nz, size=n_inner, replace=False)
+    c = np.stack([rng.integers(0, n, size=n_face) for n in shape])
+    axis = rng.integers(0, 3, size=n_face)
+    side = rng.integers(0, 2, size=n_face)
+    for a in range(3):
+        sel = axis == a
+        c[a, sel] = side[sel] * (shape[a] - 1)
+    face = c[0] + nx * (c[1] + ny * c[2])
+    return np.unique(np.concatenate([inner, face]))
+
+
+def block_means(v, shape, b=16):
+    """Means of each map over b x b x b blocks (partial blocks at the far
+    edges): a whole-volume summary of [K][N] maps."""
+    nx, ny, nz = shape
+    K = v.shape[0]
+    a = np.asarray(v, dtype=np.float64).reshape(K, nz, ny, nx)
+    out = []
+    for z0 in range(0, nz, b):
+        for y0 in range(0, ny, b):
+            for x0 in range(0, nx, b):
+                out.append(a[:, z0:z0 + b, y0:y0 + b, x0:x0 + b].reshape(K, -1).mean(axis=1))
+    return np.stack(out, axis=1)

@@ -16,14 +16,17 @@ def test_algorithmic_bytes_per_voxel():
     assert ab["grad_hess"] == 22 * 4 + 4 * 4 + 4 + 3 * 4 + 4 * 4 + 10 * 4   # x, y, b1+, b1-; g, H
     assert ab["grad_hess"] == 176
     assert ab["jtv"] == 20                                  # y in, w out
-    assert ab["pcg_init"] == 148                            # w, g, y, H in; L, r, p out
-    assert ab["pcg_matvec"] == 76                           # p, H, w in; q out
-    assert ab["pcg_update"] == 104                          # q, r, L in; r, z out
+    assert ab["pcg_init"] == 92                             # w, g, y, H in; z_0 out
     assert ab["uncertainty"] == 60                          # H, w in; var out
-    # direction, 29 passes per 30-iteration solve: 15 odd passes (z, p in; p out),
-    # pass 2 (also p_{k-2} in, x out) and 13 later even passes (also x in)
-    assert ab["pcg_direction_per_solve"] == 15 * 48 + 80 + 13 * 96
-    # final: x (folded through pass 28), the two pending directions, y in and out
+    # PCG iterations of a 30-iteration solve: j = 0 (z_0, w, H in; p_0, v_0 out),
+    # 29 later ones (z, v, p, w, H in; z, v, p out), the x fold at j = 2 (p_0 in,
+    # x out) and at the 13 even j > 2 (p_{j-2}, x in; x out)
+    assert bench.step_bytes(0, 4) == 92
+    assert bench.step_bytes(1, 4) == 140
+    assert bench.step_bytes(2, 4) == 172 and bench.step_bytes(4, 4) == 188
+    assert ab["pcg_step_per_solve"] == 92 + 29 * 140 + 32 + 13 * 48
+    assert ab["pcg_step"] == ab["pcg_step_per_solve"] / 30
+    # final: x (folded through iteration 28), the two pending directions, y in and out
     assert ab["pcg_final"] == 16 + 2 * 16 + 2 * 16
     assert bench.algorithmic_bytes(4, 3, 22, echo_bytes=2)["grad_hess"] == 176 - 22 * 2
 
@@ -78,36 +81,60 @@ def _ncu_csv(path, launches):
                         f'"byte","{val:,}"\n')
 
 
-def test_write_traffic_takes_the_timed_fit(tmp_path):
-    """DRAM bytes per launch come from the last whole fit of the plain capture
-    (after the second-to-last k_uncertainty) and from the second half of the
-    moved-scan capture; warm-up and autotuning launches do not count."""
-    upd = "void k_pcg_update<4, 4>(DevProblem, int, float *, Reduce)"
-    unc = "void k_uncertainty<4>(DevProblem, const float *, float *)"
-    plain = [("void k_pcg_matvec_tma<4, 16, 16>(DevProblem, int)", 9e9, 9e9),   # autotuner
-             (upd, 5e9, 5e9), (unc, 7e9, 7e9),                                 # warm-up fit
-             ("void k_jtv<4>(DevProblem, const float *)", 100, 20),              # timed fit
-             (upd, 1000, 200), (upd, 1100, 300), (unc, 600, 40)]
-    moved = [("void k_grad_hess_proj<4, 0, float>(DevProblem)", 8e9, 8e9),
-             ("void k_push_all<4>(DevProblem)", 8e9, 8e9),
-             ("void k_grad_hess_proj<4, 0, float>(DevProblem)", 500, 70),
-             ("void k_push_all<4>(DevProblem)", 900, 100)]
-    _ncu_csv(tmp_path / "plain.csv", plain)
-    _ncu_csv(tmp_path / "moved.csv", moved)
+def _capture(path, launches, voxels, hashes=None):
+    """An ncu log of one kernel kind with the captured program's own lines."""
+    _ncu_csv(path, launches)
+    with open(path, "a") as f:
+        if hashes is not None:
+            f.write(json.dumps({"kernel_source_hashes": hashes}) + "\n")
+        f.write(json.dumps({"metric": "m", "config": {"voxels": voxels}}) + "\n")
+
+
+def test_write_traffic_per_kind_captures(tmp_path):
+    """DRAM bytes per launch are the mean over each capture's launches of its
+    kind, per voxel of that capture's volume; the kind's source hash comes
+    from the captured program's own output."""
+    hashes = {k: bench.kernel_source_hash(k) for k in bench.KIND_SOURCES}
+    step = "void k_pcg_step_tma<4, 32, 8>(DevProblem, int, int, int)"
+    _capture(tmp_path / "step.csv", [(step, 1000, 200), (step, 1100, 300)], 10, hashes)
+    _capture(tmp_path / "jtv.csv", [("void k_jtv<4>(DevProblem, const float *)", 100, 20)], 4, hashes)
     out = tmp_path / "traffic.json"
-    doc = bench.write_traffic(str(tmp_path / "plain.csv"), str(tmp_path / "moved.csv"),
-                              n_vox=10, out=str(out), commands=["cmd"])
+    doc = bench.write_traffic([str(tmp_path / "step.csv"), str(tmp_path / "jtv.csv")],
+                              out=str(out), commands=["cmd"])
     k = json.load(open(out))["kernels"]
     assert doc["kernels"] == k and json.load(open(out))["capture"] == ["cmd"]
-    assert k["pcg_update"]["launches"] == 2 and k["pcg_update"]["dram_bytes_per_launch"] == 1300
-    assert k["pcg_update"]["dram_bytes_per_voxel"] == 130.0
-    assert k["jtv"]["dram_bytes_per_launch"] == 120
-    assert k["uncertainty"] == {"launches": 1, "dram_bytes_per_launch": 640,
-                                "dram_bytes_per_voxel": 64.0,
-                                "source_hash": bench.kernel_source_hash("uncertainty")}
-    assert "pcg_matvec" not in k
-    assert k["grad_hess_proj"]["dram_bytes_per_launch"] == 570
-    assert k["reslice"]["dram_bytes_per_launch"] == 1000
+    assert k["pcg_step"]["launches"] == 2 and k["pcg_step"]["dram_bytes_per_launch"] == 1300
+    assert k["pcg_step"]["dram_bytes_per_voxel"] == 130.0 and k["pcg_step"]["voxels"] == 10
+    assert k["pcg_step"]["source_hash"] == hashes["pcg_step"]
+    assert k["jtv"]["dram_bytes_per_voxel"] == 30.0
+    assert set(k) == {"pcg_step", "jtv"}
+
+
+def test_write_traffic_refuses_stale_or_unlabelled_captures(tmp_path):
+    """A capture taken from other sources than the current ones, or one whose
+    log lacks the program's hashes, is refused rather than stored as current."""
+    step = "void k_pcg_step_tma<4, 32, 8>(DevProblem, int, int, int)"
+    stale = {k: bench.kernel_source_hash(k) for k in bench.KIND_SOURCES}
+    stale["pcg_step"] = "0123456789abcdef"
+    _capture(tmp_path / "stale.csv", [(step, 1000, 200)], 10, stale)
+    with pytest.raises(ValueError, match="pcg_step was captured"):
+        bench.write_traffic([str(tmp_path / "stale.csv")], out=str(tmp_path / "t.json"))
+    _capture(tmp_path / "bare.csv", [(step, 1000, 200)], 10, None)
+    with pytest.raises(ValueError, match="no source hashes"):
+        bench.write_traffic([str(tmp_path / "bare.csv")], out=str(tmp_path / "t.json"))
+    assert not (tmp_path / "t.json").exists()
+
+
+def test_traffic_commands_are_single_kernel_small_captures():
+    """Every committed capture names one kernel, a few launches (a whole
+    30-iteration solve for the PCG iteration), the clock-control flag and the
+    176 x 240 x 128 volume, never the full-size fit."""
+    for kind, cmd in zip(bench.TRAFFIC_CAPTURES, bench.TRAFFIC_COMMANDS):
+        assert "--clock-control none" in cmd and "-k regex:" in cmd
+        assert "--shape 176,240,128" in cmd and "--print-hashes" in cmd
+        count = int(cmd.split(" -c ")[1].split()[0])
+        assert count <= (30 if kind == "pcg_step" else 3)
+    assert bench.TRAFFIC_COMMANDS[-1].startswith("python bench.py --write-traffic")
 
 
 def test_launch_table_shares(tmp_path):

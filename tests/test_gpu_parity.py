@@ -238,7 +238,7 @@ def test_bf16_echoes(mpm):
 
 @pytest.mark.parametrize("tile", [0, 1, 2])
 def test_solve_every_stencil_tile_shape(mpm, tile):
-    """The TMA matvec in each tile shape (16x16, 32x8, 64x4) on a volume with
+    """The TMA PCG iteration in each tile shape (16x16, 32x8, 64x4) on a volume with
     ragged tiles in x and y, against the oracle."""
     shape = (76, 21, 9)
     d = dataset(shape, seed=81)

@@ -1,6 +1,6 @@
 """The library's host-side decisions on the CPU: the server's arena and
 admission pick, the lanes of a batched graph and the z split of the TMA
-matvec.  They live in csrc/host_logic.h, which needs no CUDA; a small C++
+PCG iteration.  They live in csrc/host_logic.h, which needs no CUDA; a small C++
 harness compiled here with g++ exposes them through ctypes, and every check
 below is a property the decision must have, under seeded random inputs."""
 import ctypes
