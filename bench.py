@@ -676,7 +676,7 @@ def run_ours(args):
                                "PCG + posterior variance"
                                + (", echoes stored bf16" if args.echo_dtype == "bf16" else ""),
                    "echo_storage": args.echo_dtype,
-                   "stencil_tile": ["16x16", "32x8", "64x4"][tile] if tile >= 0 else "smem",
+                   "stencil_tile": ["16x16", "32x8"][tile] if tile >= 0 else "plain kernel",
                    "tile_autotune_us": [round(1000 * t, 1) for t in tile_ms],
                    "voxels": N, "gn_iters": GN_ITERS, "cg_iters": CG_ITERS, "lambda": LAMBDA,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",

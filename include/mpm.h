@@ -182,8 +182,8 @@ mpm_status mpm_solve(const mpm_problem* problem, const mpm_opts* opts, const flo
  * minus (ws, ws_bytes), and keeps its scratch in a fixed 64 MiB device array
  * owned by the library.  Every GPU that loads the library holds that array
  * until the process exits.
- *  - Size limit: problems whose solve scratch exceeds 64 MiB (about 550 000
- *    voxels with four maps, e.g. 80^3) are refused with
+ *  - Size limit: problems whose solve scratch exceeds 64 MiB (about 500 000
+ *    voxels, e.g. 96 x 80 x 64) are refused with
  *    MPM_ERR_WORKSPACE_TOO_SMALL and a message giving the bytes needed; use
  *    mpm_solve with a workspace for those.
  *  - Allocates nothing: no cudaMalloc, no cudaFree, no allocating library
@@ -221,8 +221,8 @@ mpm_status mpm_fit(const mpm_problem* problem, const mpm_opts* opts, const void*
                    void* ws, size_t ws_bytes, mpm_report* report, void* stream);
 
 /* Tile-shape autotuner for the PCG iteration kernel of the solve.  The
- * TMA-staged iteration can tile the (x, y) plane as 16 x 16, 32 x 8 or
- * 64 x 4 voxels; this
+ * TMA-staged iteration can tile the (x, y) plane as 16 x 16 or 32 x 8
+ * voxels; this
  * call times each applicable shape on this volume (zeroed operands in `ws`, a
  * MPM_CALL_SOLVE-sized workspace or larger), keeps the fastest for every later
  * solve of a volume of this size in the process, and writes its index to
@@ -233,7 +233,7 @@ mpm_status mpm_fit(const mpm_problem* problem, const mpm_opts* opts, const void*
  * be NULL).  Without either, a default shape is used.  A shape that does not
  * fit a volume falls back to the plain iteration kernel.  Synchronises
  * `stream` when timing. */
-#define MPM_TILE_SHAPES 3
+#define MPM_TILE_SHAPES 2
 mpm_status mpm_autotune(const mpm_problem* problem, const mpm_opts* opts, void* ws,
                         size_t ws_bytes, void* stream, int* tile, float* ms);
 

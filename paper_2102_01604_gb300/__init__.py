@@ -218,7 +218,7 @@ def mpm_autotune(problem, opts, ws=None, stream=None, tile=-1):
     if tile < 0 and ws is None:
         ws = workspace(problem, opts, _lib.CALL_SOLVE)
     tile = ctypes.c_int(tile)
-    ms = (ctypes.c_float * 3)()
+    ms = (ctypes.c_float * _lib.TILE_SHAPES)()
     _lib.check(lib.mpm_autotune(ctypes.byref(problem), ctypes.byref(opts),
                                 _ptr(ws, "ws", optional=True), ws.numel() if ws is not None else 0,
                                 _stream(stream), ctypes.byref(tile), ms),

@@ -248,7 +248,6 @@ FitWs layout(const DevProblem& P, int call, void* base)
         L.w = reinterpret_cast<float*>(take(sizeof(float) * (size_t)P.N));
         L.g = reinterpret_cast<float*>(take(vec));
         L.h = reinterpret_cast<float*>(take(sizeof(float) * (size_t)P.T * P.N));
-        L.xbuf = reinterpret_cast<float*>(take(vec));
     }
     if (call == MPM_CALL_FIT || call == MPM_CALL_SOLVE) L.solve = take(solve_ws_bytes(P));
     L.total = off;
@@ -424,7 +423,7 @@ static cudaError_t fit_enqueue_updates(const FitJob& j, cudaStream_t st, int* it
         if ((e = launch_jtv(P, j.y, w_fresh ? L.w : nullptr, L.jtv + it, L.red, st))) return e;
         if ((e = launch_lik(j, it, st))) return e;
         if (it >= j.opts.gn_iters) break;
-        if ((e = launch_solve(P, j.opts.cg_iters, j.opts.tol_cg, L.h, L.w, L.g, j.y, L.xbuf, j.y,
+        if ((e = launch_solve(P, j.opts.cg_iters, j.opts.tol_cg, L.h, L.w, L.g, j.y, nullptr, j.y,
                               nullptr, L.cg_rel + it, L.cg_it + it, L.solve, L.hdr, L.red, st)))
             return e;
     }
@@ -462,7 +461,7 @@ static mpm_status fit_run_adaptive(const FitJob& j, cudaStream_t st, int* iters_
             break;
         }
         F_prev = F;
-        MPM_CUDA(launch_solve(P, j.opts.cg_iters, j.opts.tol_cg, L.h, L.w, L.g, j.y, L.xbuf, j.y,
+        MPM_CUDA(launch_solve(P, j.opts.cg_iters, j.opts.tol_cg, L.h, L.w, L.g, j.y, nullptr, j.y,
                               nullptr, L.cg_rel + it, L.cg_it + it, L.solve, L.hdr, L.red, st));
     }
     if (j.var) {

@@ -64,16 +64,15 @@ size_t solve_ws_bytes(const DevProblem& P);
 // when the volume or the pointers do not meet the copy engine's alignment
 // rules; the plain kernel is used then.
 struct StepMaps {
-    CUtensorMap z[2], v[2], p[3];   // halo boxes of the solve buffers
+    CUtensorMap z[2], v[2], p[3];   // halo boxes of the solve's vectors
     CUtensorMap p2[3], x;           // tile boxes (x fold)
     CUtensorMap w, h;
     SolveBufs B;
-    float* xacc;
     int tile;          // index of the tile shape the maps were encoded for
 };
 int tma_tile_count();
 bool make_step_maps(const DevProblem& P, const float* h, const float* w, const SolveBufs& B,
-                    float* xacc, int tile, StepMaps* out);
+                    int tile, StepMaps* out);
 StencilGrid tma_grid(const DevProblem& P, int tile);
 cudaError_t prime_tma_kernels();   // shared-memory opt-ins, done before any graph capture
 int tma_tile_choice(const DevProblem& P);   // tile shape for this volume (tuned or default)
@@ -84,8 +83,10 @@ void tma_tile_set(const DevProblem& P, int tile);
 // the mean time of shape i (or -1).  Synchronises the stream.
 cudaError_t tma_autotune(const DevProblem& P, void* solve_ws, WsHeader* hdr, Reduce red,
                          cudaStream_t st, int* best, float* ms);
+// Iteration j (mode kMode*) of a solve; want_rr also reduces the |r|^2 sums.
 cudaError_t launch_step_tma(const DevProblem& P, const StencilGrid& g, const StepMaps& m, int j,
-                            int flags, WsHeader* hdr, double* resid, Reduce red, cudaStream_t st);
+                            int mode, int want_rr, WsHeader* hdr, double* resid, Reduce red,
+                            cudaStream_t st);
 // Test hook: with withhold set, the TMA iteration's producer issues no copies;
 // every bounded wait gives up after wait_cycles clock cycles (<= 0: default).
 void set_copy_test(int withhold, long long wait_cycles);
@@ -109,7 +110,6 @@ struct FitWs {
     float* w;
     float* g;
     float* h;
-    float* xbuf;
     void* solve;
     size_t total;
 };

@@ -22,6 +22,11 @@
 // six edge coefficients, is factorised in every iteration from H and the JTV
 // weights (its float32 Cholesky factor is the same each time), so the solve
 // stores no factor.
+//
+// The solve's own vectors (z, v, p and the accumulated x) are stored voxel
+// by voxel, four floats per voxel (K = 3 leaves the fourth zero), so one
+// 16-byte access moves all maps of a voxel; H, w and the caller's arrays stay
+// planar [component][N].
 #pragma once
 
 #include "device_common.cuh"
@@ -45,8 +50,7 @@ __device__ __forceinline__ bool cholesky_f32(const float (&M)[K][K], float (&L)[
             ok = false;
             s = fmaxf(fabsf(M[j][j]), 1e-30f);
         }
-        const float dj = sqrtf(s);
-        const float rj = 1.0f / dj;
+        const float rj = rsqrtf(s);      // 1 / L_jj
         L[lo(j, j)] = rj;
 #pragma unroll
         for (int i = j + 1; i < K; ++i) {
@@ -100,19 +104,37 @@ __device__ __forceinline__ float edge_sum(const float (&c)[6])
     return ((((c[0] + c[1]) + c[2]) + c[3]) + c[4]) + c[5];
 }
 
-// Per-solve workspace buffers, all [K][N] float, 256-byte aligned.
+// Per-solve workspace buffers: [N] float4 each (voxel-interleaved maps),
+// 256-byte aligned.
 struct SolveBufs {
-    float* z[2];     // preconditioned residual z_j in z[j & 1]
-    float* v[2];     // v_j = M^-1 q_j in v[j & 1]
-    float* p[3];     // direction p_j in p[j % 3]
+    float4* z[2];    // preconditioned residual z_j in z[j & 1]
+    float4* v[2];    // v_j = M^-1 q_j in v[j & 1]
+    float4* p[3];    // direction p_j in p[j % 3]
+    float4* x;       // sum of the directions folded so far, alpha_i p_i
 };
 
-// Flags of one iteration's launch.
+template <int K>
+__device__ __forceinline__ void unpack4(const float4& a, float (&o)[K])
+{
+    o[0] = a.x;
+    o[1] = a.y;
+    o[2] = a.z;
+    if constexpr (K > 3) o[3] = a.w;
+}
+
+template <int K>
+__device__ __forceinline__ float4 pack4(const float (&o)[K])
+{
+    if constexpr (K > 3) return make_float4(o[0], o[1], o[2], o[3]);
+    else return make_float4(o[0], o[1], o[2], 0.0f);
+}
+
+// What one iteration's launch does besides the common work.
 enum : int {
-    kStepFirst = 1,    // j = 0: z_0 comes from the init kernel, p_0 = z_0
-    kStepFold = 2,     // even j >= 2: x += alpha_{j-2} p_{j-2} + alpha_{j-1} p_{j-1}
-    kStepReadX = 4,    // x already holds earlier directions (j > 2)
-    kStepResid = 8     // also reduce the sums of |r_{j+1}|^2
+    kModeFirst = 0,    // j = 0: z_0 comes from the init kernel, p_0 = z_0
+    kModeStep = 1,     // odd j
+    kModeFold = 2,     // j = 2: also x = alpha_0 p_0 + alpha_1 p_1
+    kModeFoldX = 3     // even j > 2: also x += alpha_{j-2} p_{j-2} + alpha_{j-1} p_{j-1}
 };
 
 // Sums reduced by every iteration, in this order.
@@ -120,23 +142,31 @@ enum : int { kSumPQ, kSumZQ, kSumVQ, kSumZR, kSumRR, kSumRQ, kSumQQ, kStepSums }
 
 // z_j and p_j of one point from the previous iteration's z, v, p (at j = 0,
 // z is z_0 and v, p are not read).
-template <int K>
-__device__ __forceinline__ void step_point(bool first, float alpha, float beta, const float (&z)[K],
-                                           const float (&v)[K], const float (&p)[K], float (&zj)[K],
-                                           float (&pj)[K])
+template <int K, bool FIRST>
+__device__ __forceinline__ void step_point(float alpha, float beta, const float4& z4, const float4& v4,
+                                           const float4& p4, float (&zj)[K], float (&pj)[K])
 {
+    float z[K], v[K], p[K];
+    unpack4<K>(z4, z);
+    unpack4<K>(v4, v);
+    unpack4<K>(p4, p);
 #pragma unroll
     for (int a = 0; a < K; ++a) {
-        zj[a] = first ? z[a] : fmaf(-alpha, v[a], z[a]);
-        pj[a] = first ? zj[a] : fmaf(beta, p[a], zj[a]);
+        zj[a] = FIRST ? z[a] : fmaf(-alpha, v[a], z[a]);
+        pj[a] = FIRST ? zj[a] : fmaf(beta, p[a], zj[a]);
     }
 }
 
 // x after folding in the two latest directions, in the order of two single
-// updates: x + alpha_{j-2} p_{j-2}, then + alpha_{j-1} p_{j-1}.
-__device__ __forceinline__ float fold_x(float x, float alpha_prev, float p2, float alpha, float p1)
+// updates: x + alpha_{j-2} p_{j-2}, then + alpha_{j-1} p_{j-1} (all four
+// components; the padding of K = 3 stays zero).
+__device__ __forceinline__ float4 fold_x(const float4& x, float alpha_prev, const float4& p2, float alpha,
+                                         const float4& p1)
 {
-    return fmaf(alpha, p1, fmaf(alpha_prev, p2, x));
+    return make_float4(fmaf(alpha, p1.x, fmaf(alpha_prev, p2.x, x.x)),
+                       fmaf(alpha, p1.y, fmaf(alpha_prev, p2.y, x.y)),
+                       fmaf(alpha, p1.z, fmaf(alpha_prev, p2.z, x.z)),
+                       fmaf(alpha, p1.w, fmaf(alpha_prev, p2.w, x.w)));
 }
 
 // One voxel of iteration j: q = (H + L) p_j with the weighted 7-point stencil

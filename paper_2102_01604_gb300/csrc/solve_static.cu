@@ -73,7 +73,7 @@ extern "C" mpm_status mpm_solve_static(const mpm_problem* problem, const mpm_opt
                     "caller workspace",
                     need, kStaticScratchBytes,
                     (long long)((kStaticScratchBytes - kHeaderBytes - kPartialBytes) /
-                                (sizeof(float) * 7 * P.K)),
+                                (sizeof(float4) * 8)),
                     P.K);
     if ((s = check_dev(h, "h", false, 4)) != MPM_OK) return s;
     if ((s = check_dev(w, "w", false, 4)) != MPM_OK) return s;

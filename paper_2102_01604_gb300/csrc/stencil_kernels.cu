@@ -115,20 +115,18 @@ __global__ void __launch_bounds__(kBlock) k_jtv(DevProblem P, int zc, const floa
 
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-size_t solve_ws_bytes(const DevProblem& P)
-{
-    const size_t vec = align256(sizeof(float) * (size_t)P.K * P.N);
-    return 7 * vec;
-}
+// z[2], v[2], p[3] and x, each [N] float4.
+size_t solve_ws_bytes(const DevProblem& P) { return 8 * align256(sizeof(float4) * (size_t)P.N); }
 
 static SolveBufs carve(const DevProblem& P, void* ws)
 {
     SolveBufs b;
     char* c = static_cast<char*>(ws);
-    const size_t vec = align256(sizeof(float) * (size_t)P.K * P.N);
-    for (float*& v : b.z) { v = reinterpret_cast<float*>(c); c += vec; }
-    for (float*& v : b.v) { v = reinterpret_cast<float*>(c); c += vec; }
-    for (float*& v : b.p) { v = reinterpret_cast<float*>(c); c += vec; }
+    const size_t vec = align256(sizeof(float4) * (size_t)P.N);
+    for (float4*& v : b.z) { v = reinterpret_cast<float4*>(c); c += vec; }
+    for (float4*& v : b.v) { v = reinterpret_cast<float4*>(c); c += vec; }
+    for (float4*& v : b.p) { v = reinterpret_cast<float4*>(c); c += vec; }
+    b.x = reinterpret_cast<float4*>(c);
     return b;
 }
 
@@ -138,7 +136,7 @@ template <int K>
 __global__ void __launch_bounds__(kBlock) k_pcg_init(DevProblem P, int zc, const float* __restrict__ h,
                                                      const float* __restrict__ w,
                                                      const float* __restrict__ g,
-                                                     const float* __restrict__ y, float* __restrict__ z0,
+                                                     const float* __restrict__ y, float4* __restrict__ z0,
                                                      double tol2, WsHeader* hdr, double* resid,
                                                      Reduce red)
 {
@@ -175,10 +173,10 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(DevProblem P, int zc, const
             float L[T], zz[K];
             pd &= cholesky_f32<K>(M, L);
             chol_apply<K>(L, r, zz);
+            z0[n] = pack4<K>(zz);
             float vrz = 0.0f, vrr = 0.0f;
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                z0[k * N + n] = zz[k];
                 vrz += r[k] * zz[k];
                 vrr += r[k] * r[k];
             }
@@ -213,19 +211,20 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(DevProblem P, int zc, const
 // marching a run of z planes; each neighbour's p_j is formed from its own
 // (z, v, p) read from memory.  Used for volumes or pointers the TMA kernel
 // cannot take (nx not a multiple of 4, a volume smaller than a tile).
-template <int K>
-__global__ void __launch_bounds__(kBlock) k_pcg_step(DevProblem P, int zc, int j, int flags,
+template <int K, int MODE>
+__global__ void __launch_bounds__(kBlock) k_pcg_step(DevProblem P, int zc, int j, int want_rr,
                                                      const float* __restrict__ h,
                                                      const float* __restrict__ w,
-                                                     const float* __restrict__ zin,
-                                                     const float* __restrict__ vin,
-                                                     const float* __restrict__ pin,
-                                                     const float* __restrict__ p2,
-                                                     float* __restrict__ zout, float* __restrict__ vout,
-                                                     float* __restrict__ pout, float* __restrict__ xacc,
+                                                     const float4* __restrict__ zin,
+                                                     const float4* __restrict__ vin,
+                                                     const float4* __restrict__ pin,
+                                                     const float4* __restrict__ p2,
+                                                     float4* __restrict__ zout, float4* __restrict__ vout,
+                                                     float4* __restrict__ pout, float4* __restrict__ xacc,
                                                      WsHeader* hdr, double* resid, Reduce red)
 {
     constexpr int T = K * (K + 1) / 2;
+    constexpr bool first = MODE == kModeFirst;
     __shared__ float s_alpha, s_alpha_prev, s_beta;
     __shared__ int s_done;
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
@@ -237,26 +236,18 @@ __global__ void __launch_bounds__(kBlock) k_pcg_step(DevProblem P, int zc, int j
     }
     __syncthreads();
     if (s_done) return;
-    const bool first = flags & kStepFirst, fold = flags & kStepFold, readx = flags & kStepReadX;
-    const bool want_rr = flags & kStepResid;
-    if (fold && tid == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) hdr->sc.xcount = j;
+    if (MODE >= kModeFold && tid == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0)
+        hdr->sc.xcount = j;
     const float alpha = s_alpha, alpha_prev = s_alpha_prev, beta = s_beta;
-    const long long N = P.N;
     const long long sxy = (long long)P.nx * P.ny;
     const int x = blockIdx.x * kTileX + threadIdx.x;
     const int yy = blockIdx.y * kTileY + threadIdx.y;
     const int z0p = blockIdx.z * zc;
     const int z1p = min(P.nz, z0p + zc);
-    Acc acc[kStepSums];
+    float part[kStepSums] = {};
     auto point = [&](long long m, float (&zj)[K], float (&pj)[K]) {
-        float zz[K], vv[K], pp[K];
-#pragma unroll
-        for (int a = 0; a < K; ++a) {
-            zz[a] = __ldg(zin + a * N + m);
-            vv[a] = first ? 0.0f : __ldg(vin + a * N + m);
-            pp[a] = first ? 0.0f : __ldg(pin + a * N + m);
-        }
-        step_point<K>(first, alpha, beta, zz, vv, pp, zj, pj);
+        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+        step_point<K, first>(alpha, beta, zin[m], first ? zero : vin[m], first ? zero : pin[m], zj, pj);
     };
     if (x < P.nx && yy < P.ny) {
         for (int z = z0p; z < z1p; ++z) {
@@ -278,27 +269,23 @@ __global__ void __launch_bounds__(kBlock) k_pcg_step(DevProblem P, int zc, int j
             }
             float hv[T];
 #pragma unroll
-            for (int t = 0; t < T; ++t) hv[t] = __ldg(h + t * N + n);
+            for (int t = 0; t < T; ++t) hv[t] = __ldg(h + t * P.N + n);
             float v[K], sums[kStepSums];
             step_voxel<K>(P, e.c, zj, pj, [&](int m, int a) { return nb[m][a]; }, hv, want_rr, v, sums);
-#pragma unroll
-            for (int a = 0; a < K; ++a) {
-                if (!first) zout[a * N + n] = zj[a];
-                pout[a * N + n] = pj[a];
-                vout[a * N + n] = v[a];
-            }
-            if (fold) {
-#pragma unroll
-                for (int a = 0; a < K; ++a) {
-                    const float xo = readx ? xacc[a * N + n] : 0.0f;
-                    xacc[a * N + n] = fold_x(xo, alpha_prev, __ldg(p2 + a * N + n), alpha,
-                                             __ldg(pin + a * N + n));
-                }
+            if (!first) zout[n] = pack4<K>(zj);
+            pout[n] = pack4<K>(pj);
+            vout[n] = pack4<K>(v);
+            if (MODE >= kModeFold) {
+                const float4 x0 = MODE == kModeFoldX ? xacc[n] : make_float4(0.f, 0.f, 0.f, 0.f);
+                xacc[n] = fold_x(x0, alpha_prev, p2[n], alpha, pin[n]);
             }
 #pragma unroll
-            for (int i = 0; i < kStepSums; ++i) acc[i].add(sums[i]);
+            for (int i = 0; i < kStepSums; ++i) part[i] += sums[i];
         }
     }
+    Acc acc[kStepSums];
+#pragma unroll
+    for (int i = 0; i < kStepSums; ++i) acc[i].add(part[i]);
     double out[kStepSums];
     if (grid_reduce<kStepSums>(acc, red, out) && tid == 0) step_scalars(out, j, want_rr, hdr, resid);
 }
@@ -306,9 +293,9 @@ __global__ void __launch_bounds__(kBlock) k_pcg_step(DevProblem P, int zc, int j
 // -------------------------------------------------------------- PCG final
 
 // delta = x + the directions not yet folded into x (none, p_{it-1}, or
-// p_{it-2} and p_{it-1}), or y <- y - delta.
-__global__ void __launch_bounds__(kBlock) k_pcg_final(long long total, SolveBufs B,
-                                                      const float* __restrict__ xacc,
+// p_{it-2} and p_{it-1}), written planar, or y <- y - delta.
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_pcg_final(long long N, SolveBufs B,
                                                       float* __restrict__ delta,
                                                       float* __restrict__ y_update,
                                                       const WsHeader* hdr, double* report_rel,
@@ -318,17 +305,34 @@ __global__ void __launch_bounds__(kBlock) k_pcg_final(long long total, SolveBufs
     const bool have_x = sc.xcount > 0;
     const int pend = sc.it - sc.xcount;        // directions not yet in x: 0, 1 or 2
     const float alpha = (float)sc.alpha, alpha_prev = (float)sc.alpha_prev;
-    const float* __restrict__ pp = B.p[(sc.it + 2) % 3];    // p_{it-1}
-    const float* __restrict__ pp2 = B.p[(sc.it + 1) % 3];   // p_{it-2} when pend == 2
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        float v = have_x ? xacc[i] : 0.0f;
-        if (pend == 2) v = fmaf(alpha_prev, pp2[i], v);
-        if (pend >= 1) v = fmaf(alpha, pp[i], v);
-        if (y_update)
-            y_update[i] -= v;
-        else
-            delta[i] = v;
+    const float4* __restrict__ pp = B.p[(sc.it + 2) % 3];    // p_{it-1}
+    const float4* __restrict__ pp2 = B.p[(sc.it + 1) % 3];   // p_{it-2} when pend == 2
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        float v[K], t[K];
+        if (have_x) {
+            unpack4<K>(B.x[n], v);
+        } else {
+#pragma unroll
+            for (int a = 0; a < K; ++a) v[a] = 0.0f;
+        }
+        if (pend == 2) {
+            unpack4<K>(pp2[n], t);
+#pragma unroll
+            for (int a = 0; a < K; ++a) v[a] = fmaf(alpha_prev, t[a], v[a]);
+        }
+        if (pend >= 1) {
+            unpack4<K>(pp[n], t);
+#pragma unroll
+            for (int a = 0; a < K; ++a) v[a] = fmaf(alpha, t[a], v[a]);
+        }
+#pragma unroll
+        for (int a = 0; a < K; ++a) {
+            if (y_update)
+                y_update[a * N + n] -= v[a];
+            else
+                delta[a * N + n] = v[a];
+        }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         if (report_rel) *report_rel = sc.rr0 > 0.0 ? sqrt(sc.rr / sc.rr0) : 0.0;
@@ -369,15 +373,32 @@ cudaError_t launch_jtv(const DevProblem& P, const float* y, float* w, double* jt
     return cudaGetLastError();
 }
 
-// Launch flags of iteration j of a solve of cg_iters iterations.
-static int step_flags(int j, int cg_iters, bool want_resid)
+// What iteration j of a solve does besides the common work.
+static int step_mode(int j)
 {
-    int f = 0;
-    if (j == 0) f |= kStepFirst;
-    if (j >= 2 && j % 2 == 0) f |= kStepFold;
-    if (j > 2 && j % 2 == 0) f |= kStepReadX;
-    if (want_resid || j == cg_iters - 1) f |= kStepResid;
-    return f;
+    if (j == 0) return kModeFirst;
+    if (j % 2) return kModeStep;
+    return j == 2 ? kModeFold : kModeFoldX;
+}
+
+template <int K>
+static void launch_step_plain(const DevProblem& P, const StencilGrid& sg, int j, int want_rr,
+                              const float* h, const float* w, const SolveBufs& B, WsHeader* hdr,
+                              double* resid, Reduce red, cudaStream_t st)
+{
+    const int jm = j > 0 ? j - 1 : 0;
+    const float4 *zin = B.z[jm & 1], *vin = B.v[jm & 1], *pin = B.p[(j + 2) % 3], *p2 = B.p[(j + 1) % 3];
+    float4 *zout = B.z[j & 1], *vout = B.v[j & 1], *pout = B.p[j % 3];
+#define MPM_STEP_PLAIN(M)                                                                          \
+    k_pcg_step<K, M><<<sg.grid, sg.block, 0, st>>>(P, sg.zc, j, want_rr, h, w, zin, vin, pin, p2, zout, \
+                                                   vout, pout, B.x, hdr, resid, red)
+    switch (step_mode(j)) {
+    case kModeFirst: MPM_STEP_PLAIN(kModeFirst); break;
+    case kModeStep: MPM_STEP_PLAIN(kModeStep); break;
+    case kModeFold: MPM_STEP_PLAIN(kModeFold); break;
+    default: MPM_STEP_PLAIN(kModeFoldX); break;
+    }
+#undef MPM_STEP_PLAIN
 }
 
 template <int K>
@@ -388,9 +409,6 @@ static cudaError_t solve_k(const DevProblem& P, int cg_iters, double tol_cg, con
 {
     const StencilGrid sg = stencil_grid(P, kTileX, kTileY);
     SolveBufs B = carve(P, solve_ws);
-    // x accumulates in `delta` (the caller's output when solving alone, a
-    // workspace buffer inside the fit, which then passes y_update).
-    float* xacc = delta;
     const double tol2 = tol_cg > 0.0 ? tol_cg * tol_cg : 0.0;
     {
         LaunchScope ls(MPM_KERNEL_PCG_INIT, st);
@@ -398,25 +416,22 @@ static cudaError_t solve_k(const DevProblem& P, int cg_iters, double tol_cg, con
     }
     StepMaps maps;
     const int tile = tma_tile_choice(P);
-    const bool tma = tile >= 0 && make_step_maps(P, h, w, B, xacc, tile, &maps);
+    const bool tma = tile >= 0 && make_step_maps(P, h, w, B, tile, &maps);
     const StencilGrid tg = tma ? tma_grid(P, tile) : sg;
     const bool want_resid = resid != nullptr || tol2 > 0.0;
     for (int j = 0; j < cg_iters; ++j) {
-        const int flags = step_flags(j, cg_iters, want_resid);
+        const int rr = (want_resid || j == cg_iters - 1) ? 1 : 0;
         LaunchScope ls(MPM_KERNEL_PCG_STEP, st);
         if (tma) {
-            cudaError_t e = launch_step_tma(P, tg, maps, j, flags, hdr, resid, red, st);
+            cudaError_t e = launch_step_tma(P, tg, maps, j, step_mode(j), rr, hdr, resid, red, st);
             if (e != cudaSuccess) return e;
         } else {
-            const int jm = j > 0 ? j - 1 : 0;
-            k_pcg_step<K><<<sg.grid, sg.block, 0, st>>>(
-                P, sg.zc, j, flags, h, w, B.z[jm & 1], B.v[jm & 1], B.p[(j + 2) % 3], B.p[(j + 1) % 3],
-                B.z[j & 1], B.v[j & 1], B.p[j % 3], xacc, hdr, resid, red);
+            launch_step_plain<K>(P, sg, j, rr, h, w, B, hdr, resid, red, st);
         }
     }
     LaunchScope ls(MPM_KERNEL_PCG_FINAL, st);
-    k_pcg_final<<<voxel_grid(P.N * K), kBlock, 0, st>>>(P.N * K, B, xacc, delta, y_update, hdr,
-                                                        report_rel, report_it);
+    k_pcg_final<K><<<voxel_grid(P.N), kBlock, 0, st>>>(P.N, B, delta, y_update, hdr, report_rel,
+                                                       report_it);
     return cudaGetLastError();
 }
 
@@ -424,19 +439,20 @@ cudaError_t tma_autotune(const DevProblem& P, void* solve_ws, WsHeader* hdr, Red
                          cudaStream_t st, int* best, float* ms)
 {
     *best = -1;
-    // Timed on zeroed operands carved from the solve workspace's seven vectors
+    // Timed on zeroed operands carved from the solve workspace's eight vectors
     // so that no buffer the launch writes is also read: iteration 3 reads z, v
-    // and p from vectors 0-2 and p_{j-2} from 3, writes z, v, p to 4-6; H and w
-    // alias the read-only vectors 0-3.
-    const size_t vec = align256(sizeof(float) * (size_t)P.K * P.N);
+    // and p from vectors 0-2, writes z, v, p to 4-6; H and w alias the
+    // read-only vectors 0-3 (T N floats fit in 0-2 for K = 3, 4).
+    const size_t vec = align256(sizeof(float4) * (size_t)P.N);
     char* c = static_cast<char*>(solve_ws);
-    auto at = [&](int i) { return reinterpret_cast<float*>(c + i * vec); };
+    auto at = [&](int i) { return reinterpret_cast<float4*>(c + i * vec); };
     SolveBufs B;
     B.z[0] = at(0); B.z[1] = at(4);
     B.v[0] = at(1); B.v[1] = at(5);
     B.p[2] = at(2); B.p[1] = at(3); B.p[0] = at(6);
-    const float* h = at(0);       // T N floats <= 3 K N (K = 3, 4)
-    const float* w = at(3);
+    B.x = at(7);
+    const float* h = reinterpret_cast<const float*>(at(0));
+    const float* w = reinterpret_cast<const float*>(at(3));
     cudaError_t e;
     if ((e = cudaMemsetAsync(solve_ws, 0, solve_ws_bytes(P), st)) != cudaSuccess) return e;
     cudaEvent_t a, b;
@@ -449,13 +465,13 @@ cudaError_t tma_autotune(const DevProblem& P, void* solve_ws, WsHeader* hdr, Red
     for (int t = 0; t < tma_tile_count(); ++t) {
         ms[t] = -1.0f;
         StepMaps m;
-        if (!make_step_maps(P, h, w, B, at(3), t, &m)) continue;
+        if (!make_step_maps(P, h, w, B, t, &m)) continue;
         const StencilGrid g = tma_grid(P, t);
         constexpr int reps = 5;
         for (int i = 0; i <= reps && e == cudaSuccess; ++i) {
             if (i == 1) e = cudaEventRecord(a, st);
             if (e == cudaSuccess) e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st);
-            if (e == cudaSuccess) e = launch_step_tma(P, g, m, 3, kStepResid, hdr, nullptr, red, st);
+            if (e == cudaSuccess) e = launch_step_tma(P, g, m, 3, kModeStep, 0, hdr, nullptr, red, st);
         }
         if (e == cudaSuccess) e = cudaEventRecord(b, st);
         if (e == cudaSuccess) e = cudaEventSynchronize(b);

@@ -8,12 +8,14 @@
 //   q_j = (H + L) p_j,  v_j = M^-1 q_j,  and the sums for alpha_j and beta_j.
 // A block owns a TX x TY tile and marches up a run of z planes.  Per plane
 // one thread issues bulk tensor copies into a ring of "raw" stages:
-//   z, v, p   box (TX+8) x (TY+2) x 1 x K at (x0 - 4, y0 - 1, z, 0)
-//   w         box (TX+8) x (TY+2) x 1     (same origin)
-//   x, p_j-2  box TX x TY x 1 x K at (x0, y0, z, 0) (even j >= 2, x fold)
-// and H (box TX x TY x 1 x T) into a second ring.  x coordinates are
-// multiples of 4 floats (16 bytes); boxes that leave the volume are
-// zero-filled by the copy engine and masked by zero stencil coefficients.
+//   z, v, p   (TX+2) x (TY+2) voxels of 4 floats at (x0 - 1, y0 - 1, z)
+//   w         (TX+8) x (TY+2) floats at (x0 - 4, y0 - 1, z)
+//   x, p_j-2  TX x TY voxels of 4 floats at (x0, y0, z) (even j >= 2, x fold)
+// and H (TX x TY x T floats, planar) into a second ring.  The solve's own
+// vectors hold 4 floats per voxel, so their boxes start 16-byte aligned at
+// any x; the planar w box starts at a multiple of 4 floats.  Boxes that leave
+// the volume are zero-filled by the copy engine and masked by zero stencil
+// coefficients.
 //
 // Eight compute warps (one voxel per thread) take each plane in two phases:
 //   A  form z_j and p_j of the plane's points (the tile and its x / y halo,
@@ -27,7 +29,9 @@
 // of a formed plane from B's reads of it; with three formed planes in the
 // ring, A never overwrites a plane B may still read.  A producer warp keeps
 // both rings full; a stage is refilled once all eight compute warps have
-// released it.
+// released it.  Each thread sums its voxels' terms in float32 over one item
+// (at most one z range of its column) and adds that partial to compensated
+// accumulators, which the block and the grid reduce in float64.
 //
 // Every mbarrier wait is bounded: on timeout the block records
 // kStatusTimeout, stops computing (its warps still pass the same named
@@ -67,27 +71,27 @@ void set_copy_test(int withhold, long long wait_cycles)
 template <int K, int TX, int TY>
 struct StepLayout {
     static constexpr int T = K * (K + 1) / 2;
-    static constexpr int BX = TX + 8, BY = TY + 2;      // halo box (x from x0 - 4, y from y0 - 1)
-    static constexpr int SX = TX + 2, SY = TY + 2;      // formed plane: tile plus one voxel
-    static constexpr int BOX = BX * BY, TILE = TX * TY, SPL = SX * SY;
+    static constexpr int BX = TX + 2, BY = TY + 2;      // z / v / p box and formed plane (x from x0 - 1)
+    static constexpr int WX = TX + 8;                   // w box (x from x0 - 4, 16-byte aligned)
     static constexpr int NH = 2 * (TX + TY);            // halo points of a formed plane
     static constexpr int a128(int b) { return (b + 127) / 128 * 128; }
-    static constexpr int HALO_BYTES = K * BOX * 4, W_BYTES = BOX * 4;
-    static constexpr int TILE_BYTES = K * TILE * 4, H_BYTES = T * TILE * 4;
+    static constexpr int BOX_BYTES = BX * BY * 16, W_BYTES = WX * BY * 4;
+    static constexpr int TILE_BYTES = TX * TY * 16, H_BYTES = T * TX * TY * 4;
     static constexpr int Z_OFF = 0;
-    static constexpr int V_OFF = a128(HALO_BYTES);
-    static constexpr int P_OFF = V_OFF + a128(HALO_BYTES);
-    static constexpr int W_OFF = P_OFF + a128(HALO_BYTES);
+    static constexpr int V_OFF = a128(BOX_BYTES);
+    static constexpr int P_OFF = V_OFF + a128(BOX_BYTES);
+    static constexpr int W_OFF = P_OFF + a128(BOX_BYTES);
     static constexpr int X_OFF = W_OFF + a128(W_BYTES);
     static constexpr int P2_OFF = X_OFF + a128(TILE_BYTES);
     static constexpr int RAW = P2_OFF + a128(TILE_BYTES);
     static constexpr int H_STAGE = a128(H_BYTES);
-    static constexpr int SLOT = a128(K * SPL * 4);
+    static constexpr int SLOT = a128(BOX_BYTES);
     static constexpr int H_BASE = kStepRaw * RAW;
     static constexpr int S_BASE = H_BASE + kStepH * H_STAGE;
     static constexpr int SMEM = S_BASE + 3 * SLOT + 128;   // + alignment slack
     static_assert(TX * TY == kStepVoxels, "one compute thread per voxel");
     static_assert(NH <= kStepVoxels, "one halo point per thread at most");
+    static_assert(4 * BX <= 256 && 4 * TX <= 256, "TMA box rows of at most 256 elements");
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -170,18 +174,19 @@ __device__ __forceinline__ void compute_warps_sync()
 // over planes [za, zb) loads planes za - 1 .. zb (those inside the volume);
 // the planes outside [za, zb) only supply the z neighbours of its own column.
 // The rings and their phases run on from one item to the next.
-template <int K, int TX, int TY>
+template <int K, int TX, int TY, int MODE>
 __global__ void __launch_bounds__(kStepThreads, 2) k_pcg_step_tma(
-    DevProblem P, int nchunk, int j, int flags, const __grid_constant__ CUtensorMap tz,
+    DevProblem P, int nchunk, int j, int want_rr, const __grid_constant__ CUtensorMap tz,
     const __grid_constant__ CUtensorMap tv, const __grid_constant__ CUtensorMap tp,
     const __grid_constant__ CUtensorMap tw, const __grid_constant__ CUtensorMap th,
     const __grid_constant__ CUtensorMap txm, const __grid_constant__ CUtensorMap tp2,
-    float* __restrict__ zout, float* __restrict__ vout, float* __restrict__ pout,
-    float* __restrict__ xacc, WsHeader* hdr, double* resid, Reduce red, long long wait_cycles,
+    float4* __restrict__ zout, float4* __restrict__ vout, float4* __restrict__ pout,
+    float4* __restrict__ xacc, WsHeader* hdr, double* resid, Reduce red, long long wait_cycles,
     int withhold)
 {
     using L = StepLayout<K, TX, TY>;
     constexpr int T = L::T;
+    constexpr bool first = MODE == kModeFirst, fold = MODE >= kModeFold, readx = MODE == kModeFoldX;
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t raw_full[kStepRaw], raw_empty[kStepRaw];
     __shared__ __align__(8) uint64_t h_full[kStepH], h_empty[kStepH];
@@ -196,12 +201,9 @@ __global__ void __launch_bounds__(kStepThreads, 2) k_pcg_step_tma(
     const bool producer = warp == kStepWarps;
     const int tx = tid % TX, ty = tid / TX;              // meaningful for compute threads
     const int nx = P.nx, ny = P.ny, nz = P.nz;
-    const long long N = P.N;
     const int gx = (nx + TX - 1) / TX;
     const int tiles = gx * ((ny + TY - 1) / TY);
     const int items = tiles * nchunk;
-    const bool first = flags & kStepFirst, fold = flags & kStepFold;
-    const bool readx = flags & kStepReadX, want_rr = flags & kStepResid;
 
     if (tid == 0) {
         s_done = hdr->sc.done;
@@ -231,7 +233,7 @@ __global__ void __launch_bounds__(kStepThreads, 2) k_pcg_step_tma(
     auto h_stage = [](int e) { return (int)((unsigned)e % (unsigned)kStepH); };
     auto h_phase = [](int e) { return (uint32_t)(((unsigned)e / (unsigned)kStepH) & 1u); };
     auto formed = [&](int c) {
-        return reinterpret_cast<float*>(smem + L::S_BASE + ((unsigned)c % 3u) * L::SLOT);
+        return reinterpret_cast<float4*>(smem + L::S_BASE + ((unsigned)c % 3u) * L::SLOT);
     };
 
     Acc acc[kStepSums];
@@ -255,19 +257,19 @@ __global__ void __launch_bounds__(kStepThreads, 2) k_pcg_step_tma(
                     const bool inner = jj >= za && jj < zb;
                     unsigned char* st = smem + s * L::RAW;
                     const uint32_t bar = smem_u32(&raw_full[s]);
-                    uint32_t bytes = L::HALO_BYTES + L::W_BYTES;
-                    if (!first) bytes += 2 * L::HALO_BYTES;
+                    uint32_t bytes = L::BOX_BYTES + L::W_BYTES;
+                    if (!first) bytes += 2 * L::BOX_BYTES;
                     if (fold && inner) bytes += L::TILE_BYTES * (readx ? 2 : 1);
                     mbar_expect_tx(bar, bytes);
-                    tma_load_4d(smem_u32(st + L::Z_OFF), &tz, x0 - 4, y0 - 1, jj, 0, bar);
+                    tma_load_3d(smem_u32(st + L::Z_OFF), &tz, 4 * (x0 - 1), y0 - 1, jj, bar);
                     if (!first) {
-                        tma_load_4d(smem_u32(st + L::V_OFF), &tv, x0 - 4, y0 - 1, jj, 0, bar);
-                        tma_load_4d(smem_u32(st + L::P_OFF), &tp, x0 - 4, y0 - 1, jj, 0, bar);
+                        tma_load_3d(smem_u32(st + L::V_OFF), &tv, 4 * (x0 - 1), y0 - 1, jj, bar);
+                        tma_load_3d(smem_u32(st + L::P_OFF), &tp, 4 * (x0 - 1), y0 - 1, jj, bar);
                     }
                     tma_load_3d(smem_u32(st + L::W_OFF), &tw, x0 - 4, y0 - 1, jj, bar);
                     if (fold && inner) {
-                        tma_load_4d(smem_u32(st + L::P2_OFF), &tp2, x0, y0, jj, 0, bar);
-                        if (readx) tma_load_4d(smem_u32(st + L::X_OFF), &txm, x0, y0, jj, 0, bar);
+                        tma_load_3d(smem_u32(st + L::P2_OFF), &tp2, 4 * x0, y0, jj, bar);
+                        if (readx) tma_load_3d(smem_u32(st + L::X_OFF), &txm, 4 * x0, y0, jj, bar);
                     }
                     raw_issued = c;
                     if (!inner) continue;
@@ -288,6 +290,7 @@ __global__ void __launch_bounds__(kStepThreads, 2) k_pcg_step_tma(
             }
         }
     } else {
+        const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
         int cb = 0, eb = 0;
         for (int i = blockIdx.x; i < items; i += gridDim.x) {
             const int t = i % tiles, ch = i / tiles;
@@ -296,8 +299,8 @@ __global__ void __launch_bounds__(kStepThreads, 2) k_pcg_step_tma(
             const int ja = max(za - 1, 0), jb = min(zb, nz - 1);
             const bool inside = x < nx && y < ny;
             const bool okxm = x > 0, okxp = x + 1 < nx, okym = y > 0, okyp = y + 1 < ny;
-            const int cc = (ty + 1) * L::BX + tx + 4;      // own point in a halo box
-            const int sc = (ty + 1) * L::SX + tx + 1;      // own point in a formed plane
+            const int bc = (ty + 1) * L::BX + tx + 1;      // own point in a z / v / p box and formed plane
+            const int wcc = (ty + 1) * L::WX + tx + 4;     // own point in a w box
             const int tc = ty * TX + tx;                   // own point in a tile box
             // own column: p_j of planes z - 1, z, z + 1, z_j of z and z + 1,
             // the weights of z - 1, z, z + 1 and the x / y coefficients of z, z + 1
@@ -307,6 +310,9 @@ __global__ void __launch_bounds__(kStepThreads, 2) k_pcg_step_tma(
             for (int a = 0; a < K; ++a) pm[a] = pc[a] = pn[a] = zc[a] = zn[a] = 0.f;
 #pragma unroll
             for (int m = 0; m < 4; ++m) cxy[m] = cxyn[m] = 0.f;
+            float part[kStepSums] = {};
+            const long long col = (long long)x + (long long)nx * y;
+            const long long sxy = (long long)nx * ny;
 
             // Phase B for plane z (counter cz of its formed plane, H counter e):
             // `up` holds p_j of plane z + 1 (or of z itself at the top face).
@@ -317,28 +323,24 @@ __global__ void __launch_bounds__(kStepThreads, 2) k_pcg_step_tma(
                     const float* hb = reinterpret_cast<const float*>(smem + L::H_BASE + h_stage(e) * L::H_STAGE);
                     float hv[T];
 #pragma unroll
-                    for (int m = 0; m < T; ++m) hv[m] = hb[m * L::TILE + tc];
-                    const float* fp = formed(cz);
+                    for (int m = 0; m < T; ++m) hv[m] = hb[m * TX * TY + tc];
+                    const float4* fp = formed(cz);
+                    float nb[4][K];
+                    unpack4<K>(fp[bc - 1], nb[0]);
+                    unpack4<K>(fp[bc + 1], nb[1]);
+                    unpack4<K>(fp[bc - L::BX], nb[2]);
+                    unpack4<K>(fp[bc + L::BX], nb[3]);
                     const float c6[6] = {cxy[0], cxy[1], cxy[2], cxy[3],
                                          z > 0 ? (wc + wm) * P.ihz2 : 0.f,
                                          z + 1 < nz ? (wc + wup) * P.ihz2 : 0.f};
-                    auto nb = [&](int m, int a) -> float {
-                        switch (m) {
-                        case 0: return fp[a * L::SPL + sc - 1];
-                        case 1: return fp[a * L::SPL + sc + 1];
-                        case 2: return fp[a * L::SPL + sc - L::SX];
-                        case 3: return fp[a * L::SPL + sc + L::SX];
-                        case 4: return pm[a];
-                        default: return up[a];
-                        }
+                    auto nbf = [&](int m, int a) -> float {
+                        return m < 4 ? nb[m][a] : (m == 4 ? pm[a] : up[a]);
                     };
                     float v[K], sums[kStepSums];
-                    step_voxel<K>(P, c6, zc, pc, nb, hv, want_rr, v, sums);
-                    const long long n = (long long)x + (long long)nx * y + (long long)nx * ny * z;
+                    step_voxel<K>(P, c6, zc, pc, nbf, hv, want_rr, v, sums);
+                    vout[col + sxy * z] = pack4<K>(v);
 #pragma unroll
-                    for (int a = 0; a < K; ++a) vout[a * N + n] = v[a];
-#pragma unroll
-                    for (int s = 0; s < kStepSums; ++s) acc[s].add(sums[s]);
+                    for (int s = 0; s < kStepSums; ++s) part[s] += sums[s];
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&h_empty[h_stage(e)]));
@@ -352,60 +354,40 @@ __global__ void __launch_bounds__(kStepThreads, 2) k_pcg_step_tma(
                 if (ok) {
                     // Phase A: z_j and p_j of this plane
                     const unsigned char* st = smem + r_stage(c) * L::RAW;
-                    const float* bz = reinterpret_cast<const float*>(st + L::Z_OFF);
-                    const float* bv = reinterpret_cast<const float*>(st + L::V_OFF);
-                    const float* bp = reinterpret_cast<const float*>(st + L::P_OFF);
+                    const float4* bz = reinterpret_cast<const float4*>(st + L::Z_OFF);
+                    const float4* bv = reinterpret_cast<const float4*>(st + L::V_OFF);
+                    const float4* bp = reinterpret_cast<const float4*>(st + L::P_OFF);
                     const float* bw = reinterpret_cast<const float*>(st + L::W_OFF);
-                    float zz[K], vv[K], pp[K];
-#pragma unroll
-                    for (int a = 0; a < K; ++a) {
-                        zz[a] = bz[a * L::BOX + cc];
-                        vv[a] = first ? 0.f : bv[a * L::BOX + cc];
-                        pp[a] = first ? 0.f : bp[a * L::BOX + cc];
-                    }
-                    step_point<K>(first, alpha, beta, zz, vv, pp, zn, pn);
-                    wn = bw[cc];
-                    cxyn[0] = okxm ? (wn + bw[cc - 1]) * P.ihx2 : 0.f;
-                    cxyn[1] = okxp ? (wn + bw[cc + 1]) * P.ihx2 : 0.f;
-                    cxyn[2] = okym ? (wn + bw[cc - L::BX]) * P.ihy2 : 0.f;
-                    cxyn[3] = okyp ? (wn + bw[cc + L::BX]) * P.ihy2 : 0.f;
+                    const float4 p4 = first ? zero4 : bp[bc];
+                    step_point<K, first>(alpha, beta, bz[bc], first ? zero4 : bv[bc], p4, zn, pn);
+                    wn = bw[wcc];
+                    cxyn[0] = okxm ? (wn + bw[wcc - 1]) * P.ihx2 : 0.f;
+                    cxyn[1] = okxp ? (wn + bw[wcc + 1]) * P.ihx2 : 0.f;
+                    cxyn[2] = okym ? (wn + bw[wcc - L::WX]) * P.ihy2 : 0.f;
+                    cxyn[3] = okyp ? (wn + bw[wcc + L::WX]) * P.ihy2 : 0.f;
                     if (inner) {
-                        float* fp = formed(c);
-#pragma unroll
-                        for (int a = 0; a < K; ++a) fp[a * L::SPL + sc] = pn[a];
+                        float4* fp = formed(c);
+                        fp[bc] = pack4<K>(pn);
                         if (tid < L::NH) {
                             // halo point: y - 1 row, y + TY row, x - 1 column, x + TX column
-                            int sx, sy;
-                            if (tid < TX) { sx = tid + 1; sy = 0; }
-                            else if (tid < 2 * TX) { sx = tid - TX + 1; sy = TY + 1; }
-                            else if (tid < 2 * TX + TY) { sx = 0; sy = tid - 2 * TX + 1; }
-                            else { sx = TX + 1; sy = tid - 2 * TX - TY + 1; }
-                            const int hc = sy * L::BX + sx + 3;
-                            float hz[K], hv[K], hp[K], hzj[K], hpj[K];
-#pragma unroll
-                            for (int a = 0; a < K; ++a) {
-                                hz[a] = bz[a * L::BOX + hc];
-                                hv[a] = first ? 0.f : bv[a * L::BOX + hc];
-                                hp[a] = first ? 0.f : bp[a * L::BOX + hc];
-                            }
-                            step_point<K>(first, alpha, beta, hz, hv, hp, hzj, hpj);
-#pragma unroll
-                            for (int a = 0; a < K; ++a) fp[a * L::SPL + sy * L::SX + sx] = hpj[a];
+                            int hb;
+                            if (tid < TX) hb = tid + 1;
+                            else if (tid < 2 * TX) hb = (TY + 1) * L::BX + tid - TX + 1;
+                            else if (tid < 2 * TX + TY) hb = (tid - 2 * TX + 1) * L::BX;
+                            else hb = (tid - 2 * TX - TY + 1) * L::BX + TX + 1;
+                            float hzj[K], hpj[K];
+                            step_point<K, first>(alpha, beta, bz[hb], first ? zero4 : bv[hb],
+                                                 first ? zero4 : bp[hb], hzj, hpj);
+                            fp[hb] = pack4<K>(hpj);
                         }
                         if (inside) {
-                            const long long n = (long long)x + (long long)nx * y + (long long)nx * ny * jj;
-#pragma unroll
-                            for (int a = 0; a < K; ++a) {
-                                if (!first) zout[a * N + n] = zn[a];
-                                pout[a * N + n] = pn[a];
-                            }
+                            const long long n = col + sxy * jj;
+                            if (!first) zout[n] = pack4<K>(zn);
+                            pout[n] = pack4<K>(pn);
                             if (fold) {
-                                const float* bx = reinterpret_cast<const float*>(st + L::X_OFF);
-                                const float* b2 = reinterpret_cast<const float*>(st + L::P2_OFF);
-#pragma unroll
-                                for (int a = 0; a < K; ++a)
-                                    xacc[a * N + n] = fold_x(readx ? bx[a * L::TILE + tc] : 0.f, alpha_prev,
-                                                             b2[a * L::TILE + tc], alpha, pp[a]);
+                                const float4* bx = reinterpret_cast<const float4*>(st + L::X_OFF);
+                                const float4* b2 = reinterpret_cast<const float4*>(st + L::P2_OFF);
+                                xacc[n] = fold_x(readx ? bx[tc] : zero4, alpha_prev, b2[tc], alpha, p4);
                             }
                         }
                     }
@@ -413,9 +395,7 @@ __global__ void __launch_bounds__(kStepThreads, 2) k_pcg_step_tma(
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&raw_empty[r_stage(c)]));
                 compute_warps_sync();
-                if (jj - 1 >= za) {
-                    phase_b(jj - 1, c - 1, eb + (jj - 1 - za), pn, wn);
-                }
+                if (jj - 1 >= za) phase_b(jj - 1, c - 1, eb + (jj - 1 - za), pn, wn);
                 // the plane above becomes current
 #pragma unroll
                 for (int a = 0; a < K; ++a) {
@@ -434,6 +414,11 @@ __global__ void __launch_bounds__(kStepThreads, 2) k_pcg_step_tma(
             }
             cb += jb - ja + 1;
             eb += zb - za;
+#pragma unroll
+            for (int s = 0; s < kStepSums; ++s) {
+                acc[s].add(part[s]);
+                part[s] = 0.f;
+            }
         }
     }
     __syncthreads();
@@ -485,9 +470,9 @@ static bool encode(CUtensorMap* m, const float* base, int rank, const cuuint64_t
 }
 
 // Tile shapes the TMA iteration is compiled for (x by y voxels).
-static const int kTileShapes[][2] = {{16, 16}, {32, 8}, {64, 4}};
+static const int kTileShapes[][2] = {{16, 16}, {32, 8}};
 
-int tma_tile_count() { return 3; }
+int tma_tile_count() { return 2; }
 
 // Tile shape per volume: set by the autotuner (mpm_autotune), else a default.
 static std::mutex g_tile_mu;
@@ -509,63 +494,79 @@ int tma_tile_choice(const DevProblem& P)
     return (P.nx >= 40 && P.ny >= 10) ? 1 : 0;    // 32 x 8 when it fits, else 16 x 16
 }
 
-bool make_step_maps(const DevProblem& P, const float* h, const float* w, const SolveBufs& B,
-                    float* xacc, int tile, StepMaps* out)
+bool make_step_maps(const DevProblem& P, const float* h, const float* w, const SolveBufs& B, int tile,
+                    StepMaps* out)
 {
     if (tile < 0 || tile >= tma_tile_count()) return false;
     const int TX = kTileShapes[tile][0], TY = kTileShapes[tile][1];
-    const int BX = TX + 8, BY = TY + 2;
-    // TMA needs 16-byte aligned bases and row strides, and boxes no larger
-    // than the volume in x and y.
-    if (P.nx % 4 != 0 || P.nx < BX || P.ny < BY) return false;
+    const int BX = TX + 2, BY = TY + 2, WX = TX + 8;
+    // The planar maps need 16-byte row strides (nx a multiple of 4); boxes
+    // are kept no larger than the volume; every base must be 16-byte aligned.
+    if (P.nx % 4 != 0 || P.nx < WX || P.ny < BY) return false;
     uintptr_t any = reinterpret_cast<uintptr_t>(h) | reinterpret_cast<uintptr_t>(w) |
-                    reinterpret_cast<uintptr_t>(xacc);
-    for (float* v : B.z) any |= reinterpret_cast<uintptr_t>(v);
-    for (float* v : B.v) any |= reinterpret_cast<uintptr_t>(v);
-    for (float* v : B.p) any |= reinterpret_cast<uintptr_t>(v);
+                    reinterpret_cast<uintptr_t>(B.x);
+    for (float4* v : B.z) any |= reinterpret_cast<uintptr_t>(v);
+    for (float4* v : B.v) any |= reinterpret_cast<uintptr_t>(v);
+    for (float4* v : B.p) any |= reinterpret_cast<uintptr_t>(v);
     if (any % 16) return false;
     if (!encode_fn()) return false;
     const cuuint64_t nx = P.nx, ny = P.ny, nz = P.nz;
-    const cuuint64_t row = nx * 4, plane = nx * ny * 4, vol = (cuuint64_t)P.N * 4;
-    const cuuint64_t dk[4] = {nx, ny, nz, (cuuint64_t)P.K};
-    const cuuint64_t dh[4] = {nx, ny, nz, (cuuint64_t)P.T};
-    const cuuint64_t s4[3] = {row, plane, vol};
+    // voxel-interleaved vectors: 4 nx floats per row
+    const cuuint64_t da[3] = {4 * nx, ny, nz};
+    const cuuint64_t sa[2] = {16 * nx, 16 * nx * ny};
+    const cuuint32_t halo[3] = {(cuuint32_t)(4 * BX), (cuuint32_t)BY, 1};
+    const cuuint32_t tilebox[3] = {(cuuint32_t)(4 * TX), (cuuint32_t)TY, 1};
+    // planar arrays
     const cuuint64_t d3[3] = {nx, ny, nz};
-    const cuuint64_t s3[2] = {row, plane};
-    const cuuint32_t halo[4] = {(cuuint32_t)BX, (cuuint32_t)BY, 1, (cuuint32_t)P.K};
-    const cuuint32_t halo_w[3] = {(cuuint32_t)BX, (cuuint32_t)BY, 1};
-    const cuuint32_t tile_k[4] = {(cuuint32_t)TX, (cuuint32_t)TY, 1, (cuuint32_t)P.K};
-    const cuuint32_t tile_h[4] = {(cuuint32_t)TX, (cuuint32_t)TY, 1, (cuuint32_t)P.T};
-    bool ok = encode(&out->w, w, 3, d3, s3, halo_w) && encode(&out->h, h, 4, dh, s4, tile_h) &&
-              encode(&out->x, xacc, 4, dk, s4, tile_k);
+    const cuuint64_t s3[2] = {4 * nx, 4 * nx * ny};
+    const cuuint64_t dh[4] = {nx, ny, nz, (cuuint64_t)P.T};
+    const cuuint64_t sh[3] = {4 * nx, 4 * nx * ny, 4 * (cuuint64_t)P.N};
+    const cuuint32_t wbox[3] = {(cuuint32_t)WX, (cuuint32_t)BY, 1};
+    const cuuint32_t hbox[4] = {(cuuint32_t)TX, (cuuint32_t)TY, 1, (cuuint32_t)P.T};
+    auto f = [](const float4* v) { return reinterpret_cast<const float*>(v); };
+    bool ok = encode(&out->w, w, 3, d3, s3, wbox) && encode(&out->h, h, 4, dh, sh, hbox) &&
+              encode(&out->x, f(B.x), 3, da, sa, tilebox);
     for (int i = 0; i < 2 && ok; ++i)
-        ok = encode(&out->z[i], B.z[i], 4, dk, s4, halo) && encode(&out->v[i], B.v[i], 4, dk, s4, halo);
+        ok = encode(&out->z[i], f(B.z[i]), 3, da, sa, halo) && encode(&out->v[i], f(B.v[i]), 3, da, sa, halo);
     for (int i = 0; i < 3 && ok; ++i)
-        ok = encode(&out->p[i], B.p[i], 4, dk, s4, halo) && encode(&out->p2[i], B.p[i], 4, dk, s4, tile_k);
+        ok = encode(&out->p[i], f(B.p[i]), 3, da, sa, halo) &&
+             encode(&out->p2[i], f(B.p[i]), 3, da, sa, tilebox);
     out->B = B;
-    out->xacc = xacc;
     out->tile = tile;
     return ok;
 }
 
-template <int K, int TX, int TY>
-static cudaError_t launch_step_k(const DevProblem& P, int nchunk, dim3 grid, const StepMaps& m, int j,
-                                 int flags, WsHeader* hdr, double* resid, Reduce red, cudaStream_t st)
+template <int K, int TX, int TY, int MODE>
+static cudaError_t launch_step_m(const DevProblem& P, int nchunk, dim3 grid, const StepMaps& m, int j,
+                                 int want_rr, WsHeader* hdr, double* resid, Reduce red, cudaStream_t st)
 {
     using L = StepLayout<K, TX, TY>;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_pcg_step_tma<K, TX, TY>,
+        cudaError_t e = cudaFuncSetAttribute(k_pcg_step_tma<K, TX, TY, MODE>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     const int jm = j > 0 ? j - 1 : 0;
-    k_pcg_step_tma<K, TX, TY><<<grid, dim3(kStepThreads, 1, 1), L::SMEM, st>>>(
-        P, nchunk, j, flags, m.z[jm & 1], m.v[jm & 1], m.p[(j + 2) % 3], m.w, m.h, m.x,
-        m.p2[(j + 1) % 3], m.B.z[j & 1], m.B.v[j & 1], m.B.p[j % 3], m.xacc, hdr, resid, red,
+    k_pcg_step_tma<K, TX, TY, MODE><<<grid, dim3(kStepThreads, 1, 1), L::SMEM, st>>>(
+        P, nchunk, j, want_rr, m.z[jm & 1], m.v[jm & 1], m.p[(j + 2) % 3], m.w, m.h, m.x,
+        m.p2[(j + 1) % 3], m.B.z[j & 1], m.B.v[j & 1], m.B.p[j % 3], m.B.x, hdr, resid, red,
         g_wait_cycles.load(std::memory_order_relaxed), g_withhold.load(std::memory_order_relaxed));
     return cudaGetLastError();
+}
+
+template <int K, int TX, int TY>
+static cudaError_t launch_step_k(const DevProblem& P, int nchunk, dim3 grid, const StepMaps& m, int j,
+                                 int mode, int want_rr, WsHeader* hdr, double* resid, Reduce red,
+                                 cudaStream_t st)
+{
+    switch (mode) {
+    case kModeFirst: return launch_step_m<K, TX, TY, kModeFirst>(P, nchunk, grid, m, j, want_rr, hdr, resid, red, st);
+    case kModeStep: return launch_step_m<K, TX, TY, kModeStep>(P, nchunk, grid, m, j, want_rr, hdr, resid, red, st);
+    case kModeFold: return launch_step_m<K, TX, TY, kModeFold>(P, nchunk, grid, m, j, want_rr, hdr, resid, red, st);
+    default: return launch_step_m<K, TX, TY, kModeFoldX>(P, nchunk, grid, m, j, want_rr, hdr, resid, red, st);
+    }
 }
 
 template <int K, int TX, int TY>
@@ -573,10 +574,12 @@ static int resident_one()
 {
     // the occupancy query needs the kernel's shared-memory opt-in first
     int nb = 0;
-    if (cudaFuncSetAttribute(k_pcg_step_tma<K, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             StepLayout<K, TX, TY>::SMEM) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pcg_step_tma<K, TX, TY>, kStepThreads,
-                                                      StepLayout<K, TX, TY>::SMEM) != cudaSuccess) {
+    if (cudaFuncSetAttribute(k_pcg_step_tma<K, TX, TY, kModeFoldX>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, StepLayout<K, TX, TY>::SMEM) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pcg_step_tma<K, TX, TY, kModeFoldX>,
+                                                      kStepThreads, StepLayout<K, TX, TY>::SMEM) !=
+            cudaSuccess) {
         cudaGetLastError();
         nb = 1;
     }
@@ -602,9 +605,9 @@ static int tma_wave(const DevProblem& P, int tile)
     }
     int nb;
     if (P.K == 4)
-        nb = tile == 1 ? resident_one<4, 32, 8>() : tile == 2 ? resident_one<4, 64, 4>() : resident_one<4, 16, 16>();
+        nb = tile == 1 ? resident_one<4, 32, 8>() : resident_one<4, 16, 16>();
     else
-        nb = tile == 1 ? resident_one<3, 32, 8>() : tile == 2 ? resident_one<3, 64, 4>() : resident_one<3, 16, 16>();
+        nb = tile == 1 ? resident_one<3, 32, 8>() : resident_one<3, 16, 16>();
     return cache[key] = nb * sms;
 }
 
@@ -623,22 +626,20 @@ StencilGrid tma_grid(const DevProblem& P, int tile)
     return g;
 }
 
-template <int K>
-static cudaError_t launch_step_tile(const DevProblem& P, const StencilGrid& g, const StepMaps& m, int j,
-                                    int flags, WsHeader* hdr, double* resid, Reduce red, cudaStream_t st)
-{
-    switch (m.tile) {
-    case 1: return launch_step_k<K, 32, 8>(P, g.zc, g.grid, m, j, flags, hdr, resid, red, st);
-    case 2: return launch_step_k<K, 64, 4>(P, g.zc, g.grid, m, j, flags, hdr, resid, red, st);
-    default: return launch_step_k<K, 16, 16>(P, g.zc, g.grid, m, j, flags, hdr, resid, red, st);
-    }
-}
-
 template <int K, int TX, int TY>
 static cudaError_t prime_one()
 {
-    return cudaFuncSetAttribute(k_pcg_step_tma<K, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                StepLayout<K, TX, TY>::SMEM);
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void* f) {
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     StepLayout<K, TX, TY>::SMEM);
+    };
+    set(reinterpret_cast<const void*>(k_pcg_step_tma<K, TX, TY, kModeFirst>));
+    set(reinterpret_cast<const void*>(k_pcg_step_tma<K, TX, TY, kModeStep>));
+    set(reinterpret_cast<const void*>(k_pcg_step_tma<K, TX, TY, kModeFold>));
+    set(reinterpret_cast<const void*>(k_pcg_step_tma<K, TX, TY, kModeFoldX>));
+    return e;
 }
 
 cudaError_t prime_tma_kernels()
@@ -647,19 +648,22 @@ cudaError_t prime_tma_kernels()
     if (done) return cudaSuccess;
     cudaError_t e = prime_one<4, 16, 16>();
     if (!e) e = prime_one<4, 32, 8>();
-    if (!e) e = prime_one<4, 64, 4>();
     if (!e) e = prime_one<3, 16, 16>();
     if (!e) e = prime_one<3, 32, 8>();
-    if (!e) e = prime_one<3, 64, 4>();
     if (!e) done = true;
     return e;
 }
 
 cudaError_t launch_step_tma(const DevProblem& P, const StencilGrid& g, const StepMaps& m, int j,
-                            int flags, WsHeader* hdr, double* resid, Reduce red, cudaStream_t st)
+                            int mode, int want_rr, WsHeader* hdr, double* resid, Reduce red,
+                            cudaStream_t st)
 {
-    if (P.K == 4) return launch_step_tile<4>(P, g, m, j, flags, hdr, resid, red, st);
-    return launch_step_tile<3>(P, g, m, j, flags, hdr, resid, red, st);
+    if (P.K == 4) {
+        if (m.tile == 1) return launch_step_k<4, 32, 8>(P, g.zc, g.grid, m, j, mode, want_rr, hdr, resid, red, st);
+        return launch_step_k<4, 16, 16>(P, g.zc, g.grid, m, j, mode, want_rr, hdr, resid, red, st);
+    }
+    if (m.tile == 1) return launch_step_k<3, 32, 8>(P, g.zc, g.grid, m, j, mode, want_rr, hdr, resid, red, st);
+    return launch_step_k<3, 16, 16>(P, g.zc, g.grid, m, j, mode, want_rr, hdr, resid, red, st);
 }
 
 }  // namespace mpm
