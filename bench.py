@@ -45,7 +45,7 @@ EPS = 1e-3
 SNR = 20.0
 L2_BYTES = 129 * 2 ** 20
 CPU_SAMPLE_Z = 32        # cpu_baseline: a 176 x 240 x 32 slab, one update
-REF_SAMPLE_Z = 8         # reference arm: a 176 x 240 x 8 slab per step, one update
+REF_SAMPLE_Z = 32        # reference arm: a 176 x 240 x 32 slab per step, one update
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
 
@@ -473,26 +473,62 @@ def oracle_sample(z_planes: int, seed: int):
     return orc.make_problem(prot, shape, lam=LAMBDA, eps=EPS), shape, x, b1p, b1m
 
 
-def time_oracle(z_planes: int, seed: int, reps: int = 1):
+def time_oracle(z_planes: int, seed: int, reps: int = 1, threads: int = 1):
+    """Seconds of one oracle update (30 PCG, objective at both ends) on a
+    176 x 240 x z slab, on `threads` host threads (0: all cores; the threaded
+    build rounds exactly like the serial one).  Returns (voxels, times, threads)."""
     import oracle as orc
     p, shape, x, b1p, b1m = oracle_sample(z_planes, seed)
     n = shape[0] * shape[1] * shape[2]
+    used = orc.use_threads(threads)
     times = []
-    for _ in range(reps):
-        t0 = time.perf_counter()
-        r = orc.fit(p, x, None, b1p, b1m, gn_iters=1, cg_iters=CG_ITERS)
-        times.append(time.perf_counter() - t0)
-        assert r["iters"] == 1
-    return n, times
+    try:
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            r = orc.fit(p, x, None, b1p, b1m, gn_iters=1, cg_iters=CG_ITERS)
+            times.append(time.perf_counter() - t0)
+            assert r["iters"] == 1
+    finally:
+        orc.use_threads(1)
+    return n, times, used
+
+
+def time_small_fit():
+    """Seconds of the oracle's whole fit of the small configuration (32 x 32 x
+    16 voxels, 10 updates x 30 PCG), single-threaded."""
+    import oracle as orc
+    from paper_2102_01604_gb300 import phantom
+    shape = (32, 32, 16)
+    ph = phantom.phantom(shape, seed=0, with_b1m=False)
+    prot = phantom.protocol()
+    s = orc.forward(orc.make_problem(prot, shape), ph["y"], ph["b1p"], None)
+    prot["sigma2"] = phantom.noise_sigma2(s, prot, SNR)
+    x = phantom.rician(s, prot, 1).astype(np.float32)
+    p = orc.make_problem(prot, shape, lam=LAMBDA, eps=EPS)
+    t0 = time.perf_counter()
+    r = orc.fit(p, x, None, ph["b1p"], None, gn_iters=10, cg_iters=CG_ITERS)
+    t = time.perf_counter() - t0
+    assert r["iters"] == 10
+    return int(np.prod(shape)), t
 
 
 def cpu_baseline(seed: int):
-    n, times = time_oracle(CPU_SAMPLE_Z, seed)
+    """The FP64 oracle on the host: all cores (the reported value) and one
+    core on the same 176 x 240 x 32 slab, plus the small configuration's whole
+    fit on one core."""
+    n, times, used = time_oracle(CPU_SAMPLE_Z, seed, threads=0)
     t = times[0]
-    return {"value": round(n / t / 1e6, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+    n1, times1, _ = time_oracle(CPU_SAMPLE_Z, seed, threads=1)
+    t1 = times1[0]
+    ns, ts = time_small_fit()
+    return {"value": round(n / t / 1e6, 5), "unit": UNIT, "cores": used, "kind": "oracle",
             "sample": f"176x240x{CPU_SAMPLE_Z} slab of the same phantom, 1 update (30 PCG) "
-                      f"with objective at both ends, FP64 single-threaded C; {t:.2f} s; "
-                      f"host has {os.cpu_count()} cores"}
+                      f"with objective at both ends, FP64 C on {used} OpenMP threads; {t:.2f} s; "
+                      f"host has {os.cpu_count()} cores",
+            "single_core": {"value": round(n1 / t1 / 1e6, 5), "cores": 1, "seconds": round(t1, 2)},
+            "small_config_fit": {"value": round(ns * 10 / ts / 1e6, 5), "cores": 1,
+                                 "seconds": round(ts, 3),
+                                 "sample": "32x32x16, 10 updates x 30 PCG, whole fit"}}
 
 
 def run_reference(args):
@@ -500,10 +536,10 @@ def run_reference(args):
     if rank != 0:
         return 0
     for _ in range(args.warmup):
-        time_oracle(REF_SAMPLE_Z, args.seed)
-    total_t, total_units = 0.0, 0
+        time_oracle(REF_SAMPLE_Z, args.seed, threads=0)
+    total_t, total_units, used = 0.0, 0, 1
     for _ in range(args.steps):
-        n, times = time_oracle(REF_SAMPLE_Z, args.seed)
+        n, times, used = time_oracle(REF_SAMPLE_Z, args.seed, threads=0)
         total_t += times[0]
         total_units += n * 1
     value = total_units / total_t / 1e6
@@ -514,8 +550,8 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"176x240x{REF_SAMPLE_Z} slab of the 1 mm MPM JTV-MAP "
                                f"workload, 1 update x {CG_ITERS} PCG per step",
-                   "runs_on": "host CPU (FP64 oracle)"},
-        "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "runs_on": f"host CPU (FP64 oracle, {used} OpenMP threads)"},
+        "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": used, "kind": "oracle",
                          "sample": f"176x240x{REF_SAMPLE_Z} slab, 1 update per step"},
         "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},

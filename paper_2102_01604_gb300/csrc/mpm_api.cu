@@ -10,11 +10,31 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "mpm_internal.cuh"
 
 namespace mpm {
 
 static std::atomic<unsigned long long> g_launches{0};
+
+// NVTX range names of the kernel kinds (MPM_KERNEL_*): every launch is
+// wrapped in a host-side range of its kind, every Newton update of a fit in
+// one named after its index, so profilers can attribute and filter them
+// (no cost when no tool is attached).
+static const char* const kKindNames[MPM_KERNEL_KINDS] = {
+    "grad_hess", "jtv", "pcg_init", "pcg_step", "pcg_final", "uncertainty", "forward", "init",
+    "grad_hess_proj", "reslice"};
+
+struct NvtxUpdate {
+    explicit NvtxUpdate(int it)
+    {
+        char name[32];
+        snprintf(name, sizeof name, "mpm update %d", it);
+        nvtxRangePushA(name);
+    }
+    ~NvtxUpdate() { nvtxRangePop(); }
+};
 
 // ------------------------------------------------- diagnostic kernel timing
 
@@ -46,6 +66,7 @@ static cudaEvent_t pool_get()
 LaunchScope::LaunchScope(int k, cudaStream_t s) : kind(k), st(s), rec(nullptr)
 {
     g_launches.fetch_add(1, std::memory_order_relaxed);
+    nvtxRangePushA(k >= 0 && k < MPM_KERNEL_KINDS ? kKindNames[k] : "mpm kernel");
     if (t_capturing || !g_prof_on.load(std::memory_order_relaxed)) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     ProfRecord r{kind, pool_get(), pool_get()};
@@ -57,6 +78,7 @@ LaunchScope::LaunchScope(int k, cudaStream_t s) : kind(k), st(s), rec(nullptr)
 
 LaunchScope::~LaunchScope()
 {
+    nvtxRangePop();
     if (!rec) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     const size_t i = reinterpret_cast<size_t>(rec) - 1;
@@ -419,6 +441,7 @@ static cudaError_t fit_enqueue_updates(const FitJob& j, cudaStream_t st, int* it
     cudaError_t e = cudaSuccess;
     int it = 0;
     for (;; ++it) {
+        NvtxUpdate range(it);
         w_fresh = (it % npi == 0);
         if ((e = launch_jtv(P, j.y, w_fresh ? L.w : nullptr, L.jtv + it, L.red, st))) return e;
         if ((e = launch_lik(j, it, st))) return e;
@@ -447,6 +470,7 @@ static mpm_status fit_run_adaptive(const FitJob& j, cudaStream_t st, int* iters_
     int it = 0;
     *converged = false;
     for (;; ++it) {
+        NvtxUpdate range(it);
         w_fresh = (it % npi == 0);
         MPM_CUDA(launch_jtv(P, j.y, w_fresh ? L.w : nullptr, L.jtv + it, L.red, st));
         MPM_CUDA(launch_lik(j, it, st));
