@@ -100,7 +100,19 @@ class OrcOpts(ctypes.Structure):
         ("gn_iters", ctypes.c_int), ("cg_iters", ctypes.c_int),
         ("newton_per_irls", ctypes.c_int), ("init", ctypes.c_int),
         ("tol_gn", ctypes.c_double), ("tol_cg", ctypes.c_double),
+        ("mg_levels", ctypes.c_int), ("mg_nu", ctypes.c_int),
+        ("mg_omega", ctypes.c_double), ("mg_coarse_sweeps", ctypes.c_int),
     ]
+
+
+class OrcMG(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("nu", ctypes.c_int), ("omega", ctypes.c_double),
+                ("coarse_sweeps", ctypes.c_int)]
+
+
+def make_mg(levels=8, nu=1, omega=0.7, coarse_sweeps=20) -> OrcMG:
+    """Multigrid V-cycle settings (levels: at most this many)."""
+    return OrcMG(int(levels), int(nu), float(omega), int(coarse_sweeps))
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -155,6 +167,17 @@ def _lib():
         lib.orc_fit_proj.argtypes = [_P, _Q, ctypes.POINTER(OrcOpts), _DD, _DD, _DD, _D, _D, _D,
                                      _D, _D]
         lib.orc_fit_proj.restype = ctypes.c_int
+        _G = ctypes.POINTER(OrcMG)
+        lib.orc_mg_levels.argtypes = [_P, _G, ctypes.POINTER(ctypes.c_int * 3)]
+        lib.orc_mg_levels.restype = ctypes.c_int
+        lib.orc_mg_vcycle.argtypes = [_P, _D, _D, _G, _D, _D]
+        lib.orc_mg_vcycle.restype = None
+        lib.orc_mg_energy.argtypes = [_P, _D, _D, _G, ctypes.c_int, _D]
+        lib.orc_mg_energy.restype = ctypes.c_double
+        lib.orc_mg_pcg.argtypes = [_P, _D, _D, _D, _D, ctypes.c_int, ctypes.c_double, _G, _D]
+        lib.orc_mg_pcg.restype = ctypes.c_int
+        lib.orc_mg_solve.argtypes = [_P, _D, _D, _D, _D, _D, ctypes.c_int, ctypes.c_double, _G, _D]
+        lib.orc_mg_solve.restype = ctypes.c_int
         _handles[_variant] = lib
     return lib
 
@@ -290,6 +313,47 @@ def solve(p, h, w, g, y, iters, tol=0.0):
     return d, it, resid[:max(it, 0) + 1]
 
 
+def mg_levels(p, mg):
+    """Dimensions (nx, ny, nz) of every multigrid level."""
+    dims = ((ctypes.c_int * 3) * 16)()
+    L = _lib().orc_mg_levels(ctypes.byref(p), ctypes.byref(mg), dims)
+    return [tuple(dims[l]) for l in range(L)]
+
+
+def mg_vcycle(p, h, w, mg, r):
+    h, w, r = _f64(h), _f64(w), _f64(r)
+    z = np.zeros((p.n_maps, _nvox(p)))
+    _lib().orc_mg_vcycle(ctypes.byref(p), _ptr(h), _ptr(w), ctypes.byref(mg), _ptr(r), _ptr(z))
+    return z
+
+
+def mg_energy(p, h, w, mg, level, e):
+    """e' A_l e on multigrid level `level` (e is [K][N_l])."""
+    h, w, e = _f64(h), _f64(w), _f64(e)
+    return _lib().orc_mg_energy(ctypes.byref(p), _ptr(h), _ptr(w), ctypes.byref(mg), int(level),
+                                _ptr(e))
+
+
+def mg_pcg(p, h, w, b, iters, mg, tol=0.0):
+    """orc_pcg with the multigrid preconditioner: (x, iterations, resid)."""
+    h, w, b = _f64(h), _f64(w), _f64(b)
+    x = np.zeros((p.n_maps, _nvox(p)))
+    resid = np.zeros(iters + 1)
+    it = _lib().orc_mg_pcg(ctypes.byref(p), _ptr(h), _ptr(w), _ptr(b), _ptr(x), iters, tol,
+                           ctypes.byref(mg), _ptr(resid))
+    return x, it, resid[:max(it, 0) + 1]
+
+
+def mg_solve(p, h, w, g, y, iters, mg, tol=0.0):
+    """delta = (H + L)^-1 (g + L y) by mg_pcg: (delta, iterations, resid)."""
+    h, w, g, y = _f64(h), _f64(w), _f64(g), _f64(y)
+    d = np.zeros((p.n_maps, _nvox(p)))
+    resid = np.zeros(iters + 1)
+    it = _lib().orc_mg_solve(ctypes.byref(p), _ptr(h), _ptr(w), _ptr(g), _ptr(y), _ptr(d), iters,
+                             tol, ctypes.byref(mg), _ptr(resid))
+    return d, it, resid[:max(it, 0) + 1]
+
+
 def uncertainty(p, h, w, y=None):
     """Returns (var [K][N], logdet [N], moments [4][N] or None, status)."""
     h, w, y = _f64(h), _f64(w), _f64(y)
@@ -310,11 +374,15 @@ def init(p, x):
 
 
 def fit(p, x, y0=None, b1p=None, b1m=None, gn_iters=10, cg_iters=30, newton_per_irls=1,
-        tol_gn=0.0, tol_cg=0.0):
-    """Whole fit.  ``y0=None`` starts from the constant initial maps.  Returns a
-    dict with ``y``, ``iters``, ``F``, ``nll``, ``jtv``, ``cg_rel``."""
+        tol_gn=0.0, tol_cg=0.0, mg=None):
+    """Whole fit.  ``y0=None`` starts from the constant initial maps; ``mg``
+    (make_mg) solves with the multigrid-preconditioned CG.  Returns a dict
+    with ``y``, ``iters``, ``F``, ``nll``, ``jtv``, ``cg_rel``."""
     x, b1p, b1m = _f64(x), _f64(b1p), _f64(b1m)
     o = OrcOpts(gn_iters, cg_iters, newton_per_irls, 1 if y0 is None else 0, tol_gn, tol_cg)
+    if mg is not None:
+        o.mg_levels, o.mg_nu, o.mg_omega, o.mg_coarse_sweeps = (mg.levels, mg.nu, mg.omega,
+                                                                 mg.coarse_sweeps)
     y = np.zeros((p.n_maps, _nvox(p))) if y0 is None else np.array(y0, dtype=np.float64)
     F = np.zeros(gn_iters + 1)
     nll = np.zeros(gn_iters + 1)

@@ -636,6 +636,270 @@ int orc_solve(const orc_problem* p, const double* h, const double* w, const doub
     return it;
 }
 
+/* ---------------------------------- multigrid preconditioner (an option) */
+
+/* Not part of the paper's solver (Sec. 2.6 uses the block preconditioner of
+ * orc_pcg).  An aggregation multigrid V-cycle for A = H + L, used as the
+ * preconditioner of the same conjugate-gradient recurrence:
+ *   - levels: level l + 1 merges 2 x 2 x 2 voxels of level l (ceil(n / 2) per
+ *     axis); a level of at most ORC_MG_MIN_VOXELS voxels is the coarsest;
+ *   - prolongation P: a coarse voxel's value copied to its children;
+ *     restriction P' (sum over the children);
+ *   - coarse operators by the Galerkin product A_c = P' A P, which keeps the
+ *     form of A: H_c = sum of the children's blocks, and the coefficient of a
+ *     coarse edge = sum of the coefficients of the fine edges crossing it
+ *     (edges inside a coarse voxel drop out); level 0 has the coefficients
+ *     (w_n + w_m) / h^2 of L;
+ *   - smoother: damped block-Jacobi, x += omega D^-1 (r - A x), D the 4 x 4
+ *     voxel blocks of A (on level 0 exactly the block preconditioner of Eq. 42);
+ *   - V-cycle from x = 0: nu sweeps, coarse correction with the restricted
+ *     residual, nu sweeps; coarse_sweeps sweeps on the coarsest level.  Equal
+ *     sweeps before and after make the cycle a symmetric operator. */
+
+#define ORC_MG_MIN_VOXELS 512L
+#define ORC_MG_MAX_LEVELS 16
+
+typedef struct {
+    int n[3];
+    long N;
+    double* h;      /* [T][N] */
+    double* kap;    /* [3][N]: edge from voxel v to v + e_a, 0 where it leaves the level */
+    long* parent;   /* [N]: voxel of level l + 1 holding v (NULL on the coarsest) */
+} orc_level;
+
+int orc_mg_levels(const orc_problem* p, const orc_mg* mg, int dims[][3])
+{
+    int n[3] = {p->nx, p->ny, p->nz};
+    int L = 0;
+    int max_l = mg->levels < ORC_MG_MAX_LEVELS ? mg->levels : ORC_MG_MAX_LEVELS;
+    for (;;) {
+        if (dims) { dims[L][0] = n[0]; dims[L][1] = n[1]; dims[L][2] = n[2]; }
+        ++L;
+        if (L >= max_l || (long)n[0] * n[1] * n[2] <= ORC_MG_MIN_VOXELS) break;
+        for (int a = 0; a < 3; ++a) n[a] = (n[a] + 1) / 2;
+    }
+    return L;
+}
+
+static long lvox(const int n[3], int x, int y, int z) { return x + (long)n[0] * (y + (long)n[1] * z); }
+
+/* Level 0 from H and w; every coarser level by the Galerkin product. */
+static int mg_build(const orc_problem* p, const double* h, const double* w, const orc_mg* mg,
+                    orc_level* lv)
+{
+    int dims[ORC_MG_MAX_LEVELS][3];
+    int L = orc_mg_levels(p, mg, dims);
+    int T = n_tri(p->n_maps);
+    double ih2[3] = {1.0 / (p->vx[0] * p->vx[0]), 1.0 / (p->vx[1] * p->vx[1]),
+                     1.0 / (p->vx[2] * p->vx[2])};
+    for (int l = 0; l < L; ++l) {
+        for (int a = 0; a < 3; ++a) lv[l].n[a] = dims[l][a];
+        lv[l].N = (long)dims[l][0] * dims[l][1] * dims[l][2];
+        lv[l].h = calloc((size_t)T * lv[l].N, sizeof(double));
+        lv[l].kap = calloc((size_t)3 * lv[l].N, sizeof(double));
+        lv[l].parent = l + 1 < L ? malloc(sizeof(long) * lv[l].N) : NULL;
+    }
+    /* level 0 */
+    long N = lv[0].N;
+    memcpy(lv[0].h, h, sizeof(double) * T * N);
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                long v = lvox(lv[0].n, x, y, z);
+                if (x + 1 < p->nx) lv[0].kap[0 * N + v] = (w[v] + w[v + 1]) * ih2[0];
+                if (y + 1 < p->ny) lv[0].kap[1 * N + v] = (w[v] + w[v + p->nx]) * ih2[1];
+                if (z + 1 < p->nz) lv[0].kap[2 * N + v] = (w[v] + w[v + (long)p->nx * p->ny]) * ih2[2];
+            }
+    /* coarser levels */
+    for (int l = 0; l + 1 < L; ++l) {
+        orc_level* f = &lv[l];
+        orc_level* c = &lv[l + 1];
+        for (int z = 0; z < f->n[2]; ++z)
+            for (int y = 0; y < f->n[1]; ++y)
+                for (int x = 0; x < f->n[0]; ++x) {
+                    long v = lvox(f->n, x, y, z);
+                    long pv = lvox(c->n, x / 2, y / 2, z / 2);
+                    f->parent[v] = pv;
+                    for (int t = 0; t < T; ++t) c->h[(long)t * c->N + pv] += f->h[(long)t * f->N + v];
+                    int q[3] = {x, y, z};
+                    for (int a = 0; a < 3; ++a) {
+                        /* the fine edge v -> v + e_a crosses into the next coarse voxel */
+                        if (q[a] + 1 < f->n[a] && (q[a] + 1) / 2 != q[a] / 2)
+                            c->kap[(long)a * c->N + pv] += f->kap[(long)a * f->N + v];
+                    }
+                }
+    }
+    return L;
+}
+
+static void mg_free(orc_level* lv, int L)
+{
+    for (int l = 0; l < L; ++l) { free(lv[l].h); free(lv[l].kap); free(lv[l].parent); }
+}
+
+/* out = A_l x on one level. */
+static void mg_apply(const orc_problem* p, const orc_level* lv, const double* x, double* out)
+{
+    int K = p->n_maps;
+    long N = lv->N;
+    long st[3] = {1, lv->n[0], (long)lv->n[0] * lv->n[1]};
+#pragma omp parallel for schedule(static)
+    for (long v = 0; v < N; ++v) {
+        long q[3] = {v % lv->n[0], (v / lv->n[0]) % lv->n[1], v / ((long)lv->n[0] * lv->n[1])};
+        for (int k = 0; k < K; ++k) {
+            double acc = 0.0;
+            for (int j = 0; j < K; ++j) acc += lv->h[(long)tri_index(K, k, j) * N + v] * x[(long)j * N + v];
+            double lap = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                if (q[a] + 1 < lv->n[a])
+                    lap += lv->kap[(long)a * N + v] * (x[(long)k * N + v] - x[(long)k * N + v + st[a]]);
+                if (q[a] > 0)
+                    lap += lv->kap[(long)a * N + v - st[a]] * (x[(long)k * N + v] - x[(long)k * N + v - st[a]]);
+            }
+            out[(long)k * N + v] = acc + p->lambda[k] * lap;
+        }
+    }
+}
+
+/* x += omega D^-1 (r - A x), D the voxel blocks of A_l. */
+static int mg_sweep(const orc_problem* p, const orc_level* lv, double omega, const double* r,
+                    double* x, double* t)
+{
+    int K = p->n_maps;
+    long N = lv->N;
+    long st[3] = {1, lv->n[0], (long)lv->n[0] * lv->n[1]};
+    mg_apply(p, lv, x, t);
+    int bad = 0;
+#pragma omp parallel for schedule(static) reduction(|:bad)
+    for (long v = 0; v < N; ++v) {
+        long q[3] = {v % lv->n[0], (v / lv->n[0]) % lv->n[1], v / ((long)lv->n[0] * lv->n[1])};
+        double d = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            if (q[a] + 1 < lv->n[a]) d += lv->kap[(long)a * N + v];
+            if (q[a] > 0) d += lv->kap[(long)a * N + v - st[a]];
+        }
+        double M[4][4], Lc[4][4], b[4], e[4];
+        for (int k = 0; k < K; ++k)
+            for (int j = 0; j < K; ++j) M[k][j] = lv->h[(long)tri_index(K, k, j) * N + v];
+        for (int k = 0; k < K; ++k) M[k][k] += p->lambda[k] * d;
+        if (cholesky(K, M, Lc)) { bad = 1; continue; }
+        for (int k = 0; k < K; ++k) b[k] = r[(long)k * N + v] - t[(long)k * N + v];
+        chol_solve(K, Lc, b, e);
+        for (int k = 0; k < K; ++k) x[(long)k * N + v] += omega * e[k];
+    }
+    return bad ? -1 : 0;
+}
+
+/* x = V-cycle applied to r on level l (x starts at zero). */
+static int mg_cycle(const orc_problem* p, orc_level* lv, int l, int L, const orc_mg* mg,
+                    const double* r, double* x)
+{
+    int K = p->n_maps;
+    long N = lv[l].N;
+    double* t = malloc(sizeof(double) * K * N);
+    int st = 0;
+    for (long i = 0; i < (long)K * N; ++i) x[i] = 0.0;
+    if (l == L - 1) {
+        for (int s = 0; s < mg->coarse_sweeps && !st; ++s) st = mg_sweep(p, &lv[l], mg->omega, r, x, t);
+        free(t);
+        return st;
+    }
+    for (int s = 0; s < mg->nu && !st; ++s) st = mg_sweep(p, &lv[l], mg->omega, r, x, t);
+    long Nc = lv[l + 1].N;
+    double* rc = calloc((size_t)K * Nc, sizeof(double));
+    double* ec = malloc(sizeof(double) * K * Nc);
+    mg_apply(p, &lv[l], x, t);                          /* restricted residual P'(r - A x) */
+    for (long v = 0; v < N; ++v)
+        for (int k = 0; k < K; ++k)
+            rc[(long)k * Nc + lv[l].parent[v]] += r[(long)k * N + v] - t[(long)k * N + v];
+    if (!st) st = mg_cycle(p, lv, l + 1, L, mg, rc, ec);
+    for (long v = 0; v < N; ++v)                       /* x += P e_c */
+        for (int k = 0; k < K; ++k) x[(long)k * N + v] += ec[(long)k * Nc + lv[l].parent[v]];
+    for (int s = 0; s < mg->nu && !st; ++s) st = mg_sweep(p, &lv[l], mg->omega, r, x, t);
+    free(rc); free(ec); free(t);
+    return st;
+}
+
+void orc_mg_vcycle(const orc_problem* p, const double* h, const double* w, const orc_mg* mg,
+                   const double* r, double* z)
+{
+    orc_level lv[ORC_MG_MAX_LEVELS];
+    int L = mg_build(p, h, w, mg, lv);
+    mg_cycle(p, lv, 0, L, mg, r, z);
+    mg_free(lv, L);
+}
+
+double orc_mg_energy(const orc_problem* p, const double* h, const double* w, const orc_mg* mg,
+                     int level, const double* e)
+{
+    orc_level lv[ORC_MG_MAX_LEVELS];
+    int L = mg_build(p, h, w, mg, lv);
+    double en = 0.0;
+    if (level >= 0 && level < L) {
+        long n = (long)p->n_maps * lv[level].N;
+        double* t = malloc(sizeof(double) * n);
+        mg_apply(p, &lv[level], e, t);
+        for (long i = 0; i < n; ++i) en += e[i] * t[i];
+        free(t);
+    }
+    mg_free(lv, L);
+    return en;
+}
+
+/* The conjugate-gradient recurrence of orc_pcg with z = V-cycle(r). */
+int orc_mg_pcg(const orc_problem* p, const double* h, const double* w, const double* b,
+               double* x, int max_iters, double tol, const orc_mg* mg, double* resid)
+{
+    long N = n_vox(p);
+    long L = (long)p->n_maps * N;
+    double* r = malloc(sizeof(double) * L);
+    double* z = malloc(sizeof(double) * L);
+    double* pv = malloc(sizeof(double) * L);
+    double* q = malloc(sizeof(double) * L);
+    orc_level lv[ORC_MG_MAX_LEVELS];
+    int nl = mg_build(p, h, w, mg, lv);
+    int it = 0;
+
+    for (long i = 0; i < L; ++i) { x[i] = 0.0; r[i] = b[i]; }
+    if (mg_cycle(p, lv, 0, nl, mg, r, z)) { it = -1; goto done; }
+    memcpy(pv, z, sizeof(double) * L);
+    double rz = dot(L, r, z);
+    double rr0 = dot(L, r, r);
+    if (resid) resid[0] = sqrt(rr0);
+    for (it = 0; it < max_iters; ++it) {
+        if (!(rz > 0.0)) break;
+        if (tol > 0.0 && sqrt(dot(L, r, r)) <= tol * sqrt(rr0)) break;
+        apply_system(p, h, w, pv, q);
+        double pq = dot(L, pv, q);
+        if (!(pq > 0.0)) break;
+        double alpha = rz / pq;
+        for (long i = 0; i < L; ++i) { x[i] += alpha * pv[i]; r[i] -= alpha * q[i]; }
+        if (mg_cycle(p, lv, 0, nl, mg, r, z)) { it = -1; goto done; }
+        double rz_new = dot(L, r, z);
+        double beta = rz_new / rz;
+        rz = rz_new;
+        for (long i = 0; i < L; ++i) pv[i] = z[i] + beta * pv[i];
+        if (resid) resid[it + 1] = sqrt(dot(L, r, r));
+    }
+done:
+    mg_free(lv, nl);
+    free(r); free(z); free(pv); free(q);
+    return it;
+}
+
+int orc_mg_solve(const orc_problem* p, const double* h, const double* w, const double* g,
+                 const double* y, double* delta, int max_iters, double tol, const orc_mg* mg,
+                 double* resid)
+{
+    long L = (long)p->n_maps * n_vox(p);
+    double* b = malloc(sizeof(double) * L);
+    orc_membrane(p, w, y, b);                       /* b = g + L y (Eq. 42) */
+    for (long i = 0; i < L; ++i) b[i] += g[i];
+    int it = orc_mg_pcg(p, h, w, b, delta, max_iters, tol, mg, resid);
+    free(b);
+    return it;
+}
+
 /* ------------------------------------------------ uncertainty, Sec. 3.6 */
 
 int orc_uncertainty(const orc_problem* p, const double* h, const double* w,
@@ -846,7 +1110,13 @@ static int fit_loop(const orc_problem* p, const orc_projection* q, const orc_opt
         if (it >= o->gn_iters) break;
         if (it > 0 && o->tol_gn > 0.0 && fabs(F_prev - Fi) < o->tol_gn * fabs(F_prev)) break;
         F_prev = Fi;
-        int cg = orc_solve(p, h, w, g, y, delta, o->cg_iters, o->tol_cg, resid);
+        int cg;
+        if (o->mg_levels > 0) {
+            orc_mg mg = {o->mg_levels, o->mg_nu, o->mg_omega, o->mg_coarse_sweeps};
+            cg = orc_mg_solve(p, h, w, g, y, delta, o->cg_iters, o->tol_cg, &mg, resid);
+        } else {
+            cg = orc_solve(p, h, w, g, y, delta, o->cg_iters, o->tol_cg, resid);
+        }
         if (cg < 0) { it = -1; break; }
         if (cg_rel) cg_rel[it] = resid[0] > 0.0 ? resid[cg] / resid[0] : 0.0;
 #pragma omp parallel for schedule(static)

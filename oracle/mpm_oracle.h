@@ -49,7 +49,20 @@ typedef struct {
     int init;              /* 1: constant initial maps from the data means */
     double tol_gn;         /* stop when |F_prev - F| / |F_prev| < tol_gn (0: off) */
     double tol_cg;         /* stop PCG when |r_k| <= tol_cg |r_0| (0: off) */
+    int mg_levels;         /* 0: the block preconditioner of Sec. 2.6; > 0: multigrid (orc_mg) */
+    int mg_nu;
+    double mg_omega;
+    int mg_coarse_sweeps;
 } orc_opts;
+
+/* Multigrid V-cycle used as the CG preconditioner instead of the block
+ * preconditioner (an option; not the paper's solver). */
+typedef struct {
+    int levels;          /* at most this many levels (>= 1) */
+    int nu;              /* damped block-Jacobi sweeps before and after the coarse correction */
+    double omega;        /* damping of the sweeps */
+    int coarse_sweeps;   /* sweeps on the coarsest level */
+} orc_mg;
 
 /* Signal of one image in one voxel (Eq. 26 with the B1 footnote). */
 double orc_signal(const double y[4], double alpha, double tr, double te,
@@ -121,6 +134,27 @@ int orc_pcg(const orc_problem* p, const double* h, const double* w, const double
 /* delta = (H + L)^-1 (g + L y) by orc_pcg (Eq. 42). */
 int orc_solve(const orc_problem* p, const double* h, const double* w, const double* g,
               const double* y, double* delta, int max_iters, double tol, double* resid);
+
+/* Number of multigrid levels for this grid (at most mg->levels; a level of
+ * at most 512 voxels is the coarsest) and their dimensions (dims may be NULL). */
+int orc_mg_levels(const orc_problem* p, const orc_mg* mg, int dims[][3]);
+
+/* z = one V-cycle applied to r ([K][N]). */
+void orc_mg_vcycle(const orc_problem* p, const double* h, const double* w, const orc_mg* mg,
+                   const double* r, double* z);
+
+/* e' A_l e for a vector e ([K][N_l]) of level `level` (the Galerkin coarse operator). */
+double orc_mg_energy(const orc_problem* p, const double* h, const double* w, const orc_mg* mg,
+                     int level, const double* e);
+
+/* orc_pcg with the V-cycle as preconditioner. */
+int orc_mg_pcg(const orc_problem* p, const double* h, const double* w, const double* b,
+               double* x, int max_iters, double tol, const orc_mg* mg, double* resid);
+
+/* delta = (H + L)^-1 (g + L y) by orc_mg_pcg. */
+int orc_mg_solve(const orc_problem* p, const double* h, const double* w, const double* g,
+                 const double* y, double* delta, int max_iters, double tol, const orc_mg* mg,
+                 double* resid);
 
 /* var[K][N]: diagonal of (H + diag(G'WG) (x) lambda)^-1 (Eq. 43); logdet[N]
  * (may be NULL): log-determinant of that covariance block; moments[4][N] (may be
