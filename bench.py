@@ -76,6 +76,9 @@ def parse_args(argv=None):
                     help="plain: one subject per fit; batched: 16 uneven subjects per "
                          "mpm_fit_batch call, compared with plain fits of the same subjects; "
                          "served: Poisson arrivals through mpm_server_* vs FIFO plain fits")
+    ap.add_argument("--solver", choices=["pcg", "mg"], default="pcg",
+                    help="mg: time to |r| <= 1e-3 |r_0| of the fit's Newton systems, block-Jacobi "
+                         "PCG against multigrid-preconditioned CG (instead of the fit)")
     ap.add_argument("--requests", type=int, default=24, help="served: number of requests")
     ap.add_argument("--rate", type=float, default=3.0, help="served: arrivals per second")
     args = ap.parse_args(argv)
@@ -732,6 +735,91 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------------- solver arm
+
+MG_OPTS = dict(mg_levels=8, mg_nu=1, mg_omega=0.7, mg_coarse_sweeps=20)
+SOLVER_TOL = 1e-3        # the paper's CG tolerance (Sec. 2.7)
+SOLVER_UPDATES = (0, 1, 5)
+
+
+def run_solvers(args):
+    """Time to |r| <= 1e-3 |r_0| of the Newton systems of the 1 mm fit (after
+    0, 1 and 5 updates), block-Jacobi PCG (the paper's preconditioner) against
+    the multigrid-preconditioned CG; device time of whole mpm_solve calls,
+    CUDA events, after warm-up."""
+    import torch
+
+    import paper_2102_01604_gb300 as mpm
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    seed = args.seed + 1000 * rank
+    prot, ph, x, b1p, b1m = workload_inputs(seed, dev, args.echo_dtype)
+    problem = mpm.make_problem(prot, SHAPE, vx=VX, lam=LAMBDA, eps=EPS,
+                               echo_dtype=1 if args.echo_dtype == "bf16" else 0)
+    K = problem.n_maps
+    N = int(np.prod(SHAPE))
+    fit_opts = mpm.make_opts(gn_iters=GN_ITERS, cg_iters=CG_ITERS)
+    ws = mpm.workspace(problem, fit_opts, device=dev)
+    mpm.mpm_autotune(problem, fit_opts, ws=ws)
+    y = torch.empty((K, N), dtype=torch.float32, device=dev)
+    systems = []
+    for k in SOLVER_UPDATES:
+        mpm.mpm_fit(problem, mpm.make_opts(gn_iters=k, cg_iters=CG_ITERS), x, y, b1p, b1m, ws=ws)
+        w, _ = mpm.mpm_jtv_weights(problem, y)
+        g, h, _ = mpm.mpm_grad_hess(problem, x, y, b1p, b1m)
+        systems.append((k, h, w, g, y.clone()))
+    del ws
+    torch.cuda.synchronize()
+    max_it = 400
+    delta = torch.empty((K, N), dtype=torch.float32, device=dev)
+    resid = torch.empty(max_it + 1, dtype=torch.float64, device=dev)
+    results = []
+    for k, h, w, g, yk in systems:
+        row = {"update": k}
+        for name, extra in (("block_jacobi", {}), ("multigrid", MG_OPTS)):
+            # the iterations the tolerance needs, then the solve capped there: a
+            # solve enqueues all cg_iters iterations (those after the stop return
+            # at once), so a loose cap would time empty launches
+            opts = mpm.make_opts(cg_iters=max_it, tol_cg=SOLVER_TOL, **extra)
+            sws = mpm.workspace(problem, opts, mpm._lib.CALL_SOLVE, device=dev)
+            resid.fill_(float("nan"))
+            mpm.mpm_solve(problem, opts, h, w, g, yk, delta=delta, resid=resid, ws=sws)
+            need = int(np.sum(np.isfinite(resid.cpu().numpy()))) - 1
+            opts = mpm.make_opts(cg_iters=max(need, 1), tol_cg=SOLVER_TOL, **extra)
+            for _ in range(max(args.warmup, 1)):
+                resid.fill_(float("nan"))
+                mpm.mpm_solve(problem, opts, h, w, g, yk, delta=delta, resid=resid, ws=sws)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.steps):
+                mpm.mpm_solve(problem, opts, h, w, g, yk, delta=delta, resid=resid, ws=sws)
+            e1.record()
+            torch.cuda.synchronize()
+            r = resid.cpu().numpy()
+            iters = int(np.sum(np.isfinite(r))) - 1
+            row[name] = {"iters": iters, "rel_resid": float(r[iters] / r[0]),
+                         "ms": round(e0.elapsed_time(e1) / args.steps, 3)}
+            del sws
+        row["speedup"] = round(row["block_jacobi"]["ms"] / row["multigrid"]["ms"], 3)
+        results.append(row)
+    if rank == 0:
+        line = {"metric": f"ms to |r| <= {SOLVER_TOL:g} |r_0| per Newton system, 1 mm MPM JTV fit",
+                "value": results[0]["multigrid"]["ms"], "unit": "ms", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"Newton systems of the {VX[0]:g} mm fit "
+                                       f"({SHAPE[0]}x{SHAPE[1]}x{SHAPE[2]}) after "
+                                       f"{', '.join(str(k) for k in SOLVER_UPDATES)} updates",
+                           "multigrid": MG_OPTS, "max_iters": max_it},
+                "systems": results}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------- batched arm
 
 BATCH_SUBJECTS = 16
@@ -1174,6 +1262,8 @@ def main(argv=None):
         return run_served(args)
     if args.workload == "moved":
         return run_moved(args)
+    if args.solver == "mg":
+        return run_solvers(args)
     return run_ours(args)
 
 

@@ -118,6 +118,17 @@ typedef struct {
     int graph;             /* 1: with tol_gn = 0, run all updates as one captured CUDA
                               graph (instantiated on first use, cached per argument
                               set, replayed afterwards); 0: direct launches */
+    /* Preconditioner of the solve.  mg_levels = 0: the block preconditioner
+     * H + diag(G'WG) (x) diag(lambda) of Sec. 2.6 (the paper's solver).
+     * mg_levels >= 1 (an option the paper does not have): conjugate gradient
+     * preconditioned by one aggregation multigrid V-cycle with at most
+     * mg_levels levels (each merging 2 x 2 x 2 voxels; a level of at most 512
+     * voxels is the coarsest), Galerkin coarse operators, damped block-Jacobi
+     * smoothing.  The three fields below take their defaults when 0. */
+    int mg_levels;         /* 0..16 */
+    int mg_nu;             /* sweeps before and after each coarse correction (1) */
+    double mg_omega;       /* damping of the sweeps, in (0, 2) (0.7) */
+    int mg_coarse_sweeps;  /* sweeps on the coarsest level (20) */
 } mpm_opts;
 
 /* Per-update record filled by mpm_fit (host memory, caller-owned). */
@@ -182,8 +193,8 @@ mpm_status mpm_solve(const mpm_problem* problem, const mpm_opts* opts, const flo
  * minus (ws, ws_bytes), and keeps its scratch in a fixed 64 MiB device array
  * owned by the library.  Every GPU that loads the library holds that array
  * until the process exits.
- *  - Size limit: problems whose solve scratch exceeds 64 MiB (about 500 000
- *    voxels, e.g. 96 x 80 x 64) are refused with
+ *  - Size limit: problems whose solve scratch exceeds 64 MiB (about 450 000
+ *    voxels, e.g. 80 x 80 x 64) are refused with
  *    MPM_ERR_WORKSPACE_TOO_SMALL and a message giving the bytes needed; use
  *    mpm_solve with a workspace for those.
  *  - Allocates nothing: no cudaMalloc, no cudaFree, no allocating library
@@ -404,7 +415,8 @@ enum {
     MPM_KERNEL_INIT = 7,         /* image means and constant maps */
     MPM_KERNEL_GRAD_HESS_PROJ = 8, /* projected voxel pass, one contrast */
     MPM_KERNEL_RESLICE = 9,      /* pull / push of the spatial projection */
-    MPM_KERNEL_KINDS = 10
+    MPM_KERNEL_MG = 10,          /* multigrid hierarchy and V-cycle (mg_levels > 0) */
+    MPM_KERNEL_KINDS = 11
 };
 
 /* Diagnostic timing.  While enabled (on != 0, process-wide), every kernel

@@ -54,6 +54,8 @@ class Opts(ctypes.Structure):
         ("newton_per_irls", ctypes.c_int), ("init", ctypes.c_int),
         ("tol_gn", ctypes.c_double), ("tol_cg", ctypes.c_double),
         ("graph", ctypes.c_int),
+        ("mg_levels", ctypes.c_int), ("mg_nu", ctypes.c_int), ("mg_omega", ctypes.c_double),
+        ("mg_coarse_sweeps", ctypes.c_int),
     ]
 
 
@@ -126,7 +128,7 @@ PROTOTYPES = {
 TILE_SHAPES = 2      # MPM_TILE_SHAPES
 
 KERNEL_KINDS = ["grad_hess", "jtv", "pcg_init", "pcg_step", "pcg_final", "uncertainty",
-                "forward", "init", "grad_hess_proj", "reslice"]
+                "forward", "init", "grad_hess_proj", "reslice", "multigrid"]
 
 _handle = None
 

@@ -24,7 +24,7 @@ static std::atomic<unsigned long long> g_launches{0};
 // (no cost when no tool is attached).
 static const char* const kKindNames[MPM_KERNEL_KINDS] = {
     "grad_hess", "jtv", "pcg_init", "pcg_step", "pcg_final", "uncertainty", "forward", "init",
-    "grad_hess_proj", "reslice"};
+    "grad_hess_proj", "reslice", "multigrid"};
 
 struct NvtxUpdate {
     explicit NvtxUpdate(int it)
@@ -171,6 +171,13 @@ mpm_status check_opts(const mpm_opts* o)
     if (o->graph != 0 && o->graph != 1) return fail(MPM_ERR_INVALID_ARG, "graph must be 0 or 1");
     if (!(std::isfinite(o->tol_gn) && o->tol_gn >= 0.0) || !(std::isfinite(o->tol_cg) && o->tol_cg >= 0.0))
         return fail(MPM_ERR_INVALID_ARG, "tolerances must be finite and >= 0");
+    if (o->mg_levels < 0 || o->mg_levels > 16)
+        return fail(MPM_ERR_INVALID_ARG, "mg_levels = %d outside [0, 16]", o->mg_levels);
+    if (o->mg_nu < 0 || o->mg_nu > 8) return fail(MPM_ERR_INVALID_ARG, "mg_nu = %d outside [0, 8]", o->mg_nu);
+    if (!(std::isfinite(o->mg_omega) && o->mg_omega >= 0.0 && o->mg_omega < 2.0))
+        return fail(MPM_ERR_INVALID_ARG, "mg_omega must be in [0, 2)");
+    if (o->mg_coarse_sweeps < 0 || o->mg_coarse_sweeps > 1000)
+        return fail(MPM_ERR_INVALID_ARG, "mg_coarse_sweeps = %d outside [0, 1000]", o->mg_coarse_sweeps);
     return MPM_OK;
 }
 
@@ -446,7 +453,7 @@ static cudaError_t fit_enqueue_updates(const FitJob& j, cudaStream_t st, int* it
         if ((e = launch_jtv(P, j.y, w_fresh ? L.w : nullptr, L.jtv + it, L.red, st))) return e;
         if ((e = launch_lik(j, it, st))) return e;
         if (it >= j.opts.gn_iters) break;
-        if ((e = launch_solve(P, j.opts.cg_iters, j.opts.tol_cg, L.h, L.w, L.g, j.y, nullptr, j.y,
+        if ((e = launch_solve(P, solve_opts(j.opts), L.h, L.w, L.g, j.y, nullptr, j.y,
                               nullptr, L.cg_rel + it, L.cg_it + it, L.solve, L.hdr, L.red, st)))
             return e;
     }
@@ -485,7 +492,7 @@ static mpm_status fit_run_adaptive(const FitJob& j, cudaStream_t st, int* iters_
             break;
         }
         F_prev = F;
-        MPM_CUDA(launch_solve(P, j.opts.cg_iters, j.opts.tol_cg, L.h, L.w, L.g, j.y, nullptr, j.y,
+        MPM_CUDA(launch_solve(P, solve_opts(j.opts), L.h, L.w, L.g, j.y, nullptr, j.y,
                               nullptr, L.cg_rel + it, L.cg_it + it, L.solve, L.hdr, L.red, st));
     }
     if (j.var) {
@@ -539,9 +546,10 @@ static std::string graph_key(const FitJob* jobs, int n)
         // type, the schedule field by field (mpm_opts has tail padding), and
         // every pointer the launches use.
         k.append(reinterpret_cast<const char*>(&j.P), sizeof(DevProblem));
-        const long long sched[6] = {j.problem->echo_dtype, j.opts.gn_iters, j.opts.cg_iters,
-                                    j.opts.newton_per_irls, j.opts.init, j.opts.graph};
-        const double tols[2] = {j.opts.tol_gn, j.opts.tol_cg};
+        const long long sched[9] = {j.problem->echo_dtype, j.opts.gn_iters, j.opts.cg_iters,
+                                    j.opts.newton_per_irls, j.opts.init, j.opts.graph,
+                                    j.opts.mg_levels, j.opts.mg_nu, j.opts.mg_coarse_sweeps};
+        const double tols[3] = {j.opts.tol_gn, j.opts.tol_cg, j.opts.mg_omega};
         k.append(reinterpret_cast<const char*>(sched), sizeof sched);
         k.append(reinterpret_cast<const char*>(tols), sizeof tols);
         const void* ptrs[7] = {j.x, j.b1p, j.b1m, j.y, j.var, j.ws, (const void*)j.ws_bytes};
@@ -913,7 +921,7 @@ mpm_status mpm_solve(const mpm_problem* problem, const mpm_opts* opts, const flo
     FitWs L;
     MPM_TRY(check_ws(P, MPM_CALL_SOLVE, ws, ws_bytes, L));
     MPM_CUDA(cudaMemsetAsync(L.hdr, 0, sizeof(WsHeader), st));
-    MPM_CUDA(launch_solve(P, opts->cg_iters, opts->tol_cg, h, w, g, y, delta, nullptr, resid,
+    MPM_CUDA(launch_solve(P, solve_opts(*opts), h, w, g, y, delta, nullptr, resid,
                           nullptr, nullptr, L.solve, L.hdr, L.red, st));
     return MPM_OK;
 }

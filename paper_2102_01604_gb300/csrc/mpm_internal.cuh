@@ -53,12 +53,28 @@ cudaError_t launch_fill_maps(const DevProblem& P, const float* values, float* y,
 
 cudaError_t launch_jtv(const DevProblem& P, const float* y, float* w, double* jtv,
                        Reduce red, cudaStream_t st);
-cudaError_t launch_solve(const DevProblem& P, int cg_iters, double tol_cg, const float* h,
+// Schedule of one solve (from mpm_opts; the multigrid fields resolved to
+// their defaults).
+struct SolveOpts {
+    int cg_iters;
+    double tol_cg;
+    int mg_levels;          // 0: block-Jacobi PCG (Eq. 42); > 0: multigrid-preconditioned CG
+    int mg_nu;
+    float mg_omega;
+    int mg_coarse_sweeps;
+};
+SolveOpts solve_opts(const mpm_opts& o);
+cudaError_t launch_solve(const DevProblem& P, const SolveOpts& so, const float* h,
                          const float* w, const float* g, const float* y, float* delta,
                          float* y_update, double* resid, double* report_rel,
                          int* report_it, void* solve_ws, WsHeader* hdr, Reduce red,
                          cudaStream_t st);
-size_t solve_ws_bytes(const DevProblem& P);
+size_t solve_ws_bytes(const DevProblem& P);   // enough for either solver
+size_t mg_ws_bytes(const DevProblem& P);      // multigrid.cu
+cudaError_t launch_solve_mg(const DevProblem& P, const SolveOpts& o, const float* h, const float* w,
+                            const float* g, const float* y, float* delta, float* y_update,
+                            double* resid, double* report_rel, int* report_it, void* solve_ws,
+                            WsHeader* hdr, Reduce red, cudaStream_t st);
 
 // TMA-staged PCG iteration (stencil_tma.cu).  make_step_maps returns false
 // when the volume or the pointers do not meet the copy engine's alignment

@@ -262,7 +262,7 @@ mpm_status mpm_server_step(mpm_server* s, int* n_active, int* n_queued, int* n_f
             } else {
                 r.F_prev = F;
                 const FitWs& L = r.L;
-                SRV_CUDA(launch_solve(r.P, r.opts.cg_iters, r.opts.tol_cg, L.h, L.w, L.g, r.y, nullptr,
+                SRV_CUDA(launch_solve(r.P, solve_opts(r.opts), L.h, L.w, L.g, r.y, nullptr,
                                       r.y, nullptr, L.cg_rel + r.it, L.cg_it + r.it, L.solve, L.hdr,
                                       L.red, r.stream));
                 r.it += 1;

@@ -73,7 +73,7 @@ extern "C" mpm_status mpm_solve_static(const mpm_problem* problem, const mpm_opt
                     "caller workspace",
                     need, kStaticScratchBytes,
                     (long long)((kStaticScratchBytes - kHeaderBytes - kPartialBytes) /
-                                (sizeof(float4) * 8)),
+                                (solve_ws_bytes(P) / (P.N > 0 ? P.N : 1))),
                     P.K);
     if ((s = check_dev(h, "h", false, 4)) != MPM_OK) return s;
     if ((s = check_dev(w, "w", false, 4)) != MPM_OK) return s;
@@ -93,7 +93,7 @@ extern "C" mpm_status mpm_solve_static(const mpm_problem* problem, const mpm_opt
     // reduction arrival counter must start at zero.
     cudaError_t e = cudaMemsetAsync(hdr, 0, sizeof(WsHeader), st);
     if (e != cudaSuccess) return fail(MPM_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
-    e = launch_solve(P, opts->cg_iters, opts->tol_cg, h, w, g, y, delta, nullptr, resid, nullptr,
+    e = launch_solve(P, solve_opts(*opts), h, w, g, y, delta, nullptr, resid, nullptr,
                      nullptr, solve, hdr, red, st);
     if (e != cudaSuccess) return fail(MPM_ERR_CUDA, "launch: %s", cudaGetErrorString(e));
     return MPM_OK;

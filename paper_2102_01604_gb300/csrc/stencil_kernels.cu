@@ -115,8 +115,26 @@ __global__ void __launch_bounds__(kBlock) k_jtv(DevProblem P, int zc, const floa
 
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-// z[2], v[2], p[3] and x, each [N] float4.
-size_t solve_ws_bytes(const DevProblem& P) { return 8 * align256(sizeof(float4) * (size_t)P.N); }
+// z[2], v[2], p[3] and x, each [N] float4; or the multigrid solver's
+// buffers (multigrid.cu), whichever is larger.
+size_t solve_ws_bytes(const DevProblem& P)
+{
+    const size_t pcg = 8 * align256(sizeof(float4) * (size_t)P.N);
+    const size_t mg = mg_ws_bytes(P);
+    return pcg > mg ? pcg : mg;
+}
+
+SolveOpts solve_opts(const mpm_opts& o)
+{
+    SolveOpts s;
+    s.cg_iters = o.cg_iters;
+    s.tol_cg = o.tol_cg;
+    s.mg_levels = o.mg_levels;
+    s.mg_nu = o.mg_nu > 0 ? o.mg_nu : 1;
+    s.mg_omega = o.mg_omega > 0.0 ? (float)o.mg_omega : 0.7f;
+    s.mg_coarse_sweeps = o.mg_coarse_sweeps > 0 ? o.mg_coarse_sweeps : 20;
+    return s;
+}
 
 static SolveBufs carve(const DevProblem& P, void* ws)
 {
@@ -490,15 +508,18 @@ cudaError_t tma_autotune(const DevProblem& P, void* solve_ws, WsHeader* hdr, Red
     return e;
 }
 
-cudaError_t launch_solve(const DevProblem& P, int cg_iters, double tol_cg, const float* h,
+cudaError_t launch_solve(const DevProblem& P, const SolveOpts& so, const float* h,
                          const float* w, const float* g, const float* y, float* delta,
                          float* y_update, double* resid, double* report_rel, int* report_it,
                          void* solve_ws, WsHeader* hdr, Reduce red, cudaStream_t st)
 {
+    if (so.mg_levels > 0)
+        return launch_solve_mg(P, so, h, w, g, y, delta, y_update, resid, report_rel, report_it,
+                               solve_ws, hdr, red, st);
     if (P.K == 4)
-        return solve_k<4>(P, cg_iters, tol_cg, h, w, g, y, delta, y_update, resid, report_rel,
+        return solve_k<4>(P, so.cg_iters, so.tol_cg, h, w, g, y, delta, y_update, resid, report_rel,
                           report_it, solve_ws, hdr, red, st);
-    return solve_k<3>(P, cg_iters, tol_cg, h, w, g, y, delta, y_update, resid, report_rel,
+    return solve_k<3>(P, so.cg_iters, so.tol_cg, h, w, g, y, delta, y_update, resid, report_rel,
                       report_it, solve_ws, hdr, red, st);
 }
 
