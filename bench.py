@@ -715,7 +715,7 @@ def run_ours(args):
                                "PCG + posterior variance"
                                + (", echoes stored bf16" if args.echo_dtype == "bf16" else ""),
                    "echo_storage": args.echo_dtype,
-                   "stencil_tile": ["16x16", "32x8"][tile] if tile >= 0 else "plain kernel",
+                   "stencil_tile": ["16x16", "32x8", "32x16"][tile] if tile >= 0 else "plain kernel",
                    "tile_autotune_us": [round(1000 * t, 1) for t in tile_ms],
                    "voxels": N, "gn_iters": GN_ITERS, "cg_iters": CG_ITERS, "lambda": LAMBDA,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",

@@ -232,8 +232,8 @@ mpm_status mpm_fit(const mpm_problem* problem, const mpm_opts* opts, const void*
                    void* ws, size_t ws_bytes, mpm_report* report, void* stream);
 
 /* Tile-shape autotuner for the PCG iteration kernel of the solve.  The
- * TMA-staged iteration can tile the (x, y) plane as 16 x 16 or 32 x 8
- * voxels; this
+ * TMA-staged iteration can tile the (x, y) plane as 16 x 16, 32 x 8 or
+ * 32 x 16 voxels; this
  * call times each applicable shape on this volume (zeroed operands in `ws`, a
  * MPM_CALL_SOLVE-sized workspace or larger), keeps the fastest for every later
  * solve of a volume of this size in the process, and writes its index to
@@ -244,7 +244,7 @@ mpm_status mpm_fit(const mpm_problem* problem, const mpm_opts* opts, const void*
  * be NULL).  Without either, a default shape is used.  A shape that does not
  * fit a volume falls back to the plain iteration kernel.  Synchronises
  * `stream` when timing. */
-#define MPM_TILE_SHAPES 2
+#define MPM_TILE_SHAPES 3
 mpm_status mpm_autotune(const mpm_problem* problem, const mpm_opts* opts, void* ws,
                         size_t ws_bytes, void* stream, int* tile, float* ms);
 

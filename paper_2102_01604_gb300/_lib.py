@@ -125,7 +125,7 @@ PROTOTYPES = {
                                         ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int]),
 }
 
-TILE_SHAPES = 2      # MPM_TILE_SHAPES
+TILE_SHAPES = 3      # MPM_TILE_SHAPES
 
 KERNEL_KINDS = ["grad_hess", "jtv", "pcg_init", "pcg_step", "pcg_final", "uncertainty",
                 "forward", "init", "grad_hess_proj", "reslice", "multigrid"]

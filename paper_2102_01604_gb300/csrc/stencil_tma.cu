@@ -17,7 +17,7 @@
 // the volume are zero-filled by the copy engine and masked by zero stencil
 // coefficients.
 //
-// Eight compute warps (one voxel per thread) take each plane in two phases:
+// The compute warps (one voxel per thread) take each plane in two phases:
 //   A  form z_j and p_j of the plane's points (the tile and its x / y halo,
 //      recomputed from the staged z, v, p) into a shared "formed" plane (a
 //      ring of three), write z_j and p_j of the tile and fold x; the raw
@@ -28,8 +28,8 @@
 // One named barrier among the compute warps per plane separates A's writes
 // of a formed plane from B's reads of it; with three formed planes in the
 // ring, A never overwrites a plane B may still read.  A producer warp keeps
-// both rings full; a stage is refilled once all eight compute warps have
-// released it.  Each thread sums its voxels' terms in float32 over one item
+// both rings full; a stage is refilled once all compute warps have released
+// it.  Each thread sums its voxels' terms in float32 over one item
 // (at most one z range of its column) and adds that partial to compensated
 // accumulators, which the block and the grid reduce in float64.
 //
@@ -50,11 +50,6 @@
 
 namespace mpm {
 
-constexpr int kStepRaw = 2;                    // raw (z, v, p, w, x, p_{j-2}) stages
-constexpr int kStepH = 2;                      // H stages
-constexpr int kStepVoxels = 256;               // voxels per tile, one compute thread each
-constexpr int kStepWarps = kStepVoxels / 32;   // compute warps
-constexpr int kStepThreads = kStepVoxels + 32; // plus the producer warp
 constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
 
 // Test hooks (mpm_test_copy_timeout): the producer issues no copies, and the
@@ -68,8 +63,17 @@ void set_copy_test(int withhold, long long wait_cycles)
     g_wait_cycles.store(wait_cycles > 0 ? wait_cycles : kWaitCycles);
 }
 
+// Per tile shape: one compute thread per voxel plus a producer warp.  256-
+// voxel tiles run two blocks per SM with two raw stages; 512-voxel tiles one
+// block per SM with three.
 template <int K, int TX, int TY>
 struct StepLayout {
+    static constexpr int VOX = TX * TY;                 // voxels per tile = compute threads
+    static constexpr int WARPS = VOX / 32;              // compute warps
+    static constexpr int THREADS = VOX + 32;            // plus the producer warp
+    static constexpr int MINB = VOX >= 512 ? 1 : 2;     // resident blocks per SM aimed for
+    static constexpr int RS = VOX >= 512 ? 3 : 2;       // raw (z, v, p, w, x, p_{j-2}) stages
+    static constexpr int HS = 2;                        // H stages
     static constexpr int T = K * (K + 1) / 2;
     static constexpr int BX = TX + 2, BY = TY + 2;      // z / v / p box and formed plane (x from x0 - 1)
     static constexpr int WX = TX + 8;                   // w box (x from x0 - 4, 16-byte aligned)
@@ -86,11 +90,12 @@ struct StepLayout {
     static constexpr int RAW = P2_OFF + a128(TILE_BYTES);
     static constexpr int H_STAGE = a128(H_BYTES);
     static constexpr int SLOT = a128(BOX_BYTES);
-    static constexpr int H_BASE = kStepRaw * RAW;
-    static constexpr int S_BASE = H_BASE + kStepH * H_STAGE;
+    static constexpr int H_BASE = RS * RAW;
+    static constexpr int S_BASE = H_BASE + HS * H_STAGE;
     static constexpr int SMEM = S_BASE + 3 * SLOT + 128;   // + alignment slack
-    static_assert(TX * TY == kStepVoxels, "one compute thread per voxel");
-    static_assert(NH <= kStepVoxels, "one halo point per thread at most");
+    static_assert(VOX % 32 == 0, "whole compute warps");
+    static_assert(NH <= VOX, "one halo point per thread at most");
+    static_assert(SMEM <= 227 * 1024, "shared memory of one block");
     static_assert(4 * BX <= 256 && 4 * TX <= 256, "TMA box rows of at most 256 elements");
 };
 
@@ -160,10 +165,11 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
-// Barrier 1 among the eight compute warps (the producer warp never joins it).
+// Barrier 1 among the compute warps (the producer warp never joins it).
+template <int NTHREADS>
 __device__ __forceinline__ void compute_warps_sync()
 {
-    asm volatile("bar.sync 1, %0;" ::"n"(kStepVoxels) : "memory");
+    asm volatile("bar.sync 1, %0;" ::"n"(NTHREADS) : "memory");
 }
 
 // Work split: the launch is one wave of resident blocks.  The volume is cut
@@ -175,7 +181,7 @@ __device__ __forceinline__ void compute_warps_sync()
 // the planes outside [za, zb) only supply the z neighbours of its own column.
 // The rings and their phases run on from one item to the next.
 template <int K, int TX, int TY, int MODE>
-__global__ void __launch_bounds__(kStepThreads, 2) k_pcg_step_tma(
+__global__ void __launch_bounds__(StepLayout<K, TX, TY>::THREADS, StepLayout<K, TX, TY>::MINB) k_pcg_step_tma(
     DevProblem P, int nchunk, int j, int want_rr, const __grid_constant__ CUtensorMap tz,
     const __grid_constant__ CUtensorMap tv, const __grid_constant__ CUtensorMap tp,
     const __grid_constant__ CUtensorMap tw, const __grid_constant__ CUtensorMap th,
@@ -186,6 +192,7 @@ __global__ void __launch_bounds__(kStepThreads, 2) k_pcg_step_tma(
 {
     using L = StepLayout<K, TX, TY>;
     constexpr int T = L::T;
+    constexpr int kStepRaw = L::RS, kStepH = L::HS, kStepWarps = L::WARPS;
     constexpr bool first = MODE == kModeFirst, fold = MODE >= kModeFold, readx = MODE == kModeFoldX;
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t raw_full[kStepRaw], raw_empty[kStepRaw];
@@ -394,7 +401,7 @@ __global__ void __launch_bounds__(kStepThreads, 2) k_pcg_step_tma(
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&raw_empty[r_stage(c)]));
-                compute_warps_sync();
+                compute_warps_sync<L::VOX>();
                 if (jj - 1 >= za) phase_b(jj - 1, c - 1, eb + (jj - 1 - za), pn, wn);
                 // the plane above becomes current
 #pragma unroll
@@ -470,9 +477,9 @@ static bool encode(CUtensorMap* m, const float* base, int rank, const cuuint64_t
 }
 
 // Tile shapes the TMA iteration is compiled for (x by y voxels).
-static const int kTileShapes[][2] = {{16, 16}, {32, 8}};
+static const int kTileShapes[][2] = {{16, 16}, {32, 8}, {32, 16}};
 
-int tma_tile_count() { return 2; }
+int tma_tile_count() { return 3; }
 
 // Tile shape per volume: set by the autotuner (mpm_autotune), else a default.
 static std::mutex g_tile_mu;
@@ -549,7 +556,7 @@ static cudaError_t launch_step_m(const DevProblem& P, int nchunk, dim3 grid, con
         attr = true;
     }
     const int jm = j > 0 ? j - 1 : 0;
-    k_pcg_step_tma<K, TX, TY, MODE><<<grid, dim3(kStepThreads, 1, 1), L::SMEM, st>>>(
+    k_pcg_step_tma<K, TX, TY, MODE><<<grid, dim3(L::THREADS, 1, 1), L::SMEM, st>>>(
         P, nchunk, j, want_rr, m.z[jm & 1], m.v[jm & 1], m.p[(j + 2) % 3], m.w, m.h, m.x,
         m.p2[(j + 1) % 3], m.B.z[j & 1], m.B.v[j & 1], m.B.p[j % 3], m.B.x, hdr, resid, red,
         g_wait_cycles.load(std::memory_order_relaxed), g_withhold.load(std::memory_order_relaxed));
@@ -578,7 +585,8 @@ static int resident_one()
                              cudaFuncAttributeMaxDynamicSharedMemorySize, StepLayout<K, TX, TY>::SMEM) !=
             cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pcg_step_tma<K, TX, TY, kModeFoldX>,
-                                                      kStepThreads, StepLayout<K, TX, TY>::SMEM) !=
+                                                      StepLayout<K, TX, TY>::THREADS,
+                                                      StepLayout<K, TX, TY>::SMEM) !=
             cudaSuccess) {
         cudaGetLastError();
         nb = 1;
@@ -605,9 +613,9 @@ static int tma_wave(const DevProblem& P, int tile)
     }
     int nb;
     if (P.K == 4)
-        nb = tile == 1 ? resident_one<4, 32, 8>() : resident_one<4, 16, 16>();
+        nb = tile == 2 ? resident_one<4, 32, 16>() : tile == 1 ? resident_one<4, 32, 8>() : resident_one<4, 16, 16>();
     else
-        nb = tile == 1 ? resident_one<3, 32, 8>() : resident_one<3, 16, 16>();
+        nb = tile == 2 ? resident_one<3, 32, 16>() : tile == 1 ? resident_one<3, 32, 8>() : resident_one<3, 16, 16>();
     return cache[key] = nb * sms;
 }
 
@@ -621,7 +629,7 @@ StencilGrid tma_grid(const DevProblem& P, int tile)
     const int best = tma_chunks(T, P.nz, W);
     StencilGrid g;
     g.grid = dim3((unsigned)std::min<long long>(T * best, W), 1, 1);
-    g.block = dim3(kStepThreads, 1, 1);
+    g.block = dim3(tile == 2 ? StepLayout<4, 32, 16>::THREADS : StepLayout<4, 16, 16>::THREADS, 1, 1);
     g.zc = best;
     return g;
 }
@@ -648,8 +656,10 @@ cudaError_t prime_tma_kernels()
     if (done) return cudaSuccess;
     cudaError_t e = prime_one<4, 16, 16>();
     if (!e) e = prime_one<4, 32, 8>();
+    if (!e) e = prime_one<4, 32, 16>();
     if (!e) e = prime_one<3, 16, 16>();
     if (!e) e = prime_one<3, 32, 8>();
+    if (!e) e = prime_one<3, 32, 16>();
     if (!e) done = true;
     return e;
 }
@@ -659,9 +669,11 @@ cudaError_t launch_step_tma(const DevProblem& P, const StencilGrid& g, const Ste
                             cudaStream_t st)
 {
     if (P.K == 4) {
+        if (m.tile == 2) return launch_step_k<4, 32, 16>(P, g.zc, g.grid, m, j, mode, want_rr, hdr, resid, red, st);
         if (m.tile == 1) return launch_step_k<4, 32, 8>(P, g.zc, g.grid, m, j, mode, want_rr, hdr, resid, red, st);
         return launch_step_k<4, 16, 16>(P, g.zc, g.grid, m, j, mode, want_rr, hdr, resid, red, st);
     }
+    if (m.tile == 2) return launch_step_k<3, 32, 16>(P, g.zc, g.grid, m, j, mode, want_rr, hdr, resid, red, st);
     if (m.tile == 1) return launch_step_k<3, 32, 8>(P, g.zc, g.grid, m, j, mode, want_rr, hdr, resid, red, st);
     return launch_step_k<3, 16, 16>(P, g.zc, g.grid, m, j, mode, want_rr, hdr, resid, red, st);
 }

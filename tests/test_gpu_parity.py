@@ -236,9 +236,9 @@ def test_bf16_echoes(mpm):
     _check_fit(rep, to_np(yy), ref)
 
 
-@pytest.mark.parametrize("tile", [0, 1])
+@pytest.mark.parametrize("tile", [0, 1, 2])
 def test_solve_every_stencil_tile_shape(mpm, tile):
-    """The TMA PCG iteration in each tile shape (16x16, 32x8) on a volume with
+    """The TMA PCG iteration in each tile shape (16x16, 32x8, 32x16) on a volume with
     ragged tiles in x and y, against the oracle."""
     shape = (76, 21, 9)
     d = dataset(shape, seed=81)
@@ -256,7 +256,7 @@ def test_autotune_times_the_shapes(mpm):
     d = dataset((96, 48, 20), seed=83)
     pg = mpm.make_problem(d["prot"], (96, 48, 20))
     tile, ms = mpm.mpm_autotune(pg, mpm.make_opts())
-    assert tile in (0, 1)
+    assert tile in (0, 1, 2)
     assert all(t > 0 for t in ms)
     assert ms[tile] == min(ms)
 
