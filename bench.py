@@ -339,7 +339,8 @@ def read_ncu_csv(path: str):
     for i in sorted(launches):
         name = launches[i]["name"]
         name = name[5:] if name.startswith("void ") else name
-        out.append((name.split("(")[0].split("<")[0].strip(), launches[i]["metrics"]))
+        name = name.split("(")[0].split("<")[0].strip()
+        out.append((name.split("::")[-1], launches[i]["metrics"]))
     return out
 
 
@@ -936,6 +937,7 @@ def run_batched(args):
                        "subjects": [[sj["problem"].nx, sj["problem"].ny, sj["problem"].nz,
                                      sj["problem"].n_contrasts] for sj in subjects],
                        "voxels": total_vox,
+                       "voxels": N,
                        "plain_value": round(v_plain / 1e6, 3),
                        "batched_over_plain": round(v_batch / v_plain, 3),
                        "l2": "inputs larger than L2; no flush"},
@@ -1085,6 +1087,7 @@ def run_moved(args):
                                    "shifted (1.5, -1, 0.5) voxels, MTw turned 3 deg about x and "
                                    "shifted (-0.75, 2, 1); Rician SNR 20; 20 updates x 30 PCG + "
                                    "posterior variance (mpm_fit_proj)",
+                       "voxels": N,
                        "plain_value": round(v_plain / 1e6, 3),
                        "projection_cost": round(v_plain / value - 1.0, 4),
                        "map_error_vs_truth": [round(v, 4) for v in err],

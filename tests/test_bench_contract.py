@@ -95,7 +95,7 @@ def test_write_traffic_per_kind_captures(tmp_path):
     kind, per voxel of that capture's volume; the kind's source hash comes
     from the captured program's own output."""
     hashes = {k: bench.kernel_source_hash(k) for k in bench.KIND_SOURCES}
-    step = "void k_pcg_step_tma<4, 32, 8>(DevProblem, int, int, int)"
+    step = "void mpm::k_pcg_step_tma<4, 32, 8, 1>(mpm::DevProblem, int, int, int)"
     _capture(tmp_path / "step.csv", [(step, 1000, 200), (step, 1100, 300)], 10, hashes)
     _capture(tmp_path / "jtv.csv", [("void k_jtv<4>(DevProblem, const float *)", 100, 20)], 4, hashes)
     out = tmp_path / "traffic.json"
