@@ -414,7 +414,8 @@ def write_traffic(paths, out: str = TRAFFIC_FILE, commands=()):
     """Per kernel kind, the mean DRAM bytes per launch and per voxel
     (`dram__bytes_read.sum + dram__bytes_write.sum` of the captured launches,
     divided by the capture's voxel count) into `out`, with the source hash of
-    the kind that the captured program printed.  Refuses (ValueError) when a
+    the kind that the captured program printed; kinds of `out` that these
+    logs do not cover are kept.  Refuses (ValueError) when a
     log lacks the program's hashes or voxel count, or when a captured kind's
     sources have changed since the capture."""
     doc = {"workload": f"{'x'.join(str(v) for v in TRAFFIC_SHAPE)} volume, one capture per "
@@ -423,6 +424,13 @@ def write_traffic(paths, out: str = TRAFFIC_FILE, commands=()):
            "per_voxel_of": "reconstruction voxels (k_grad_hess_proj: acquisition voxels of one "
                            "contrast, here the same count)",
            "kernels": {}}
+    try:
+        with open(out) as f:
+            old = json.load(f).get("kernels", {})
+    except (OSError, ValueError):
+        old = {}
+    # kinds not recaptured keep their entry (their source hash still guards them)
+    doc["kernels"].update({k: v for k, v in old.items() if "voxels" in v})
     for path in paths:
         hashes = read_log_json(path, "kernel_source_hashes")
         line = read_log_json(path, "config")

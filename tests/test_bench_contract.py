@@ -108,6 +108,10 @@ def test_write_traffic_per_kind_captures(tmp_path):
     assert k["pcg_step"]["source_hash"] == hashes["pcg_step"]
     assert k["jtv"]["dram_bytes_per_voxel"] == 30.0
     assert set(k) == {"pcg_step", "jtv"}
+    # a later capture of one kind replaces that kind and keeps the others
+    _capture(tmp_path / "jtv2.csv", [("void k_jtv<4>(DevProblem, const float *)", 50, 10)], 4, hashes)
+    k2 = bench.write_traffic([str(tmp_path / "jtv2.csv")], out=str(out))["kernels"]
+    assert k2["jtv"]["dram_bytes_per_voxel"] == 15.0 and k2["pcg_step"] == k["pcg_step"]
 
 
 def test_write_traffic_refuses_stale_or_unlabelled_captures(tmp_path):
