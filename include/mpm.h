@@ -117,7 +117,9 @@ typedef struct {
     double tol_cg;         /* stop PCG when |r_k| <= tol_cg |r_0| (0 = off) */
     int graph;             /* 1: with tol_gn = 0, run all updates as one captured CUDA
                               graph (instantiated on first use, cached per argument
-                              set, replayed afterwards); 0: direct launches */
+                              set, replayed afterwards); 2: the same, phase-batched
+                              across the subjects of mpm_fit_batch (see there);
+                              0: direct launches */
     /* Preconditioner of the solve.  mg_levels = 0: the block preconditioner
      * H + diag(G'WG) (x) diag(lambda) of Sec. 2.6 (the paper's solver).
      * mg_levels >= 1 (an option the paper does not have): conjugate gradient
@@ -259,8 +261,19 @@ mpm_status mpm_autotune(const mpm_problem* problem, const mpm_opts* opts, void* 
  * another in one lane, the smaller ones dealt over as many lanes as keep the
  * load of the lanes running together within 1.5 (0.5 beside the large lane;
  * a subject's load is voxels / 2^21), so uneven volumes share the GPU in one
- * graph launch;
- * otherwise subjects run one after another.  Each subject's result equals its
+ * graph launch.  With opts->graph = 2 the graph is phase-batched instead:
+ * subjects that share the map count, the preconditioner choice and the echo
+ * type form a class; in groups of at most 16, each phase of each update
+ * (JTV reweighting, voxel pass, PCG start, every PCG iteration, PCG end, the
+ * posterior variance) is ONE kernel launch for the whole group, each subject
+ * taking its own share of the blocks (the PCG iteration's wave of resident
+ * blocks is divided in proportion to the subjects' voxels) and keeping its own
+ * scalars and reductions; a class also shares the tile shape of the PCG
+ * iteration (each subject keeps its solo fit's), and groups run side by side.
+ * Subjects that the TMA-staged iteration cannot take (x size not a multiple
+ * of 4, a volume smaller than the tile's box, an unaligned buffer) run in
+ * lanes as with graph = 1, beside the groups.  Otherwise subjects run one
+ * after another.  Each subject's result equals its
  * mpm_fit result.  Synchronises `stream`.  0 <= n <= MPM_MAX_BATCH; n = 0
  * returns MPM_OK at once, without touching any argument or the stream. */
 mpm_status mpm_fit_batch(int n, const mpm_problem* const* problems, const mpm_opts* opts,

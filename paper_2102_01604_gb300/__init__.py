@@ -62,11 +62,14 @@ def make_problem(protocol: dict, shape, vx=(1.0, 1.0, 1.0), lam=10.0, eps=1e-3,
 def make_opts(gn_iters=10, cg_iters=30, newton_per_irls=1, init=True, tol_gn=0.0,
               tol_cg=0.0, graph=False, mg_levels=0, mg_nu=1, mg_omega=0.7,
               mg_coarse_sweeps=20) -> Opts:
-    """Schedule of a fit or solve (mpm_opts).  mg_levels > 0 selects the
+    """Schedule of a fit or solve (mpm_opts).  graph: False / True (one
+    captured graph, subjects in lanes) or "phased" (one launch per phase across
+    the subjects of a batch).  mg_levels > 0 selects the
     multigrid-preconditioned CG (an option; 0 is the paper's block
     preconditioner)."""
+    g = 2 if graph == "phased" else (1 if graph else 0)
     return Opts(int(gn_iters), int(cg_iters), int(newton_per_irls), 1 if init else 0,
-                float(tol_gn), float(tol_cg), 1 if graph else 0, int(mg_levels), int(mg_nu),
+                float(tol_gn), float(tol_cg), g, int(mg_levels), int(mg_nu),
                 float(mg_omega), int(mg_coarse_sweeps))
 
 

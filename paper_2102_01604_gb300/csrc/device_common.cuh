@@ -159,19 +159,53 @@ __device__ __forceinline__ double block_acc(Acc a, double* sh /* one per warp */
     return v;
 }
 
+// A block's place in its launch: the hardware grid for a launch of one
+// subject, or the subject's share of a launch that serves several subjects
+// (blocks [start, start + count) of it belong to one subject and see a grid
+// of `count` blocks, shaped gx x gy x gz).
+struct VGrid {
+    unsigned bx, by, bz;     // block index
+    unsigned gx, gy, gz;     // grid dimensions
+    __device__ unsigned id() const { return bx + gx * (by + gy * bz); }
+    __device__ unsigned count() const { return gx * gy * gz; }
+};
+
+__device__ __forceinline__ VGrid hw_grid()
+{
+    return VGrid{blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x, gridDim.y, gridDim.z};
+}
+
+// The subject of this block in a launch of several (start[s] is the first
+// hardware block of subject s, start[n] the total), and its virtual grid of
+// shape gx x gy x gz (gx gy gz = start[s + 1] - start[s]).
+__device__ __forceinline__ int batch_subject(const unsigned* start, int n)
+{
+    int s = 0;
+    while (s + 1 < n && blockIdx.x >= start[s + 1]) ++s;
+    return s;
+}
+
+__device__ __forceinline__ VGrid batch_grid(unsigned first, unsigned gx, unsigned gy, unsigned gz)
+{
+    const unsigned v = blockIdx.x - first;
+    return VGrid{v % gx, (v / gx) % gy, v / (gx * gy), gx, gy, gz};
+}
+
 // Last-block-done reduction of NV values per block.  Every thread calls it
 // with its own compensated partials; returns true in exactly one block (the
 // last to arrive), where out[j] (valid in thread 0) holds the grid-wide sums
 // in a fixed summation order.  The counter is reset for the next launch.
+// The grid is the block's launch, or its subject's share of a launch (vg).
 template <int NV>
-__device__ __forceinline__ bool grid_reduce(const Acc (&v)[NV], Reduce red, double (&out)[NV])
+__device__ __forceinline__ bool grid_reduce(const Acc (&v)[NV], Reduce red, double (&out)[NV],
+                                            const VGrid& vg)
 {
     __shared__ double sh[32];          // one slot per warp of the block (up to 1024 threads)
     __shared__ bool am_last;
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     const int nthreads = blockDim.x * blockDim.y;
-    const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-    const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
+    const unsigned bid = vg.id();
+    const unsigned nblocks = vg.count();
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
         double s = block_acc(v[j], sh);
@@ -194,6 +228,12 @@ __device__ __forceinline__ bool grid_reduce(const Acc (&v)[NV], Reduce red, doub
     }
     if (tid == 0) *red.counter = 0u;
     return true;
+}
+
+template <int NV>
+__device__ __forceinline__ bool grid_reduce(const Acc (&v)[NV], Reduce red, double (&out)[NV])
+{
+    return grid_reduce<NV>(v, red, out, hw_grid());
 }
 
 template <typename T>

@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -168,7 +169,7 @@ mpm_status check_opts(const mpm_opts* o)
         return fail(MPM_ERR_INVALID_ARG, "cg_iters = %d outside [1, 1e6]", o->cg_iters);
     if (o->newton_per_irls < 1) return fail(MPM_ERR_INVALID_ARG, "newton_per_irls must be >= 1");
     if (o->init != 0 && o->init != 1) return fail(MPM_ERR_INVALID_ARG, "init must be 0 or 1");
-    if (o->graph != 0 && o->graph != 1) return fail(MPM_ERR_INVALID_ARG, "graph must be 0 or 1");
+    if (o->graph < 0 || o->graph > 2) return fail(MPM_ERR_INVALID_ARG, "graph must be 0, 1 or 2");
     if (!(std::isfinite(o->tol_gn) && o->tol_gn >= 0.0) || !(std::isfinite(o->tol_cg) && o->tol_cg >= 0.0))
         return fail(MPM_ERR_INVALID_ARG, "tolerances must be finite and >= 0");
     if (o->mg_levels < 0 || o->mg_levels > 16)
@@ -560,30 +561,17 @@ static std::string graph_key(const FitJob* jobs, int n)
     return k;
 }
 
-// Capture the updates of every job as parallel branches of one graph.
-static mpm_status capture_updates(FitJob* jobs, int n, GraphEntry& out)
+// Capture `nlanes` chains of launches as parallel branches of one graph:
+// enqueue(l, stream) puts lane l's launches on its stream.
+template <class Enqueue>
+static mpm_status capture_lanes(size_t nlanes, Enqueue enqueue, GraphEntry& out)
 {
     MPM_CUDA(prime_tma_kernels());
-    // Lanes of the graph, each a chain of subjects on one stream, all lanes
-    // side by side (lane_plan).  Subjects that fill the GPU on their own run
-    // in one lane: side by side, two such fits only interleave their one-wave
-    // kernels.
-    std::vector<long long> voxels(n);
-    std::vector<char> empty(n);
-    for (int i = 0; i < n; ++i) {
-        voxels[i] = jobs[i].P.N;
-        empty[i] = jobs[i].empty ? 1 : 0;
-    }
-    const std::vector<std::vector<int>> lanes = lane_plan(voxels, empty);
-
     std::vector<cudaStream_t> ss;
-    MPM_CUDA(private_streams((int)lanes.size() + 1, ss));
+    MPM_CUDA(private_streams((int)nlanes + 1, ss));
     cudaStream_t root = ss[0];
     cudaGraph_t graph = nullptr;
     std::vector<cudaEvent_t> evs;
-    auto cleanup = [&]() {
-        for (cudaEvent_t e : evs) cudaEventDestroy(e);
-    };
     cudaEvent_t fork;
     MPM_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
     evs.push_back(fork);
@@ -591,12 +579,10 @@ static mpm_status capture_updates(FitJob* jobs, int n, GraphEntry& out)
     const unsigned long long before = g_launches.load();
     cudaError_t e = cudaStreamBeginCapture(root, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) e = cudaEventRecord(fork, root);
-    out.iters.assign(n, 0);
-    for (size_t l = 0; l < lanes.size() && e == cudaSuccess; ++l) {
+    for (size_t l = 0; l < nlanes && e == cudaSuccess; ++l) {
         cudaStream_t b = ss[1 + l];
         e = cudaStreamWaitEvent(b, fork, 0);
-        for (size_t k = 0; k < lanes[l].size() && e == cudaSuccess; ++k)
-            e = fit_enqueue_updates(jobs[lanes[l][k]], b, &out.iters[lanes[l][k]]);
+        if (e == cudaSuccess) e = enqueue(l, b);
         cudaEvent_t join;
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
         if (e == cudaSuccess) {
@@ -613,12 +599,237 @@ static mpm_status capture_updates(FitJob* jobs, int n, GraphEntry& out)
     if (e == cudaSuccess) e = e2;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&out.exec, graph, 0);
     if (graph) cudaGraphDestroy(graph);
-    cleanup();
+    for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(MPM_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
     }
     return MPM_OK;
+}
+
+// Capture the updates of every job as parallel branches of one graph.
+static mpm_status capture_updates(FitJob* jobs, int n, GraphEntry& out)
+{
+    // Lanes of the graph, each a chain of subjects on one stream, all lanes
+    // side by side (lane_plan).  Subjects that fill the GPU on their own run
+    // in one lane: side by side, two such fits only interleave their one-wave
+    // kernels.
+    std::vector<long long> voxels(n);
+    std::vector<char> empty(n);
+    for (int i = 0; i < n; ++i) {
+        voxels[i] = jobs[i].P.N;
+        empty[i] = jobs[i].empty ? 1 : 0;
+    }
+    const std::vector<std::vector<int>> lanes = lane_plan(voxels, empty);
+    out.iters.assign(n, 0);
+    return capture_lanes(
+        lanes.size(),
+        [&](size_t l, cudaStream_t b) {
+            cudaError_t e = cudaSuccess;
+            for (size_t k = 0; k < lanes[l].size() && e == cudaSuccess; ++k)
+                e = fit_enqueue_updates(jobs[lanes[l][k]], b, &out.iters[lanes[l][k]]);
+            return e;
+        },
+        out);
+}
+
+// ------------------------------------------- phase-batched graph (graph = 2)
+
+// One subject of a phase-batched fit: its grids and the TMA maps of its solve.
+struct PhasedSubject {
+    FitJob* j;
+    StencilGrid sg;          // 32 x 8 stencil grid (JTV, PCG init)
+    SolveBufs B;
+    StepMaps maps;
+    int nchunk;              // z ranges of its share of the iteration's wave
+    unsigned step_blocks;    // that share
+    unsigned vox_blocks;     // grid of the per-voxel kernels
+};
+
+// Batch classes: subjects that share every template parameter of the kernels
+// (map count, Hessian loading, echo storage, tile shape of the iteration).
+static long long phased_class(const FitJob& j, int tile)
+{
+    return ((j.P.K * 10LL + j.P.precond) * 10 + j.problem->echo_dtype) * 10 + tile;
+}
+
+// Every launch of the fits of one group (at most kBatchMax subjects of one
+// class), each phase of each update as one launch for the whole group.  Enqueued on `st`; nothing
+// here synchronises, so it can be captured.
+static cudaError_t enqueue_phased(std::vector<PhasedSubject>& subj, int tile, cudaStream_t st,
+                                  std::vector<int>& iters, const std::vector<int>& index)
+{
+    const int n = (int)subj.size();
+    const FitJob& j0 = *subj[0].j;
+    const mpm_opts& o = j0.opts;          // one schedule for the whole batch
+    const int K = j0.P.K, pre = j0.P.precond, dtype = j0.problem->echo_dtype;
+    const int npi = o.newton_per_irls;
+    const double tol2 = o.tol_cg > 0.0 ? o.tol_cg * o.tol_cg : 0.0;
+    std::vector<JtvArgs> ja(n);
+    std::vector<GradArgs> ga(n);
+    std::vector<InitArgs> ia(n);
+    std::vector<StepArgs> sa(n);
+    std::vector<FinalArgs> fa(n);
+    std::vector<UncArgs> ua;
+    std::vector<unsigned> bst(n), bvox(n), bstep(n);
+    for (int s = 0; s < n; ++s) {
+        const StencilGrid& g = subj[s].sg;
+        bst[s] = g.grid.x * g.grid.y * g.grid.z;
+        bvox[s] = subj[s].vox_blocks;
+        bstep[s] = subj[s].step_blocks;
+    }
+    auto jtv = [&](bool fresh, int slot) {
+        for (int s = 0; s < n; ++s) {
+            const FitJob& j = *subj[s].j;
+            const StencilGrid& g = subj[s].sg;
+            ja[s] = JtvArgs{j.P, g.zc, g.grid.x, g.grid.y, g.grid.z, j.y, fresh ? j.L.w : nullptr,
+                            j.L.jtv + slot, j.L.red};
+        }
+        return launch_jtv_batch(K, ja.data(), bst.data(), n, st);
+    };
+    cudaError_t e = cudaSuccess;
+    bool w_fresh = false;
+    int it = 0;
+    for (;; ++it) {
+        NvtxUpdate range(it);
+        w_fresh = (it % npi == 0);
+        if ((e = jtv(w_fresh, it))) return e;
+        for (int s = 0; s < n; ++s) {
+            const FitJob& j = *subj[s].j;
+            ga[s] = GradArgs{j.P, j.x, j.y, j.b1p, j.b1m, j.L.g, j.L.h, j.L.nll + it, j.L.red};
+        }
+        if ((e = launch_grad_hess_batch(K, pre, dtype, ga.data(), bvox.data(), n, st))) return e;
+        if (it >= o.gn_iters) break;
+        for (int s = 0; s < n; ++s) {
+            const FitJob& j = *subj[s].j;
+            const StencilGrid& g = subj[s].sg;
+            ia[s] = InitArgs{j.P, g.zc, g.grid.x, g.grid.y, g.grid.z, j.L.h, j.L.w, j.L.g, j.y,
+                             subj[s].B.z[0], tol2, j.L.hdr, nullptr, j.L.red};
+        }
+        if ((e = launch_pcg_init_batch(K, ia.data(), bst.data(), n, st))) return e;
+        for (int c = 0; c < o.cg_iters; ++c) {
+            const int rr = (tol2 > 0.0 || c == o.cg_iters - 1) ? 1 : 0;
+            for (int s = 0; s < n; ++s) {
+                const FitJob& j = *subj[s].j;
+                sa[s] = step_args(j.P, subj[s].maps, subj[s].nchunk, c, rr, j.L.hdr, nullptr, j.L.red);
+            }
+            if ((e = launch_step_batch(K, tile, step_mode(c), sa.data(), bstep.data(), n, st))) return e;
+        }
+        for (int s = 0; s < n; ++s) {
+            const FitJob& j = *subj[s].j;
+            fa[s] = FinalArgs{j.P.N, subj[s].B, nullptr, j.y, j.L.hdr, j.L.cg_rel + it, j.L.cg_it + it};
+        }
+        if ((e = launch_pcg_final_batch(K, fa.data(), bvox.data(), n, st))) return e;
+    }
+    // the posterior variance of the subjects that ask for it
+    std::vector<JtvArgs> jv;
+    std::vector<unsigned> bjv, buv;
+    ua.clear();
+    for (int s = 0; s < n; ++s) {
+        const FitJob& j = *subj[s].j;
+        if (!j.var) continue;
+        const StencilGrid& g = subj[s].sg;
+        jv.push_back(JtvArgs{j.P, g.zc, g.grid.x, g.grid.y, g.grid.z, j.y, j.L.w,
+                             j.L.jtv + MPM_MAX_REPORT + 1, j.L.red});
+        bjv.push_back(bst[s]);
+        ua.push_back(UncArgs{j.P, j.L.h, j.L.w, j.y, j.var, nullptr, nullptr, &j.L.hdr->status});
+        buv.push_back(bvox[s]);
+    }
+    if (!ua.empty()) {
+        const int m = (int)ua.size();
+        if (!w_fresh && (e = launch_jtv_batch(K, jv.data(), bjv.data(), m, st))) return e;
+        if ((e = launch_uncertainty_batch(K, ua.data(), buv.data(), m, st))) return e;
+    }
+    for (int s = 0; s < n; ++s) iters[index[s]] = it;
+    return e;
+}
+
+// The groups of a phase-batched graph: each batch class split into groups of
+// at most kBatchMax subjects that share the GPU's wave of the iteration kernel
+// in proportion to their voxels.  A subject takes its solo fit's tile shape;
+// one that cannot take part (projection, multigrid, a volume or buffer the
+// TMA-staged iteration cannot take) is marked in `rest` and runs in a lane of
+// its own kind (capture_updates' lanes) beside the groups.
+static void plan_phased(FitJob* jobs, int n, std::vector<std::vector<PhasedSubject>>& groups,
+                        std::vector<int>& tiles, std::vector<std::vector<int>>& index,
+                        std::vector<char>& rest)
+{
+    std::map<long long, std::vector<PhasedSubject>> classes;
+    std::map<long long, int> class_tile;
+    rest.assign(n, 0);
+    for (int i = 0; i < n; ++i) {
+        FitJob& j = jobs[i];
+        if (j.empty) continue;
+        rest[i] = 1;
+        if (j.proj || j.opts.mg_levels > 0) continue;
+        const int tile = tma_tile_choice(j.P);
+        PhasedSubject ps;
+        ps.j = &j;
+        ps.B = solve_bufs(j.P, j.L.solve);
+        if (!make_step_maps(j.P, j.L.h, j.L.w, ps.B, tile, &ps.maps)) continue;
+        ps.sg = stencil_grid(j.P, kTileX, kTileY);
+        ps.vox_blocks = (unsigned)voxel_grid(j.P.N);
+        rest[i] = 0;
+        const long long key = phased_class(j, tile);
+        classes[key].push_back(ps);
+        class_tile[key] = tile;
+    }
+    for (auto& kv : classes) {
+        std::vector<PhasedSubject>& members = kv.second;
+        const int tile = class_tile[kv.first];
+        for (size_t g0 = 0; g0 < members.size(); g0 += kBatchMax) {
+            const size_t g1 = std::min(members.size(), g0 + (size_t)kBatchMax);
+            std::vector<PhasedSubject> grp(members.begin() + g0, members.begin() + g1);
+            std::vector<int> idx;
+            long long vox = 0;
+            for (const PhasedSubject& ps : grp) vox += ps.j->P.N;
+            const long long wave = tma_wave_blocks(grp[0].j->P, tile);
+            for (PhasedSubject& ps : grp) {
+                const DevProblem& P = ps.j->P;
+                long long share = (long long)std::llround((double)wave * (double)P.N / (double)vox);
+                if (share < 1) share = 1;
+                const long long t = tma_tiles_of(P, tile);
+                ps.nchunk = tma_chunks(t, P.nz, share);
+                ps.step_blocks = (unsigned)std::min<long long>(share, t * ps.nchunk);
+                idx.push_back((int)(ps.j - jobs));
+            }
+            groups.push_back(grp);
+            tiles.push_back(tile);
+            index.push_back(idx);
+        }
+    }
+}
+
+// Capture the updates of every job phase by phase: one launch per phase of
+// every update for each group of plan_phased, the groups side by side, and
+// beside them the lanes of the subjects that cannot be batched.
+static mpm_status capture_phased(FitJob* jobs, int n, GraphEntry& out)
+{
+    std::vector<std::vector<PhasedSubject>> groups;
+    std::vector<int> tiles;
+    std::vector<std::vector<int>> index;
+    std::vector<char> rest;
+    plan_phased(jobs, n, groups, tiles, index, rest);
+    if (groups.empty()) return capture_updates(jobs, n, out);
+    std::vector<long long> voxels(n);
+    std::vector<char> skip(n);
+    for (int i = 0; i < n; ++i) {
+        voxels[i] = jobs[i].P.N;
+        skip[i] = rest[i] ? 0 : 1;
+    }
+    const std::vector<std::vector<int>> lanes = lane_plan(voxels, skip);
+    out.iters.assign(n, 0);
+    return capture_lanes(
+        groups.size() + lanes.size(),
+        [&](size_t l, cudaStream_t b) {
+            if (l < groups.size()) return enqueue_phased(groups[l], tiles[l], b, out.iters, index[l]);
+            const std::vector<int>& lane = lanes[l - groups.size()];
+            cudaError_t e = cudaSuccess;
+            for (size_t k = 0; k < lane.size() && e == cudaSuccess; ++k)
+                e = fit_enqueue_updates(jobs[lane[k]], b, &out.iters[lane[k]]);
+            return e;
+        },
+        out);
 }
 
 // Initial maps (host round trip for the image means), then the updates -- as
@@ -679,7 +890,10 @@ static mpm_status fit_run(FitJob* jobs, int n, mpm_report* reports, cudaStream_t
         if (!exec) {
             GraphEntry ge;
             ge.key = key;
-            MPM_TRY(capture_updates(jobs, n, ge));
+            if (jobs[0].opts.graph == 2)
+                MPM_TRY(capture_phased(jobs, n, ge));
+            else
+                MPM_TRY(capture_updates(jobs, n, ge));
             exec = ge.exec;
             iters = ge.iters;
             kernels = ge.kernels;

@@ -9,6 +9,7 @@
 #include "device_common.cuh"
 #include "host_logic.h"
 #include "pcg_step.cuh"
+#include "batch.cuh"
 
 namespace mpm {
 
@@ -103,6 +104,26 @@ cudaError_t tma_autotune(const DevProblem& P, void* solve_ws, WsHeader* hdr, Red
 cudaError_t launch_step_tma(const DevProblem& P, const StencilGrid& g, const StepMaps& m, int j,
                             int mode, int want_rr, WsHeader* hdr, double* resid, Reduce red,
                             cudaStream_t st);
+// Launches serving several subjects (batch.cuh): blocks[s] hardware blocks
+// for subject s, n <= kBatchMax.
+SolveBufs solve_bufs(const DevProblem& P, void* solve_ws);
+cudaError_t launch_jtv_batch(int K, const JtvArgs* a, const unsigned* blocks, int n, cudaStream_t st);
+cudaError_t launch_grad_hess_batch(int K, int precond, int echo_dtype, const GradArgs* a,
+                                   const unsigned* blocks, int n, cudaStream_t st);
+cudaError_t launch_pcg_init_batch(int K, const InitArgs* a, const unsigned* blocks, int n,
+                                  cudaStream_t st);
+StepArgs step_args(const DevProblem& P, const StepMaps& m, int nchunk, int j, int want_rr,
+                   WsHeader* hdr, double* resid, Reduce red);
+cudaError_t launch_step_batch(int K, int tile, int mode, const StepArgs* a, const unsigned* blocks,
+                              int n, cudaStream_t st);
+cudaError_t launch_pcg_final_batch(int K, const FinalArgs* a, const unsigned* blocks, int n,
+                                   cudaStream_t st);
+cudaError_t launch_uncertainty_batch(int K, const UncArgs* a, const unsigned* blocks, int n,
+                                     cudaStream_t st);
+int step_mode(int j);                               // kMode* of PCG iteration j
+int tma_tiles_of(const DevProblem& P, int tile);    // tiles of the (x, y) plane
+int tma_wave_blocks(const DevProblem& P, int tile); // resident blocks of the TMA iteration, whole GPU
+
 // Test hook: with withhold set, the TMA iteration's producer issues no copies;
 // every bounded wait gives up after wait_cycles clock cycles (<= 0: default).
 void set_copy_test(int withhold, long long wait_cycles);

@@ -51,14 +51,14 @@ __device__ __forceinline__ void make_edges(const DevProblem& P, int x, int y, in
 // computed.  The x / y neighbours come from the current plane (L1).  The six
 // terms are summed in the order x-, x+, y-, y+, z-, z+.
 template <int K>
-__global__ void __launch_bounds__(kBlock) k_jtv(DevProblem P, int zc, const float* __restrict__ y,
-                                                float* __restrict__ w, double* jtv, Reduce red)
+__device__ __forceinline__ void jtv_body(const DevProblem& P, int zc, const float* __restrict__ y,
+                                         float* __restrict__ w, double* jtv, Reduce red, const VGrid& vg)
 {
     const long long N = P.N;
     const long long sxy = (long long)P.nx * P.ny;
-    const int x = blockIdx.x * kTileX + threadIdx.x;
-    const int yy = blockIdx.y * kTileY + threadIdx.y;
-    const int z0 = blockIdx.z * zc;
+    const int x = vg.bx * kTileX + threadIdx.x;
+    const int yy = vg.by * kTileY + threadIdx.y;
+    const int z0 = vg.bz * zc;
     const int z1 = min(P.nz, z0 + zc);
     Acc acc;
     if (x < P.nx && yy < P.ny && z0 < z1) {
@@ -108,7 +108,22 @@ __global__ void __launch_bounds__(kBlock) k_jtv(DevProblem P, int zc, const floa
     }
     Acc v[1] = {acc};
     double out[1];
-    if (grid_reduce<1>(v, red, out) && threadIdx.x == 0 && threadIdx.y == 0) *jtv = out[0];
+    if (grid_reduce<1>(v, red, out, vg) && threadIdx.x == 0 && threadIdx.y == 0) *jtv = out[0];
+}
+
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_jtv(DevProblem P, int zc, const float* __restrict__ y,
+                                                float* __restrict__ w, double* jtv, Reduce red)
+{
+    jtv_body<K>(P, zc, y, w, jtv, red, hw_grid());
+}
+
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_jtv_batch(const __grid_constant__ Batch<JtvArgs> b)
+{
+    const int s = batch_subject(b.start, b.n);
+    const JtvArgs& a = b.a[s];
+    jtv_body<K>(a.P, a.zc, a.y, a.w, a.jtv, a.red, batch_grid(b.start[s], a.gx, a.gy, a.gz));
 }
 
 // ------------------------------------------------------ solve workspace
@@ -151,19 +166,18 @@ static SolveBufs carve(const DevProblem& P, void* ws)
 // --------------------------------------------------------------- PCG init
 
 template <int K>
-__global__ void __launch_bounds__(kBlock) k_pcg_init(DevProblem P, int zc, const float* __restrict__ h,
-                                                     const float* __restrict__ w,
-                                                     const float* __restrict__ g,
-                                                     const float* __restrict__ y, float4* __restrict__ z0,
-                                                     double tol2, WsHeader* hdr, double* resid,
-                                                     Reduce red)
+__device__ __forceinline__ void pcg_init_body(const DevProblem& P, int zc, const float* __restrict__ h,
+                                              const float* __restrict__ w, const float* __restrict__ g,
+                                              const float* __restrict__ y, float4* __restrict__ z0,
+                                              double tol2, WsHeader* hdr, double* resid, Reduce red,
+                                              const VGrid& vg)
 {
     constexpr int T = K * (K + 1) / 2;
     const long long N = P.N;
     const long long sxy = (long long)P.nx * P.ny;
-    const int x = blockIdx.x * kTileX + threadIdx.x;
-    const int yy = blockIdx.y * kTileY + threadIdx.y;
-    const int z0p = blockIdx.z * zc;
+    const int x = vg.bx * kTileX + threadIdx.x;
+    const int yy = vg.by * kTileY + threadIdx.y;
+    const int z0p = vg.bz * zc;
     const int z1p = min(P.nz, z0p + zc);
     Acc rz, rr;
     bool pd = true;
@@ -205,7 +219,7 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(DevProblem P, int zc, const
     if (!pd) atomicOr(&hdr->status, kStatusNotPD);
     Acc v[2] = {rz, rr};
     double out[2];
-    if (grid_reduce<2>(v, red, out) && threadIdx.x == 0 && threadIdx.y == 0) {
+    if (grid_reduce<2>(v, red, out, vg) && threadIdx.x == 0 && threadIdx.y == 0) {
         SolveScalars& sc = hdr->sc;
         sc.rz = out[0];
         sc.rr0 = out[1];
@@ -221,6 +235,26 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(DevProblem P, int zc, const
         sc.done = (bad || !(out[0] > 0.0) || (tol2 > 0.0 && out[1] <= tol2 * out[1])) ? 1 : 0;
         if (resid) resid[0] = sqrt(out[1]);
     }
+}
+
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_pcg_init(DevProblem P, int zc, const float* __restrict__ h,
+                                                     const float* __restrict__ w,
+                                                     const float* __restrict__ g,
+                                                     const float* __restrict__ y, float4* __restrict__ z0,
+                                                     double tol2, WsHeader* hdr, double* resid,
+                                                     Reduce red)
+{
+    pcg_init_body<K>(P, zc, h, w, g, y, z0, tol2, hdr, resid, red, hw_grid());
+}
+
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_pcg_init_batch(const __grid_constant__ Batch<InitArgs> b)
+{
+    const int s = batch_subject(b.start, b.n);
+    const InitArgs& a = b.a[s];
+    pcg_init_body<K>(a.P, a.zc, a.h, a.w, a.g, a.y, a.z0, a.tol2, a.hdr, a.resid, a.red,
+                     batch_grid(b.start[s], a.gx, a.gy, a.gz));
 }
 
 // -------------------------------------------------------- PCG iteration
@@ -313,11 +347,9 @@ __global__ void __launch_bounds__(kBlock) k_pcg_step(DevProblem P, int zc, int j
 // delta = x + the directions not yet folded into x (none, p_{it-1}, or
 // p_{it-2} and p_{it-1}), written planar, or y <- y - delta.
 template <int K>
-__global__ void __launch_bounds__(kBlock) k_pcg_final(long long N, SolveBufs B,
-                                                      float* __restrict__ delta,
-                                                      float* __restrict__ y_update,
-                                                      const WsHeader* hdr, double* report_rel,
-                                                      int* report_it)
+__device__ __forceinline__ void pcg_final_body(long long N, const SolveBufs& B, float* __restrict__ delta,
+                                               float* __restrict__ y_update, const WsHeader* hdr,
+                                               double* report_rel, int* report_it, const VGrid& vg)
 {
     const SolveScalars sc = hdr->sc;
     const bool have_x = sc.xcount > 0;
@@ -325,8 +357,8 @@ __global__ void __launch_bounds__(kBlock) k_pcg_final(long long N, SolveBufs B,
     const float alpha = (float)sc.alpha, alpha_prev = (float)sc.alpha_prev;
     const float4* __restrict__ pp = B.p[(sc.it + 2) % 3];    // p_{it-1}
     const float4* __restrict__ pp2 = B.p[(sc.it + 1) % 3];   // p_{it-2} when pend == 2
-    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
-         n += (long long)gridDim.x * blockDim.x) {
+    for (long long n = vg.bx * (long long)blockDim.x + threadIdx.x; n < N;
+         n += (long long)vg.gx * blockDim.x) {
         float v[K], t[K];
         if (have_x) {
             unpack4<K>(B.x[n], v);
@@ -352,10 +384,29 @@ __global__ void __launch_bounds__(kBlock) k_pcg_final(long long N, SolveBufs B,
                 delta[a * N + n] = v[a];
         }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (vg.bx == 0 && threadIdx.x == 0) {
         if (report_rel) *report_rel = sc.rr0 > 0.0 ? sqrt(sc.rr / sc.rr0) : 0.0;
         if (report_it) *report_it = sc.it;
     }
+}
+
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_pcg_final(long long N, SolveBufs B,
+                                                      float* __restrict__ delta,
+                                                      float* __restrict__ y_update,
+                                                      const WsHeader* hdr, double* report_rel,
+                                                      int* report_it)
+{
+    pcg_final_body<K>(N, B, delta, y_update, hdr, report_rel, report_it, hw_grid());
+}
+
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_pcg_final_batch(const __grid_constant__ Batch<FinalArgs> b)
+{
+    const int s = batch_subject(b.start, b.n);
+    const FinalArgs& a = b.a[s];
+    pcg_final_body<K>(a.N, a.B, a.delta, a.y_update, a.hdr, a.report_rel, a.report_it,
+                      batch_grid(b.start[s], b.start[s + 1] - b.start[s], 1, 1));
 }
 
 // ------------------------------------------------------------- launchers
@@ -392,7 +443,7 @@ cudaError_t launch_jtv(const DevProblem& P, const float* y, float* w, double* jt
 }
 
 // What iteration j of a solve does besides the common work.
-static int step_mode(int j)
+int step_mode(int j)
 {
     if (j == 0) return kModeFirst;
     if (j % 2) return kModeStep;
@@ -506,6 +557,50 @@ cudaError_t tma_autotune(const DevProblem& P, void* solve_ws, WsHeader* hdr, Red
     cudaEventDestroy(b);
     if (e == cudaSuccess && *best >= 0) tma_tile_set(P, *best);
     return e;
+}
+
+// ------------------------------------------------- batched launches
+
+SolveBufs solve_bufs(const DevProblem& P, void* solve_ws) { return carve(P, solve_ws); }
+
+cudaError_t launch_jtv_batch(int K, const JtvArgs* a, const unsigned* blocks, int n, cudaStream_t st)
+{
+    Batch<JtvArgs> b;
+    fill_batch(b, a, blocks, n);
+    LaunchScope ls(MPM_KERNEL_JTV, st);
+    const dim3 blk(kTileX, kTileY, 1);
+    if (K == 4)
+        k_jtv_batch<4><<<b.start[n], blk, 0, st>>>(b);
+    else
+        k_jtv_batch<3><<<b.start[n], blk, 0, st>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_init_batch(int K, const InitArgs* a, const unsigned* blocks, int n,
+                                  cudaStream_t st)
+{
+    Batch<InitArgs> b;
+    fill_batch(b, a, blocks, n);
+    LaunchScope ls(MPM_KERNEL_PCG_INIT, st);
+    const dim3 blk(kTileX, kTileY, 1);
+    if (K == 4)
+        k_pcg_init_batch<4><<<b.start[n], blk, 0, st>>>(b);
+    else
+        k_pcg_init_batch<3><<<b.start[n], blk, 0, st>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_final_batch(int K, const FinalArgs* a, const unsigned* blocks, int n,
+                                   cudaStream_t st)
+{
+    Batch<FinalArgs> b;
+    fill_batch(b, a, blocks, n);
+    LaunchScope ls(MPM_KERNEL_PCG_FINAL, st);
+    if (K == 4)
+        k_pcg_final_batch<4><<<b.start[n], kBlock, 0, st>>>(b);
+    else
+        k_pcg_final_batch<3><<<b.start[n], kBlock, 0, st>>>(b);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_solve(const DevProblem& P, const SolveOpts& so, const float* h,

@@ -181,14 +181,12 @@ __device__ __forceinline__ void compute_warps_sync()
 // the planes outside [za, zb) only supply the z neighbours of its own column.
 // The rings and their phases run on from one item to the next.
 template <int K, int TX, int TY, int MODE>
-__global__ void __launch_bounds__(StepLayout<K, TX, TY>::THREADS, StepLayout<K, TX, TY>::MINB) k_pcg_step_tma(
-    DevProblem P, int nchunk, int j, int want_rr, const __grid_constant__ CUtensorMap tz,
-    const __grid_constant__ CUtensorMap tv, const __grid_constant__ CUtensorMap tp,
-    const __grid_constant__ CUtensorMap tw, const __grid_constant__ CUtensorMap th,
-    const __grid_constant__ CUtensorMap txm, const __grid_constant__ CUtensorMap tp2,
-    float4* __restrict__ zout, float4* __restrict__ vout, float4* __restrict__ pout,
-    float4* __restrict__ xacc, WsHeader* hdr, double* resid, Reduce red, long long wait_cycles,
-    int withhold)
+__device__ __forceinline__ void step_body(
+    const DevProblem& P, int nchunk, int j, int want_rr, const CUtensorMap* tz, const CUtensorMap* tv,
+    const CUtensorMap* tp, const CUtensorMap* tw, const CUtensorMap* th, const CUtensorMap* txm,
+    const CUtensorMap* tp2, float4* __restrict__ zout, float4* __restrict__ vout,
+    float4* __restrict__ pout, float4* __restrict__ xacc, WsHeader* hdr, double* resid, Reduce red,
+    long long wait_cycles, int withhold, const VGrid& vg)
 {
     using L = StepLayout<K, TX, TY>;
     constexpr int T = L::T;
@@ -230,7 +228,7 @@ __global__ void __launch_bounds__(StepLayout<K, TX, TY>::THREADS, StepLayout<K, 
     }
     __syncthreads();
     if (s_done) return;                                   // the same in every block
-    if (fold && tid == 0 && blockIdx.x == 0) hdr->sc.xcount = j;
+    if (fold && tid == 0 && vg.bx == 0) hdr->sc.xcount = j;
     const float alpha = s_alpha, alpha_prev = s_alpha_prev, beta = s_beta;
 
     // Counters: c over the raw planes this block loads, e over its H planes
@@ -248,7 +246,7 @@ __global__ void __launch_bounds__(StepLayout<K, TX, TY>::THREADS, StepLayout<K, 
     if (producer) {
         if (lane == 0 && !withhold) {
             int cb = 0, eb = 0;           // counters of the item's first planes
-            for (int i = blockIdx.x; i < items && !s_fail; i += gridDim.x) {
+            for (int i = (int)vg.bx; i < items && !s_fail; i += (int)vg.gx) {
                 const int t = i % tiles, ch = i / tiles;
                 const int za = (int)((long long)ch * nz / nchunk), zb = (int)((long long)(ch + 1) * nz / nchunk);
                 const int x0 = (t % gx) * TX, y0 = (t / gx) * TY;
@@ -268,15 +266,15 @@ __global__ void __launch_bounds__(StepLayout<K, TX, TY>::THREADS, StepLayout<K, 
                     if (!first) bytes += 2 * L::BOX_BYTES;
                     if (fold && inner) bytes += L::TILE_BYTES * (readx ? 2 : 1);
                     mbar_expect_tx(bar, bytes);
-                    tma_load_3d(smem_u32(st + L::Z_OFF), &tz, 4 * (x0 - 1), y0 - 1, jj, bar);
+                    tma_load_3d(smem_u32(st + L::Z_OFF), tz, 4 * (x0 - 1), y0 - 1, jj, bar);
                     if (!first) {
-                        tma_load_3d(smem_u32(st + L::V_OFF), &tv, 4 * (x0 - 1), y0 - 1, jj, bar);
-                        tma_load_3d(smem_u32(st + L::P_OFF), &tp, 4 * (x0 - 1), y0 - 1, jj, bar);
+                        tma_load_3d(smem_u32(st + L::V_OFF), tv, 4 * (x0 - 1), y0 - 1, jj, bar);
+                        tma_load_3d(smem_u32(st + L::P_OFF), tp, 4 * (x0 - 1), y0 - 1, jj, bar);
                     }
-                    tma_load_3d(smem_u32(st + L::W_OFF), &tw, x0 - 4, y0 - 1, jj, bar);
+                    tma_load_3d(smem_u32(st + L::W_OFF), tw, x0 - 4, y0 - 1, jj, bar);
                     if (fold && inner) {
-                        tma_load_3d(smem_u32(st + L::P2_OFF), &tp2, 4 * x0, y0, jj, bar);
-                        if (readx) tma_load_3d(smem_u32(st + L::X_OFF), &txm, 4 * x0, y0, jj, bar);
+                        tma_load_3d(smem_u32(st + L::P2_OFF), tp2, 4 * x0, y0, jj, bar);
+                        if (readx) tma_load_3d(smem_u32(st + L::X_OFF), txm, 4 * x0, y0, jj, bar);
                     }
                     raw_issued = c;
                     if (!inner) continue;
@@ -289,7 +287,7 @@ __global__ void __launch_bounds__(StepLayout<K, TX, TY>::THREADS, StepLayout<K, 
                     }
                     const uint32_t hbar = smem_u32(&h_full[sh]);
                     mbar_expect_tx(hbar, L::H_BYTES);
-                    tma_load_4d(smem_u32(smem + L::H_BASE + sh * L::H_STAGE), &th, x0, y0, jj, 0, hbar);
+                    tma_load_4d(smem_u32(smem + L::H_BASE + sh * L::H_STAGE), th, x0, y0, jj, 0, hbar);
                     h_issued = e;
                 }
                 cb += jb - ja + 1;
@@ -299,7 +297,7 @@ __global__ void __launch_bounds__(StepLayout<K, TX, TY>::THREADS, StepLayout<K, 
     } else {
         const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
         int cb = 0, eb = 0;
-        for (int i = blockIdx.x; i < items; i += gridDim.x) {
+        for (int i = (int)vg.bx; i < items; i += (int)vg.gx) {
             const int t = i % tiles, ch = i / tiles;
             const int za = (int)((long long)ch * nz / nchunk), zb = (int)((long long)(ch + 1) * nz / nchunk);
             const int x = (t % gx) * TX + tx, y = (t / gx) * TY + ty;
@@ -443,7 +441,33 @@ __global__ void __launch_bounds__(StepLayout<K, TX, TY>::THREADS, StepLayout<K, 
         __syncthreads();
     }
     double out[kStepSums];
-    if (grid_reduce<kStepSums>(acc, red, out) && tid == 0) step_scalars(out, j, want_rr, hdr, resid);
+    if (grid_reduce<kStepSums>(acc, red, out, vg) && tid == 0) step_scalars(out, j, want_rr, hdr, resid);
+}
+
+template <int K, int TX, int TY, int MODE>
+__global__ void __launch_bounds__(StepLayout<K, TX, TY>::THREADS, StepLayout<K, TX, TY>::MINB) k_pcg_step_tma(
+    DevProblem P, int nchunk, int j, int want_rr, const __grid_constant__ CUtensorMap tz,
+    const __grid_constant__ CUtensorMap tv, const __grid_constant__ CUtensorMap tp,
+    const __grid_constant__ CUtensorMap tw, const __grid_constant__ CUtensorMap th,
+    const __grid_constant__ CUtensorMap txm, const __grid_constant__ CUtensorMap tp2,
+    float4* __restrict__ zout, float4* __restrict__ vout, float4* __restrict__ pout,
+    float4* __restrict__ xacc, WsHeader* hdr, double* resid, Reduce red, long long wait_cycles,
+    int withhold)
+{
+    step_body<K, TX, TY, MODE>(P, nchunk, j, want_rr, &tz, &tv, &tp, &tw, &th, &txm, &tp2, zout, vout,
+                               pout, xacc, hdr, resid, red, wait_cycles, withhold, hw_grid());
+}
+
+// Several subjects in one launch (mpm_fit_batch with opts.graph = 2).
+template <int K, int TX, int TY, int MODE>
+__global__ void __launch_bounds__(StepLayout<K, TX, TY>::THREADS, StepLayout<K, TX, TY>::MINB)
+    k_pcg_step_tma_batch(const __grid_constant__ Batch<StepArgs> b)
+{
+    const int s = batch_subject(b.start, b.n);
+    const StepArgs& a = b.a[s];
+    step_body<K, TX, TY, MODE>(a.P, a.nchunk, a.j, a.want_rr, &a.tz, &a.tv, &a.tp, &a.tw, &a.th, &a.tx,
+                               &a.tp2, a.zout, a.vout, a.pout, a.xacc, a.hdr, a.resid, a.red,
+                               a.wait_cycles, a.withhold, batch_grid(b.start[s], b.start[s + 1] - b.start[s], 1, 1));
 }
 
 // ------------------------------------------------------------------ host
@@ -475,6 +499,8 @@ static bool encode(CUtensorMap* m, const float* base, int rank, const cuuint64_t
                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
+
+static int tma_wave(const DevProblem& P, int tile);
 
 // Tile shapes the TMA iteration is compiled for (x by y voxels).
 static const int kTileShapes[][2] = {{16, 16}, {32, 8}, {32, 16}};
@@ -576,6 +602,84 @@ static cudaError_t launch_step_k(const DevProblem& P, int nchunk, dim3 grid, con
     }
 }
 
+StepArgs step_args(const DevProblem& P, const StepMaps& m, int nchunk, int j, int want_rr,
+                   WsHeader* hdr, double* resid, Reduce red)
+{
+    StepArgs a;
+    const int jm = j > 0 ? j - 1 : 0;
+    a.tz = m.z[jm & 1];
+    a.tv = m.v[jm & 1];
+    a.tp = m.p[(j + 2) % 3];
+    a.tw = m.w;
+    a.th = m.h;
+    a.tx = m.x;
+    a.tp2 = m.p2[(j + 1) % 3];
+    a.P = P;
+    a.nchunk = nchunk;
+    a.j = j;
+    a.want_rr = want_rr;
+    a.zout = m.B.z[j & 1];
+    a.vout = m.B.v[j & 1];
+    a.pout = m.B.p[j % 3];
+    a.xacc = m.B.x;
+    a.hdr = hdr;
+    a.resid = resid;
+    a.red = red;
+    a.wait_cycles = g_wait_cycles.load(std::memory_order_relaxed);
+    a.withhold = g_withhold.load(std::memory_order_relaxed);
+    return a;
+}
+
+template <int K, int TX, int TY, int MODE>
+static cudaError_t launch_step_batch_m(const Batch<StepArgs>& b, cudaStream_t st)
+{
+    using L = StepLayout<K, TX, TY>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_pcg_step_tma_batch<K, TX, TY, MODE>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_pcg_step_tma_batch<K, TX, TY, MODE><<<b.start[b.n], dim3(L::THREADS, 1, 1), L::SMEM, st>>>(b);
+    return cudaGetLastError();
+}
+
+template <int K, int TX, int TY>
+static cudaError_t launch_step_batch_k(int mode, const Batch<StepArgs>& b, cudaStream_t st)
+{
+    switch (mode) {
+    case kModeFirst: return launch_step_batch_m<K, TX, TY, kModeFirst>(b, st);
+    case kModeStep: return launch_step_batch_m<K, TX, TY, kModeStep>(b, st);
+    case kModeFold: return launch_step_batch_m<K, TX, TY, kModeFold>(b, st);
+    default: return launch_step_batch_m<K, TX, TY, kModeFoldX>(b, st);
+    }
+}
+
+cudaError_t launch_step_batch(int K, int tile, int mode, const StepArgs* a, const unsigned* blocks,
+                              int n, cudaStream_t st)
+{
+    static thread_local Batch<StepArgs> b;   // 27 KB, kept off the stack
+    fill_batch(b, a, blocks, n);
+    LaunchScope ls(MPM_KERNEL_PCG_STEP, st);
+    if (K == 4) {
+        if (tile == 2) return launch_step_batch_k<4, 32, 16>(mode, b, st);
+        if (tile == 1) return launch_step_batch_k<4, 32, 8>(mode, b, st);
+        return launch_step_batch_k<4, 16, 16>(mode, b, st);
+    }
+    if (tile == 2) return launch_step_batch_k<3, 32, 16>(mode, b, st);
+    if (tile == 1) return launch_step_batch_k<3, 32, 8>(mode, b, st);
+    return launch_step_batch_k<3, 16, 16>(mode, b, st);
+}
+
+int tma_tiles_of(const DevProblem& P, int tile)
+{
+    const int TX = kTileShapes[tile][0], TY = kTileShapes[tile][1];
+    return ((P.nx + TX - 1) / TX) * ((P.ny + TY - 1) / TY);
+}
+
+int tma_wave_blocks(const DevProblem& P, int tile) { return tma_wave(P, tile); }
+
 template <int K, int TX, int TY>
 static int resident_one()
 {
@@ -647,6 +751,10 @@ static cudaError_t prime_one()
     set(reinterpret_cast<const void*>(k_pcg_step_tma<K, TX, TY, kModeStep>));
     set(reinterpret_cast<const void*>(k_pcg_step_tma<K, TX, TY, kModeFold>));
     set(reinterpret_cast<const void*>(k_pcg_step_tma<K, TX, TY, kModeFoldX>));
+    set(reinterpret_cast<const void*>(k_pcg_step_tma_batch<K, TX, TY, kModeFirst>));
+    set(reinterpret_cast<const void*>(k_pcg_step_tma_batch<K, TX, TY, kModeStep>));
+    set(reinterpret_cast<const void*>(k_pcg_step_tma_batch<K, TX, TY, kModeFold>));
+    set(reinterpret_cast<const void*>(k_pcg_step_tma_batch<K, TX, TY, kModeFoldX>));
     return e;
 }
 

@@ -55,20 +55,18 @@ __device__ __forceinline__ void prefetch_voxel(const DevProblem& P, const XT* x,
 
 // The fused voxel pass: per voxel, accumulate_contrast for every contrast.
 template <int K, int PRE, typename XT>
-__global__ void __launch_bounds__(kBlock, 4) k_grad_hess(DevProblem P, const XT* __restrict__ x,
-                                                      const float* __restrict__ y,
-                                                      const float* __restrict__ b1p,
-                                                      const float* __restrict__ b1m,
-                                                      float* __restrict__ g,
-                                                      float* __restrict__ h, double* nll,
-                                                      Reduce red)
+__device__ __forceinline__ void grad_hess_body(const DevProblem& P, const XT* __restrict__ x,
+                                               const float* __restrict__ y, const float* __restrict__ b1p,
+                                               const float* __restrict__ b1m, float* __restrict__ g,
+                                               float* __restrict__ h, double* nll, Reduce red,
+                                               const VGrid& vg)
 {
     constexpr int T = K * (K + 1) / 2;
     const long long N = P.N;
     Acc nll_acc;
-    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
-         n += (long long)gridDim.x * blockDim.x) {
-        const long long next = n + (long long)gridDim.x * blockDim.x;
+    for (long long n = vg.bx * (long long)blockDim.x + threadIdx.x; n < N;
+         n += (long long)vg.gx * blockDim.x) {
+        const long long next = n + (long long)vg.gx * blockDim.x;
         if (next < N) prefetch_voxel<XT>(P, x, y, b1p, b1m, next);
         float a, r1, r2, dl, m;
         map_params(y, N, n, K, a, r1, r2, dl, m);
@@ -95,7 +93,28 @@ __global__ void __launch_bounds__(kBlock, 4) k_grad_hess(DevProblem P, const XT*
     }
     Acc v[1] = {nll_acc};
     double out[1];
-    if (grid_reduce<1>(v, red, out) && threadIdx.x == 0) *nll = out[0];
+    if (grid_reduce<1>(v, red, out, vg) && threadIdx.x == 0) *nll = out[0];
+}
+
+template <int K, int PRE, typename XT>
+__global__ void __launch_bounds__(kBlock, 4) k_grad_hess(DevProblem P, const XT* __restrict__ x,
+                                                      const float* __restrict__ y,
+                                                      const float* __restrict__ b1p,
+                                                      const float* __restrict__ b1m,
+                                                      float* __restrict__ g,
+                                                      float* __restrict__ h, double* nll,
+                                                      Reduce red)
+{
+    grad_hess_body<K, PRE, XT>(P, x, y, b1p, b1m, g, h, nll, red, hw_grid());
+}
+
+template <int K, int PRE, typename XT>
+__global__ void __launch_bounds__(kBlock, 4) k_grad_hess_batch(const __grid_constant__ Batch<GradArgs> b)
+{
+    const int s = batch_subject(b.start, b.n);
+    const GradArgs& a = b.a[s];
+    grad_hess_body<K, PRE, XT>(a.P, static_cast<const XT*>(a.x), a.y, a.b1p, a.b1m, a.g, a.h, a.nll,
+                               a.red, batch_grid(b.start[s], b.start[s + 1] - b.start[s], 1, 1));
 }
 
 // --------------------------------------------------------- uncertainty
@@ -104,18 +123,16 @@ __global__ void __launch_bounds__(kBlock, 4) k_grad_hess(DevProblem P, const XT*
 // d_n = sum_{m in N(n)} (w_n + w_m) / h^2, inverted in float64 through its
 // Cholesky factor: var_k = sum_j (L^-1)_{jk}^2, logdet = -2 sum log L_kk.
 template <int K>
-__global__ void __launch_bounds__(kBlock) k_uncertainty(DevProblem P, const float* __restrict__ h,
-                                                        const float* __restrict__ w,
-                                                        const float* __restrict__ y,
-                                                        float* __restrict__ var,
-                                                        float* __restrict__ logdet,
-                                                        float* __restrict__ moments,
-                                                        unsigned* status)
+__device__ __forceinline__ void uncertainty_body(const DevProblem& P, const float* __restrict__ h,
+                                                 const float* __restrict__ w, const float* __restrict__ y,
+                                                 float* __restrict__ var, float* __restrict__ logdet,
+                                                 float* __restrict__ moments, unsigned* status,
+                                                 const VGrid& vg)
 {
     const long long N = P.N;
     const long long sxy = (long long)P.nx * P.ny;
-    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
-         n += (long long)gridDim.x * blockDim.x) {
+    for (long long n = vg.bx * (long long)blockDim.x + threadIdx.x; n < N;
+         n += (long long)vg.gx * blockDim.x) {
         const int x = (int)(n % P.nx);
         const int yy = (int)((n / P.nx) % P.ny);
         const int z = (int)(n / sxy);
@@ -189,6 +206,27 @@ __global__ void __launch_bounds__(kBlock) k_uncertainty(DevProblem P, const floa
             moments[3 * N + n] = (float)((es2 - 1.0) * es2 * exp(-2.0 * lr1));
         }
     }
+}
+
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_uncertainty(DevProblem P, const float* __restrict__ h,
+                                                        const float* __restrict__ w,
+                                                        const float* __restrict__ y,
+                                                        float* __restrict__ var,
+                                                        float* __restrict__ logdet,
+                                                        float* __restrict__ moments,
+                                                        unsigned* status)
+{
+    uncertainty_body<K>(P, h, w, y, var, logdet, moments, status, hw_grid());
+}
+
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_uncertainty_batch(const __grid_constant__ Batch<UncArgs> b)
+{
+    const int s = batch_subject(b.start, b.n);
+    const UncArgs& a = b.a[s];
+    uncertainty_body<K>(a.P, a.h, a.w, a.y, a.var, a.logdet, a.moments, a.status,
+                        batch_grid(b.start[s], b.start[s + 1] - b.start[s], 1, 1));
 }
 
 // -------------------------------------------------- constant initial maps
@@ -293,6 +331,52 @@ cudaError_t launch_uncertainty(const DevProblem& P, const float* h, const float*
     else
         k_uncertainty<3><<<voxel_grid(P.N), kBlock, 0, st>>>(P, h, w, y, var, logdet, moments,
                                                               status);
+    return cudaGetLastError();
+}
+
+template <int K, int PRE>
+static void grad_hess_batch_dtype(int echo_dtype, const Batch<GradArgs>& b, cudaStream_t st)
+{
+    const unsigned grid = b.start[b.n];
+    if (echo_dtype == 1)
+        k_grad_hess_batch<K, PRE, __nv_bfloat16><<<grid, kBlock, 0, st>>>(b);
+    else
+        k_grad_hess_batch<K, PRE, float><<<grid, kBlock, 0, st>>>(b);
+}
+
+template <int K>
+static void grad_hess_batch_pre(int precond, int echo_dtype, const Batch<GradArgs>& b, cudaStream_t st)
+{
+    switch (precond) {
+    case 0: grad_hess_batch_dtype<K, 0>(echo_dtype, b, st); break;
+    case 1: grad_hess_batch_dtype<K, 1>(echo_dtype, b, st); break;
+    default: grad_hess_batch_dtype<K, 2>(echo_dtype, b, st); break;
+    }
+}
+
+cudaError_t launch_grad_hess_batch(int K, int precond, int echo_dtype, const GradArgs* a,
+                                   const unsigned* blocks, int n, cudaStream_t st)
+{
+    Batch<GradArgs> b;
+    fill_batch(b, a, blocks, n);
+    LaunchScope ls(MPM_KERNEL_GRAD_HESS, st);
+    if (K == 4)
+        grad_hess_batch_pre<4>(precond, echo_dtype, b, st);
+    else
+        grad_hess_batch_pre<3>(precond, echo_dtype, b, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_uncertainty_batch(int K, const UncArgs* a, const unsigned* blocks, int n,
+                                     cudaStream_t st)
+{
+    Batch<UncArgs> b;
+    fill_batch(b, a, blocks, n);
+    LaunchScope ls(MPM_KERNEL_UNCERTAINTY, st);
+    if (K == 4)
+        k_uncertainty_batch<4><<<b.start[n], kBlock, 0, st>>>(b);
+    else
+        k_uncertainty_batch<3><<<b.start[n], kBlock, 0, st>>>(b);
     return cudaGetLastError();
 }
 
