@@ -79,6 +79,8 @@ def parse_args(argv=None):
     ap.add_argument("--solver", choices=["pcg", "mg"], default="pcg",
                     help="mg: time to |r| <= 1e-3 |r_0| of the fit's Newton systems, block-Jacobi "
                          "PCG against multigrid-preconditioned CG (instead of the fit)")
+    ap.add_argument("--batch-mix", choices=["uneven", "small"], default="uneven",
+                    help="batched: 16 subjects of uneven sizes (64^3 .. 176x240x256), or 16 x 64^3")
     ap.add_argument("--requests", type=int, default=24, help="served: number of requests")
     ap.add_argument("--rate", type=float, default=3.0, help="served: arrivals per second")
     args = ap.parse_args(argv)
@@ -834,13 +836,14 @@ def run_solvers(args):
 BATCH_SUBJECTS = 16
 
 
-def batch_specs(seed: int):
-    """16 subjects: sizes between 64^3 and 176x240x256 (multiples of 4), 2-3
-    contrasts (PDw, T1w[, MTw]), 4-8 echoes per contrast, seeded."""
+def batch_specs(seed: int, mix: str = "uneven"):
+    """16 subjects: sizes between 64^3 and 176x240x256 (multiples of 4; all
+    64^3 for the small mix), 2-3 contrasts (PDw, T1w[, MTw]), 4-8 echoes per
+    contrast, seeded."""
     rng = np.random.default_rng(seed + 4242)
     specs = []
     for i in range(BATCH_SUBJECTS):
-        t = rng.uniform(0.0, 1.0)
+        t = rng.uniform(0.0, 1.0) if mix == "uneven" else 0.0
         dims = tuple(int(round((64 + t * (m - 64)) / 4)) * 4 for m in (176, 240, 256))
         nc = int(rng.integers(2, 4))
         contrasts = ("PDw", "T1w", "MTw")[:nc]
@@ -862,7 +865,7 @@ def run_batched(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     subjects = []
-    for i, (dims, contrasts, echoes) in enumerate(batch_specs(args.seed + 1000 * rank)):
+    for i, (dims, contrasts, echoes) in enumerate(batch_specs(args.seed + 1000 * rank, args.batch_mix)):
         prot = phantom.protocol(contrasts, echoes)
         with_mt = "MTw" in contrasts
         ph = phantom.phantom(dims, seed=args.seed + 17 * i + 1000 * rank, n_contrasts=len(contrasts),
@@ -885,7 +888,8 @@ def run_batched(args):
                          "y": torch.empty((problem.n_maps, N), device=dev),
                          "var": torch.empty((problem.n_maps, N), device=dev)})
     plain_opts = mpm.make_opts(gn_iters=GN_ITERS, cg_iters=CG_ITERS, graph=False)
-    batch_opts = mpm.make_opts(gn_iters=GN_ITERS, cg_iters=CG_ITERS, graph=True)
+    lanes_opts = mpm.make_opts(gn_iters=GN_ITERS, cg_iters=CG_ITERS, graph=True)
+    phased_opts = mpm.make_opts(gn_iters=GN_ITERS, cg_iters=CG_ITERS, graph="phased")
     for sj in subjects:
         sj["ws"] = mpm.workspace(sj["problem"], plain_opts, device=dev)
         mpm.mpm_autotune(sj["problem"], plain_opts, ws=sj["ws"])
@@ -897,11 +901,17 @@ def run_batched(args):
             mpm.mpm_fit(sj["problem"], plain_opts, sj["x"], sj["y"], sj["b1p"], sj["b1m"],
                         var=sj["var"], ws=sj["ws"])
 
-    def batch_step():
-        mpm.mpm_fit_batch([sj["problem"] for sj in subjects], batch_opts,
+    def batch_step(opts):
+        mpm.mpm_fit_batch([sj["problem"] for sj in subjects], opts,
                           [sj["x"] for sj in subjects], [sj["y"] for sj in subjects],
                           b1ps=[sj["b1p"] for sj in subjects], b1ms=[sj["b1m"] for sj in subjects],
                           vars=[sj["var"] for sj in subjects], wss=[sj["ws"] for sj in subjects])
+
+    def phased_step():
+        batch_step(phased_opts)
+
+    def lanes_step():
+        batch_step(lanes_opts)
 
     counted = {}
 
@@ -924,30 +934,40 @@ def run_batched(args):
 
     clocks = ClockSampler(local)
     clocks.start()
-    t_batch = timed(batch_step)
+    t_batch = timed(phased_step)
     clk = clocks.stop()
     launches = counted["n"]
+    t_lanes = timed(lanes_step)
+    launches_lanes = counted["n"]
     t_plain = timed(plain_step)
+    launches_plain = counted["n"]
     units = float(total_vox) * GN_ITERS * args.steps
     v_batch, tb = aggregate(t_batch, units, world, dev)
+    v_lanes, tl = aggregate(t_lanes, units, world, dev)
     v_plain, tp = aggregate(t_plain, units, world, dev)
     if rank == 0:
+        sizes = "64^3..176x240x256" if args.batch_mix == "uneven" else "all 64^3"
         line = {
-            "metric": "Mvoxel·GN-iter/s, batched MPM JTV fits (16 uneven subjects)",
+            "metric": f"Mvoxel·GN-iter/s, batched MPM JTV fits (16 subjects, {sizes})",
             "value": round(v_batch / 1e6, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(1000 * tb / args.steps, 2),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "16 subjects, sizes 64^3..176x240x256, 2-3 contrasts, 4-8 echoes "
+            "config": {"workload": f"16 subjects, sizes {sizes}, 2-3 contrasts, 4-8 echoes "
                                    "per contrast, echoes stored bf16, 20 updates x 30 PCG + "
-                                   "posterior variance each; one mpm_fit_batch call per step "
-                                   "(all subjects' updates in one CUDA graph)",
+                                   "posterior variance each; one mpm_fit_batch call per step, "
+                                   "phase-batched (opts.graph = 2: one launch per phase for "
+                                   "each class of subjects)",
                        "subjects": [[sj["problem"].nx, sj["problem"].ny, sj["problem"].nz,
                                      sj["problem"].n_contrasts] for sj in subjects],
                        "voxels": total_vox,
-                       "voxels": N,
+                       "lanes_value": round(v_lanes / 1e6, 3),
                        "plain_value": round(v_plain / 1e6, 3),
                        "batched_over_plain": round(v_batch / v_plain, 3),
+                       "lanes_over_plain": round(v_lanes / v_plain, 3),
+                       "launches_per_step": {"phased": launches // args.steps,
+                                             "lanes": launches_lanes // args.steps,
+                                             "plain": launches_plain // args.steps},
                        "l2": "inputs larger than L2; no flush"},
             "gpu_launches": int(launches), "clocks": clk,
         }

@@ -261,20 +261,23 @@ mpm_status mpm_autotune(const mpm_problem* problem, const mpm_opts* opts, void* 
  * another in one lane, the smaller ones dealt over as many lanes as keep the
  * load of the lanes running together within 1.5 (0.5 beside the large lane;
  * a subject's load is voxels / 2^21), so uneven volumes share the GPU in one
- * graph launch.  With opts->graph = 2 the graph is phase-batched instead:
- * subjects that share the map count, the preconditioner choice and the echo
- * type form a class; in groups of at most 16, each phase of each update
- * (JTV reweighting, voxel pass, PCG start, every PCG iteration, PCG end, the
- * posterior variance) is ONE kernel launch for the whole group, each subject
- * taking its own share of the blocks (the PCG iteration's wave of resident
- * blocks is divided in proportion to the subjects' voxels) and keeping its own
- * scalars and reductions; a class also shares the tile shape of the PCG
- * iteration (each subject keeps its solo fit's), and groups run side by side.
- * Subjects that the TMA-staged iteration cannot take (x size not a multiple
- * of 4, a volume smaller than the tile's box, an unaligned buffer) run in
- * lanes as with graph = 1, beside the groups.  Otherwise subjects run one
- * after another.  Each subject's result equals its
- * mpm_fit result.  Synchronises `stream`.  0 <= n <= MPM_MAX_BATCH; n = 0
+ * graph launch; each subject's result is its mpm_fit result bit for bit.
+ * With opts->graph = 2 the graph is phase-batched instead: subjects that
+ * share the map count, the preconditioner choice, the echo type and the tile
+ * shape of the PCG iteration (each keeps its solo fit's) form a class; in
+ * groups of at most 16, each phase of each update (JTV reweighting, voxel
+ * pass, PCG start, every PCG iteration, PCG end, the posterior variance) is
+ * ONE kernel launch for the whole group, each subject on its own share of the
+ * blocks with its own scalars and reductions (the PCG iteration's wave of
+ * resident blocks is divided so that the subject that finishes last does so
+ * soonest); groups run side by side.  Subjects that the TMA-staged iteration
+ * cannot take (x size not a multiple of 4, a volume smaller than the tile's
+ * box, an unaligned buffer), projected fits and multigrid solves run in lanes
+ * as with graph = 1, beside the groups.  A batched subject's reductions sum
+ * over fewer blocks than in its solo fit, so its result matches the solo
+ * result to float32 rounding, not bit for bit.  Otherwise (graph = 0 or
+ * tol_gn > 0) subjects run one after another, each exactly as its
+ * mpm_fit.  Synchronises `stream`.  0 <= n <= MPM_MAX_BATCH; n = 0
  * returns MPM_OK at once, without touching any argument or the stream. */
 mpm_status mpm_fit_batch(int n, const mpm_problem* const* problems, const mpm_opts* opts,
                          const void* const* x, const float* const* b1p, const float* const* b1m,

@@ -166,4 +166,66 @@ inline int tma_chunks(long long tiles, int nz, long long wave)
     return best;
 }
 
+// Shares of one launch of the TMA PCG iteration between several volumes (a
+// phase-batched group): volume s, of tiles[s] tiles per plane and nz[s]
+// planes, gets blocks[s] blocks and chunks[s] z ranges.  Each of its blocks
+// walks ceil(tiles c / blocks) items of ceil(nz / c) + 2 planes (splits of
+// fewer than 4 planes are not considered, as in tma_chunks), so the launch
+// lasts about the largest such cost among the volumes.  The shares minimise
+// that largest cost with at least one block per volume and at most `wave`
+// blocks in all (given n <= wave), each volume taking the fewest blocks that
+// keep it within the minimum.  Returns the minimum.
+inline long long share_wave(const std::vector<long long>& tiles, const std::vector<int>& nz,
+                            long long wave, std::vector<long long>& blocks, std::vector<int>& chunks)
+{
+    const size_t n = tiles.size();
+    blocks.assign(n, 1);
+    chunks.assign(n, 1);
+    if (n == 0) return 0;
+    // fewest blocks that keep volume s within cost T, and the split for it
+    // (-1: no split fits T)
+    auto need = [&](size_t s, long long T, int* c_out) {
+        long long best = -1;
+        for (int c = 1; c <= nz[s]; ++c) {
+            const long long per = (nz[s] + c - 1) / c;
+            if (per < 4 && c > 1) break;
+            const long long rounds = T / (per + 2);
+            if (rounds < 1) continue;
+            const long long b = (tiles[s] * c + rounds - 1) / rounds;
+            if (best < 0 || b < best) {
+                best = b;
+                *c_out = c;
+            }
+        }
+        return best;
+    };
+    auto fits = [&](long long T, bool keep) {
+        long long sum = 0;
+        for (size_t s = 0; s < n; ++s) {
+            int c = 1;
+            const long long b = need(s, T, &c);
+            if (b < 0) return false;
+            sum += b;
+            if (keep) {
+                blocks[s] = b;
+                chunks[s] = c;
+            }
+        }
+        return sum <= wave;
+    };
+    long long hi = 0;   // one block per volume, whole columns: always fits
+    for (size_t s = 0; s < n; ++s) hi = std::max(hi, tiles[s] * (nz[s] + 2LL));
+    if ((long long)n > wave) return hi;
+    long long lo = 0;   // never fits
+    while (hi - lo > 1) {
+        const long long mid = lo + (hi - lo) / 2;
+        if (fits(mid, false))
+            hi = mid;
+        else
+            lo = mid;
+    }
+    fits(hi, true);
+    return hi;
+}
+
 }  // namespace mpm

@@ -746,7 +746,7 @@ static cudaError_t enqueue_phased(std::vector<PhasedSubject>& subj, int tile, cu
 
 // The groups of a phase-batched graph: each batch class split into groups of
 // at most kBatchMax subjects that share the GPU's wave of the iteration kernel
-// in proportion to their voxels.  A subject takes its solo fit's tile shape;
+// (share_wave: the shares that let the launch end soonest).  A subject takes its solo fit's tile shape;
 // one that cannot take part (projection, multigrid, a volume or buffer the
 // TMA-staged iteration cannot take) is marked in `rest` and runs in a lane of
 // its own kind (capture_updates' lanes) beside the groups.
@@ -781,17 +781,17 @@ static void plan_phased(FitJob* jobs, int n, std::vector<std::vector<PhasedSubje
             const size_t g1 = std::min(members.size(), g0 + (size_t)kBatchMax);
             std::vector<PhasedSubject> grp(members.begin() + g0, members.begin() + g1);
             std::vector<int> idx;
-            long long vox = 0;
-            for (const PhasedSubject& ps : grp) vox += ps.j->P.N;
-            const long long wave = tma_wave_blocks(grp[0].j->P, tile);
-            for (PhasedSubject& ps : grp) {
-                const DevProblem& P = ps.j->P;
-                long long share = (long long)std::llround((double)wave * (double)P.N / (double)vox);
-                if (share < 1) share = 1;
-                const long long t = tma_tiles_of(P, tile);
-                ps.nchunk = tma_chunks(t, P.nz, share);
-                ps.step_blocks = (unsigned)std::min<long long>(share, t * ps.nchunk);
-                idx.push_back((int)(ps.j - jobs));
+            std::vector<long long> t, blocks;
+            std::vector<int> nz, chunks;
+            for (const PhasedSubject& ps : grp) {
+                t.push_back(tma_tiles_of(ps.j->P, tile));
+                nz.push_back(ps.j->P.nz);
+            }
+            share_wave(t, nz, tma_wave_blocks(grp[0].j->P, tile), blocks, chunks);
+            for (size_t k = 0; k < grp.size(); ++k) {
+                grp[k].nchunk = chunks[k];
+                grp[k].step_blocks = (unsigned)blocks[k];
+                idx.push_back((int)(grp[k].j - jobs));
             }
             groups.push_back(grp);
             tiles.push_back(tile);

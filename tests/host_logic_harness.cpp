@@ -53,6 +53,20 @@ int hl_lane_plan(int n, const long long* voxels, const char* empty, int* lane_of
 
 int hl_tma_chunks(long long tiles, int nz, long long wave) { return tma_chunks(tiles, nz, wave); }
 
+long long hl_share_wave(int n, const long long* tiles, const int* nz, long long wave, long long* blocks,
+                        int* chunks)
+{
+    std::vector<long long> b;
+    std::vector<int> c;
+    const long long cost = share_wave(std::vector<long long>(tiles, tiles + n),
+                                      std::vector<int>(nz, nz + n), wave, b, c);
+    for (int i = 0; i < n; ++i) {
+        blocks[i] = b[i];
+        chunks[i] = c[i];
+    }
+    return cost;
+}
+
 int hl_admit_pick(void* a, int n, const long long* n_vox, const size_t* ws, const int* overtaken,
                   double load, int max_slots, size_t* off)
 {

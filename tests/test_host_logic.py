@@ -39,6 +39,9 @@ def hl(tmp_path_factory):
     h.hl_lane_plan.argtypes = [ctypes.c_int, ctypes.POINTER(LL), ctypes.c_char_p,
                                ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     h.hl_tma_chunks.argtypes = [LL, ctypes.c_int, LL]
+    h.hl_share_wave.restype = LL
+    h.hl_share_wave.argtypes = [ctypes.c_int, ctypes.POINTER(LL), ctypes.POINTER(ctypes.c_int), LL,
+                                ctypes.POINTER(LL), ctypes.POINTER(ctypes.c_int)]
     h.hl_admit_pick.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(LL), ctypes.POINTER(ULL),
                                 ctypes.POINTER(ctypes.c_int), ctypes.c_double, ctypes.c_int,
                                 ctypes.POINTER(ULL)]
@@ -236,6 +239,54 @@ def test_tma_chunks(hl, seed):
         bounds = [ch * nz // c for ch in range(c + 1)]
         assert bounds[0] == 0 and bounds[-1] == nz
         assert all(b > a for a, b in zip(bounds, bounds[1:]))
+
+
+def share_wave(hl, tiles, nz, wave):
+    n = len(tiles)
+    b, c = (LL * n)(), (ctypes.c_int * n)()
+    cost = hl.hl_share_wave(n, (LL * n)(*tiles), (ctypes.c_int * n)(*nz), wave, b, c)
+    return cost, list(b), list(c)
+
+
+def _splits(nz):
+    return [d for d in range(1, nz + 1) if d == 1 or -(-nz // d) >= 4]
+
+
+def _min_cost(tiles, nz, b):
+    """Lowest rounds x (planes + 2) of one volume with b blocks."""
+    return min(chunk_cost(tiles, nz, b, c) for c in _splits(nz))
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_share_wave_is_optimal(hl, seed):
+    """Brute force over every assignment of blocks on small groups: the
+    returned largest cost is the minimum, the returned shares reach it, sum
+    to at most the wave and cannot lose a block without exceeding it."""
+    import itertools
+    rng = random.Random(500 + seed)
+    for _ in range(40):
+        n = rng.randrange(1, 4)
+        tiles = [rng.randrange(1, 9) for _ in range(n)]
+        nz = [rng.randrange(1, 24) for _ in range(n)]
+        wave = rng.randrange(n, 14)
+        best = min(max(_min_cost(t, z, b) for t, z, b in zip(tiles, nz, bs))
+                   for bs in itertools.product(range(1, wave + 1), repeat=n) if sum(bs) <= wave)
+        cost, blocks, chunks = share_wave(hl, tiles, nz, wave)
+        assert cost == best, (tiles, nz, wave)
+        assert sum(blocks) <= wave and min(blocks) >= 1
+        for t, z, b, c in zip(tiles, nz, blocks, chunks):
+            assert c in _splits(z)
+            assert chunk_cost(t, z, b, c) <= cost
+            assert b == 1 or _min_cost(t, z, b - 1) > cost
+
+
+def test_share_wave_single_volume_is_the_solo_launch(hl):
+    """One volume: the cost of the solo launch (tma_chunks over the whole wave)."""
+    for tiles, nz, wave in [(180, 256, 304), (165, 256, 456), (16, 64, 304), (44, 64, 304)]:
+        cost, blocks, chunks = share_wave(hl, [tiles], [nz], wave)
+        c = hl.hl_tma_chunks(tiles, nz, wave)
+        assert cost == chunk_cost(tiles, nz, wave, c)
+        assert blocks[0] <= min(wave, tiles * c)
 
 
 # ---------------------------------------------------------------- admission
