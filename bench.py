@@ -282,11 +282,11 @@ def measured_peak():
 # Source files that define each kernel kind (besides device_common.cuh,
 # which every kernel includes).
 KIND_SOURCES = {
-    "grad_hess": ["voxel_kernels.cu", "voxel_model.cuh"],
+    "grad_hess": ["voxel_kernels.cu", "voxel_tma.cu", "voxel_model.cuh", "tma_common.cuh"],
     "uncertainty": ["voxel_kernels.cu"],
     "jtv": ["stencil_kernels.cu"],
     "pcg_init": ["stencil_kernels.cu", "pcg_step.cuh"],
-    "pcg_step": ["stencil_kernels.cu", "stencil_tma.cu", "pcg_step.cuh"],
+    "pcg_step": ["stencil_kernels.cu", "stencil_tma.cu", "pcg_step.cuh", "tma_common.cuh"],
     "pcg_final": ["stencil_kernels.cu", "pcg_step.cuh"],
     "grad_hess_proj": ["projection.cu", "voxel_model.cuh"],
     "reslice": ["projection.cu"],

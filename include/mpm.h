@@ -400,19 +400,21 @@ mpm_status mpm_server_destroy(mpm_server* server);
  * workspace recorded a failure since the workspace was last cleared (every
  * mpm_solve / mpm_fit clears it): a preconditioner block that is not positive
  * definite, a NaN in a reduction, or a bounded copy wait of the PCG iteration
- * that ran out (mpm_last_error() names which).  Otherwise MPM_OK. */
+ * or of the voxel pass that ran out (mpm_last_error() names which).  Every
+ * mpm_grad_hess call clears it too.  Otherwise MPM_OK. */
 mpm_status mpm_workspace_status(const void* ws, size_t ws_bytes, void* stream);
 
-/* Test hook for the bounded waits of the TMA-staged PCG iteration (the paper
- * has no counterpart; tests use it to drive the timeout path without a
- * fault).  withhold != 0: from the next launch on, the iteration's producer
- * issues no copies, so every copy wait of its compute warps runs out.
+/* Test hook for the bounded waits of the staged kernels, the TMA-staged PCG
+ * iteration and the staged voxel pass (the paper has no counterpart; tests
+ * use it to drive the timeout path without a fault).  withhold != 0: from the
+ * next launch on, their producers issue no copies, so every copy wait of
+ * their compute warps runs out.
  * wait_us > 0 sets the bound of every such wait (converted to clock cycles
  * at the current device's clock rate); 0 restores the default of about 2 s.
  * A launch whose wait ran out skips its work, drains its own copies, records
  * the failure in the workspace status (mpm_workspace_status reports
  * MPM_ERR_NUMERIC, "copy wait timed out") and returns; the solve then stops
- * without a step.  Process-wide.  Returns MPM_ERR_INVALID_ARG for
+ * without a step, and the voxel pass leaves g and h undefined.  Process-wide.  Returns MPM_ERR_INVALID_ARG for
  * wait_us < 0. */
 mpm_status mpm_test_copy_timeout(int withhold, double wait_us);
 

@@ -406,7 +406,7 @@ static cudaError_t launch_lik(const FitJob& j, int it, cudaStream_t st)
     const FitWs& L = j.L;
     if (j.proj) return launch_grad_hess_proj(j.P, j.pj, j.y, L.g, L.h, L.nll + it, L.red, st);
     return launch_grad_hess(j.P, j.problem->echo_dtype, j.x, j.y, j.b1p, j.b1m, L.g, L.h,
-                            L.nll + it, L.red, st);
+                            L.nll + it, L.red, &L.hdr->status, st);
 }
 
 static mpm_status fit_prepare(const mpm_problem* problem, const mpm_opts* opts, const void* x,
@@ -1087,7 +1087,8 @@ mpm_status mpm_grad_hess(const mpm_problem* problem, const void* x, const float*
     FitWs L;
     MPM_TRY(check_ws(P, MPM_CALL_GRAD_HESS, ws, ws_bytes, L));
     MPM_CUDA(cudaMemsetAsync(L.hdr, 0, sizeof(WsHeader), st));
-    MPM_CUDA(launch_grad_hess(P, problem->echo_dtype, x, y, b1p, b1m, g, h, nll, L.red, st));
+    MPM_CUDA(launch_grad_hess(P, problem->echo_dtype, x, y, b1p, b1m, g, h, nll, L.red,
+                              &L.hdr->status, st));
     return MPM_OK;
 }
 

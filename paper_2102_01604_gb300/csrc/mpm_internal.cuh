@@ -41,9 +41,16 @@ struct LaunchScope {
 
 cudaError_t launch_forward(const DevProblem& P, const float* y, const float* b1p,
                            const float* b1m, float* s, cudaStream_t st);
+// The voxel pass; `status` receives kStatusTimeout if a staged copy never
+// lands (voxel_tma.cu).
 cudaError_t launch_grad_hess(const DevProblem& P, int echo_dtype, const void* x,
                              const float* y, const float* b1p, const float* b1m, float* g,
-                             float* h, double* nll, Reduce red, cudaStream_t st);
+                             float* h, double* nll, Reduce red, unsigned* status, cudaStream_t st);
+bool grad_hess_tma_ok(const DevProblem& P, const void* x, const float* y, const float* b1p,
+                      const float* b1m, const float* g, const float* h);
+cudaError_t launch_grad_hess_tma(const DevProblem& P, int echo_dtype, const void* x, const float* y,
+                                 const float* b1p, const float* b1m, float* g, float* h, double* nll,
+                                 Reduce red, unsigned* status, cudaStream_t st);
 cudaError_t launch_uncertainty(const DevProblem& P, const float* h, const float* w,
                                const float* y, float* var, float* logdet, float* moments,
                                unsigned* status, cudaStream_t st);
@@ -127,6 +134,8 @@ int tma_wave_blocks(const DevProblem& P, int tile); // resident blocks of the TM
 // Test hook: with withhold set, the TMA iteration's producer issues no copies;
 // every bounded wait gives up after wait_cycles clock cycles (<= 0: default).
 void set_copy_test(int withhold, long long wait_cycles);
+int copy_withhold();
+long long copy_wait_cycles();
 
 // ------------------------------------------- host helpers of the entry points
 // (mpm_api.cu)

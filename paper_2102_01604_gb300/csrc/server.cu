@@ -98,7 +98,7 @@ static mpm_status srv_eval(mpm_server* s, Request& r)
     r.w_fresh = (r.it % r.opts.newton_per_irls == 0);
     SRV_CUDA(launch_jtv(r.P, r.y, r.w_fresh ? L.w : nullptr, L.jtv + r.it, L.red, st));
     SRV_CUDA(launch_grad_hess(r.P, r.problem.echo_dtype, r.x, r.y, r.b1p, r.b1m, L.g, L.h,
-                              L.nll + r.it, L.red, st));
+                              L.nll + r.it, L.red, &L.hdr->status, st));
     SlotHost& h = s->host[r.slot];
     SRV_CUDA(cudaMemcpyAsync(&h.f[0], L.nll + r.it, sizeof(double), cudaMemcpyDeviceToHost, st));
     SRV_CUDA(cudaMemcpyAsync(&h.f[1], L.jtv + r.it, sizeof(double), cudaMemcpyDeviceToHost, st));

@@ -47,13 +47,14 @@
 
 #include "mpm_internal.cuh"
 #include "pcg_step.cuh"
+#include "tma_common.cuh"
 
 namespace mpm {
 
 constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
 
-// Test hooks (mpm_test_copy_timeout): the producer issues no copies, and the
-// bound of every wait, in clock cycles.
+// Test hooks (mpm_test_copy_timeout): the producers of the staged kernels
+// issue no copies, and the bound of every wait, in clock cycles.
 static std::atomic<int> g_withhold{0};
 static std::atomic<long long> g_wait_cycles{kWaitCycles};
 
@@ -62,6 +63,9 @@ void set_copy_test(int withhold, long long wait_cycles)
     g_withhold.store(withhold ? 1 : 0);
     g_wait_cycles.store(wait_cycles > 0 ? wait_cycles : kWaitCycles);
 }
+
+int copy_withhold() { return g_withhold.load(std::memory_order_relaxed); }
+long long copy_wait_cycles() { return g_wait_cycles.load(std::memory_order_relaxed); }
 
 // Per tile shape: one compute thread per voxel plus a producer warp.  256-
 // voxel tiles run two blocks per SM with two raw stages; 512-voxel tiles one
@@ -98,72 +102,6 @@ struct StepLayout {
     static_assert(SMEM <= 227 * 1024, "shared memory of one block");
     static_assert(4 * BX <= 256 && 4 * TX <= 256, "TMA box rows of at most 256 elements");
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p)
-{
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-// One try: the thread may be suspended until the phase completes or about
-// 20 us pass (the suspend-time hint), so waiting warps do not spin on issue
-// slots the compute warps need.
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity), "r"(20000u)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait: false after about `cycles` clock cycles.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long cycles)
-{
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > cycles) return false;
-    return true;
-}
-
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
-                                            int c2, uint32_t bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-        "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
-                                            int c2, int c3, uint32_t bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-        "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
-        : "memory");
-}
 
 // Barrier 1 among the compute warps (the producer warp never joins it).
 template <int NTHREADS>

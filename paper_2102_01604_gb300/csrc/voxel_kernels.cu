@@ -6,8 +6,9 @@
 //                   float64, log-determinant, log-normal moments (Eqs. 44-47)
 //   k_image_means / k_means_final / k_fill_maps   constant initial maps
 //
-// One thread per voxel (grid-stride); images are read as planes [I][N], so
-// each warp loads 128 contiguous bytes per echo.
+// One thread per voxel (grid-stride), or two neighbouring voxels per thread in
+// the voxel pass; images are read as planes [I][N], so each warp loads 128
+// (256) contiguous bytes per echo.
 #include "mpm_internal.cuh"
 #include "voxel_model.cuh"
 
@@ -54,67 +55,128 @@ __device__ __forceinline__ void prefetch_voxel(const DevProblem& P, const XT* x,
 }
 
 // The fused voxel pass: per voxel, accumulate_contrast for every contrast.
-template <int K, int PRE, typename XT>
+// Each thread takes V neighbouring voxels per grid-stride step (V divides N,
+// every array aligned to V elements), reading each plane with one V-wide load;
+// every voxel's arithmetic is the same for V = 1 and V = 2.
+template <int K, int PRE, typename XT, int V>
 __device__ __forceinline__ void grad_hess_body(const DevProblem& P, const XT* __restrict__ x,
-                                               const float* __restrict__ y, const float* __restrict__ b1p,
+                                               const float* __restrict__ y,
+                                               const float* __restrict__ b1p,
                                                const float* __restrict__ b1m, float* __restrict__ g,
                                                float* __restrict__ h, double* nll, Reduce red,
                                                const VGrid& vg)
 {
     constexpr int T = K * (K + 1) / 2;
     const long long N = P.N;
+    const long long NV = N / V;
+    const long long step = (long long)vg.gx * blockDim.x;
     Acc nll_acc;
-    for (long long n = vg.bx * (long long)blockDim.x + threadIdx.x; n < N;
-         n += (long long)vg.gx * blockDim.x) {
-        const long long next = n + (long long)vg.gx * blockDim.x;
-        if (next < N) prefetch_voxel<XT>(P, x, y, b1p, b1m, next);
-        float a, r1, r2, dl, m;
-        map_params(y, N, n, K, a, r1, r2, dl, m);
-        const float bp = b1p ? __ldg(b1p + n) : 1.0f;
-        float G[K], H[T];
+    for (long long u = vg.bx * (long long)blockDim.x + threadIdx.x; u < NV; u += step) {
+        const long long n = u * V;
+        if (u + step < NV) prefetch_voxel<XT>(P, x, y, b1p, b1m, (u + step) * V);
+        float a[V], r1[V], r2[V], dl[V], m[V], bp[V];
+        {
+            float yv[K][V];
 #pragma unroll
-        for (int k = 0; k < K; ++k) G[k] = 0.0f;
+            for (int k = 0; k < K; ++k) load_vec<V, float>(y + k * N + n, yv[k]);
 #pragma unroll
-        for (int k = 0; k < T; ++k) H[k] = 0.0f;
-        float nll_v = 0.0f;
-        Relax R{0.f, 0.f, 0.f};
+            for (int v = 0; v < V; ++v) {
+                float yk[4];
+#pragma unroll
+                for (int k = 0; k < K; ++k) yk[k] = yv[k][v];
+                map_params_v(yk, K, a[v], r1[v], r2[v], dl[v], m[v]);
+            }
+        }
+        if (b1p) {
+            load_vec<V, float>(b1p + n, bp);
+        } else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) bp[v] = 1.0f;
+        }
+        float G[V][K], H[V][T], nll_v[V];
+        Relax R[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) G[v][k] = 0.0f;
+#pragma unroll
+            for (int k = 0; k < T; ++k) H[v][k] = 0.0f;
+            nll_v[v] = 0.0f;
+            R[v] = Relax{0.f, 0.f, 0.f};
+        }
         for (int c = 0; c < P.C; ++c) {
-            const float bm = b1m ? __ldg(b1m + c * N + n) : 1.0f;
-            if (!P.same_tr[c]) R = relax(P.tr[c], r1);
-            const ContrastTerms t = contrast_terms(P, c, a, R, dl, m, bp, bm);
-            const XT* xp = x + (long long)P.echo0[c] * N + n;
-            accumulate_contrast<K, PRE, XT>(P, c, t, r2, xp, N, G, H, nll_v);
+            float bm[V];
+            if (b1m) {
+                load_vec<V, float>(b1m + c * N + n, bm);
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v) bm[v] = 1.0f;
+            }
+            ContrastTerms t[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                if (!P.same_tr[c]) R[v] = relax(P.tr[c], r1[v]);
+                t[v] = contrast_terms(P, c, a[v], R[v], dl[v], m[v], bp[v], bm[v]);
+            }
+            accumulate_contrast_v<K, PRE, XT, V>(P, c, t, r2, x + (long long)P.echo0[c] * N + n, N,
+                                                 G, H, nll_v);
         }
 #pragma unroll
-        for (int k = 0; k < K; ++k) g[k * N + n] = G[k];
+        for (int k = 0; k < K; ++k) {
+            float o[V];
 #pragma unroll
-        for (int k = 0; k < T; ++k) h[k * N + n] = H[k];
-        nll_acc.add(nll_v);
+            for (int v = 0; v < V; ++v) o[v] = G[v][k];
+            store_vec<V>(g + k * N + n, o);
+        }
+#pragma unroll
+        for (int k = 0; k < T; ++k) {
+            float o[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) o[v] = H[v][k];
+            store_vec<V>(h + k * N + n, o);
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) nll_acc.add(nll_v[v]);
     }
     Acc v[1] = {nll_acc};
     double out[1];
     if (grid_reduce<1>(v, red, out, vg) && threadIdx.x == 0) *nll = out[0];
 }
 
-template <int K, int PRE, typename XT>
-__global__ void __launch_bounds__(kBlock, 4) k_grad_hess(DevProblem P, const XT* __restrict__ x,
-                                                      const float* __restrict__ y,
-                                                      const float* __restrict__ b1p,
-                                                      const float* __restrict__ b1m,
-                                                      float* __restrict__ g,
-                                                      float* __restrict__ h, double* nll,
-                                                      Reduce red)
+// Two voxels per thread hold twice the state: half the resident blocks.
+template <int V>
+struct GradOcc {
+    static constexpr int kMinBlocks = V == 1 ? 4 : 2;
+};
+
+template <int K, int PRE, typename XT, int V>
+__global__ void __launch_bounds__(kBlock, GradOcc<V>::kMinBlocks)
+    k_grad_hess(DevProblem P, const XT* __restrict__ x, const float* __restrict__ y,
+                const float* __restrict__ b1p, const float* __restrict__ b1m, float* __restrict__ g,
+                float* __restrict__ h, double* nll, Reduce red)
 {
-    grad_hess_body<K, PRE, XT>(P, x, y, b1p, b1m, g, h, nll, red, hw_grid());
+    grad_hess_body<K, PRE, XT, V>(P, x, y, b1p, b1m, g, h, nll, red, hw_grid());
 }
 
-template <int K, int PRE, typename XT>
-__global__ void __launch_bounds__(kBlock, 4) k_grad_hess_batch(const __grid_constant__ Batch<GradArgs> b)
+template <int K, int PRE, typename XT, int V>
+__global__ void __launch_bounds__(kBlock, GradOcc<V>::kMinBlocks)
+    k_grad_hess_batch(const __grid_constant__ Batch<GradArgs> b)
 {
     const int s = batch_subject(b.start, b.n);
     const GradArgs& a = b.a[s];
-    grad_hess_body<K, PRE, XT>(a.P, static_cast<const XT*>(a.x), a.y, a.b1p, a.b1m, a.g, a.h, a.nll,
-                               a.red, batch_grid(b.start[s], b.start[s + 1] - b.start[s], 1, 1));
+    grad_hess_body<K, PRE, XT, V>(a.P, static_cast<const XT*>(a.x), a.y, a.b1p, a.b1m, a.g, a.h,
+                                  a.nll, a.red,
+                                  batch_grid(b.start[s], b.start[s + 1] - b.start[s], 1, 1));
+}
+
+// Whether the voxel pass may take two voxels per thread: N even and every
+// array aligned to two elements (each plane then starts aligned too).
+static bool pairs_ok(long long N, int echo_dtype, const void* x, const float* y, const float* b1p,
+                     const float* b1m, const float* g, const float* h)
+{
+    auto al = [](const void* p, uintptr_t a) { return reinterpret_cast<uintptr_t>(p) % a == 0; };
+    return N % 2 == 0 && al(x, echo_dtype == 1 ? 4 : 8) && al(y, 8) && al(b1p, 8) && al(b1m, 8) &&
+           al(g, 8) && al(h, 8);
 }
 
 // --------------------------------------------------------- uncertainty
@@ -282,18 +344,29 @@ cudaError_t launch_forward(const DevProblem& P, const float* y, const float* b1p
     return cudaGetLastError();
 }
 
+template <int K, int PRE, int V>
+static void grad_hess_v(const DevProblem& P, int echo_dtype, const void* x, const float* y,
+                        const float* b1p, const float* b1m, float* g, float* h, double* nll,
+                        Reduce red, cudaStream_t st)
+{
+    const int grid = voxel_grid(P.N / V);
+    if (echo_dtype == 1)
+        k_grad_hess<K, PRE, __nv_bfloat16, V><<<grid, kBlock, 0, st>>>(
+            P, static_cast<const __nv_bfloat16*>(x), y, b1p, b1m, g, h, nll, red);
+    else
+        k_grad_hess<K, PRE, float, V><<<grid, kBlock, 0, st>>>(
+            P, static_cast<const float*>(x), y, b1p, b1m, g, h, nll, red);
+}
+
 template <int K, int PRE>
 static void grad_hess_dtype(const DevProblem& P, int echo_dtype, const void* x,
                             const float* y, const float* b1p, const float* b1m, float* g,
                             float* h, double* nll, Reduce red, cudaStream_t st)
 {
-    const int grid = voxel_grid(P.N);
-    if (echo_dtype == 1)
-        k_grad_hess<K, PRE, __nv_bfloat16><<<grid, kBlock, 0, st>>>(
-            P, static_cast<const __nv_bfloat16*>(x), y, b1p, b1m, g, h, nll, red);
+    if (pairs_ok(P.N, echo_dtype, x, y, b1p, b1m, g, h))
+        grad_hess_v<K, PRE, 2>(P, echo_dtype, x, y, b1p, b1m, g, h, nll, red, st);
     else
-        k_grad_hess<K, PRE, float><<<grid, kBlock, 0, st>>>(
-            P, static_cast<const float*>(x), y, b1p, b1m, g, h, nll, red);
+        grad_hess_v<K, PRE, 1>(P, echo_dtype, x, y, b1p, b1m, g, h, nll, red, st);
 }
 
 template <int K>
@@ -310,9 +383,11 @@ static void grad_hess_pre(const DevProblem& P, int echo_dtype, const void* x, co
 
 cudaError_t launch_grad_hess(const DevProblem& P, int echo_dtype, const void* x,
                              const float* y, const float* b1p, const float* b1m, float* g,
-                             float* h, double* nll, Reduce red, cudaStream_t st)
+                             float* h, double* nll, Reduce red, unsigned* status, cudaStream_t st)
 {
     LaunchScope ls(MPM_KERNEL_GRAD_HESS, st);
+    if (grad_hess_tma_ok(P, x, y, b1p, b1m, g, h))
+        return launch_grad_hess_tma(P, echo_dtype, x, y, b1p, b1m, g, h, nll, red, status, st);
     if (P.K == 4)
         grad_hess_pre<4>(P, echo_dtype, x, y, b1p, b1m, g, h, nll, red, st);
     else
@@ -334,14 +409,28 @@ cudaError_t launch_uncertainty(const DevProblem& P, const float* h, const float*
     return cudaGetLastError();
 }
 
-template <int K, int PRE>
-static void grad_hess_batch_dtype(int echo_dtype, const Batch<GradArgs>& b, cudaStream_t st)
+template <int K, int PRE, int V>
+static void grad_hess_batch_v(int echo_dtype, const Batch<GradArgs>& b, cudaStream_t st)
 {
     const unsigned grid = b.start[b.n];
     if (echo_dtype == 1)
-        k_grad_hess_batch<K, PRE, __nv_bfloat16><<<grid, kBlock, 0, st>>>(b);
+        k_grad_hess_batch<K, PRE, __nv_bfloat16, V><<<grid, kBlock, 0, st>>>(b);
     else
-        k_grad_hess_batch<K, PRE, float><<<grid, kBlock, 0, st>>>(b);
+        k_grad_hess_batch<K, PRE, float, V><<<grid, kBlock, 0, st>>>(b);
+}
+
+template <int K, int PRE>
+static void grad_hess_batch_dtype(int echo_dtype, const Batch<GradArgs>& b, cudaStream_t st)
+{
+    bool pairs = true;
+    for (int i = 0; i < b.n; ++i) {
+        const GradArgs& a = b.a[i];
+        pairs = pairs && pairs_ok(a.P.N, echo_dtype, a.x, a.y, a.b1p, a.b1m, a.g, a.h);
+    }
+    if (pairs)
+        grad_hess_batch_v<K, PRE, 2>(echo_dtype, b, st);
+    else
+        grad_hess_batch_v<K, PRE, 1>(echo_dtype, b, st);
 }
 
 template <int K>
@@ -357,6 +446,8 @@ static void grad_hess_batch_pre(int precond, int echo_dtype, const Batch<GradArg
 cudaError_t launch_grad_hess_batch(int K, int precond, int echo_dtype, const GradArgs* a,
                                    const unsigned* blocks, int n, cudaStream_t st)
 {
+    // blocks[s] is sized for one voxel per thread; with two the blocks'
+    // grid-stride loops take half the steps
     Batch<GradArgs> b;
     fill_batch(b, a, blocks, n);
     LaunchScope ls(MPM_KERNEL_GRAD_HESS, st);

@@ -120,57 +120,74 @@ template <int PRE>
 struct EchoSums {
     float S0 = 0.f, S1 = 0.f, S2 = 0.f, R0 = 0.f, R1 = 0.f, N2 = 0.f;
     float A0 = 0.f, A2 = 0.f, B1 = 0.f;
-    // one echo: signal s, q2 = -TE r2, measured value xv
+    // One echo: signal s, q2 = -TE r2, measured value xv.  Every rounding is
+    // spelled out (no contraction left to the compiler), so EchoSums2 below
+    // gives each of its two voxels exactly these sums.  (1 + q2) q2 is taken
+    // as fma(q2, q2, q2).
     __device__ __forceinline__ void add(float s, float q2, float xv)
     {
-        const float r = s - xv;
-        const float ss = s * s;
-        S0 += ss;
-        S1 += ss * q2;
-        S2 += ss * q2 * q2;
-        const float rs = r * s;
-        R0 += rs;
-        R1 += rs * q2;
-        N2 += r * r;
+        const float r = __fadd_rn(s, -xv);
+        const float rs = __fmul_rn(r, s);
+        R0 = __fmaf_rn(r, s, R0);
+        R1 = __fmaf_rn(rs, q2, R1);
+        N2 = __fmaf_rn(r, r, N2);
+        const float ss = __fmul_rn(s, s);
+        S0 = __fmaf_rn(s, s, S0);
+        S1 = __fmaf_rn(ss, q2, S1);
+        S2 = __fmaf_rn(__fmul_rn(ss, q2), q2, S2);
         if (PRE != 2) {
             const float ars = fabsf(rs);
-            A0 += ars;
-            A2 += ars * fabsf((1.0f + q2) * q2);
-            if (PRE == 1) B1 += ars * fabsf(q2);
+            A0 = __fadd_rn(A0, ars);
+            A2 = __fmaf_rn(ars, fabsf(__fmaf_rn(q2, q2, q2)), A2);
+            if (PRE == 1) B1 = __fmaf_rn(ars, fabsf(q2), B1);
         }
     }
 };
 
-template <int K, int PRE, typename XT>
-__device__ __forceinline__ void accumulate_contrast(const DevProblem& P, int c,
-                                                    const ContrastTerms& t, float r2,
-                                                    const XT* xp, long long stride,
-                                                    float (&G)[K], float (&H)[K * (K + 1) / 2],
-                                                    float& nll_v)
-{
-    EchoSums<PRE> es;
-    const int i0 = P.echo0[c];
-    const int ne = P.n_echoes[c];
-    float q2 = -P.te[i0] * r2;
-    float s = t.s0 * expf(q2);
-    if (P.te_uniform[c] != 0) {
-        // equally spaced echoes: s_e = s_0 exp(-TE_0 r2) rho^e, rho = exp(-dTE r2)
-        const float dq = -P.dte[c] * r2;
-        const float rho = expf(dq);
-#pragma unroll 4
-        for (int e = 0; e < ne; ++e) {
-            es.add(s, q2, load_echo<XT>(xp, e * stride));
-            q2 += dq;
-            s *= rho;
-        }
-    } else {
-        es.add(s, q2, load_echo<XT>(xp, 0));
-#pragma unroll 4
-        for (int e = 1; e < ne; ++e) {
-            q2 = -P.te[i0 + e] * r2;
-            es.add(t.s0 * expf(q2), q2, load_echo<XT>(xp, e * stride));
+__device__ __forceinline__ float2 abs2(float2 v) { return make_float2(fabsf(v.x), fabsf(v.y)); }
+__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
+
+// EchoSums of two voxels at once, in paired float32 instructions (each lane
+// rounds as its scalar counterpart in EchoSums::add).
+template <int PRE>
+struct EchoSums2 {
+    float2 S0 = {0.f, 0.f}, S1 = {0.f, 0.f}, S2 = {0.f, 0.f}, R0 = {0.f, 0.f}, R1 = {0.f, 0.f};
+    float2 N2 = {0.f, 0.f}, A0 = {0.f, 0.f}, A2 = {0.f, 0.f}, B1 = {0.f, 0.f};
+    __device__ __forceinline__ void add(float2 s, float2 q2, float2 xv)
+    {
+        const float2 r = __fadd2_rn(s, neg2(xv));
+        const float2 rs = __fmul2_rn(r, s);
+        R0 = __ffma2_rn(r, s, R0);
+        R1 = __ffma2_rn(rs, q2, R1);
+        N2 = __ffma2_rn(r, r, N2);
+        const float2 ss = __fmul2_rn(s, s);
+        S0 = __ffma2_rn(s, s, S0);
+        S1 = __ffma2_rn(ss, q2, S1);
+        S2 = __ffma2_rn(__fmul2_rn(ss, q2), q2, S2);
+        if (PRE != 2) {
+            const float2 ars = abs2(rs);
+            A0 = __fadd2_rn(A0, ars);
+            A2 = __ffma2_rn(ars, abs2(__ffma2_rn(q2, q2, q2)), A2);
+            if (PRE == 1) B1 = __ffma2_rn(ars, abs2(q2), B1);
         }
     }
+    // the sums of voxel v (0: x lanes, 1: y lanes)
+    __device__ __forceinline__ EchoSums<PRE> lane(int v) const
+    {
+        EchoSums<PRE> e;
+        auto pick = [v](float2 a) { return v == 0 ? a.x : a.y; };
+        e.S0 = pick(S0), e.S1 = pick(S1), e.S2 = pick(S2), e.R0 = pick(R0), e.R1 = pick(R1);
+        e.N2 = pick(N2), e.A0 = pick(A0), e.A2 = pick(A2), e.B1 = pick(B1);
+        return e;
+    }
+};
+
+// Eq. 24 of contrast c from its echo sums: gradient, Hessian and NLL terms.
+template <int K, int PRE>
+__device__ __forceinline__ void finish_contrast(const DevProblem& P, int c, const ContrastTerms& t,
+                                                const EchoSums<PRE>& es, float (&G)[K],
+                                                float (&H)[K * (K + 1) / 2], float& nll_v)
+{
     const float S0 = es.S0, S1 = es.S1, S2 = es.S2, R0 = es.R0, R1 = es.R1, N2 = es.N2;
     const float A0 = es.A0, A2 = es.A2, B1 = es.B1;
     const float is2 = P.isig2[c];
@@ -207,6 +224,135 @@ __device__ __forceinline__ void accumulate_contrast(const DevProblem& P, int c,
                 is2 * (A0 * (fabsf(t.hd * qd) + aqd + c13) + aqd * B1);
     }
     nll_v += 0.5f * is2 * N2;
+}
+
+template <int K, int PRE, typename XT>
+__device__ __forceinline__ void accumulate_contrast(const DevProblem& P, int c,
+                                                    const ContrastTerms& t, float r2,
+                                                    const XT* xp, long long stride,
+                                                    float (&G)[K], float (&H)[K * (K + 1) / 2],
+                                                    float& nll_v)
+{
+    EchoSums<PRE> es;
+    const int i0 = P.echo0[c];
+    const int ne = P.n_echoes[c];
+    float q2 = -P.te[i0] * r2;
+    float s = t.s0 * expf(q2);
+    if (P.te_uniform[c] != 0) {
+        // equally spaced echoes: s_e = s_0 exp(-TE_0 r2) rho^e, rho = exp(-dTE r2)
+        const float dq = -P.dte[c] * r2;
+        const float rho = expf(dq);
+#pragma unroll 4
+        for (int e = 0; e < ne; ++e) {
+            es.add(s, q2, load_echo<XT>(xp, e * stride));
+            q2 = __fadd_rn(q2, dq);
+            s = __fmul_rn(s, rho);
+        }
+    } else {
+        es.add(s, q2, load_echo<XT>(xp, 0));
+#pragma unroll 4
+        for (int e = 1; e < ne; ++e) {
+            q2 = -P.te[i0 + e] * r2;
+            es.add(t.s0 * expf(q2), q2, load_echo<XT>(xp, e * stride));
+        }
+    }
+    finish_contrast<K, PRE>(P, c, t, es, G, H, nll_v);
+}
+
+// V consecutive values from p (p aligned to V elements), as floats.
+template <int V, typename T>
+__device__ __forceinline__ void load_vec(const T* __restrict__ p, float (&o)[V]);
+
+template <>
+__device__ __forceinline__ void load_vec<1, float>(const float* __restrict__ p, float (&o)[1])
+{
+    o[0] = __ldg(p);
+}
+
+template <>
+__device__ __forceinline__ void load_vec<2, float>(const float* __restrict__ p, float (&o)[2])
+{
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    o[0] = v.x;
+    o[1] = v.y;
+}
+
+template <>
+__device__ __forceinline__ void load_vec<1, __nv_bfloat16>(const __nv_bfloat16* __restrict__ p,
+                                                           float (&o)[1])
+{
+    o[0] = __bfloat162float(p[0]);
+}
+
+template <>
+__device__ __forceinline__ void load_vec<2, __nv_bfloat16>(const __nv_bfloat16* __restrict__ p,
+                                                           float (&o)[2])
+{
+    const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(p);
+    o[0] = __low2float(v);
+    o[1] = __high2float(v);
+}
+
+// V consecutive floats to p (p aligned to V elements).
+template <int V>
+__device__ __forceinline__ void store_vec(float* p, const float (&v)[V])
+{
+    if (V == 2)
+        *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+    else
+        p[0] = v[0];
+}
+
+// accumulate_contrast for V neighbouring voxels at once: one vector load per
+// echo serves all V, and their echo recurrences run side by side.  Each
+// voxel's arithmetic is that of accumulate_contrast, in the same order.
+template <int K, int PRE, typename XT, int V>
+__device__ __forceinline__ void accumulate_contrast_v(const DevProblem& P, int c,
+                                                      const ContrastTerms (&t)[V],
+                                                      const float (&r2)[V], const XT* xp,
+                                                      long long stride, float (&G)[V][K],
+                                                      float (&H)[V][K * (K + 1) / 2],
+                                                      float (&nll_v)[V])
+{
+    static_assert(V == 1 || V == 2, "one or two voxels per thread");
+    if (V == 1) {
+        accumulate_contrast<K, PRE, XT>(P, c, t[0], r2[0], xp, stride, G[0], H[0], nll_v[0]);
+        return;
+    }
+    EchoSums2<PRE> es;
+    const int i0 = P.echo0[c];
+    const int ne = P.n_echoes[c];
+    const float2 r22 = make_float2(r2[0], r2[V - 1]);
+    const float te0 = -P.te[i0];
+    float2 q2 = make_float2(te0 * r22.x, te0 * r22.y);
+    float2 s = make_float2(t[0].s0 * expf(q2.x), t[V - 1].s0 * expf(q2.y));
+    if (P.te_uniform[c] != 0) {
+        const float dte = -P.dte[c];
+        const float2 dq = make_float2(dte * r22.x, dte * r22.y);
+        const float2 rho = make_float2(expf(dq.x), expf(dq.y));
+#pragma unroll 4
+        for (int e = 0; e < ne; ++e) {
+            float xv[2];
+            load_vec<2, XT>(xp + e * stride, xv);
+            es.add(s, q2, make_float2(xv[0], xv[1]));
+            q2 = __fadd2_rn(q2, dq);
+            s = __fmul2_rn(s, rho);
+        }
+    } else {
+        float xv[2];
+        load_vec<2, XT>(xp, xv);
+        es.add(s, q2, make_float2(xv[0], xv[1]));
+#pragma unroll 4
+        for (int e = 1; e < ne; ++e) {
+            load_vec<2, XT>(xp + e * stride, xv);
+            const float te = -P.te[i0 + e];
+            q2 = make_float2(te * r22.x, te * r22.y);
+            s = make_float2(t[0].s0 * expf(q2.x), t[V - 1].s0 * expf(q2.y));
+            es.add(s, q2, make_float2(xv[0], xv[1]));
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) finish_contrast<K, PRE>(P, c, t[v], es.lane(v), G[v], H[v], nll_v[v]);
 }
 
 }  // namespace mpm

@@ -1,5 +1,5 @@
-"""The bounded copy waits of the TMA-staged PCG iteration, driven to their
-timeout on the GPU without any fault.
+"""The bounded copy waits of the TMA-staged PCG iteration and of the staged
+voxel pass, driven to their timeout on the GPU without any fault.
 
 The test hook mpm_test_copy_timeout makes the iteration's producer warp issue
 no copies and bounds every wait at 1 ms, so each compute warp's first wait
@@ -72,3 +72,45 @@ def test_copy_wait_timeout_is_reported_and_the_context_survives(mpm):
     delta2, resid2 = mpm.mpm_solve(pg, opts, *args, ws=ws)
     assert mpm.mpm_workspace_status(ws) == _lib.OK
     assert_close_scaled(to_np(delta2), d_o, 2e-4, "delta after")
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+def test_voxel_pass_copy_timeout(mpm, bf16):
+    """The staged voxel pass (N a multiple of 8, aligned arrays) under the
+    same hook: its producer issues no row copies, every compute warp's first
+    wait runs out, the timeout is recorded, and afterwards the same context
+    computes g, h and the NLL of the oracle."""
+    import torch
+    from paper_2102_01604_gb300 import _lib
+    shape = (40, 24, 12)
+    d = dataset(shape, seed=93)
+    pg = mpm.make_problem(d["prot"], shape, echo_dtype=1 if bf16 else 0)
+    po = orc.make_problem(d["prot"], shape)
+    x = to_dev(d["x"])
+    if bf16:
+        x = x.to(torch.bfloat16)
+        d["x"] = x.float().cpu().numpy()
+    y = d["y_true"].astype(np.float32)
+    ws = mpm.workspace(pg, None, _lib.CALL_GRAD_HESS)
+    args = (x, to_dev(y), to_dev(d["b1p"]), to_dev(d["b1m"]))
+    mpm.mpm_test_copy_timeout(True, 1000.0)
+    try:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mpm.mpm_grad_hess(pg, *args, ws=ws)
+        torch.cuda.synchronize()
+        elapsed = time.perf_counter() - t0
+        st = mpm.mpm_workspace_status(ws)
+        msg = _lib.load().mpm_last_error().decode()
+    finally:
+        mpm.mpm_test_copy_timeout(False, 0.0)
+    assert st == _lib.ERR_NUMERIC, st
+    assert "copy wait timed out" in msg, msg
+    assert elapsed < 1.0, elapsed
+
+    g, h, nll = mpm.mpm_grad_hess(pg, *args, ws=ws)
+    assert mpm.mpm_workspace_status(ws) == _lib.OK
+    nll_o, g_o, h_o = orc.grad_hess(po, d["x"], y, d["b1p"], d["b1m"])
+    assert_close_scaled(to_np(g), g_o, 1e-4, "g")
+    assert_close_scaled(to_np(h), h_o, 1e-4, "h")
+    assert abs(nll.item() - nll_o) <= 2e-6 * abs(nll_o)
