@@ -236,6 +236,13 @@ __device__ __forceinline__ bool grid_reduce(const Acc (&v)[NV], Reduce red, doub
     return grid_reduce<NV>(v, red, out, hw_grid());
 }
 
+// Hint the line holding p into L2 (kernels fetch the operands of a later
+// voxel or plane this way while they compute the current one).
+__device__ __forceinline__ void prefetch_l2(const void* p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 template <typename T>
 __device__ __forceinline__ float load_echo(const T* p, long long i);
 

@@ -45,6 +45,8 @@ __device__ __forceinline__ void make_edges(const DevProblem& P, int x, int y, in
 
 // ------------------------------------------------------------- JTV weights
 
+constexpr int kInitAhead = 2;     // planes between the PCG start's L2 hint and the use
+
 // Each thread marches up its z range with the centre values of planes z - 1,
 // z and z + 1 in registers; the centre of plane z + 2 is loaded one plane
 // ahead, so the only far (next-plane) load is in flight while plane z is
@@ -184,6 +186,18 @@ __device__ __forceinline__ void pcg_init_body(const DevProblem& P, int zc, const
     if (x < P.nx && yy < P.ny) {
         for (int z = z0p; z < z1p; ++z) {
             const long long n = x + (long long)P.nx * yy + sxy * z;
+            // the operands of plane z + kInitAhead into L2 while plane z is computed
+            if (z + kInitAhead < z1p) {
+                const long long na = n + kInitAhead * sxy;
+                prefetch_l2(w + na);
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    prefetch_l2(y + k * N + na);
+                    prefetch_l2(g + k * N + na);
+                }
+#pragma unroll
+                for (int t = 0; t < T; ++t) prefetch_l2(h + t * N + na);
+            }
             const float wn = __ldg(w + n);
             Edges e;
             make_edges(P, x, yy, z, n, w, wn, e);
@@ -357,8 +371,19 @@ __device__ __forceinline__ void pcg_final_body(long long N, const SolveBufs& B, 
     const float alpha = (float)sc.alpha, alpha_prev = (float)sc.alpha_prev;
     const float4* __restrict__ pp = B.p[(sc.it + 2) % 3];    // p_{it-1}
     const float4* __restrict__ pp2 = B.p[(sc.it + 1) % 3];   // p_{it-2} when pend == 2
-    for (long long n = vg.bx * (long long)blockDim.x + threadIdx.x; n < N;
-         n += (long long)vg.gx * blockDim.x) {
+    const long long stride = (long long)vg.gx * blockDim.x;
+    for (long long n = vg.bx * (long long)blockDim.x + threadIdx.x; n < N; n += stride) {
+        // the next voxel's operands into L2 while this one is done
+        const long long na = n + stride;
+        if (na < N) {
+            if (have_x) prefetch_l2(B.x + na);
+            if (pend == 2) prefetch_l2(pp2 + na);
+            if (pend >= 1) prefetch_l2(pp + na);
+            if (y_update) {
+#pragma unroll
+                for (int a = 0; a < K; ++a) prefetch_l2(y_update + a * N + na);
+            }
+        }
         float v[K], t[K];
         if (have_x) {
             unpack4<K>(B.x[n], v);

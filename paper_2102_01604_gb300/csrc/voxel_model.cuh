@@ -8,13 +8,6 @@
 
 namespace mpm {
 
-// Hint the line holding p into L2 (the voxel passes fetch their next voxel's
-// operands this way while they compute the current one).
-__device__ __forceinline__ void prefetch_l2(const void* p)
-{
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
 // Per-contrast factors shared by every echo of contrast c in one voxel.  With
 // q_k = (ds/dy_k) / s  (Eqs. 27-30):
 //   q_A = 1, q_R1 = q1, q_R2* = -TE r2 (echo dependent), q_delta = qd,
