@@ -110,7 +110,11 @@ def test_grad_hess_without_b1_and_mt(mpm):
     assert abs(nll.item() - nll_o) <= 2e-6 * abs(nll_o)
 
 
-@pytest.mark.parametrize("shape", SHAPES)
+# plus volumes with several z ranges per tile column and a 3-plane one
+JTV_SHAPES = SHAPES + [(48, 20, 9), (44, 10, 3), (64, 24, 40)]
+
+
+@pytest.mark.parametrize("shape", JTV_SHAPES)
 @pytest.mark.parametrize("vx", [(1.0, 1.0, 1.0), (0.8, 1.1, 1.7)])
 def test_jtv_weights(mpm, shape, vx):
     d = dataset(shape, seed=5)
@@ -207,7 +211,11 @@ def test_fit_plain_32x32x16(mpm):
     st, rep, y, var, ref, po = _fit_both(mpm, d)
     err = _check_fit(rep, y, ref)
     print(f"fit 32x32x16: max map error {err.max():.2e}, F {rep.F[rep.iters]:.6e}")
-    # uncertainty at the final maps
+    # Uncertainty at the final maps.  The GPU's variance is Eq. 43 at its own
+    # final maps, which sit within the 1e-3 map bound of the oracle's; H and w
+    # move with the maps (the echo signal is exponential in log R2*, so H's
+    # terms move by a few times the map error), hence 5e-3 relative, not the
+    # 1e-5 of the per-call test, which feeds both sides the same H and w.
     _, w_o = orc.jtv(po, ref["y"])
     _, _, h_o = orc.grad_hess(po, d["x"], ref["y"], d["b1p"], d["b1m"])
     v_o, _, _, _ = orc.uncertainty(po, h_o, w_o)
