@@ -38,6 +38,7 @@ struct GradArgs {
     float *g, *h;
     double* nll;
     Reduce red;
+    unsigned* status;     // kStatusTimeout of the staged pass
 };
 
 struct InitArgs {

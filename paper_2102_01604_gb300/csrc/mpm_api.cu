@@ -696,7 +696,8 @@ static cudaError_t enqueue_phased(std::vector<PhasedSubject>& subj, int tile, cu
         if ((e = jtv(w_fresh, it))) return e;
         for (int s = 0; s < n; ++s) {
             const FitJob& j = *subj[s].j;
-            ga[s] = GradArgs{j.P, j.x, j.y, j.b1p, j.b1m, j.L.g, j.L.h, j.L.nll + it, j.L.red};
+            ga[s] = GradArgs{j.P, j.x, j.y, j.b1p, j.b1m, j.L.g, j.L.h, j.L.nll + it, j.L.red,
+                             &j.L.hdr->status};
         }
         if ((e = launch_grad_hess_batch(K, pre, dtype, ga.data(), bvox.data(), n, st))) return e;
         if (it >= o.gn_iters) break;

@@ -48,6 +48,10 @@ cudaError_t launch_grad_hess(const DevProblem& P, int echo_dtype, const void* x,
                              float* h, double* nll, Reduce red, unsigned* status, cudaStream_t st);
 bool grad_hess_tma_ok(const DevProblem& P, const void* x, const float* y, const float* b1p,
                       const float* b1m, const float* g, const float* h);
+// The staged pass over several subjects (one wave shared by their chunks);
+// false, with nothing launched, when some subject cannot take it.
+bool launch_grad_hess_tma_batch(int K, int precond, int echo_dtype, const GradArgs* a, int n,
+                                cudaStream_t st, cudaError_t* err);
 cudaError_t launch_grad_hess_tma(const DevProblem& P, int echo_dtype, const void* x, const float* y,
                                  const float* b1p, const float* b1m, float* g, float* h, double* nll,
                                  Reduce red, unsigned* status, cudaStream_t st);
@@ -99,6 +103,7 @@ bool make_step_maps(const DevProblem& P, const float* h, const float* w, const S
                     int tile, StepMaps* out);
 StencilGrid tma_grid(const DevProblem& P, int tile);
 cudaError_t prime_tma_kernels();   // shared-memory opt-ins, done before any graph capture
+cudaError_t prime_voxel_kernels(); // those of the staged voxel pass (voxel_tma.cu)
 int tma_tile_choice(const DevProblem& P);   // tile shape for this volume (tuned or default)
 void tma_tile_set(const DevProblem& P, int tile);
 // Times every applicable tile shape of the TMA iteration on this volume

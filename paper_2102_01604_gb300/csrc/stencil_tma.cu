@@ -700,7 +700,8 @@ cudaError_t prime_tma_kernels()
 {
     static bool done = false;
     if (done) return cudaSuccess;
-    cudaError_t e = prime_one<4, 16, 16>();
+    cudaError_t e = prime_voxel_kernels();
+    if (!e) e = prime_one<4, 16, 16>();
     if (!e) e = prime_one<4, 32, 8>();
     if (!e) e = prime_one<4, 32, 16>();
     if (!e) e = prime_one<3, 16, 16>();

@@ -446,11 +446,14 @@ static void grad_hess_batch_pre(int precond, int echo_dtype, const Batch<GradArg
 cudaError_t launch_grad_hess_batch(int K, int precond, int echo_dtype, const GradArgs* a,
                                    const unsigned* blocks, int n, cudaStream_t st)
 {
-    // blocks[s] is sized for one voxel per thread; with two the blocks'
-    // grid-stride loops take half the steps
+    // The staged pass splits its own wave between the subjects; otherwise
+    // blocks[s] is sized for one voxel per thread, and with two the blocks'
+    // grid-stride loops take half the steps.
+    LaunchScope ls(MPM_KERNEL_GRAD_HESS, st);
+    cudaError_t e;
+    if (launch_grad_hess_tma_batch(K, precond, echo_dtype, a, n, st, &e)) return e;
     Batch<GradArgs> b;
     fill_batch(b, a, blocks, n);
-    LaunchScope ls(MPM_KERNEL_GRAD_HESS, st);
     if (K == 4)
         grad_hess_batch_pre<4>(precond, echo_dtype, b, st);
     else

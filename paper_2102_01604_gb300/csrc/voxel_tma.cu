@@ -58,11 +58,13 @@ __device__ __forceinline__ void slot_pair(const __nv_bfloat16* p, float (&o)[2])
 }
 
 template <int K, int PRE, typename XT>
-__global__ void __launch_bounds__(kGhThreads, 2)
-    k_grad_hess_tma(DevProblem P, const XT* __restrict__ x, const float* __restrict__ y,
-                    const float* __restrict__ b1p, const float* __restrict__ b1m,
-                    float* __restrict__ g, float* __restrict__ h, double* nll, Reduce red,
-                    unsigned* status, long long wait_cycles, int withhold)
+__device__ __forceinline__ void grad_hess_tma_body(const DevProblem& P, const XT* __restrict__ x,
+                                                   const float* __restrict__ y,
+                                                   const float* __restrict__ b1p,
+                                                   const float* __restrict__ b1m, float* __restrict__ g,
+                                                   float* __restrict__ h, double* nll, Reduce red,
+                                                   unsigned* status, long long wait_cycles, int withhold,
+                                                   const VGrid& vg)
 {
     constexpr int T = K * (K + 1) / 2;
     extern __shared__ unsigned char smem_raw[];
@@ -119,7 +121,7 @@ __global__ void __launch_bounds__(kGhThreads, 2)
     if (warp == kGhWarps) {
         if (lane == 0 && !withhold) {
             unsigned q = 0, gq = 0, freed = 0;   // rows and groups issued, groups known released
-            for (long long ch = blockIdx.x; ch < nchunks && !s_fail; ch += gridDim.x) {
+            for (long long ch = vg.bx; ch < nchunks && !s_fail; ch += vg.gx) {
                 const long long v0 = ch * kChunk;
                 const uint32_t cnt = (uint32_t)min((long long)kChunk, N - v0);
                 for (int gi = 0; gi < ng && !s_fail; ++gi) {
@@ -180,7 +182,7 @@ __global__ void __launch_bounds__(kGhThreads, 2)
             slot_pair(reinterpret_cast<const E*>(smem + (q % kSlots) * kSlotBytes) + 2 * t, o);
             ++q;
         };
-        for (long long ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        for (long long ch = vg.bx; ch < nchunks; ch += vg.gx) {
             const long long v0 = ch * kChunk;
             const long long n = v0 + 2 * t;
             const bool valid = n < N;           // N is a multiple of 8: pairs are whole
@@ -286,7 +288,31 @@ __global__ void __launch_bounds__(kGhThreads, 2)
     }
     Acc v[1] = {nll_acc};
     double out[1];
-    if (grid_reduce<1>(v, red, out) && tid == 0) *nll = out[0];
+    if (grid_reduce<1>(v, red, out, vg) && tid == 0) *nll = out[0];
+}
+
+template <int K, int PRE, typename XT>
+__global__ void __launch_bounds__(kGhThreads, 2)
+    k_grad_hess_tma(DevProblem P, const XT* __restrict__ x, const float* __restrict__ y,
+                    const float* __restrict__ b1p, const float* __restrict__ b1m,
+                    float* __restrict__ g, float* __restrict__ h, double* nll, Reduce red,
+                    unsigned* status, long long wait_cycles, int withhold)
+{
+    grad_hess_tma_body<K, PRE, XT>(P, x, y, b1p, b1m, g, h, nll, red, status, wait_cycles, withhold,
+                                   hw_grid());
+}
+
+// Several subjects in one launch (batch.cuh): blocks [start[s], start[s + 1])
+// run subject s's chunks.
+template <int K, int PRE, typename XT>
+__global__ void __launch_bounds__(kGhThreads, 2)
+    k_grad_hess_tma_batch(const __grid_constant__ Batch<GradArgs> b, long long wait_cycles, int withhold)
+{
+    const int s = batch_subject(b.start, b.n);
+    const GradArgs& a = b.a[s];
+    grad_hess_tma_body<K, PRE, XT>(a.P, static_cast<const XT*>(a.x), a.y, a.b1p, a.b1m, a.g, a.h, a.nll,
+                                   a.red, a.status, wait_cycles, withhold,
+                                   batch_grid(b.start[s], b.start[s + 1] - b.start[s], 1, 1));
 }
 
 // Whether the staged pass applies: every row copy must start on a 16-byte
@@ -304,6 +330,17 @@ bool grad_hess_tma_ok(const DevProblem& P, const void* x, const float* y, const 
     return true;
 }
 
+static int sm_count()
+{
+    int sms = kNumSm, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        sms = kNumSm;
+    }
+    return sms;
+}
+
 template <int K, int PRE, typename XT>
 static cudaError_t launch_tma_k(const DevProblem& P, const void* x, const float* y, const float* b1p,
                                 const float* b1m, float* g, float* h, double* nll, Reduce red,
@@ -316,15 +353,8 @@ static cudaError_t launch_tma_k(const DevProblem& P, const void* x, const float*
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    int sms = kNumSm;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-        cudaGetLastError();
-        sms = kNumSm;
-    }
     const long long chunks = (P.N + kChunk - 1) / kChunk;
-    const int grid = (int)std::min<long long>(chunks, 2LL * sms);
+    const int grid = (int)std::min<long long>(chunks, 2LL * sm_count());
     f<<<grid, kGhThreads, kGhSmem, st>>>(P, static_cast<const XT*>(x), y, b1p, b1m, g, h, nll, red,
                                          status, copy_wait_cycles(), copy_withhold());
     return cudaGetLastError();
@@ -350,6 +380,81 @@ static cudaError_t launch_tma_pre(const DevProblem& P, int echo_dtype, const voi
     case 1: return launch_tma_dtype<K, 1>(P, echo_dtype, x, y, b1p, b1m, g, h, nll, red, status, st);
     default: return launch_tma_dtype<K, 2>(P, echo_dtype, x, y, b1p, b1m, g, h, nll, red, status, st);
     }
+}
+
+template <int K, int PRE, typename XT>
+static cudaError_t launch_tma_batch_k(Batch<GradArgs>& b, cudaStream_t st)
+{
+    auto* f = k_grad_hess_tma_batch<K, PRE, XT>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kGhSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    f<<<b.start[b.n], kGhThreads, kGhSmem, st>>>(b, copy_wait_cycles(), copy_withhold());
+    return cudaGetLastError();
+}
+
+template <int K, int PRE>
+static cudaError_t launch_tma_batch_pre(int echo_dtype, Batch<GradArgs>& b, cudaStream_t st)
+{
+    if (echo_dtype == 1) return launch_tma_batch_k<K, PRE, __nv_bfloat16>(b, st);
+    return launch_tma_batch_k<K, PRE, float>(b, st);
+}
+
+bool launch_grad_hess_tma_batch(int K, int precond, int echo_dtype, const GradArgs* a, int n,
+                                cudaStream_t st, cudaError_t* err)
+{
+    long long total = 0;
+    for (int s = 0; s < n; ++s) {
+        if (!grad_hess_tma_ok(a[s].P, a[s].x, a[s].y, a[s].b1p, a[s].b1m, a[s].g, a[s].h)) return false;
+        total += (a[s].P.N + kChunk - 1) / kChunk;
+    }
+    // one wave of two blocks per SM, shared in proportion to the chunks
+    const long long wave = 2LL * sm_count();
+    unsigned blocks[kBatchMax];
+    for (int s = 0; s < n; ++s) {
+        const long long c = (a[s].P.N + kChunk - 1) / kChunk;
+        long long bs = (long long)std::llround((double)wave * (double)c / (double)total);
+        blocks[s] = (unsigned)std::max(1LL, std::min(bs, c));
+    }
+    static thread_local Batch<GradArgs> b;
+    fill_batch(b, a, blocks, n);
+    switch (K * 10 + precond) {
+    case 40: *err = launch_tma_batch_pre<4, 0>(echo_dtype, b, st); break;
+    case 41: *err = launch_tma_batch_pre<4, 1>(echo_dtype, b, st); break;
+    case 42: *err = launch_tma_batch_pre<4, 2>(echo_dtype, b, st); break;
+    case 30: *err = launch_tma_batch_pre<3, 0>(echo_dtype, b, st); break;
+    case 31: *err = launch_tma_batch_pre<3, 1>(echo_dtype, b, st); break;
+    default: *err = launch_tma_batch_pre<3, 2>(echo_dtype, b, st); break;
+    }
+    return true;
+}
+
+template <int K, int PRE>
+static cudaError_t prime_voxel_k()
+{
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void* f) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kGhSmem);
+    };
+    set(reinterpret_cast<const void*>(k_grad_hess_tma<K, PRE, float>));
+    set(reinterpret_cast<const void*>(k_grad_hess_tma<K, PRE, __nv_bfloat16>));
+    set(reinterpret_cast<const void*>(k_grad_hess_tma_batch<K, PRE, float>));
+    set(reinterpret_cast<const void*>(k_grad_hess_tma_batch<K, PRE, __nv_bfloat16>));
+    return e;
+}
+
+cudaError_t prime_voxel_kernels()
+{
+    cudaError_t e = prime_voxel_k<4, 0>();
+    if (!e) e = prime_voxel_k<4, 1>();
+    if (!e) e = prime_voxel_k<4, 2>();
+    if (!e) e = prime_voxel_k<3, 0>();
+    if (!e) e = prime_voxel_k<3, 1>();
+    if (!e) e = prime_voxel_k<3, 2>();
+    return e;
 }
 
 cudaError_t launch_grad_hess_tma(const DevProblem& P, int echo_dtype, const void* x, const float* y,
