@@ -323,7 +323,12 @@ def measured_traffic(kind: str, n_vox: int):
 KERNEL_KIND = {
     "k_pcg_step_tma": "pcg_step", "k_pcg_step": "pcg_step", "k_pcg_init": "pcg_init",
     "k_jtv": "jtv", "k_pcg_final": "pcg_final", "k_grad_hess": "grad_hess",
-    "k_uncertainty": "uncertainty", "k_grad_hess_proj": "grad_hess_proj", "k_push_all": "reslice",
+    "k_grad_hess_tma": "grad_hess", "k_uncertainty": "uncertainty",
+    "k_grad_hess_proj": "grad_hess_proj", "k_push_all": "reslice",
+    # the phase-batched forms (mpm_fit_batch with opts.graph = 2)
+    "k_pcg_step_tma_batch": "pcg_step", "k_pcg_init_batch": "pcg_init", "k_jtv_batch": "jtv",
+    "k_pcg_final_batch": "pcg_final", "k_grad_hess_batch": "grad_hess",
+    "k_grad_hess_tma_batch": "grad_hess", "k_uncertainty_batch": "uncertainty",
 }
 
 
@@ -341,7 +346,7 @@ def read_ncu_csv(path: str):
     for i in sorted(launches):
         name = launches[i]["name"]
         name = name[5:] if name.startswith("void ") else name
-        name = name.split("(")[0].split("<")[0].strip()
+        name = name.replace("<unnamed>", "unnamed").split("(")[0].split("<")[0].strip()
         out.append((name.split("::")[-1], launches[i]["metrics"]))
     return out
 
