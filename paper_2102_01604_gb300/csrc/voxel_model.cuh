@@ -175,48 +175,94 @@ struct EchoSums2 {
     }
 };
 
-// Eq. 24 of contrast c from its echo sums: gradient, Hessian and NLL terms.
+// Elementwise float32 arithmetic on one voxel (float) or on two at once
+// (float2, paired instructions), every rounding explicit, so that each lane
+// of the paired form rounds exactly as the single form.
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float vabs(float a) { return fabsf(a); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 vabs(float2 a) { return abs2(a); }
+template <typename F>
+__device__ __forceinline__ F vsplat(float v);
+template <>
+__device__ __forceinline__ float vsplat<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ float2 vsplat<float2>(float v) { return make_float2(v, v); }
+
+// Eq. 24 of contrast c from its echo sums (S0 .. B1) and factors (q1, qd,
+// h1, hd, cross of ContrastTerms): the gradient, Hessian and NLL terms added
+// to G, H and nll, for one voxel (F = float) or two (F = float2).
+template <int K, int PRE, typename F>
+__device__ __forceinline__ void finish_terms(float is2s, F q1, F qd, F h1, F hd, F cross, F S0, F S1,
+                                             F S2, F R0, F R1, F N2, F A0, F A2, F B1, F (&G)[K],
+                                             F (&H)[K * (K + 1) / 2], F& nll)
+{
+    const F is2 = vsplat<F>(is2s);
+    const F is2R0 = vmul(is2, R0), is2S0 = vmul(is2, S0), is2S1 = vmul(is2, S1);
+    const F is2S0q1 = vmul(is2S0, q1);
+    G[0] = vadd(G[0], is2R0);
+    G[1] = vfma(is2R0, q1, G[1]);
+    G[2] = vfma(is2, R1, G[2]);
+    H[tri(K, 0, 0)] = vadd(H[tri(K, 0, 0)], is2S0);
+    H[tri(K, 0, 1)] = vadd(H[tri(K, 0, 1)], is2S0q1);
+    H[tri(K, 0, 2)] = vadd(H[tri(K, 0, 2)], is2S1);
+    H[tri(K, 1, 1)] = vfma(is2S0q1, q1, H[tri(K, 1, 1)]);
+    H[tri(K, 1, 2)] = vfma(is2S1, q1, H[tri(K, 1, 2)]);
+    H[tri(K, 2, 2)] = vfma(is2, S2, H[tri(K, 2, 2)]);
+    if (K == 4) {
+        G[K - 1] = vfma(is2R0, qd, G[K - 1]);
+        H[tri(K, 0, K - 1)] = vfma(is2S0, qd, H[tri(K, 0, K - 1)]);
+        H[tri(K, 1, K - 1)] = vfma(is2S0q1, qd, H[tri(K, 1, K - 1)]);
+        H[tri(K, 2, K - 1)] = vfma(is2S1, qd, H[tri(K, 2, K - 1)]);
+        H[tri(K, K - 1, K - 1)] = vfma(vmul(is2S0, qd), qd, H[tri(K, K - 1, K - 1)]);
+    }
+    if (PRE == 0) {
+        const F is2A0 = vmul(is2, A0);
+        H[tri(K, 0, 0)] = vadd(H[tri(K, 0, 0)], is2A0);
+        H[tri(K, 1, 1)] = vfma(is2A0, vabs(vmul(h1, q1)), H[tri(K, 1, 1)]);
+        H[tri(K, 2, 2)] = vfma(is2, A2, H[tri(K, 2, 2)]);
+        if (K == 4) H[tri(K, K - 1, K - 1)] = vfma(is2A0, vabs(vmul(hd, qd)), H[tri(K, K - 1, K - 1)]);
+    } else if (PRE == 1) {
+        const F aq1 = vabs(q1), aqd = vabs(qd);
+        const F c13 = vabs(vfma(q1, qd, cross));
+        const F t1 = vadd(vadd(vsplat<F>(1.0f), aq1), aqd);      // 1 + |q1| + |qd|
+        H[tri(K, 0, 0)] = vfma(is2, vfma(A0, t1, B1), H[tri(K, 0, 0)]);
+        const F u1 = vadd(vadd(vabs(vmul(h1, q1)), aq1), c13);
+        H[tri(K, 1, 1)] = vfma(is2, vfma(aq1, B1, vmul(A0, u1)), H[tri(K, 1, 1)]);
+        H[tri(K, 2, 2)] = vfma(is2, vfma(B1, t1, A2), H[tri(K, 2, 2)]);
+        if (K == 4) {
+            const F ud = vadd(vadd(vabs(vmul(hd, qd)), aqd), c13);
+            H[tri(K, K - 1, K - 1)] = vfma(is2, vfma(aqd, B1, vmul(A0, ud)), H[tri(K, K - 1, K - 1)]);
+        }
+    }
+    nll = vfma(vmul(vsplat<F>(0.5f), is2), N2, nll);
+}
+
+// finish_terms for one voxel from its EchoSums.
 template <int K, int PRE>
 __device__ __forceinline__ void finish_contrast(const DevProblem& P, int c, const ContrastTerms& t,
                                                 const EchoSums<PRE>& es, float (&G)[K],
                                                 float (&H)[K * (K + 1) / 2], float& nll_v)
 {
-    const float S0 = es.S0, S1 = es.S1, S2 = es.S2, R0 = es.R0, R1 = es.R1, N2 = es.N2;
-    const float A0 = es.A0, A2 = es.A2, B1 = es.B1;
-    const float is2 = P.isig2[c];
-    const float q1 = t.q1, qd = t.qd;
-    G[0] += is2 * R0;
-    G[1] += is2 * R0 * q1;
-    G[2] += is2 * R1;
-    H[tri(K, 0, 0)] += is2 * S0;
-    H[tri(K, 0, 1)] += is2 * S0 * q1;
-    H[tri(K, 0, 2)] += is2 * S1;
-    H[tri(K, 1, 1)] += is2 * S0 * q1 * q1;
-    H[tri(K, 1, 2)] += is2 * S1 * q1;
-    H[tri(K, 2, 2)] += is2 * S2;
-    if (K == 4) {
-        G[K - 1] += is2 * R0 * qd;
-        H[tri(K, 0, K - 1)] += is2 * S0 * qd;
-        H[tri(K, 1, K - 1)] += is2 * S0 * q1 * qd;
-        H[tri(K, 2, K - 1)] += is2 * S1 * qd;
-        H[tri(K, K - 1, K - 1)] += is2 * S0 * qd * qd;
-    }
-    if (PRE == 0) {
-        H[tri(K, 0, 0)] += is2 * A0;
-        H[tri(K, 1, 1)] += is2 * A0 * fabsf(t.h1 * q1);
-        H[tri(K, 2, 2)] += is2 * A2;
-        if (K == 4) H[tri(K, K - 1, K - 1)] += is2 * A0 * fabsf(t.hd * qd);
-    } else if (PRE == 1) {
-        const float aq1 = fabsf(q1), aqd = fabsf(qd);
-        const float c13 = fabsf(q1 * qd + t.cross);
-        H[tri(K, 0, 0)] += is2 * (A0 * (1.0f + aq1 + aqd) + B1);
-        H[tri(K, 1, 1)] += is2 * (A0 * (fabsf(t.h1 * q1) + aq1 + c13) + aq1 * B1);
-        H[tri(K, 2, 2)] += is2 * (A2 + B1 * (1.0f + aq1 + aqd));
-        if (K == 4)
-            H[tri(K, K - 1, K - 1)] +=
-                is2 * (A0 * (fabsf(t.hd * qd) + aqd + c13) + aqd * B1);
-    }
-    nll_v += 0.5f * is2 * N2;
+    finish_terms<K, PRE, float>(P.isig2[c], t.q1, t.qd, t.h1, t.hd, t.cross, es.S0, es.S1, es.S2, es.R0,
+                                es.R1, es.N2, es.A0, es.A2, es.B1, G, H, nll_v);
+}
+
+// finish_terms for two voxels at once from their paired sums.
+template <int K, int PRE>
+__device__ __forceinline__ void finish_contrast2(const DevProblem& P, int c, const ContrastTerms& t0,
+                                                 const ContrastTerms& t1, const EchoSums2<PRE>& es,
+                                                 float2 (&G)[K], float2 (&H)[K * (K + 1) / 2],
+                                                 float2& nll)
+{
+    finish_terms<K, PRE, float2>(P.isig2[c], make_float2(t0.q1, t1.q1), make_float2(t0.qd, t1.qd),
+                                 make_float2(t0.h1, t1.h1), make_float2(t0.hd, t1.hd),
+                                 make_float2(t0.cross, t1.cross), es.S0, es.S1, es.S2, es.R0, es.R1,
+                                 es.N2, es.A0, es.A2, es.B1, G, H, nll);
 }
 
 template <int K, int PRE, typename XT>
@@ -344,8 +390,25 @@ __device__ __forceinline__ void accumulate_contrast_v(const DevProblem& P, int c
             es.add(s, q2, make_float2(xv[0], xv[1]));
         }
     }
+    constexpr int T = K * (K + 1) / 2;
+    float2 G2[K], H2[T], n2 = make_float2(nll_v[0], nll_v[V - 1]);
 #pragma unroll
-    for (int v = 0; v < V; ++v) finish_contrast<K, PRE>(P, c, t[v], es.lane(v), G[v], H[v], nll_v[v]);
+    for (int k = 0; k < K; ++k) G2[k] = make_float2(G[0][k], G[V - 1][k]);
+#pragma unroll
+    for (int k = 0; k < T; ++k) H2[k] = make_float2(H[0][k], H[V - 1][k]);
+    finish_contrast2<K, PRE>(P, c, t[0], t[V - 1], es, G2, H2, n2);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        G[0][k] = G2[k].x;
+        G[V - 1][k] = G2[k].y;
+    }
+#pragma unroll
+    for (int k = 0; k < T; ++k) {
+        H[0][k] = H2[k].x;
+        H[V - 1][k] = H2[k].y;
+    }
+    nll_v[0] = n2.x;
+    nll_v[V - 1] = n2.y;
 }
 
 }  // namespace mpm

@@ -202,17 +202,14 @@ __device__ __forceinline__ void grad_hess_tma_body(const DevProblem& P, const XT
                     map_params_v(yk, K, a[v], r1[v], r2[v], dl[v], m[v]);
                 }
             }
-            float G[2][K], H[2][T], nll_v[2];
+            float2 G[K], H[T], nll2 = make_float2(0.f, 0.f);   // x: first voxel, y: second
             Relax R[2];
 #pragma unroll
-            for (int v = 0; v < 2; ++v) {
+            for (int k = 0; k < K; ++k) G[k] = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int k = 0; k < K; ++k) G[v][k] = 0.0f;
+            for (int k = 0; k < T; ++k) H[k] = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int k = 0; k < T; ++k) H[v][k] = 0.0f;
-                nll_v[v] = 0.0f;
-                R[v] = Relax{0.f, 0.f, 0.f};
-            }
+            for (int v = 0; v < 2; ++v) R[v] = Relax{0.f, 0.f, 0.f};
             for (int c = 0; c < P.C; ++c) {
                 begin_group();
                 float bm[2] = {1.0f, 1.0f};
@@ -255,22 +252,15 @@ __device__ __forceinline__ void grad_hess_tma_body(const DevProblem& P, const XT
                     }
                 }
                 end_group();
-#pragma unroll
-                for (int v = 0; v < 2; ++v) finish_contrast<K, PRE>(P, c, tc[v], es.lane(v), G[v], H[v], nll_v[v]);
+                finish_contrast2<K, PRE>(P, c, tc[0], tc[1], es, G, H, nll2);
             }
             if (valid && !bad) {
 #pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    const float o[2] = {G[0][k], G[1][k]};
-                    store_vec<2>(g + k * N + n, o);
-                }
+                for (int k = 0; k < K; ++k) *reinterpret_cast<float2*>(g + k * N + n) = G[k];
 #pragma unroll
-                for (int k = 0; k < T; ++k) {
-                    const float o[2] = {H[0][k], H[1][k]};
-                    store_vec<2>(h + k * N + n, o);
-                }
-                nll_acc.add(nll_v[0]);
-                nll_acc.add(nll_v[1]);
+                for (int k = 0; k < T; ++k) *reinterpret_cast<float2*>(h + k * N + n) = H[k];
+                nll_acc.add(nll2.x);
+                nll_acc.add(nll2.y);
             }
         }
     }
