@@ -49,62 +49,101 @@ constexpr int kInitAhead = 2;     // planes between the PCG start's L2 hint and 
 
 // Each thread marches up its z range with the centre values of planes z - 1,
 // z and z + 1 in registers; the centre of plane z + 2 is loaded one plane
-// ahead, so the only far (next-plane) load is in flight while plane z is
-// computed.  The x / y neighbours come from the current plane (L1).  The six
-// terms are summed in the order x-, x+, y-, y+, z-, z+.
+// ahead.  The x / y neighbours come from the plane's tile in shared memory
+// (double-buffered, one barrier per plane): every thread writes its centre,
+// and 80 threads the tile's halo (rows y0 - 1 and y0 + 8, columns x0 - 1 and
+// x0 + 32), which they too load two planes ahead.  The six terms are summed in
+// the order x-, x+, y-, y+, z-, z+.
 template <int K>
 __device__ __forceinline__ void jtv_body(const DevProblem& P, int zc, const float* __restrict__ y,
                                          float* __restrict__ w, double* jtv, Reduce red, const VGrid& vg)
 {
+    constexpr int TW = kTileX + 2, TH = kTileY + 2;
+    __shared__ float tile[2][K][TH][TW];
     const long long N = P.N;
-    const long long sxy = (long long)P.nx * P.ny;
-    const int x = vg.bx * kTileX + threadIdx.x;
-    const int yy = vg.by * kTileY + threadIdx.y;
+    const int nx = P.nx, ny = P.ny, nz = P.nz;
+    const long long sxy = (long long)nx * ny;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int x = vg.bx * kTileX + tx;
+    const int yy = vg.by * kTileY + ty;
     const int z0 = vg.bz * zc;
-    const int z1 = min(P.nz, z0 + zc);
+    const int z1 = min(nz, z0 + zc);
+    // this thread's halo point, if any: its place in the tile and the volume
+    const int t = ty * kTileX + tx;
+    int hx = -1, hy = -1, hr = 0, hc = 0;
+    if (t < 2 * kTileX) {                       // rows above and below the tile
+        hr = t < kTileX ? 0 : TH - 1;
+        hc = 1 + t % kTileX;
+    } else if (t < 2 * kTileX + 2 * kTileY) {   // columns left and right
+        const int u = t - 2 * kTileX;
+        hr = 1 + u % kTileY;
+        hc = u < kTileY ? 0 : TW - 1;
+    }
+    if (t < 2 * kTileX + 2 * kTileY) {
+        hx = vg.bx * kTileX + hc - 1;
+        hy = vg.by * kTileY + hr - 1;
+    }
+    const bool halo = hx >= 0 && hx < nx && hy >= 0 && hy < ny;
+    const bool inside = x < nx && yy < ny;
     Acc acc;
-    if (x < P.nx && yy < P.ny && z0 < z1) {
-        const long long base = x + (long long)P.nx * yy;
-        const bool okx0 = x > 0, okx1 = x < P.nx - 1, oky0 = yy > 0, oky1 = yy < P.ny - 1;
-        float dn[K], cu[K], up[K], nx2[K];
+    if (z0 < z1) {
+        const long long base = inside ? x + (long long)nx * yy : 0;
+        const long long hbase = halo ? hx + (long long)nx * hy : 0;
+        const bool okx0 = x > 0, okx1 = x < nx - 1, oky0 = yy > 0, oky1 = yy < ny - 1;
+        float dn[K], cu[K], up[K], nx2[K], h0[K], h1[K], h2[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const float* yk = y + k * N + base;
-            cu[k] = __ldg(yk + sxy * z0);
-            dn[k] = z0 > 0 ? __ldg(yk + sxy * (z0 - 1)) : 0.0f;
-            up[k] = z0 + 1 < P.nz ? __ldg(yk + sxy * (z0 + 1)) : 0.0f;
+            const float* hk = y + k * N + hbase;
+            cu[k] = inside ? __ldg(yk + sxy * z0) : 0.0f;
+            dn[k] = inside && z0 > 0 ? __ldg(yk + sxy * (z0 - 1)) : 0.0f;
+            up[k] = inside && z0 + 1 < nz ? __ldg(yk + sxy * (z0 + 1)) : 0.0f;
+            h0[k] = halo ? __ldg(hk + sxy * z0) : 0.0f;
+            h1[k] = halo && z0 + 1 < z1 ? __ldg(hk + sxy * (z0 + 1)) : 0.0f;
         }
         for (int z = z0; z < z1; ++z) {
+            const int b = z & 1;
             const long long n = base + sxy * z;
-            const bool okz0 = z > 0, okz1 = z < P.nz - 1;
-            // the centre two planes up, for the next step
-#pragma unroll
-            for (int k = 0; k < K; ++k)
-                nx2[k] = (z + 2 < P.nz && z + 1 < z1) ? __ldg(y + k * N + n + 2 * sxy) : 0.0f;
-            float u = 0.0f;
+            const bool okz0 = z > 0, okz1 = z < nz - 1;
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                const float* yk = y + k * N + n;
-                const float v = cu[k];
-                float s = 0.0f;
-                float d;
-                if (okx0) { d = __ldg(yk - 1) - v; s += d * d * P.ihx2; }
-                if (okx1) { d = __ldg(yk + 1) - v; s += d * d * P.ihx2; }
-                if (oky0) { d = __ldg(yk - P.nx) - v; s += d * d * P.ihy2; }
-                if (oky1) { d = __ldg(yk + P.nx) - v; s += d * d * P.ihy2; }
-                if (okz0) { d = dn[k] - v; s += d * d * P.ihz2; }
-                if (okz1) { d = up[k] - v; s += d * d * P.ihz2; }
-                u += P.lambda[k] * s;
+                tile[b][k][ty + 1][tx + 1] = cu[k];
+                if (t < 2 * kTileX + 2 * kTileY) tile[b][k][hr][hc] = h0[k];
             }
-            const float val = u + P.eps2;
-            const float sq = sqrtf(val);
-            if (w) w[n] = 1.0f / sq;
-            acc.add(sq);
+            // the centre two planes up, and the halo two planes up, for later steps
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                nx2[k] = inside && z + 2 < nz && z + 1 < z1 ? __ldg(y + k * N + n + 2 * sxy) : 0.0f;
+                h2[k] = halo && z + 2 < z1 ? __ldg(y + k * N + hbase + sxy * (z + 2)) : 0.0f;
+            }
+            __syncthreads();
+            if (inside) {
+                float u = 0.0f;
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const float v = cu[k];
+                    float s = 0.0f;
+                    float d;
+                    if (okx0) { d = tile[b][k][ty + 1][tx] - v; s += d * d * P.ihx2; }
+                    if (okx1) { d = tile[b][k][ty + 1][tx + 2] - v; s += d * d * P.ihx2; }
+                    if (oky0) { d = tile[b][k][ty][tx + 1] - v; s += d * d * P.ihy2; }
+                    if (oky1) { d = tile[b][k][ty + 2][tx + 1] - v; s += d * d * P.ihy2; }
+                    if (okz0) { d = dn[k] - v; s += d * d * P.ihz2; }
+                    if (okz1) { d = up[k] - v; s += d * d * P.ihz2; }
+                    u += P.lambda[k] * s;
+                }
+                const float val = u + P.eps2;
+                const float sq = sqrtf(val);
+                if (w) w[n] = 1.0f / sq;
+                acc.add(sq);
+            }
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 dn[k] = cu[k];
                 cu[k] = up[k];
                 up[k] = nx2[k];
+                h0[k] = h1[k];
+                h1[k] = h2[k];
             }
         }
     }

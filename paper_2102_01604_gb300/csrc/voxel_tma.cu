@@ -10,12 +10,13 @@
 // in groups (the maps with B1+, then each contrast's B1- and echoes, at most
 // kGroupMax rows; contrasts with more echoes take the unstaged pass): a
 // group's copies complete one full mbarrier, and each compute warp releases
-// the group, on its empty mbarrier, once it has read the group's last row.  So the DRAM reads are always in flight ahead of the
-// arithmetic, whatever the occupancy (two blocks per SM at the 128 registers
-// the two-voxel arithmetic needs), and a compute thread waits once per group,
-// not once per row.  Each compute thread takes two neighbouring voxels of the
-// chunk, with the arithmetic of the unstaged pass (voxel_model.cuh), so g and
-// h are the same bit for bit.
+// the group, on its empty mbarrier, once it has read the group's last row.
+// So the DRAM reads are always in flight ahead of the arithmetic, whatever the
+// occupancy (two blocks per SM at the 128 registers the two-voxel arithmetic
+// needs), and a compute thread waits once per group, not once per row.  Each
+// compute thread takes two neighbouring voxels of the chunk, with the
+// arithmetic of the unstaged pass (voxel_model.cuh) in paired float32
+// instructions, so g and h are the same bit for bit.
 //
 // Every mbarrier wait is bounded: on timeout the block stops waiting, drains
 // the copies it issued (bounded again), records kStatusTimeout and still
