@@ -638,7 +638,8 @@ static mpm_status capture_updates(FitJob* jobs, int n, GraphEntry& out)
 // One subject of a phase-batched fit: its grids and the TMA maps of its solve.
 struct PhasedSubject {
     FitJob* j;
-    StencilGrid sg;          // 32 x 8 stencil grid (JTV, PCG init)
+    StencilGrid sg;          // 32 x 8 stencil grid of the JTV kernel
+    StencilGrid ig;          // and of the PCG start
     SolveBufs B;
     StepMaps maps;
     int nchunk;              // z ranges of its share of the iteration's wave
@@ -671,10 +672,12 @@ static cudaError_t enqueue_phased(std::vector<PhasedSubject>& subj, int tile, cu
     std::vector<StepArgs> sa(n);
     std::vector<FinalArgs> fa(n);
     std::vector<UncArgs> ua;
-    std::vector<unsigned> bst(n), bvox(n), bstep(n);
+    std::vector<unsigned> bst(n), bini(n), bvox(n), bstep(n);
     for (int s = 0; s < n; ++s) {
         const StencilGrid& g = subj[s].sg;
         bst[s] = g.grid.x * g.grid.y * g.grid.z;
+        const StencilGrid& gi = subj[s].ig;
+        bini[s] = gi.grid.x * gi.grid.y * gi.grid.z;
         bvox[s] = subj[s].vox_blocks;
         bstep[s] = subj[s].step_blocks;
     }
@@ -703,11 +706,11 @@ static cudaError_t enqueue_phased(std::vector<PhasedSubject>& subj, int tile, cu
         if (it >= o.gn_iters) break;
         for (int s = 0; s < n; ++s) {
             const FitJob& j = *subj[s].j;
-            const StencilGrid& g = subj[s].sg;
+            const StencilGrid& g = subj[s].ig;
             ia[s] = InitArgs{j.P, g.zc, g.grid.x, g.grid.y, g.grid.z, j.L.h, j.L.w, j.L.g, j.y,
                              subj[s].B.z[0], tol2, j.L.hdr, nullptr, j.L.red};
         }
-        if ((e = launch_pcg_init_batch(K, ia.data(), bst.data(), n, st))) return e;
+        if ((e = launch_pcg_init_batch(K, ia.data(), bini.data(), n, st))) return e;
         for (int c = 0; c < o.cg_iters; ++c) {
             const int rr = (tol2 > 0.0 || c == o.cg_iters - 1) ? 1 : 0;
             for (int s = 0; s < n; ++s) {
@@ -769,6 +772,7 @@ static void plan_phased(FitJob* jobs, int n, std::vector<std::vector<PhasedSubje
         ps.B = solve_bufs(j.P, j.L.solve);
         if (!make_step_maps(j.P, j.L.h, j.L.w, ps.B, tile, &ps.maps)) continue;
         ps.sg = stencil_grid(j.P, kTileX, kTileY);
+        ps.ig = stencil_grid(j.P, kTileX, kTileY, kInitWaves);
         ps.vox_blocks = (unsigned)voxel_grid(j.P.N);
         rest[i] = 0;
         const long long key = phased_class(j, tile);

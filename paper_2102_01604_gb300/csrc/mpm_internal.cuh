@@ -20,7 +20,10 @@ struct StencilGrid {
     int zc;           // z planes per block (TMA iteration: number of z ranges)
 };
 
-StencilGrid stencil_grid(const DevProblem& P, int tile_x, int tile_y);
+// Blocks of a z-marching stencil kernel: about `waves` waves of 8 resident
+// blocks per SM over tile columns cut into z ranges.
+StencilGrid stencil_grid(const DevProblem& P, int tile_x, int tile_y, int waves = 2);
+constexpr int kInitWaves = 4;   // the PCG start's (shorter z ranges measured faster)
 int voxel_grid(long long N);
 
 // Every kernel launch goes through a LaunchScope: it counts the launch and,

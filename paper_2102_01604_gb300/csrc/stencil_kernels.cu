@@ -475,15 +475,15 @@ __global__ void __launch_bounds__(kBlock) k_pcg_final_batch(const __grid_constan
 
 // ------------------------------------------------------------- launchers
 
-StencilGrid stencil_grid(const DevProblem& P, int tx, int ty)
+StencilGrid stencil_grid(const DevProblem& P, int tx, int ty, int waves)
 {
     StencilGrid sg;
     sg.block = dim3(tx, ty, 1);
     const int gx = (P.nx + tx - 1) / tx;
     const int gy = (P.ny + ty - 1) / ty;
     const long long tiles = (long long)gx * gy;
-    // about two waves of 8 resident blocks per SM, at most kMaxBlocks blocks
-    const long long target = 2LL * 8 * kNumSm;
+    // about `waves` waves of 8 resident blocks per SM, at most kMaxBlocks blocks
+    const long long target = (long long)waves * 8 * kNumSm;
     long long gz = target / (tiles > 0 ? tiles : 1);
     if (gz < 1) gz = 1;
     if (gz > P.nz) gz = P.nz;
@@ -541,11 +541,12 @@ static cudaError_t solve_k(const DevProblem& P, int cg_iters, double tol_cg, con
                            void* solve_ws, WsHeader* hdr, Reduce red, cudaStream_t st)
 {
     const StencilGrid sg = stencil_grid(P, kTileX, kTileY);
+    const StencilGrid ig = stencil_grid(P, kTileX, kTileY, kInitWaves);
     SolveBufs B = carve(P, solve_ws);
     const double tol2 = tol_cg > 0.0 ? tol_cg * tol_cg : 0.0;
     {
         LaunchScope ls(MPM_KERNEL_PCG_INIT, st);
-        k_pcg_init<K><<<sg.grid, sg.block, 0, st>>>(P, sg.zc, h, w, g, y, B.z[0], tol2, hdr, resid, red);
+        k_pcg_init<K><<<ig.grid, ig.block, 0, st>>>(P, ig.zc, h, w, g, y, B.z[0], tol2, hdr, resid, red);
     }
     StepMaps maps;
     const int tile = tma_tile_choice(P);

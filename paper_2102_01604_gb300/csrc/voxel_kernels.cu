@@ -181,6 +181,20 @@ static bool pairs_ok(long long N, int echo_dtype, const void* x, const float* y,
 
 // --------------------------------------------------------- uncertainty
 
+// 1 / sqrt(s) in float64 without a float64 square root or division: the
+// float32 estimate refined by two Newton-Raphson steps on f(r) = r^-2 - s,
+// r <- r (3 - s r^2) / 2, each of which doubles the correct bits (about 23,
+// 46, then the full 53).  Outside the float32 range it falls back to
+// 1 / sqrt(s).
+__device__ __forceinline__ double rsqrt_newton(double s)
+{
+    if (!(s > 1e-30 && s < 1e30)) return 1.0 / sqrt(s);
+    double r = (double)rsqrtf((float)s);
+    r = r * (1.5 - 0.5 * s * r * r);
+    r = r * (1.5 - 0.5 * s * r * r);
+    return r;
+}
+
 // Block n of the preconditioner, M = H_n + diag(lambda_k d_n) with
 // d_n = sum_{m in N(n)} (w_n + w_m) / h^2, inverted in float64 through its
 // Cholesky factor: var_k = sum_j (L^-1)_{jk}^2, logdet = -2 sum log L_kk.
@@ -195,9 +209,17 @@ __device__ __forceinline__ void uncertainty_body(const DevProblem& P, const floa
     const long long sxy = (long long)P.nx * P.ny;
     for (long long n = vg.bx * (long long)blockDim.x + threadIdx.x; n < N;
          n += (long long)vg.gx * blockDim.x) {
-        const int x = (int)(n % P.nx);
-        const int yy = (int)((n / P.nx) % P.ny);
-        const int z = (int)(n / sxy);
+        int x, yy, z;
+        if (N <= 0xffffffffLL) {        // 32-bit division where the index fits
+            const unsigned u = (unsigned)n, r = u / (unsigned)P.nx;
+            x = (int)(u - r * (unsigned)P.nx);
+            yy = (int)(r % (unsigned)P.ny);
+            z = (int)(r / (unsigned)P.ny);
+        } else {
+            x = (int)(n % P.nx);
+            yy = (int)((n / P.nx) % P.ny);
+            z = (int)(n / sxy);
+        }
         const double wn = __ldg(w + n);
         double d = 0.0;
         if (x > 0) d += (wn + __ldg(w + n - 1)) * P.ihx2;
@@ -215,16 +237,16 @@ __device__ __forceinline__ void uncertainty_body(const DevProblem& P, const floa
         for (int a = 0; a < K; ++a) M[a][a] += (double)P.lambda[a] * d;
         bool ok = true;
         double ld = 0.0;                // log det L, only when asked (log in float64 is costly)
-        double inv[K];                  // 1 / L_jj, one division per diagonal entry
+        double inv[K];                  // 1 / L_jj
 #pragma unroll
         for (int j = 0; j < K; ++j) {
             double s = M[j][j];
 #pragma unroll
             for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
             if (!(s > 0.0)) { ok = false; s = 1e-300; }
-            L[j][j] = sqrt(s);
+            inv[j] = rsqrt_newton(s);
+            L[j][j] = s * inv[j];
             if (logdet) ld += log(L[j][j]);
-            inv[j] = 1.0 / L[j][j];
 #pragma unroll
             for (int i = j + 1; i < K; ++i) {
                 double v = M[i][j];
