@@ -68,15 +68,16 @@ int copy_withhold() { return g_withhold.load(std::memory_order_relaxed); }
 long long copy_wait_cycles() { return g_wait_cycles.load(std::memory_order_relaxed); }
 
 // Per tile shape: one compute thread per voxel plus a producer warp.  256-
-// voxel tiles run two blocks per SM with two raw stages; 512-voxel tiles one
-// block per SM with three.
-template <int K, int TX, int TY>
+// voxel tiles run two blocks per SM with two raw stages in the x-fold
+// iterations (whose stages also hold the x and p_{j-2} tiles) and three in
+// the others; 512-voxel tiles one block per SM with three and four.
+template <int K, int TX, int TY, bool FOLD = true>
 struct StepLayout {
     static constexpr int VOX = TX * TY;                 // voxels per tile = compute threads
     static constexpr int WARPS = VOX / 32;              // compute warps
     static constexpr int THREADS = VOX + 32;            // plus the producer warp
     static constexpr int MINB = VOX >= 512 ? 1 : 2;     // resident blocks per SM aimed for
-    static constexpr int RS = VOX >= 512 ? 3 : 2;       // raw (z, v, p, w, x, p_{j-2}) stages
+    static constexpr int RS = (VOX >= 512 ? 3 : 2) + (FOLD ? 0 : 1);   // raw (z, v, p, w[, x, p_{j-2}]) stages
     static constexpr int HS = 2;                        // H stages
     static constexpr int T = K * (K + 1) / 2;
     static constexpr int BX = TX + 2, BY = TY + 2;      // z / v / p box and formed plane (x from x0 - 1)
@@ -91,7 +92,7 @@ struct StepLayout {
     static constexpr int W_OFF = P_OFF + a128(BOX_BYTES);
     static constexpr int X_OFF = W_OFF + a128(W_BYTES);
     static constexpr int P2_OFF = X_OFF + a128(TILE_BYTES);
-    static constexpr int RAW = P2_OFF + a128(TILE_BYTES);
+    static constexpr int RAW = FOLD ? P2_OFF + a128(TILE_BYTES) : X_OFF;
     static constexpr int H_STAGE = a128(H_BYTES);
     static constexpr int SLOT = a128(BOX_BYTES);
     static constexpr int H_BASE = RS * RAW;
@@ -102,6 +103,17 @@ struct StepLayout {
     static_assert(SMEM <= 227 * 1024, "shared memory of one block");
     static_assert(4 * BX <= 256 && 4 * TX <= 256, "TMA box rows of at most 256 elements");
 };
+
+// Dynamic shared memory a step kernel of this tile shape asks for: the larger
+// of the two layouts, so that every mode's launch fits the same opt-in and the
+// occupancy query holds for both.
+template <int K, int TX, int TY>
+constexpr int step_smem_max()
+{
+    return StepLayout<K, TX, TY, true>::SMEM > StepLayout<K, TX, TY, false>::SMEM
+               ? StepLayout<K, TX, TY, true>::SMEM
+               : StepLayout<K, TX, TY, false>::SMEM;
+}
 
 // Barrier 1 among the compute warps (the producer warp never joins it).
 template <int NTHREADS>
@@ -126,7 +138,7 @@ __device__ __forceinline__ void step_body(
     float4* __restrict__ pout, float4* __restrict__ xacc, WsHeader* hdr, double* resid, Reduce red,
     long long wait_cycles, int withhold, const VGrid& vg)
 {
-    using L = StepLayout<K, TX, TY>;
+    using L = StepLayout<K, TX, TY, (MODE >= kModeFold)>;
     constexpr int T = L::T;
     constexpr int kStepRaw = L::RS, kStepH = L::HS, kStepWarps = L::WARPS;
     constexpr bool first = MODE == kModeFirst, fold = MODE >= kModeFold, readx = MODE == kModeFoldX;
@@ -434,7 +446,7 @@ static bool encode(CUtensorMap* m, const float* base, int rank, const cuuint64_t
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     return encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<float*>(base),
                        dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -511,11 +523,12 @@ template <int K, int TX, int TY, int MODE>
 static cudaError_t launch_step_m(const DevProblem& P, int nchunk, dim3 grid, const StepMaps& m, int j,
                                  int want_rr, WsHeader* hdr, double* resid, Reduce red, cudaStream_t st)
 {
-    using L = StepLayout<K, TX, TY>;
+    using L = StepLayout<K, TX, TY, (MODE >= kModeFold)>;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_pcg_step_tma<K, TX, TY, MODE>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             step_smem_max<K, TX, TY>());
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -571,11 +584,12 @@ StepArgs step_args(const DevProblem& P, const StepMaps& m, int nchunk, int j, in
 template <int K, int TX, int TY, int MODE>
 static cudaError_t launch_step_batch_m(const Batch<StepArgs>& b, cudaStream_t st)
 {
-    using L = StepLayout<K, TX, TY>;
+    using L = StepLayout<K, TX, TY, (MODE >= kModeFold)>;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_pcg_step_tma_batch<K, TX, TY, MODE>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             step_smem_max<K, TX, TY>());
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -624,11 +638,11 @@ static int resident_one()
     // the occupancy query needs the kernel's shared-memory opt-in first
     int nb = 0;
     if (cudaFuncSetAttribute(k_pcg_step_tma<K, TX, TY, kModeFoldX>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, StepLayout<K, TX, TY>::SMEM) !=
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, step_smem_max<K, TX, TY>()) !=
             cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pcg_step_tma<K, TX, TY, kModeFoldX>,
                                                       StepLayout<K, TX, TY>::THREADS,
-                                                      StepLayout<K, TX, TY>::SMEM) !=
+                                                      step_smem_max<K, TX, TY>()) !=
             cudaSuccess) {
         cudaGetLastError();
         nb = 1;
@@ -683,7 +697,7 @@ static cudaError_t prime_one()
     auto set = [&](const void* f) {
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     StepLayout<K, TX, TY>::SMEM);
+                                     step_smem_max<K, TX, TY>());
     };
     set(reinterpret_cast<const void*>(k_pcg_step_tma<K, TX, TY, kModeFirst>));
     set(reinterpret_cast<const void*>(k_pcg_step_tma<K, TX, TY, kModeStep>));
