@@ -78,7 +78,7 @@ struct StepLayout {
     static constexpr int THREADS = VOX + 32;            // plus the producer warp
     static constexpr int MINB = VOX >= 512 ? 1 : 2;     // resident blocks per SM aimed for
     static constexpr int RS = (VOX >= 512 ? 3 : 2) + (FOLD ? 0 : 1);   // raw (z, v, p, w[, x, p_{j-2}]) stages
-    static constexpr int HS = 2;                        // H stages
+    static constexpr int HS = FOLD ? 2 : 3;             // H stages
     static constexpr int T = K * (K + 1) / 2;
     static constexpr int BX = TX + 2, BY = TY + 2;      // z / v / p box and formed plane (x from x0 - 1)
     static constexpr int WX = TX + 8;                   // w box (x from x0 - 4, 16-byte aligned)
