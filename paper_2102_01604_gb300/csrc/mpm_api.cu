@@ -771,9 +771,7 @@ static void plan_phased(FitJob* jobs, int n, std::vector<std::vector<PhasedSubje
         ps.j = &j;
         ps.B = solve_bufs(j.P, j.L.solve);
         if (!make_step_maps(j.P, j.L.h, j.L.w, ps.B, tile, &ps.maps)) continue;
-        ps.sg = stencil_grid(j.P, kTileX, kTileY);
-        ps.ig = stencil_grid(j.P, kTileX, kTileY, kInitWaves);
-        ps.vox_blocks = (unsigned)voxel_grid(j.P.N);
+
         rest[i] = 0;
         const long long key = phased_class(j, tile);
         classes[key].push_back(ps);
@@ -786,6 +784,16 @@ static void plan_phased(FitJob* jobs, int n, std::vector<std::vector<PhasedSubje
             const size_t g1 = std::min(members.size(), g0 + (size_t)kBatchMax);
             std::vector<PhasedSubject> grp(members.begin() + g0, members.begin() + g1);
             std::vector<int> idx;
+            // the stencil kernels' blocks shared in proportion to the voxels
+            long long vox = 0;
+            for (const PhasedSubject& ps : grp) vox += ps.j->P.N;
+            for (PhasedSubject& ps : grp) {
+                const double share = (double)ps.j->P.N / (double)vox;
+                ps.sg = stencil_grid(ps.j->P, kTileX, kTileY, 2, share);
+                ps.ig = stencil_grid(ps.j->P, kTileX, kTileY, kInitWaves, share);
+                const long long cap = std::max(1LL, std::llround(share * voxel_grid(1LL << 40)));
+                ps.vox_blocks = (unsigned)std::min<long long>(voxel_grid(ps.j->P.N), cap);
+            }
             std::vector<long long> t, blocks;
             std::vector<int> nz, chunks;
             for (const PhasedSubject& ps : grp) {
@@ -806,8 +814,8 @@ static void plan_phased(FitJob* jobs, int n, std::vector<std::vector<PhasedSubje
 }
 
 // Capture the updates of every job phase by phase: one launch per phase of
-// every update for each group of plan_phased, the groups side by side, and
-// beside them the lanes of the subjects that cannot be batched.
+// every update for each group of plan_phased, the groups in lanes, and beside
+// them the lanes of the subjects that cannot be batched.
 static mpm_status capture_phased(FitJob* jobs, int n, GraphEntry& out)
 {
     std::vector<std::vector<PhasedSubject>> groups;
@@ -824,12 +832,26 @@ static mpm_status capture_phased(FitJob* jobs, int n, GraphEntry& out)
     }
     const std::vector<std::vector<int>> lanes = lane_plan(voxels, skip);
     out.iters.assign(n, 0);
+    // The groups are placed in lanes by the same rule as single subjects
+    // (lane_plan on their voxel totals): groups that fill the GPU run one
+    // after another, each of their launches sized for the whole GPU; smaller
+    // groups run side by side.
+    std::vector<long long> gvox(groups.size(), 0);
+    for (size_t g = 0; g < groups.size(); ++g)
+        for (const PhasedSubject& ps : groups[g]) gvox[g] += ps.j->P.N;
+    const std::vector<std::vector<int>> glanes = lane_plan(gvox, std::vector<char>(groups.size(), 0));
     return capture_lanes(
-        groups.size() + lanes.size(),
+        glanes.size() + lanes.size(),
         [&](size_t l, cudaStream_t b) {
-            if (l < groups.size()) return enqueue_phased(groups[l], tiles[l], b, out.iters, index[l]);
-            const std::vector<int>& lane = lanes[l - groups.size()];
             cudaError_t e = cudaSuccess;
+            if (l < glanes.size()) {
+                for (size_t k = 0; k < glanes[l].size() && e == cudaSuccess; ++k) {
+                    const int g = glanes[l][k];
+                    e = enqueue_phased(groups[g], tiles[g], b, out.iters, index[g]);
+                }
+                return e;
+            }
+            const std::vector<int>& lane = lanes[l - glanes.size()];
             for (size_t k = 0; k < lane.size() && e == cudaSuccess; ++k)
                 e = fit_enqueue_updates(jobs[lane[k]], b, &out.iters[lane[k]]);
             return e;

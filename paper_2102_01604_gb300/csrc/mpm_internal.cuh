@@ -21,8 +21,10 @@ struct StencilGrid {
 };
 
 // Blocks of a z-marching stencil kernel: about `waves` waves of 8 resident
-// blocks per SM over tile columns cut into z ranges.
-StencilGrid stencil_grid(const DevProblem& P, int tile_x, int tile_y, int waves = 2);
+// blocks per SM over tile columns cut into z ranges; a volume that shares a
+// launch with others takes `share` of those blocks.
+StencilGrid stencil_grid(const DevProblem& P, int tile_x, int tile_y, int waves = 2,
+                         double share = 1.0);
 constexpr int kInitWaves = 4;   // the PCG start's (shorter z ranges measured faster)
 int voxel_grid(long long N);
 

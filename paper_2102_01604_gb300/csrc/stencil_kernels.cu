@@ -13,6 +13,8 @@
 // (x, y) tile and march along z.  All CG scalars (alpha, beta, |r|) live in
 // device memory and are produced by the last block of each reducing launch,
 // so the whole PCG runs without a host round trip.
+#include <algorithm>
+
 #include "mpm_internal.cuh"
 #include "pcg_step.cuh"
 
@@ -475,15 +477,16 @@ __global__ void __launch_bounds__(kBlock) k_pcg_final_batch(const __grid_constan
 
 // ------------------------------------------------------------- launchers
 
-StencilGrid stencil_grid(const DevProblem& P, int tx, int ty, int waves)
+StencilGrid stencil_grid(const DevProblem& P, int tx, int ty, int waves, double share)
 {
     StencilGrid sg;
     sg.block = dim3(tx, ty, 1);
     const int gx = (P.nx + tx - 1) / tx;
     const int gy = (P.ny + ty - 1) / ty;
     const long long tiles = (long long)gx * gy;
-    // about `waves` waves of 8 resident blocks per SM, at most kMaxBlocks blocks
-    const long long target = (long long)waves * 8 * kNumSm;
+    // about `waves` waves of 8 resident blocks per SM (times this volume's
+    // share of a launch serving several), at most kMaxBlocks blocks
+    const long long target = std::max(1LL, (long long)(share * waves * 8 * kNumSm));
     long long gz = target / (tiles > 0 ? tiles : 1);
     if (gz < 1) gz = 1;
     if (gz > P.nz) gz = P.nz;
