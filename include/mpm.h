@@ -270,7 +270,8 @@ mpm_status mpm_autotune(const mpm_problem* problem, const mpm_opts* opts, void* 
  * ONE kernel launch for the whole group, each subject on its own share of the
  * blocks with its own scalars and reductions (the PCG iteration's wave of
  * resident blocks is divided so that the subject that finishes last does so
- * soonest); groups run side by side.  Subjects that the TMA-staged iteration
+ * soonest, the other phases' blocks in proportion to the voxels); groups that
+ * fill the GPU run one after another, smaller groups side by side.  Subjects that the TMA-staged iteration
  * cannot take (x size not a multiple of 4, a volume smaller than the tile's
  * box, an unaligned buffer), projected fits and multigrid solves run in lanes
  * as with graph = 1, beside the groups.  A batched subject's reductions sum
