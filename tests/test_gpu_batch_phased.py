@@ -169,3 +169,14 @@ def test_unaligned_subject_runs_in_a_lane(mpm):
     for i in (1, 2):
         _check_equal_to_solo(solos[i], ys[i], vs[i], reps[i], gn, i)
     assert launches == 2 * _launches_per_group(gn, cg, True) + INIT_LAUNCHES * 3, launches
+
+
+def test_single_fit_with_the_phased_graph(mpm):
+    """mpm_fit with opts.graph = 2: a group of one subject, which the wave
+    split gives the solo grid; the result meets the benchmark spec's bounds of the
+    direct-launch fit."""
+    gn, cg = 4, 30
+    d, pg, x, v = _subject(mpm, SUBJECTS[0])
+    solo = _solo(mpm, d, pg, x, v, mpm.make_opts(gn_iters=gn, cg_iters=cg))
+    y, var, rep = _solo(mpm, d, pg, x, v, mpm.make_opts(gn_iters=gn, cg_iters=cg, graph="phased"))
+    _check_equal_to_solo(solo, y, var, rep, gn, "phased single")
