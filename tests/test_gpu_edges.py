@@ -119,3 +119,22 @@ def test_resume(mpm):
     mpm.mpm_fit(p, mpm.make_opts(gn_iters=3, init=False), to_dev(d["x"]), b, to_dev(d["b1p"]),
                 to_dev(d["b1m"]))
     assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("echoes,b1m", [((15, 4), True), ((16, 4), False), ((20, 3), True)])
+def test_voxel_pass_at_the_staging_limit(mpm, echoes, b1m):
+    """The staged voxel pass takes a contrast's B1- and echoes as one group
+    of at most 16 rows; 16 rows (15 echoes with B1-, 16 without) stage, 21 do
+    not and take the unstaged pass.  Both against the oracle."""
+    shape = (24, 16, 6)
+    d = dataset(shape, seed=31, contrasts=("PDw", "T1w"), n_echoes=echoes, b1m=b1m)
+    pg = mpm.make_problem(d["prot"], shape)
+    po = orc.make_problem(d["prot"], shape)
+    rng = np.random.default_rng(32)
+    y = (d["y_true"] + 0.05 * rng.standard_normal(d["y_true"].shape)).astype(np.float32)
+    g, h, nll = mpm.mpm_grad_hess(pg, to_dev(d["x"]), to_dev(y), to_dev(d["b1p"]), to_dev(d["b1m"]))
+    nll_o, g_o, h_o = orc.grad_hess(po, d["x"], y, d["b1p"], d["b1m"])
+    from cases import assert_close_scaled
+    assert_close_scaled(to_np(g), g_o, 1e-4, "g")
+    assert_close_scaled(to_np(h), h_o, 1e-4, "h")
+    assert abs(nll.item() - nll_o) <= 2e-6 * abs(nll_o)
