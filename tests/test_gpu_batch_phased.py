@@ -7,7 +7,7 @@ one kernel launch for up to 16 subjects, each subject on its own share of the
 blocks with its own CG scalars.  The iteration kernel's wave of blocks is
 split between the subjects, so a subject's reductions run over fewer blocks
 than in its solo fit and sum in another order: each subject must match its
-solo fit within the benchmark spec's bounds (objective 1e-5 relative at every
+solo fit within the fit tolerances (objective 1e-5 relative at every
 update, maps 1e-3 in map units, posterior variance 5e-3 relative), and two
 subjects must match the FP64 oracle's fit.  The launch count checks that a
 group really takes one launch per phase.
@@ -173,7 +173,7 @@ def test_unaligned_subject_runs_in_a_lane(mpm):
 
 def test_single_fit_with_the_phased_graph(mpm):
     """mpm_fit with opts.graph = 2: a group of one subject, which the wave
-    split gives the solo grid; the result meets the benchmark spec's bounds of the
+    split gives the solo grid; the result meets the fit tolerances of the
     direct-launch fit."""
     gn, cg = 4, 30
     d, pg, x, v = _subject(mpm, SUBJECTS[0])

@@ -5,7 +5,7 @@ of the same inputs, stored by tests/golden/make_fullsize.py (which calls only
 the oracle).  The inputs are regenerated here from the same seeded recipe
 (tests/cases.py: fullsize_case), with the oracle's threaded forward model.
 
-Checked, with the benchmark spec's bounds:
+Checked, with the fit tolerances:
   objective F = NLL + JTV_eps    1e-5 relative, before every update and at the end
   maps                           |y - y_orc| <= 1e-3 max(1, |y_orc|) at the
                                  stored sample voxels (uniform over the volume

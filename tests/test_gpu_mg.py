@@ -7,7 +7,7 @@ iterations, element by element.
 Tolerances as for the block-Jacobi solve (float32 arithmetic through the
 cycle and the recurrence): delta within 2e-4 x (|ref| + rms of the map),
 residual norms within the same relative bound above 1e-6 |r_0|; the whole fit
-at the benchmark spec's bounds.
+at the fit tolerances.
 """
 import numpy as np
 import pytest

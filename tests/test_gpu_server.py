@@ -4,7 +4,7 @@ and slots free up, and each result equals the same request fitted alone with
 mpm_fit (bit for bit: the same launches on the same data).  Two served
 requests -- the four-contrast one with the 15 degree VFA contrast and a
 two-contrast one, both stopped by the objective tolerance -- are also checked
-against the FP64 oracle's fit with the same schedule, at the benchmark spec's bounds
+against the FP64 oracle's fit with the same schedule, at the fit tolerances
 (maps 1e-3 max(1, |y|), objective 1e-5 relative at every update).  The
 tolerance stop has margin here: the oracle's last relative objective change is
 8e-5 against the 1e-4 threshold and the one before it 2e-4."""
