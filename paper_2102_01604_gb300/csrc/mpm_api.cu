@@ -13,6 +13,7 @@
 
 #include <nvtx3/nvToolsExt.h>
 
+#include "init_maps.cuh"
 #include "mpm_internal.cuh"
 
 namespace mpm {
@@ -296,88 +297,10 @@ mpm_status check_ws(const DevProblem& P, int call, void* ws, size_t ws_bytes, Fi
 
 // ------------------------------------------------------ initial maps
 
-// Constant starting maps from the image means (Sec. 2.7 starts from constant
-// maps derived from the mean intensity of every volume; the formulas are this
-// library's reading of Eqs. 1 and 3):
-//  - one R2* shared by all contrasts and one TE = 0 intercept per contrast
-//    from least squares on log(mean) against TE;
-//  - the non-MT intercepts lie on the line S/sin a = E (S/tan a) + A (1 - E):
-//    slope E (at the mean TR of those contrasts), intercept A (1 - E);
-//  - MT contrasts give 1 - delta = S / (A sin a (1 - E) + S cos a E), averaged;
-//  - clamps R2* >= 1e-3, E in [1e-6, 1 - 1e-6], delta in [1e-4, 0.5];
-//    fallbacks R1 = 1/s and A from the first contrast when fewer than two
-//    distinct non-MT flip angles exist, R2* = 20/s without multi-echo data.
+// The starting maps from host-side means (init_maps.cuh; the server's path).
 void initial_maps(const mpm_problem* p, const double* mean, float out[4])
 {
-    const int C = p->n_contrasts;
-    double lm[MPM_MAX_IMAGES];
-    const int I = n_images(p);
-    for (int i = 0; i < I; ++i) lm[i] = std::log(mean[i] > 1e-30 ? mean[i] : 1e-30);
-    double tbar[MPM_MAX_CONTRASTS], lbar[MPM_MAX_CONTRASTS];
-    double sxy = 0.0, sxx = 0.0;
-    for (int c = 0, i0 = 0; c < C; i0 += p->n_echoes[c], ++c) {
-        const int E = p->n_echoes[c];
-        double st = 0.0, sl = 0.0;
-        for (int e = 0; e < E; ++e) {
-            st += p->te[i0 + e];
-            sl += lm[i0 + e];
-        }
-        tbar[c] = st / E;
-        lbar[c] = sl / E;
-        for (int e = 0; e < E; ++e) {
-            const double dt = p->te[i0 + e] - tbar[c];
-            sxy += dt * (lm[i0 + e] - lbar[c]);
-            sxx += dt * dt;
-        }
-    }
-    double r2 = sxx > 0.0 ? -sxy / sxx : 20.0;
-    if (r2 < 1e-3) r2 = 1e-3;
-    double S0[MPM_MAX_CONTRASTS];
-    for (int c = 0; c < C; ++c) S0[c] = std::exp(lbar[c] + r2 * tbar[c]);
-
-    int first = -1, cnt = 0;
-    double mx = 0, my = 0, mxx = 0, mxy = 0, trsum = 0;
-    for (int c = 0; c < C; ++c) {
-        if (p->mt[c]) continue;
-        if (first < 0) first = c;
-        const double X = S0[c] / std::tan(p->alpha[c]);
-        const double Y = S0[c] / std::sin(p->alpha[c]);
-        mx += X; my += Y; mxx += X * X; mxy += X * Y; trsum += p->tr[c];
-        ++cnt;
-    }
-    if (first < 0) first = 0;
-    const double varx = cnt > 0 ? mxx - mx * mx / cnt : 0.0;
-    double A, r1;
-    auto from_first = [&](double E) {
-        return S0[first] * (1.0 - std::cos(p->alpha[first]) * E) /
-               (std::sin(p->alpha[first]) * (1.0 - E));
-    };
-    if (cnt >= 2 && varx > 1e-12 * mxx) {
-        double E = (mxy - mx * my / cnt) / varx;
-        E = std::fmin(std::fmax(E, 1e-6), 1.0 - 1e-6);
-        r1 = -std::log(E) / (trsum / cnt);
-        A = ((my - E * mx) / cnt) / (1.0 - E);
-        if (!(A > 0.0)) A = from_first(E);
-    } else {
-        r1 = 1.0;
-        A = from_first(std::exp(-r1 * p->tr[first]));
-    }
-    double dsum = 0.0;
-    int nmt = 0;
-    for (int c = 0; c < C; ++c) {
-        if (!p->mt[c]) continue;
-        const double E = std::exp(-r1 * p->tr[c]);
-        const double mfac = S0[c] / (A * std::sin(p->alpha[c]) * (1.0 - E) + S0[c] * std::cos(p->alpha[c]) * E);
-        dsum += 1.0 - mfac;
-        ++nmt;
-    }
-    double delta = nmt ? dsum / nmt : 0.01;
-    if (!(delta >= 1e-4)) delta = 1e-4;
-    if (delta > 0.5) delta = 0.5;
-    out[0] = (float)std::log(A);
-    out[1] = (float)std::log(r1);
-    out[2] = (float)std::log(r2);
-    out[3] = (float)std::log(delta / (1.0 - delta));
+    initial_map_values(make_dev(p), mean, out);
 }
 
 
@@ -859,38 +782,25 @@ static mpm_status capture_phased(FitJob* jobs, int n, GraphEntry& out)
         out);
 }
 
-// Initial maps (host round trip for the image means), then the updates -- as
-// one graph launch when the schedule is fixed and opts.graph is set, else as
-// direct launches -- then one read-back of every report.
+// Initial maps (image means and the constant maps, on the device), then the
+// updates -- as one graph launch when the schedule is fixed and opts.graph is
+// set, else as direct launches -- then one read-back of every report.
 static mpm_status fit_run(FitJob* jobs, int n, mpm_report* reports, cudaStream_t st)
 {
     for (int i = 0; i < n; ++i)
         if (reports) memset(&reports[i], 0, sizeof(mpm_report));
-    // clear status words and counters; image means for the constant maps
-    std::vector<double> means((size_t)n * MPM_MAX_IMAGES);
-    bool any_init = false;
+    // clear status words and counters; image means and, from them, the
+    // constant starting maps, all on the device (no host round trip)
     for (int i = 0; i < n; ++i) {
         FitJob& j = jobs[i];
         if (j.empty) continue;
         MPM_CUDA(cudaMemsetAsync(j.L.hdr, 0, sizeof(WsHeader), st));
         if (j.opts.init) {
-            any_init = true;
             if (j.proj)
                 MPM_CUDA(proj_image_means(j.P, j.pj, j.L.mean_parts, j.L.means, st));
             else
                 MPM_CUDA(launch_image_means(j.P, j.problem->echo_dtype, j.x, j.L.mean_parts, j.L.means, st));
-            MPM_CUDA(cudaMemcpyAsync(&means[(size_t)i * MPM_MAX_IMAGES], j.L.means,
-                                     sizeof(double) * j.P.I, cudaMemcpyDeviceToHost, st));
-        }
-    }
-    if (any_init) {
-        MPM_CUDA(cudaStreamSynchronize(st));
-        for (int i = 0; i < n; ++i) {
-            FitJob& j = jobs[i];
-            if (j.empty || !j.opts.init) continue;
-            float vals[4];
-            initial_maps(j.problem, &means[(size_t)i * MPM_MAX_IMAGES], vals);
-            MPM_CUDA(launch_fill_maps(j.P, vals, j.y, st));
+            MPM_CUDA(launch_init_maps(j.P, j.L.means, j.y, st));
         }
     }
 

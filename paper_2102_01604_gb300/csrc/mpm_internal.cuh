@@ -67,6 +67,9 @@ cudaError_t launch_image_means(const DevProblem& P, int echo_dtype, const void* 
                                double* partials, double* means, cudaStream_t st);
 cudaError_t launch_fill_maps(const DevProblem& P, const float* values, float* y,
                              cudaStream_t st);
+// The constant starting maps from the image means in device memory
+// (init_maps.cuh), written to y.
+cudaError_t launch_init_maps(const DevProblem& P, const double* means, float* y, cudaStream_t st);
 
 cudaError_t launch_jtv(const DevProblem& P, const float* y, float* w, double* jtv,
                        Reduce red, cudaStream_t st);

@@ -4,11 +4,13 @@
 //                   approximate Hessian of Eq. 24, NLL reduced in float64
 //   k_uncertainty   diagonal of the inverse preconditioner blocks (Eq. 43) in
 //                   float64, log-determinant, log-normal moments (Eqs. 44-47)
-//   k_image_means / k_means_final / k_fill_maps   constant initial maps
+//   k_image_means / k_means_final / k_init_maps / k_fill_maps   constant
+//                   initial maps
 //
 // One thread per voxel (grid-stride), or two neighbouring voxels per thread in
 // the voxel pass; images are read as planes [I][N], so each warp loads 128
 // (256) contiguous bytes per echo.
+#include "init_maps.cuh"
 #include "mpm_internal.cuh"
 #include "voxel_model.cuh"
 
@@ -357,6 +359,21 @@ __global__ void __launch_bounds__(kBlock) k_fill_maps(DevProblem P, MapValues mv
         y[i] = mv.v[i / P.N];
 }
 
+// The starting maps from the image means: each block's first thread derives
+// the K values (a few hundred float64 operations) and the block fills its
+// share of the maps.
+__global__ void __launch_bounds__(kBlock) k_init_maps(DevProblem P, const double* __restrict__ means,
+                                                      float* __restrict__ y)
+{
+    __shared__ float v[4];
+    if (threadIdx.x == 0) initial_map_values(P, means, v);
+    __syncthreads();
+    const long long total = P.N * P.K;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x)
+        y[i] = v[i / P.N];
+}
+
 // ------------------------------------------------------------- launchers
 
 cudaError_t launch_forward(const DevProblem& P, const float* y, const float* b1p,
@@ -516,6 +533,13 @@ cudaError_t launch_image_means(const DevProblem& P, int echo_dtype, const void* 
     if (e != cudaSuccess) return e;
     LaunchScope ls(MPM_KERNEL_INIT, st);
     k_means_final<<<P.I, kBlock, 0, st>>>(P, partials, nb, means);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_maps(const DevProblem& P, const double* means, float* y, cudaStream_t st)
+{
+    LaunchScope ls(MPM_KERNEL_INIT, st);
+    k_init_maps<<<voxel_grid(P.N * P.K), kBlock, 0, st>>>(P, means, y);
     return cudaGetLastError();
 }
 
