@@ -1,6 +1,6 @@
 // init_maps.cuh -- the constant initial maps of a fit from the mean intensity
-// of every image, one arithmetic for the host and the device (mpm_fit derives
-// them on the device, the server on the host).  Internal.
+// of every image (k_init_maps derives them on the device for mpm_fit and the
+// server; the function also compiles for the host).  Internal.
 #pragma once
 
 #include <math.h>

@@ -297,13 +297,6 @@ mpm_status check_ws(const DevProblem& P, int call, void* ws, size_t ws_bytes, Fi
 
 // ------------------------------------------------------ initial maps
 
-// The starting maps from host-side means (init_maps.cuh; the server's path).
-void initial_maps(const mpm_problem* p, const double* mean, float out[4])
-{
-    initial_map_values(make_dev(p), mean, out);
-}
-
-
 // ------------------------------------------------------------------ fits
 
 // One subject's fit: arguments checked, workspace carved.

@@ -65,8 +65,6 @@ cudaError_t launch_uncertainty(const DevProblem& P, const float* h, const float*
                                unsigned* status, cudaStream_t st);
 cudaError_t launch_image_means(const DevProblem& P, int echo_dtype, const void* x,
                                double* partials, double* means, cudaStream_t st);
-cudaError_t launch_fill_maps(const DevProblem& P, const float* values, float* y,
-                             cudaStream_t st);
 // The constant starting maps from the image means in device memory
 // (init_maps.cuh), written to y.
 cudaError_t launch_init_maps(const DevProblem& P, const double* means, float* y, cudaStream_t st);
@@ -199,7 +197,6 @@ void proj_key(const ProjJob& pj, std::string& k);
 cudaError_t proj_image_means(const DevProblem& P, const ProjJob& pj, double* parts, double* means,
                              cudaStream_t st);
 mpm_status check_ws(const DevProblem& P, int call, void* ws, size_t ws_bytes, FitWs& L);
-void initial_maps(const mpm_problem* p, const double* mean, float out[4]);
 
 mpm_status fail(mpm_status s, const char* fmt, ...);
 

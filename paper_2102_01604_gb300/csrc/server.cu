@@ -3,10 +3,10 @@
 // Requests (one subject each, any matrix size, contrasts and echo counts) are
 // queued by mpm_server_submit and run asynchronously, each on its own slot
 // stream, through a small state machine driven by mpm_server_step:
-//   admitted  -> image means enqueued (constant initial maps need them on the
-//                host), workspace carved from the caller's device arena;
-//   init      -> when the means have landed: initial maps, first evaluation
-//                of the objective, its two doubles copied to pinned memory;
+//   admitted  -> workspace carved from the caller's device arena; image
+//                means and the constant initial maps (on the device), first
+//                evaluation of the objective, its two doubles copied to
+//                pinned memory;
 //   evaluate  -> when that copy has landed: the stopping rule of mpm_fit
 //                (|F_prev - F| < tol_gn |F_prev|, or gn_iters); if it goes
 //                on, the PCG solve and update and the next evaluation are
@@ -30,7 +30,7 @@
 namespace mpm {
 
 enum ReqState { kQueued = 0, kActive = 1, kDone = 2, kFailed = 3 };
-enum Phase { kInit = 0, kEval = 1, kFinish = 2 };
+enum Phase { kEval = 1, kFinish = 2 };
 
 struct Request {
     int ticket;
@@ -59,7 +59,6 @@ struct Request {
 // Pinned host staging of one slot.
 struct SlotHost {
     double f[2];              // nll, jtv of the latest evaluation
-    double means[MPM_MAX_IMAGES];
     unsigned status;
     mpm_report report;
 };
@@ -238,15 +237,7 @@ mpm_status mpm_server_step(mpm_server* s, int* n_active, int* n_queued, int* n_f
         if (q == cudaErrorNotReady) continue;
         if (q != cudaSuccess) return fail(MPM_ERR_CUDA, "cudaEventQuery: %s", cudaGetErrorString(q));
         SlotHost& h = s->host[k];
-        if (r.phase == kInit) {
-            if (r.opts.init) {
-                float vals[4];
-                initial_maps(&r.problem, h.means, vals);
-                SRV_CUDA(launch_fill_maps(r.P, vals, r.y, r.stream));
-            }
-            mpm_status st = srv_eval(s, r);
-            if (st != MPM_OK) return st;
-        } else if (r.phase == kEval) {
+        if (r.phase == kEval) {
             const double F = h.f[0] + h.f[1];
             bool stop = r.it >= r.opts.gn_iters;
             bool converged = false;
@@ -318,7 +309,6 @@ mpm_status mpm_server_step(mpm_server* s, int* n_active, int* n_queued, int* n_f
         a.L = layout(a.P, MPM_CALL_FIT, s->arena.base + off);
         a.slot = k;
         a.state = kActive;
-        a.phase = kInit;
         a.it = 0;
         s->slot_owner[k] = a.ticket;
         // priority level by size: volumes below 2^19 voxels highest, one level
@@ -331,10 +321,10 @@ mpm_status mpm_server_step(mpm_server* s, int* n_active, int* n_queued, int* n_f
         SRV_CUDA(cudaMemsetAsync(a.L.hdr, 0, sizeof(WsHeader), st));
         if (a.opts.init) {
             SRV_CUDA(launch_image_means(a.P, a.problem.echo_dtype, a.x, a.L.mean_parts, a.L.means, st));
-            SRV_CUDA(cudaMemcpyAsync(s->host[k].means, a.L.means, sizeof(double) * a.P.I,
-                                     cudaMemcpyDeviceToHost, st));
+            SRV_CUDA(launch_init_maps(a.P, a.L.means, a.y, st));
         }
-        SRV_CUDA(cudaEventRecord(a.landed, st));
+        mpm_status se = srv_eval(s, a);    // records `landed` and enters kEval
+        if (se != MPM_OK) return se;
     }
     int active = 0;
     for (int k = 0; k < s->max_slots; ++k) active += s->slot_owner[k] >= 0;

@@ -4,8 +4,7 @@
 //                   approximate Hessian of Eq. 24, NLL reduced in float64
 //   k_uncertainty   diagonal of the inverse preconditioner blocks (Eq. 43) in
 //                   float64, log-determinant, log-normal moments (Eqs. 44-47)
-//   k_image_means / k_means_final / k_init_maps / k_fill_maps   constant
-//                   initial maps
+//   k_image_means / k_means_final / k_init_maps   constant initial maps
 //
 // One thread per voxel (grid-stride), or two neighbouring voxels per thread in
 // the voxel pass; images are read as planes [I][N], so each warp loads 128
@@ -346,19 +345,6 @@ __global__ void __launch_bounds__(kBlock) k_means_final(DevProblem P, const doub
     if (threadIdx.x == 0) means[i] = acc / (double)P.N;
 }
 
-struct MapValues {
-    float v[4];
-};
-
-__global__ void __launch_bounds__(kBlock) k_fill_maps(DevProblem P, MapValues mv,
-                                                      float* __restrict__ y)
-{
-    const long long total = P.N * P.K;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x)
-        y[i] = mv.v[i / P.N];
-}
-
 // The starting maps from the image means: each block's first thread derives
 // the K values (a few hundred float64 operations) and the block fills its
 // share of the maps.
@@ -540,16 +526,6 @@ cudaError_t launch_init_maps(const DevProblem& P, const double* means, float* y,
 {
     LaunchScope ls(MPM_KERNEL_INIT, st);
     k_init_maps<<<voxel_grid(P.N * P.K), kBlock, 0, st>>>(P, means, y);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_fill_maps(const DevProblem& P, const float* values, float* y,
-                             cudaStream_t st)
-{
-    MapValues mv;
-    for (int k = 0; k < 4; ++k) mv.v[k] = k < P.K ? values[k] : 0.0f;
-    LaunchScope ls(MPM_KERNEL_INIT, st);
-    k_fill_maps<<<voxel_grid(P.N * P.K), kBlock, 0, st>>>(P, mv, y);
     return cudaGetLastError();
 }
 
