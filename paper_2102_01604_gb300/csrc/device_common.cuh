@@ -35,6 +35,9 @@ struct DevProblem {
     float dte[MPM_MAX_CONTRASTS];       // echo spacing when the echoes are equally spaced
     int te_uniform[MPM_MAX_CONTRASTS];  // 1: te = te0 + e * dte for every echo of c
     int same_tr[MPM_MAX_CONTRASTS];     // 1: tr[c] == tr[c - 1]
+    unsigned flip_as_c0;                // bit c (c > 0): alpha[c] == alpha[0]
+    unsigned echoes_as_prev;            // bit c (c > 0): c and c - 1 both have equally spaced
+                                        // echoes with the same first time and spacing
     float lambda[4];
     float eps2;
     int precond;

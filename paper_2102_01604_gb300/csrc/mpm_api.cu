@@ -221,6 +221,13 @@ DevProblem make_dev(const mpm_problem* p)
         P.dte[c] = (float)dt;
         P.same_tr[c] = (c > 0 && p->tr[c] == p->tr[c - 1]) ? 1 : 0;
     }
+    P.flip_as_c0 = P.echoes_as_prev = 0u;
+    for (int c = 1; c < P.C; ++c) {
+        if (P.alpha[c] == P.alpha[0]) P.flip_as_c0 |= 1u << c;
+        if (P.te_uniform[c] && P.te_uniform[c - 1] && P.te[P.echo0[c]] == P.te[P.echo0[c - 1]] &&
+            P.dte[c] == P.dte[c - 1])
+            P.echoes_as_prev |= 1u << c;
+    }
     for (int k = 0; k < 4; ++k) P.lambda[k] = (float)p->lambda[k];
     P.eps2 = (float)(p->eps * p->eps);
     P.precond = p->precond;

@@ -35,14 +35,27 @@ __device__ __forceinline__ Relax relax(float tr, float r1)
     return R;
 }
 
-__device__ __forceinline__ ContrastTerms contrast_terms(const DevProblem& P, int c, float a,
-                                                        const Relax& R, float dl, float m,
-                                                        float bp, float bm)
+// The local flip angle's factors: sa = sin(a), ca = cos(a), omc = 1 - cos(a).
+struct Flip {
+    float sa, ca, omc;
+};
+
+__device__ __forceinline__ Flip flip(float angle)
+{
+    Flip f;
+    sincosf(angle, &f.sa, &f.ca);
+    f.omc = __fdividef(f.sa * f.sa, 1.0f + f.ca);
+    return f;
+}
+
+// ContrastTerms of contrast c from the flip factors of its local angle
+// alpha_c b1+.
+__device__ __forceinline__ ContrastTerms contrast_terms_f(const DevProblem& P, int c, float a,
+                                                          const Relax& R, float dl, float m,
+                                                          const Flip& f, float bm)
 {
     ContrastTerms t;
-    float sa, ca;
-    sincosf(P.alpha[c] * bp, &sa, &ca);
-    const float omc = __fdividef(sa * sa, 1.0f + ca);
+    const float sa = f.sa, ca = f.ca, omc = f.omc;
     const float tt = R.tt, E = R.E, omE = R.omE;
     const bool mt = P.mt[c] != 0;
     const float d = mt ? dl : 0.0f;
@@ -57,6 +70,13 @@ __device__ __forceinline__ ContrastTerms contrast_terms(const DevProblem& P, int
     t.hd = 2.0f * mm * (omE + E * omc) * iD - 1.0f;  // 1 - cos(a) E = (1-E) + E (1 - cos a)
     t.cross = mt ? tt * E * ca * d * mm * iD * iD : 0.0f;
     return t;
+}
+
+__device__ __forceinline__ ContrastTerms contrast_terms(const DevProblem& P, int c, float a,
+                                                        const Relax& R, float dl, float m,
+                                                        float bp, float bm)
+{
+    return contrast_terms_f(P, c, a, R, dl, m, flip(P.alpha[c] * bp), bm);
 }
 
 // exp of the log-parameters; delta = logistic(y_delta) and m = 1 - delta from

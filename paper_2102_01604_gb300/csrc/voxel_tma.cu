@@ -211,15 +211,23 @@ __device__ __forceinline__ void grad_hess_tma_body(const DevProblem& P, const XT
             for (int k = 0; k < T; ++k) H[k] = make_float2(0.f, 0.f);
 #pragma unroll
             for (int v = 0; v < 2; ++v) R[v] = Relax{0.f, 0.f, 0.f};
+            // Contrasts at contrast 0's flip angle reuse its flip factors, and
+            // contrasts with the previous one's echo times its two echo
+            // exponentials: the same values the unstaged pass recomputes.
+            Flip f0[2];
+            float2 e0 = make_float2(0.f, 0.f), rho = make_float2(0.f, 0.f);
             for (int c = 0; c < P.C; ++c) {
                 begin_group();
                 float bm[2] = {1.0f, 1.0f};
                 if (b1m) take(float(), bm);
                 ContrastTerms tc[2];
+                const bool same_flip = (P.flip_as_c0 >> c) & 1u;
 #pragma unroll
                 for (int v = 0; v < 2; ++v) {
                     if (!P.same_tr[c]) R[v] = relax(P.tr[c], r1[v]);
-                    tc[v] = contrast_terms(P, c, a[v], R[v], dl[v], m[v], bp[v], bm[v]);
+                    const Flip f = same_flip ? f0[v] : flip(P.alpha[c] * bp[v]);
+                    if (c == 0) f0[v] = f;
+                    tc[v] = contrast_terms_f(P, c, a[v], R[v], dl[v], m[v], f, bm[v]);
                 }
                 // the echo loop of accumulate_contrast_v, echoes from the slots
                 EchoSums2<PRE> es;
@@ -227,12 +235,15 @@ __device__ __forceinline__ void grad_hess_tma_body(const DevProblem& P, const XT
                 const int ne = P.n_echoes[c];
                 const float te0 = -P.te[i0];
                 float2 q2 = make_float2(te0 * r2[0], te0 * r2[1]);
-                float2 sg = make_float2(tc[0].s0 * expf(q2.x), tc[1].s0 * expf(q2.y));
                 float xv[2];
                 if (P.te_uniform[c] != 0) {
                     const float dte = -P.dte[c];
                     const float2 dq = make_float2(dte * r2[0], dte * r2[1]);
-                    const float2 rho = make_float2(expf(dq.x), expf(dq.y));
+                    if (!((P.echoes_as_prev >> c) & 1u)) {
+                        e0 = make_float2(expf(q2.x), expf(q2.y));
+                        rho = make_float2(expf(dq.x), expf(dq.y));
+                    }
+                    float2 sg = make_float2(tc[0].s0 * e0.x, tc[1].s0 * e0.y);
 #pragma unroll 4
                     for (int e = 0; e < ne; ++e) {
                         take(XT(), xv);
@@ -241,6 +252,7 @@ __device__ __forceinline__ void grad_hess_tma_body(const DevProblem& P, const XT
                         sg = __fmul2_rn(sg, rho);
                     }
                 } else {
+                    float2 sg = make_float2(tc[0].s0 * expf(q2.x), tc[1].s0 * expf(q2.y));
                     take(XT(), xv);
                     es.add(sg, q2, make_float2(xv[0], xv[1]));
 #pragma unroll 4

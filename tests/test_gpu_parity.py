@@ -62,17 +62,25 @@ def test_grad_hess(mpm, shape, precond):
     assert abs(nll.item() - nll_o) <= 2e-6 * abs(nll_o)
 
 
-@pytest.mark.parametrize("bf16", [False, True])
-def test_grad_hess_pairs_equal_single_voxels(mpm, bf16):
+@pytest.mark.parametrize("bf16,contrasts,echoes", [
+    (False, ("PDw", "T1w", "MTw"), (8, 8, 6)),
+    (True, ("PDw", "T1w", "MTw"), (8, 8, 6)),
+    (False, ("T1w", "MTw", "PDw"), (6, 8, 8)),
+    (False, ("MTw", "PDw", "VFA15", "T1w"), (5, 7, 7, 4)),
+])
+def test_grad_hess_pairs_equal_single_voxels(mpm, bf16, contrasts, echoes):
     """The voxel pass stages its rows in shared memory when N is a multiple of
     8 and every array is 16-byte aligned; otherwise it takes two voxels per
     thread when N is even and every array is aligned to two elements, else one.
     With the images 0, 2 and 1 elements off, the three forms run on the same
     inputs.  Each voxel's arithmetic is the same, so g and h agree bit for bit
-    (the NLL sums in another order)."""
+    (the NLL sums in another order).  The staged form reuses contrast 0's flip
+    factors for the contrasts at its angle and the previous contrast's echo
+    exponentials for the same echo times; the contrast orders cover reuse and
+    none (T1w first: no other contrast at 21 degrees)."""
     import torch
     shape = (36, 22, 10)
-    d = dataset(shape, seed=21)
+    d = dataset(shape, seed=21, contrasts=contrasts, n_echoes=echoes)
     pg, po = _problems(mpm, d)
     if bf16:
         pg.echo_dtype = 1
