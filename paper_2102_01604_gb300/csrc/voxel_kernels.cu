@@ -2,8 +2,9 @@
 //   k_forward       noise-free images (Eq. 26 with the B1 footnote)
 //   k_grad_hess     the fused voxel pass: signal, residual, gradient and the
 //                   approximate Hessian of Eq. 24, NLL reduced in float64
-//   k_uncertainty   diagonal of the inverse preconditioner blocks (Eq. 43) in
-//                   float64, log-determinant, log-normal moments (Eqs. 44-47)
+//   k_uncertainty   diagonal of the inverse preconditioner blocks (Eq. 43),
+//                   log-determinant, log-normal moments (Eqs. 44-47); float32
+//                   on equilibrated blocks, float64 for ill-conditioned ones
 //   k_image_means / k_means_final / k_init_maps   constant initial maps
 //
 // One thread per voxel (grid-stride), or two neighbouring voxels per thread in
@@ -194,107 +195,253 @@ __device__ __forceinline__ double rsqrt_newton(double s)
     return r * (1.5 - 0.5 * s * r * r);
 }
 
-// Block n of the preconditioner, M = H_n + diag(lambda_k d_n) with
-// d_n = sum_{m in N(n)} (w_n + w_m) / h^2, inverted in float64 through its
-// Cholesky factor: var_k = sum_j (L^-1)_{jk}^2, logdet = -2 sum log L_kk.
+constexpr float kPivotMin = 1e-2f;   // smallest equilibrated pivot of the float32 path
+
+// The diagonal of M^-1 and log det M of one block M (K x K, symmetric, float32
+// entries) in float32, through the Cholesky factor L of the equilibrated block
+// A = S M S, S = diag(s_k), s_k ~ M_kk^-1/2 (so A has a unit diagonal up to
+// rounding): (M^-1)_kk = s_k^2 sum_j (L^-1)_jk^2 and log det M = sum_j log
+// L_jj^2 - 2 sum_k log s_k.  M comes from float32 H and w, so its variances
+// already carry a relative uncertainty of about kappa(M) 2^-24; the float32
+// factorization adds about K kappa(A) 2^-24, and kappa(A) is of the order of
+// 1 / (smallest pivot L_jj^2).  False, with nothing written, when a pivot is
+// below kPivotMin (or M_kk is not positive): such blocks take block_var_f64.
 template <int K>
+__device__ __forceinline__ bool block_var_f32(const float (&M)[K][K], bool want_ld, float (&var)[K],
+                                              float& ld)
+{
+    float sc[K];
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+        if (!(M[a][a] > 0.0f)) return false;
+        sc[a] = rsqrtf(M[a][a]);
+    }
+    float A[K][K];
+#pragma unroll
+    for (int a = 0; a < K; ++a)
+#pragma unroll
+        for (int b = 0; b <= a; ++b) A[a][b] = M[a][b] * sc[a] * sc[b];
+    float L[K][K], inv[K];
+    float lsum = 0.0f;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        float p = A[j][j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) p -= L[j][k] * L[j][k];
+        if (!(p >= kPivotMin)) return false;
+        inv[j] = rsqrtf(p);
+        L[j][j] = p * inv[j];
+        if (want_ld) lsum += logf(p) - 2.0f * logf(sc[j]);
+#pragma unroll
+        for (int i = j + 1; i < K; ++i) {
+            float v = A[i][j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
+            L[i][j] = v * inv[j];
+        }
+    }
+    float Li[K][K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+#pragma unroll
+        for (int i = 0; i < K; ++i) Li[i][j] = 0.0f;
+        Li[j][j] = inv[j];
+#pragma unroll
+        for (int i = j + 1; i < K; ++i) {
+            float v = 0.0f;
+#pragma unroll
+            for (int k = j; k < i; ++k) v -= L[i][k] * Li[k][j];
+            Li[i][j] = v * inv[i];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float v = 0.0f;
+#pragma unroll
+        for (int j = k; j < K; ++j) v += Li[j][k] * Li[j][k];
+        var[k] = v * sc[k] * sc[k];
+    }
+    ld = lsum;
+    return true;
+}
+
+// What block_var_f64 returns (by value, so that the float32 path keeps its
+// values in registers).
+struct BlockVar {
+    float var[4];
+    float ld;
+    bool ok;          // false: a pivot was not positive
+};
+
+// The same in float64 (H_kk + lambda_k d in float64; dl_k = lambda_k d), for
+// the blocks the float32 path declines.
+template <int K>
+__device__ __noinline__ BlockVar block_var_f64(const float* __restrict__ h, long long n, long long N,
+                                               double dl0, double dl1, double dl2, double dl3, bool want_ld)
+{
+    BlockVar out;
+    double M[K][K], L[K][K];
+#pragma unroll
+    for (int a = 0; a < K; ++a)
+#pragma unroll
+        for (int b = a; b < K; ++b) M[a][b] = M[b][a] = __ldg(h + tri(K, a, b) * N + n);
+    const double dl[4] = {dl0, dl1, dl2, dl3};
+#pragma unroll
+    for (int a = 0; a < K; ++a) M[a][a] += dl[a];
+    bool ok = true;
+    double lsum = 0.0;              // log det M, only when asked (log in float64 is costly)
+    double inv[K];                  // 1 / L_jj
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        double s = M[j][j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
+        if (!(s > 0.0)) { ok = false; s = 1e-300; }
+        inv[j] = rsqrt_newton(s);
+        L[j][j] = s * inv[j];
+        if (want_ld) lsum += log(s);
+#pragma unroll
+        for (int i = j + 1; i < K; ++i) {
+            double v = M[i][j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
+            L[i][j] = v * inv[j];
+        }
+    }
+    double Li[K][K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+#pragma unroll
+        for (int i = 0; i < K; ++i) Li[i][j] = 0.0;
+        Li[j][j] = inv[j];
+#pragma unroll
+        for (int i = j + 1; i < K; ++i) {
+            double v = 0.0;
+#pragma unroll
+            for (int k = j; k < i; ++k) v -= L[i][k] * Li[k][j];
+            Li[i][j] = v * inv[i];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double v = 0.0;
+#pragma unroll
+        for (int j = k; j < K; ++j) v += Li[j][k] * Li[j][k];
+        out.var[k] = (float)v;
+    }
+    out.ld = (float)lsum;
+    out.ok = ok;
+    return out;
+}
+
+// (x, y, z) of voxel n.
+__device__ __forceinline__ void voxel_coords(const DevProblem& P, long long n, int& x, int& yy, int& z)
+{
+    if (P.N <= 0xffffffffLL) {          // 32-bit division where the index fits
+        const unsigned u = (unsigned)n, r = u / (unsigned)P.nx;
+        x = (int)(u - r * (unsigned)P.nx);
+        yy = (int)(r % (unsigned)P.ny);
+        z = (int)(r / (unsigned)P.ny);
+    } else {
+        x = (int)(n % P.nx);
+        yy = (int)((n / P.nx) % P.ny);
+        z = (int)(n / ((long long)P.nx * P.ny));
+    }
+}
+
+// Block n of the preconditioner, M = H_n + diag(lambda_k d_n) with
+// d_n = sum_{m in N(n)} (w_n + w_m) / h^2: the diagonal of M^-1 (the
+// posterior variances, Eq. 43), -log det M, and the log-normal moments of
+// r1 = exp(y_R1) and t1 = 1 / r1 from the log-R1 variance (Eqs. 44-47).
+// Each thread takes V neighbouring voxels (V = 2: N even, arrays 8-byte
+// aligned), loading their H entries and weights as pairs before it inverts
+// the blocks one by one, so that twice the bytes are in flight per thread.
+template <int K, int V>
 __device__ __forceinline__ void uncertainty_body(const DevProblem& P, const float* __restrict__ h,
                                                  const float* __restrict__ w, const float* __restrict__ y,
                                                  float* __restrict__ var, float* __restrict__ logdet,
                                                  float* __restrict__ moments, unsigned* status,
                                                  const VGrid& vg)
 {
+    constexpr int T = K * (K + 1) / 2;
     const long long N = P.N;
     const long long sxy = (long long)P.nx * P.ny;
-    for (long long n = vg.bx * (long long)blockDim.x + threadIdx.x; n < N;
-         n += (long long)vg.gx * blockDim.x) {
-        int x, yy, z;
-        if (N <= 0xffffffffLL) {        // 32-bit division where the index fits
-            const unsigned u = (unsigned)n, r = u / (unsigned)P.nx;
-            x = (int)(u - r * (unsigned)P.nx);
-            yy = (int)(r % (unsigned)P.ny);
-            z = (int)(r / (unsigned)P.ny);
-        } else {
-            x = (int)(n % P.nx);
-            yy = (int)((n / P.nx) % P.ny);
-            z = (int)(n / sxy);
-        }
-        // d_n in float32 (six terms, relative error about 4e-7, far inside
-        // the variance's tolerance), then carried to float64
-        const float wn = __ldg(w + n);
-        float d32 = 0.0f;
-        if (x > 0) d32 += (wn + __ldg(w + n - 1)) * P.ihx2;
-        if (x < P.nx - 1) d32 += (wn + __ldg(w + n + 1)) * P.ihx2;
-        if (yy > 0) d32 += (wn + __ldg(w + n - P.nx)) * P.ihy2;
-        if (yy < P.ny - 1) d32 += (wn + __ldg(w + n + P.nx)) * P.ihy2;
-        if (z > 0) d32 += (wn + __ldg(w + n - sxy)) * P.ihz2;
-        if (z < P.nz - 1) d32 += (wn + __ldg(w + n + sxy)) * P.ihz2;
-        const double d = d32;
-        double M[K][K], L[K][K];
+    const long long units = N / V;
+    for (long long u = vg.bx * (long long)blockDim.x + threadIdx.x; u < units;
+         u += (long long)vg.gx * blockDim.x) {
+        const long long n0 = u * V;
+        float hv[T][V], wc[V];
 #pragma unroll
-        for (int a = 0; a < K; ++a)
+        for (int t = 0; t < T; ++t) load_vec<V, float>(h + t * N + n0, hv[t]);
+        load_vec<V, float>(w + n0, wc);
+        float vv[V][K], ld[V];
 #pragma unroll
-            for (int b = a; b < K; ++b) M[a][b] = M[b][a] = __ldg(h + tri(K, a, b) * N + n);
+        for (int v = 0; v < V; ++v) {
+            const long long n = n0 + v;
+            int x, yy, z;
+            voxel_coords(P, n, x, yy, z);
+            // d_n in float32 (six terms, relative error about 4e-7, far
+            // inside the variance's tolerance); the pair's own weights serve
+            // as each other's x neighbours
+            const float wn = wc[v];
+            float d32 = 0.0f;
+            if (x > 0) d32 += (wn + (v > 0 ? wc[v - 1] : __ldg(w + n - 1))) * P.ihx2;
+            if (x < P.nx - 1) d32 += (wn + (v + 1 < V ? wc[v + 1] : __ldg(w + n + 1))) * P.ihx2;
+            if (yy > 0) d32 += (wn + __ldg(w + n - P.nx)) * P.ihy2;
+            if (yy < P.ny - 1) d32 += (wn + __ldg(w + n + P.nx)) * P.ihy2;
+            if (z > 0) d32 += (wn + __ldg(w + n - sxy)) * P.ihz2;
+            if (z < P.nz - 1) d32 += (wn + __ldg(w + n + sxy)) * P.ihz2;
+            float M[K][K];
 #pragma unroll
-        for (int a = 0; a < K; ++a) M[a][a] += (double)P.lambda[a] * d;
-        bool ok = true;
-        double ld = 0.0;                // log det L, only when asked (log in float64 is costly)
-        double inv[K];                  // 1 / L_jj
+            for (int a2 = 0; a2 < K; ++a2)
 #pragma unroll
-        for (int j = 0; j < K; ++j) {
-            double s = M[j][j];
+                for (int b2 = a2; b2 < K; ++b2) M[a2][b2] = M[b2][a2] = hv[tri(K, a2, b2)][v];
 #pragma unroll
-            for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
-            if (!(s > 0.0)) { ok = false; s = 1e-300; }
-            inv[j] = rsqrt_newton(s);
-            L[j][j] = s * inv[j];
-            if (logdet) ld += log(L[j][j]);
+            for (int a2 = 0; a2 < K; ++a2) M[a2][a2] += P.lambda[a2] * d32;
+            ld[v] = 0.0f;
+            if (!block_var_f32<K>(M, logdet != nullptr, vv[v], ld[v])) {
+                const double d = d32;
+                const BlockVar b = block_var_f64<K>(h, n, N, P.lambda[0] * d, P.lambda[1] * d,
+                                                    P.lambda[2] * d, K == 4 ? P.lambda[3] * d : 0.0,
+                                                    logdet != nullptr);
 #pragma unroll
-            for (int i = j + 1; i < K; ++i) {
-                double v = M[i][j];
-#pragma unroll
-                for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
-                L[i][j] = v * inv[j];
+                for (int k = 0; k < K; ++k) vv[v][k] = b.var[k];
+                ld[v] = b.ld;
+                if (!b.ok && status) atomicOr(status, kStatusNotPD);
             }
         }
-        if (!ok && status) atomicOr(status, kStatusNotPD);
-        // inverse of the lower factor, column by column
-        double Li[K][K];
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-#pragma unroll
-            for (int i = 0; i < K; ++i) Li[i][j] = 0.0;
-            Li[j][j] = inv[j];
-#pragma unroll
-            for (int i = j + 1; i < K; ++i) {
-                double v = 0.0;
-#pragma unroll
-                for (int k = j; k < i; ++k) v -= L[i][k] * Li[k][j];
-                Li[i][j] = v * inv[i];
-            }
-        }
-        double var1 = 0.0;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            double v = 0.0;
+            float o[V];
 #pragma unroll
-            for (int j = k; j < K; ++j) v += Li[j][k] * Li[j][k];
-            var[k * N + n] = (float)v;
-            if (k == 1) var1 = v;
+            for (int v = 0; v < V; ++v) o[v] = vv[v][k];
+            store_vec<V>(var + k * N + n0, o);
         }
-        if (logdet) logdet[n] = (float)(-2.0 * ld);
+        if (logdet) {
+            float o[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) o[v] = -ld[v];
+            store_vec<V>(logdet + n0, o);
+        }
         if (moments && y) {
-            const double lr1 = __ldg(y + N + n);
-            const double es2 = exp(var1);
-            moments[n] = (float)(sqrt(es2) * exp(lr1));
-            moments[N + n] = (float)((es2 - 1.0) * es2 * exp(2.0 * lr1));
-            moments[2 * N + n] = (float)(sqrt(es2) * exp(-lr1));
-            moments[3 * N + n] = (float)((es2 - 1.0) * es2 * exp(-2.0 * lr1));
+            // E r1 = exp(y + s2 / 2), Var r1 = (exp(s2) - 1) exp(2 y + s2); t1 with -y
+            float lr1[V], m[4][V];
+            load_vec<V, float>(y + N + n0, lr1);
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const float s2 = vv[v][1], em1 = expm1f(s2);
+                m[0][v] = expf(fmaf(0.5f, s2, lr1[v]));
+                m[1][v] = em1 * expf(fmaf(2.0f, lr1[v], s2));
+                m[2][v] = expf(fmaf(0.5f, s2, -lr1[v]));
+                m[3][v] = em1 * expf(fmaf(-2.0f, lr1[v], s2));
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) store_vec<V>(moments + j * N + n0, m[j]);
         }
     }
 }
 
-template <int K>
+template <int K, int V>
 __global__ void __launch_bounds__(kBlock) k_uncertainty(DevProblem P, const float* __restrict__ h,
                                                         const float* __restrict__ w,
                                                         const float* __restrict__ y,
@@ -303,15 +450,15 @@ __global__ void __launch_bounds__(kBlock) k_uncertainty(DevProblem P, const floa
                                                         float* __restrict__ moments,
                                                         unsigned* status)
 {
-    uncertainty_body<K>(P, h, w, y, var, logdet, moments, status, hw_grid());
+    uncertainty_body<K, V>(P, h, w, y, var, logdet, moments, status, hw_grid());
 }
 
-template <int K>
+template <int K, int V>
 __global__ void __launch_bounds__(kBlock) k_uncertainty_batch(const __grid_constant__ Batch<UncArgs> b)
 {
     const int s = batch_subject(b.start, b.n);
     const UncArgs& a = b.a[s];
-    uncertainty_body<K>(a.P, a.h, a.w, a.y, a.var, a.logdet, a.moments, a.status,
+    uncertainty_body<K, V>(a.P, a.h, a.w, a.y, a.var, a.logdet, a.moments, a.status,
                         batch_grid(b.start[s], b.start[s + 1] - b.start[s], 1, 1));
 }
 
@@ -421,17 +568,29 @@ cudaError_t launch_grad_hess(const DevProblem& P, int echo_dtype, const void* x,
     return cudaGetLastError();
 }
 
+// Whether the uncertainty pass may take two voxels per thread: N even and
+// every array it reads or writes 8-byte aligned.
+static bool unc_pairs_ok(const DevProblem& P, const float* h, const float* w, const float* y,
+                         const float* var, const float* logdet, const float* moments)
+{
+    auto al = [](const void* p) { return reinterpret_cast<uintptr_t>(p) % 8 == 0; };
+    return P.N % 2 == 0 && al(h) && al(w) && al(y) && al(var) && al(logdet) && al(moments);
+}
+
 cudaError_t launch_uncertainty(const DevProblem& P, const float* h, const float* w,
                                const float* y, float* var, float* logdet, float* moments,
                                unsigned* status, cudaStream_t st)
 {
     LaunchScope ls(MPM_KERNEL_UNCERTAINTY, st);
-    if (P.K == 4)
-        k_uncertainty<4><<<voxel_grid(P.N), kBlock, 0, st>>>(P, h, w, y, var, logdet, moments,
-                                                              status);
-    else
-        k_uncertainty<3><<<voxel_grid(P.N), kBlock, 0, st>>>(P, h, w, y, var, logdet, moments,
-                                                              status);
+    const bool pairs = unc_pairs_ok(P, h, w, y, var, logdet, moments);
+    const int grid = voxel_grid(pairs ? P.N / 2 : P.N);
+#define MPM_UNC(KK, VV) k_uncertainty<KK, VV><<<grid, kBlock, 0, st>>>(P, h, w, y, var, logdet, moments, status)
+    if (P.K == 4) {
+        if (pairs) MPM_UNC(4, 2); else MPM_UNC(4, 1);
+    } else {
+        if (pairs) MPM_UNC(3, 2); else MPM_UNC(3, 1);
+    }
+#undef MPM_UNC
     return cudaGetLastError();
 }
 
@@ -492,11 +651,17 @@ cudaError_t launch_uncertainty_batch(int K, const UncArgs* a, const unsigned* bl
 {
     Batch<UncArgs> b;
     fill_batch(b, a, blocks, n);
+    bool pairs = true;
+    for (int i = 0; i < n; ++i)
+        pairs = pairs && unc_pairs_ok(a[i].P, a[i].h, a[i].w, a[i].y, a[i].var, a[i].logdet, a[i].moments);
     LaunchScope ls(MPM_KERNEL_UNCERTAINTY, st);
-    if (K == 4)
-        k_uncertainty_batch<4><<<b.start[n], kBlock, 0, st>>>(b);
-    else
-        k_uncertainty_batch<3><<<b.start[n], kBlock, 0, st>>>(b);
+    if (K == 4) {
+        if (pairs) k_uncertainty_batch<4, 2><<<b.start[n], kBlock, 0, st>>>(b);
+        else k_uncertainty_batch<4, 1><<<b.start[n], kBlock, 0, st>>>(b);
+    } else {
+        if (pairs) k_uncertainty_batch<3, 2><<<b.start[n], kBlock, 0, st>>>(b);
+        else k_uncertainty_batch<3, 1><<<b.start[n], kBlock, 0, st>>>(b);
+    }
     return cudaGetLastError();
 }
 

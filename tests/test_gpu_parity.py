@@ -186,6 +186,58 @@ def test_uncertainty(mpm, shape):
     np.testing.assert_allclose(to_np(var), v_o, rtol=1e-5)
     np.testing.assert_allclose(to_np(logdet), ld_o, rtol=1e-5, atol=1e-5)
     np.testing.assert_allclose(to_np(mom), m_o, rtol=1e-5)
+    # two voxels per thread (N even, arrays 8-byte aligned) or one (an output
+    # one element off): the same arithmetic per voxel, the same bits
+    import torch
+    K, N = pg.n_maps, h.shape[1]
+    buf = torch.empty(K * N + 1, dtype=torch.float32, device="cuda")
+    var1 = buf[1:].view(K, N)
+    mpm.mpm_uncertainty(pg, to_dev(h), to_dev(w), to_dev(y), var=var1, want_moments=True)
+    assert np.array_equal(to_np(var1), to_np(var))
+
+
+def test_uncertainty_ill_conditioned_blocks(mpm):
+    """The variances come from float32 Cholesky factors of the equilibrated
+    blocks; a block whose smallest equilibrated pivot is below 1e-2 is inverted
+    in float64 instead.  Every third voxel gets a block whose first two maps
+    are correlated at 0.999 (pivot 2e-3, condition number about 2000, where
+    float32 would miss 1e-5), the prior made too weak to mend it; every voxel
+    matches the oracle.  A block that is not positive definite gives non-finite
+    variances (mpm_uncertainty takes no workspace to report it)."""
+    d = dataset((16, 12, 6), seed=13)
+    pg, po = _problems(mpm, d)
+    h, w, g, y = _system(d, po, 14)
+    K, N = pg.n_maps, h.shape[1]
+    tri = {}
+    t = 0
+    for a in range(K):
+        for b in range(a, K):
+            tri[(a, b)] = t
+            t += 1
+    w = np.full_like(w, 1e-6)
+    sel = np.arange(0, N, 3)
+    for (a, b), t in tri.items():
+        if a != b:
+            h[t, sel] = 0.0
+    h[tri[(0, 1)], sel] = (0.999 * np.sqrt(h[tri[(0, 0)], sel].astype(np.float64)
+                                           * h[tri[(1, 1)], sel])).astype(np.float32)
+    var, logdet, mom = mpm.mpm_uncertainty(pg, to_dev(h), to_dev(w), to_dev(y), want_moments=True)
+    v_o, ld_o, m_o, st = orc.uncertainty(po, h, w, y)
+    assert st == 0
+    np.testing.assert_allclose(to_np(var), v_o, rtol=1e-5)
+    np.testing.assert_allclose(to_np(logdet), ld_o, rtol=1e-5, atol=1e-5)
+    np.testing.assert_allclose(to_np(mom), m_o, rtol=1e-5)
+    # an indefinite block
+    h[tri[(0, 1)], 4] = 1.5 * np.sqrt(h[tri[(0, 0)], 4] * h[tri[(1, 1)], 4])
+    for (a, b), t in tri.items():
+        if a != b and (a, b) != (0, 1):
+            h[t, 4] = 0.0
+    var, _, _ = mpm.mpm_uncertainty(pg, to_dev(h), to_dev(w), want_logdet=False)
+    v = to_np(var)
+    assert not np.all(np.isfinite(v[:, 4]))
+    ok = np.ones(N, bool)
+    ok[4] = False
+    assert np.all(np.isfinite(v[:, ok]))
 
 
 def _fit_both(mpm, d, gn_iters=10, cg_iters=30, npi=1, tol_gn=0.0, tol_cg=0.0, **kw):
