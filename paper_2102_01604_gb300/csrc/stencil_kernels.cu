@@ -399,55 +399,67 @@ __global__ void __launch_bounds__(kBlock) k_pcg_step(DevProblem P, int zc, int j
 
 // -------------------------------------------------------------- PCG final
 
+constexpr int kFinalUnroll = 2;   // grid-stride voxels whose operands a thread loads together
+
 // delta = x + the directions not yet folded into x (none, p_{it-1}, or
-// p_{it-2} and p_{it-1}), written planar, or y <- y - delta.
+// p_{it-2} and p_{it-1}), written planar, or y <- y - delta.  Each thread
+// loads the operands of kFinalUnroll voxels (one grid stride apart) before it
+// combines and stores them, so that more reads are in flight per thread.
 template <int K>
 __device__ __forceinline__ void pcg_final_body(long long N, const SolveBufs& B, float* __restrict__ delta,
                                                float* __restrict__ y_update, const WsHeader* hdr,
                                                double* report_rel, int* report_it, const VGrid& vg)
 {
+    constexpr int U = kFinalUnroll;
     const SolveScalars sc = hdr->sc;
     const bool have_x = sc.xcount > 0;
     const int pend = sc.it - sc.xcount;        // directions not yet in x: 0, 1 or 2
     const float alpha = (float)sc.alpha, alpha_prev = (float)sc.alpha_prev;
     const float4* __restrict__ pp = B.p[(sc.it + 2) % 3];    // p_{it-1}
     const float4* __restrict__ pp2 = B.p[(sc.it + 1) % 3];   // p_{it-2} when pend == 2
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
     const long long stride = (long long)vg.gx * blockDim.x;
-    for (long long n = vg.bx * (long long)blockDim.x + threadIdx.x; n < N; n += stride) {
-        // the next voxel's operands into L2 while this one is done
-        const long long na = n + stride;
-        if (na < N) {
-            if (have_x) prefetch_l2(B.x + na);
-            if (pend == 2) prefetch_l2(pp2 + na);
-            if (pend >= 1) prefetch_l2(pp + na);
-            if (y_update) {
+    for (long long n0 = vg.bx * (long long)blockDim.x + threadIdx.x; n0 < N; n0 += U * stride) {
+        float4 xv[U], p1[U], p2[U];
+        float yv[U][K];
 #pragma unroll
-                for (int a = 0; a < K; ++a) prefetch_l2(y_update + a * N + na);
+        for (int i = 0; i < U; ++i) {
+            const long long n = n0 + i * stride;
+            const bool in = n < N;
+            xv[i] = in && have_x ? B.x[n] : zero4;
+            p2[i] = in && pend == 2 ? pp2[n] : zero4;
+            p1[i] = in && pend >= 1 ? pp[n] : zero4;
+#pragma unroll
+            for (int a = 0; a < K; ++a) yv[i][a] = in && y_update ? y_update[a * N + n] : 0.0f;
+        }
+#pragma unroll
+        for (int i = 0; i < U; ++i) {
+            const long long n = n0 + i * stride;
+            if (n >= N) break;
+            float v[K], t[K];
+            if (have_x) {
+                unpack4<K>(xv[i], v);
+            } else {
+#pragma unroll
+                for (int a = 0; a < K; ++a) v[a] = 0.0f;
             }
-        }
-        float v[K], t[K];
-        if (have_x) {
-            unpack4<K>(B.x[n], v);
-        } else {
+            if (pend == 2) {
+                unpack4<K>(p2[i], t);
 #pragma unroll
-            for (int a = 0; a < K; ++a) v[a] = 0.0f;
-        }
-        if (pend == 2) {
-            unpack4<K>(pp2[n], t);
+                for (int a = 0; a < K; ++a) v[a] = fmaf(alpha_prev, t[a], v[a]);
+            }
+            if (pend >= 1) {
+                unpack4<K>(p1[i], t);
 #pragma unroll
-            for (int a = 0; a < K; ++a) v[a] = fmaf(alpha_prev, t[a], v[a]);
-        }
-        if (pend >= 1) {
-            unpack4<K>(pp[n], t);
+                for (int a = 0; a < K; ++a) v[a] = fmaf(alpha, t[a], v[a]);
+            }
 #pragma unroll
-            for (int a = 0; a < K; ++a) v[a] = fmaf(alpha, t[a], v[a]);
-        }
-#pragma unroll
-        for (int a = 0; a < K; ++a) {
-            if (y_update)
-                y_update[a * N + n] -= v[a];
-            else
-                delta[a * N + n] = v[a];
+            for (int a = 0; a < K; ++a) {
+                if (y_update)
+                    y_update[a * N + n] = yv[i][a] - v[a];
+                else
+                    delta[a * N + n] = v[a];
+            }
         }
     }
     if (vg.bx == 0 && threadIdx.x == 0) {
