@@ -407,18 +407,21 @@ __global__ void __launch_bounds__(kBlock) k_pcg_step(DevProblem P, int zc, int j
 
 // -------------------------------------------------------------- PCG final
 
-constexpr int kFinalUnroll = 2;   // grid-stride voxels whose operands a thread loads together
+// Grid-stride voxels whose operands a thread of the final kernel loads
+// together: two in the solo kernel (171 -> 134 us at 176x240x256), one in the
+// batched kernel, whose share of blocks per subject counts on the occupancy of
+// its 40 registers (two voxels: 76 registers, phase-batched fits 2% slower).
+constexpr int kFinalUnroll = 2;
 
 // delta = x + the directions not yet folded into x (none, p_{it-1}, or
 // p_{it-2} and p_{it-1}), written planar, or y <- y - delta.  Each thread
-// loads the operands of kFinalUnroll voxels (one grid stride apart) before it
-// combines and stores them, so that more reads are in flight per thread.
-template <int K>
+// loads the operands of U voxels (one grid stride apart) before it combines
+// and stores them, so that more reads are in flight per thread.
+template <int K, int U>
 __device__ __forceinline__ void pcg_final_body(long long N, const SolveBufs& B, float* __restrict__ delta,
                                                float* __restrict__ y_update, const WsHeader* hdr,
                                                double* report_rel, int* report_it, const VGrid& vg)
 {
-    constexpr int U = kFinalUnroll;
     const SolveScalars sc = hdr->sc;
     const bool have_x = sc.xcount > 0;
     const int pend = sc.it - sc.xcount;        // directions not yet in x: 0, 1 or 2
@@ -483,7 +486,7 @@ __global__ void __launch_bounds__(kBlock) k_pcg_final(long long N, SolveBufs B,
                                                       const WsHeader* hdr, double* report_rel,
                                                       int* report_it)
 {
-    pcg_final_body<K>(N, B, delta, y_update, hdr, report_rel, report_it, hw_grid());
+    pcg_final_body<K, kFinalUnroll>(N, B, delta, y_update, hdr, report_rel, report_it, hw_grid());
 }
 
 template <int K>
@@ -491,7 +494,7 @@ __global__ void __launch_bounds__(kBlock) k_pcg_final_batch(const __grid_constan
 {
     const int s = batch_subject(b.start, b.n);
     const FinalArgs& a = b.a[s];
-    pcg_final_body<K>(a.N, a.B, a.delta, a.y_update, a.hdr, a.report_rel, a.report_it,
+    pcg_final_body<K, 1>(a.N, a.B, a.delta, a.y_update, a.hdr, a.report_rel, a.report_it,
                       batch_grid(b.start[s], b.start[s + 1] - b.start[s], 1, 1));
 }
 
