@@ -215,9 +215,13 @@ mpm_status mpm_solve_static(const mpm_problem* problem, const mpm_opts* opts, co
                             double* resid, void* stream);
 
 /* Laplace uncertainty (Sec. 3.6, Eqs. 43-47): var[K][N] = diagonal of
- * (H_n + diag(G'WG)_n lambda)^-1, computed in float64; logdet[N] (or NULL) =
- * log-determinant of that covariance block; moments[4][N] (or NULL; needs y)
- * = E[r1], V[r1], E[t1], V[t1] under the log-normal posterior. */
+ * (H_n + diag(G'WG)_n lambda)^-1, from float32 Cholesky factors of the
+ * diagonally equilibrated blocks (float64 for a block whose smallest
+ * equilibrated pivot is below 1e-2); logdet[N] (or NULL) = log-determinant of
+ * that covariance block; moments[4][N] (or NULL; needs y) = E[r1], V[r1],
+ * E[t1], V[t1] under the log-normal posterior.  A block that is not positive
+ * definite gives non-finite entries (the call takes no workspace to report
+ * it). */
 mpm_status mpm_uncertainty(const mpm_problem* problem, const float* h, const float* w,
                            const float* y, float* var, float* logdet, float* moments,
                            void* stream);
