@@ -174,7 +174,8 @@ def test_solve_tolerance_stop(mpm):
     assert_close_scaled(to_np(delta), d_o, 1e-3, "delta")
 
 
-@pytest.mark.parametrize("shape", SHAPES[:2])
+# (65, 3, 2): N even with nx odd, so the two-voxel threads' pairs straddle rows
+@pytest.mark.parametrize("shape", SHAPES[:2] + [(65, 3, 2)])
 def test_uncertainty(mpm, shape):
     d = dataset(shape, seed=11)
     pg, po = _problems(mpm, d)
